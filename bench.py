@@ -1,0 +1,272 @@
+"""Benchmark: MOT steps/s (and Ns*Nt/s) of the marching-on-in-time TDBEM.
+
+One "step" is one pass of the whole hot path of Program 1 (incident field,
+history sum -- near field plus, in fast mode, the time-gated far field --, Z0
+solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
+already resident in HBM.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--mode fast|direct] [--workload NAME]
+
+N > 1 (torchrun): independent replicas, one per GPU; the march does not shard.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MOT steps/s and Ns·Nt/s at 7680 RWG, fast vs plain GPU at rel err ≤1e-4"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        self.path = f"/tmp/tdbem_clocks_{os.getpid()}.csv"
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        return rank, world, dist
+    return 0, 1, None
+
+
+def oracle_sample(w, rows_n: int, steps: int, seed: int = 11):
+    """Time the FP64 CPU oracle on a bounded sample: assemble `rows_n` random
+    rows, then evaluate their history sums for `steps` steps; the per-step cost
+    of the full march is extrapolated to all rows (the O(Ne) solve, under 1% of a
+    conventional step, is left out)."""
+    from oracle.oracle import Oracle, threads
+    from workloads import random_history
+
+    o = Oracle(w.verts, w.tris, w.dt)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(o.ne, rows_n, replace=False))
+    t0 = time.perf_counter()
+    mats = o.assemble(rows)
+    t_asm = time.perf_counter() - t0
+    J = random_history(o.ne, w.Nt - 1, seed=seed)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        alpha = 2 + (k * 37) % (w.Nt - 2)
+        o.history(alpha, J[: alpha - 1], rows, mats=mats)
+    t_hist = (time.perf_counter() - t0) / steps
+    per_step = t_hist * (o.ne / rows_n)
+    return {"steps_per_s": 1.0 / per_step, "assembly_s_for_sample": t_asm, "rows": rows_n, "steps": steps,
+            "cores": threads()}
+
+
+def run_reference(args, rank, world, dist):
+    from workloads import workload
+
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    rows_n = 32
+    res = oracle_sample(w, rows_n, max(args.steps // 4, 8))
+    v = res["steps_per_s"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_rwg": w.n_edge, "n_tri": w.n_tri, "Nt": w.Nt, "method": "conventional"},
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": res["cores"], "kind": "oracle",
+                         "sample": f"{rows_n} random rows assembled, history sums of {res['steps']} steps, "
+                                   "scaled to all rows"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "ns_nt_per_s": v * w.n_tri,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2303_05006_gb300 import Solver
+    from workloads import workload
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    mode = {"direct": 0, "fast": 1}[args.mode]
+    t0 = time.perf_counter()
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode)
+    setup_s = time.perf_counter() - t0
+    s.set_incident_plane(w.pulses[0])
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    W, K = args.warmup, args.steps
+    if W + K > w.Nt - 1:
+        raise SystemExit(f"warmup + steps must be <= {w.Nt - 1}")
+    out = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
+    # device-resident march: warm-up, then K timed steps
+    s.march_dev(W)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.march_dev(K, out.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t = e0.elapsed_time(e1) / 1000.0
+    if dist:
+        tt = torch.tensor([t])
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+        if dist:
+            dist.barrier()
+    steps_per_s = world * K / t
+    # per-kernel timing of the same work (instrumented second pass)
+    s.reset()
+    s.march_dev(W)
+    s.profile(True)
+    s.march_dev(K)
+    launches, ms = s.profile_read()
+    s.profile(False)
+    info = s.info()
+    # end-to-end through the C ABI with host buffers: V^{alpha-1} copied in,
+    # J^{alpha-1} copied out every step
+    s.reset()
+    Vh = torch.empty((W + K, s.ne), dtype=torch.float64).pin_memory()
+    Jh = torch.empty((s.ne,), dtype=torch.float64).pin_memory()
+    for a in range(1, W + K + 1):
+        Vh[a - 1].copy_(torch.from_numpy(s.history_eval(a, np.zeros((0, s.ne)))))
+    s.reset()
+    for a in range(W):
+        s.step_v(Vh[a].numpy(), Jh.numpy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for a in range(W, W + K):
+        s.step_v(Vh[a].numpy(), Jh.numpy())
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([te])
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt[0])
+    e2e = world * K / te
+    if rank != 0:
+        return 0
+    hbm, bf16, src = _peaks()
+    # dominant kernel: class 1 (history / near field)
+    dom = int(np.argmax(ms))
+    names = ["incident_rhs", "history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
+    avg = ms[dom] / max(launches[dom], 1) / 1000.0
+    if args.mode == "direct":
+        algo_bytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8)
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": algo_bytes / avg / 1e9 if dom == 1 else None,
+                "peak": hbm, "unit": "GB/s", "traffic": None,
+                "peak_source": f"{src} hbm_gbs",
+                "bytes_per_launch": algo_bytes}
+        if roof["achieved"] is not None:
+            roof["frac"] = roof["achieved"] / hbm
+    line = {
+        "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1000.0 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.mode == "direct" else "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
+                   "steps_timed": f"alpha {W + 1}..{W + K}",
+                   "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored coefficients)",
+                   "setup_s": setup_s},
+        "ns_nt_per_s": steps_per_s * w.n_tri,
+        "roofline": roof,
+        "kernel_ms_per_step": {names[k]: ms[k] / K for k in range(len(ms)) if launches[k]},
+        "gpu_launches": int(sum(launches)),
+        "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.ne, "d2h_bytes_per_step": 8 * s.ne},
+        "clocks": ck,
+        "solver_iters_per_step": info.total_solver_iters / K if K else None,
+    }
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+        res = oracle_sample(w, 16, 16)
+        line["cpu_baseline"] = {"value": res["steps_per_s"], "unit": "steps/s", "cores": res["cores"],
+                                "kind": "oracle",
+                                "sample": f"{res['rows']} random rows assembled, history sums of {res['steps']} "
+                                          "steps, scaled to all rows"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=12)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["fast", "direct"], default="direct")
+    ap.add_argument("--workload", default="sphere7680")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world, dist)
+    return run_ours(args, rank, world, dist)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * tdbem.h -- C ABI of the GB300 time-domain boundary element library.
+ *
+ * The library solves transient electromagnetic scattering off perfect
+ * electric conductors by marching on in time (paper section 2): the surface
+ * current J = n x H (n pointing into the conductor, section 2.1) is expanded in
+ * RWG basis functions f_j (one per mesh edge) and an order-2 B-spline in time
+ * (section 2.2),
+ *
+ *     J(x, t) = sum_j sum_beta J_j^beta f_j(x) N^{beta,2}(t),
+ *
+ * and the Galerkin-tested CFIE (eq. cfie, built from the time-differentiated
+ * EFIE, the time-differentiated MFIE and the MFIE) becomes, at every step
+ * alpha = 1 .. Nt-1 (eqs. system, solve and R),
+ *
+ *     Z0 J^{alpha-1} = R^{alpha-1},
+ *     R^{alpha-1}   = V^{alpha-1} - sum_{m >= 2} Zt^(m) J^{alpha-m},
+ *
+ * where Zt^(m) is the interaction matrix of time lag m (eq. z_ij with the
+ * B-spline of eq. J), Z0 = Zt^(1) and V is the tested incident field (eq. v_i).
+ * Two modes evaluate the history sum R:
+ *   TDBEM_DIRECT : every edge pair, FP64 (the conventional method, section
+ *                  3.6.3);
+ *   TDBEM_FAST   : near pairs directly and far pairs by the space-time
+ *                  interpolation-based FMM (section 3: P2M, M2M, M2L, L2L, L2P
+ *                  over an octree with per-level time intervals).
+ *
+ * Conventions shared by every entry point
+ *   * Units are normalised through eps and mu (c = 1/sqrt(eps mu)).
+ *   * Edges are numbered in increasing (min vertex, max vertex) order.  The
+ *     "+" triangle of an edge is the one whose winding runs from its smaller
+ *     to its larger vertex; f_j = +l/(2A+) (x - o+) there and -l/(2A-) (x - o-)
+ *     on the other triangle.  Triangles must be wound consistently.
+ *   * J^beta (beta = 0 .. Nt-2) multiplies f_j N^{beta,2}; step alpha produces
+ *     J^{alpha-1}.  Vectors are [ne] doubles in edge order.
+ *   * Every pointer argument is a HOST pointer unless the name ends in _dev.
+ *     The caller owns all arrays; the library copies what it needs during
+ *     the call and keeps no pointer to caller memory.
+ *   * Errors are returned, never thrown or trapped.  tdbem_last_error gives a
+ *     one-line description.  After TDBEM_ECUDA or TDBEM_ETIMEOUT the context
+ *     can only be destroyed.
+ *   * Calls on one context are not thread-safe; distinct contexts are.
+ */
+#ifndef TDBEM_H
+#define TDBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdbem_ctx tdbem_ctx;
+
+typedef enum {
+  TDBEM_OK = 0,
+  TDBEM_EINVAL = 1,      /* bad argument (NULL pointer, size out of range, unsupported order) */
+  TDBEM_EMESH = 2,       /* mesh not a closed consistently-wound 2-manifold, or degenerate triangle */
+  TDBEM_EBREAKDOWN = 3,  /* time interval of the finest level holds no whole step (section 3.4.1 Remark 1) */
+  TDBEM_ENOMEM = 4,      /* device or host allocation failed */
+  TDBEM_ENOCONV = 5,     /* Z0 solve did not reach the tolerance within solve_maxit; best iterate kept */
+  TDBEM_ETIMEOUT = 6,    /* a bounded device wait expired */
+  TDBEM_ESTATE = 7,      /* call out of order (e.g. step beyond Nt-1, no incident field set) */
+  TDBEM_ECUDA = 8        /* CUDA runtime error */
+} tdbem_status;
+
+typedef enum { TDBEM_DIRECT = 0, TDBEM_FAST = 1 } tdbem_mode;
+
+/* arithmetic of the M2L contraction (fast mode) */
+typedef enum {
+  TDBEM_P_FP32 = 0,   /* FP32 CUDA cores */
+  TDBEM_P_TF32 = 1,   /* TF32 tensor cores, FP32 accumulate */
+  TDBEM_P_BF16 = 2,   /* BF16 tensor cores, FP32 accumulate */
+  TDBEM_P_BF16X3 = 3  /* split-precision BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+} tdbem_prec;
+
+typedef struct {
+  int32_t d;            /* temporal B-spline order; only 2 is supported (paper's choice) */
+  int32_t p_s, p_t;     /* interpolation points per axis in space and time (fast mode), 2..8 */
+  int32_t n_leaf;       /* an octree cell is split while it holds more than n_leaf edges */
+  double theta, zeta;   /* CFIE coupling parameters of eq. cfie (paper: 1, 1) */
+  double eps, mu;       /* permittivity and permeability */
+  double s_jump;        /* weight of the MFIE identity term (+1: exterior limit, 0: omitted) */
+  int32_t mode;         /* tdbem_mode */
+  int32_t m2l_prec;     /* tdbem_prec */
+  double solve_tol;     /* relative residual of the Z0 solve */
+  int32_t solve_maxit;  /* iteration cap of the Z0 solve */
+  int32_t warm_start;   /* 0: zero initial guess, 1: cubic extrapolation of past currents */
+  int32_t n_rhs;        /* number of right-hand sides marched together (>= 1) */
+} tdbem_params;
+
+/* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
+   DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1. */
+void tdbem_default_params(tdbem_params* p);
+
+/* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
+   tris [ntri][3] (int32, consistently wound), time step dt > 0 and Nt >= 2 time
+   levels (paper Program 1 inputs).  Validates the mesh, builds the RWG edge
+   table and, in fast mode, the space-time hierarchy (section 3.4.1); assembles
+   on the device every coefficient the chosen mode stores.  Allocates device
+   memory on the current device.  Returns EMESH, EBREAKDOWN, ENOMEM, ECUDA or
+   EINVAL on failure with *out = NULL. */
+tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, double dt,
+                          int32_t Nt, const tdbem_params* params, tdbem_ctx** out);
+
+tdbem_status tdbem_num_edges(const tdbem_ctx* ctx, int64_t* ne);
+
+/* edge_vert [ne][2] (min, max vertex), edge_tri [ne][2] (+ triangle, - triangle) */
+tdbem_status tdbem_edges(const tdbem_ctx* ctx, int32_t* edge_vert, int32_t* edge_tri);
+
+/* CUDA stream (a cudaStream_t passed as void*) on which every later kernel of
+   this context is launched; NULL selects the library's own stream. */
+tdbem_status tdbem_set_stream(tdbem_ctx* ctx, void* stream);
+
+/* Incident modulated-Gaussian plane wave for right-hand side `rhs`:
+   pulse = {k[3], pol[3], f0, sigma, t0, z_min}; E = pol g(u), H = k x E / eta,
+   u = t - (k.x - z_min)/c, g(u) = cos(2 pi f0 (u - t0)) exp(-(u-t0)^2/(2 sigma^2)).
+   V^{alpha-1} (eq. v_i) is then evaluated on the device at every step. */
+tdbem_status tdbem_set_incident_plane(tdbem_ctx* ctx, int32_t rhs, const double* pulse);
+
+/* Use caller-supplied right-hand sides instead: V[(alpha-1)*ne + i] for
+   alpha = 1 .. Nt-1 (host, copied to the device). */
+tdbem_status tdbem_set_rhs(tdbem_ctx* ctx, int32_t rhs, const double* V);
+
+/* History evaluation without solving (eq. R): for a given history
+   J_hist[b*ne + j] = J_j^b (b = 0 .. n_hist-1; J^b = 0 outside) returns
+   R_out[i] = V_i^{alpha-1} - sum_{m >= 2} Zt^(m)_ij J_j^{alpha-m}, evaluated
+   exactly as tdbem_step evaluates it (far field through the FMM in fast mode,
+   with the same time gating).  V is the incident field of rhs 0 if one is
+   set, else zero.  Does not change the marching state. */
+tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_hist, int32_t n_hist,
+                                double* R_out);
+
+/* One step of Program 1: adds V^{alpha-1}, evaluates the history sum, solves
+   Z0 J^{alpha-1} = R^{alpha-1} and, in fast mode at gating steps, pushes the far
+   field of the finished time intervals into future right-hand sides.  J_out
+   ([n_rhs][ne], may be NULL) receives J^{alpha-1}; iters (may be NULL) the
+   solver iterations.  ESTATE after Nt-1 steps. */
+tdbem_status tdbem_step(tdbem_ctx* ctx, double* J_out, int32_t* iters);
+
+/* One step with a caller-supplied right-hand side for this step only:
+   V ([n_rhs][ne], host) is V^{alpha-1} (eq. v_i), copied to the device during
+   the call; J_out as in tdbem_step.  Used for end-to-end streaming where the
+   incident field is produced on the host. */
+tdbem_status tdbem_step_v(tdbem_ctx* ctx, const double* V, double* J_out, int32_t* iters);
+
+/* n_steps steps; J_all ([n_steps][n_rhs][ne], may be NULL) receives every J. */
+tdbem_status tdbem_march(tdbem_ctx* ctx, int32_t n_steps, double* J_all);
+
+/* Same with the result written to device memory J_all_dev (may be NULL). */
+tdbem_status tdbem_march_dev(tdbem_ctx* ctx, int32_t n_steps, double* J_all_dev);
+
+/* Restart the march at alpha = 1 (history and future right-hand sides cleared). */
+tdbem_status tdbem_reset(tdbem_ctx* ctx);
+
+/* Current step alpha (the next tdbem_step solves J^{alpha-1}). */
+tdbem_status tdbem_alpha(const tdbem_ctx* ctx, int32_t* alpha);
+
+/* Sizes and counters for reporting: see tdbem_info fields. */
+typedef struct {
+  int64_t ne, n_tri;
+  int32_t lmax, n_levels;          /* octree depth (fast mode) */
+  int32_t mt_leaf;                 /* steps per time interval at the finest level */
+  int64_t n_near_pairs;            /* edge pairs handled directly */
+  int64_t near_coef_bytes;         /* bytes of stored near-field coefficients */
+  int64_t device_bytes;            /* device memory held by the context */
+  double setup_seconds;            /* wall time of tdbem_create */
+  int64_t total_solver_iters;
+} tdbem_info;
+tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
+
+/* Kernel timing for reports.  While enabled, the library records CUDA events
+   on its stream around every launch of each kernel class; tdbem_profile_read
+   synchronises and returns, per class, the number of launches and the summed
+   device time in milliseconds since the last enable.  Classes (index):
+   0 incident RHS, 1 history/near field, 2 Z0 solve, 3 P2M, 4 M2M, 5 M2L,
+   6 L2L, 7 L2P.  n_classes receives the number of classes (<= 16). */
+tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
+tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
+
+const char* tdbem_last_error(const tdbem_ctx* ctx);
+
+void tdbem_destroy(tdbem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDBEM_H */

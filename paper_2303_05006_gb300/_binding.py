@@ -1,0 +1,207 @@
+"""ctypes binding of ``include/tdbem.h`` (argument marshalling only).
+
+Function names follow the C ABI one to one (``lib().tdbem_step`` ...); the
+:class:`Solver` class wraps a context with numpy arrays for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "libtdbem.so")
+
+TDBEM_DIRECT, TDBEM_FAST = 0, 1
+TDBEM_P_FP32, TDBEM_P_TF32, TDBEM_P_BF16, TDBEM_P_BF16X3 = 0, 1, 2, 3
+_STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "EBREAKDOWN", 4: "ENOMEM", 5: "ENOCONV", 6: "ETIMEOUT",
+           7: "ESTATE", 8: "ECUDA"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("p_s", ctypes.c_int32), ("p_t", ctypes.c_int32), ("n_leaf", ctypes.c_int32),
+                ("theta", ctypes.c_double), ("zeta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("mu", ctypes.c_double), ("s_jump", ctypes.c_double), ("mode", ctypes.c_int32),
+                ("m2l_prec", ctypes.c_int32), ("solve_tol", ctypes.c_double), ("solve_maxit", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("ne", ctypes.c_int64), ("n_tri", ctypes.c_int64), ("lmax", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("mt_leaf", ctypes.c_int32), ("n_near_pairs", ctypes.c_int64),
+                ("near_coef_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64)]
+
+
+class TdbemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tdbem {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB
+
+
+def lib():
+    """Load ``libtdbem.so``; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise ImportError(f"{_LIB} is not built; run __graft_entry__.build() "
+                              "(the CUDA library is the only implementation)")
+        L = ctypes.CDLL(_LIB)
+        vp = ctypes.c_void_p
+        L.tdbem_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.tdbem_default_params.restype = None
+        L.tdbem_create.argtypes = [_dp, ctypes.c_int64, _i32p, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                                   ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.tdbem_num_edges.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.tdbem_edges.argtypes = [vp, _i32p, _i32p]
+        L.tdbem_set_stream.argtypes = [vp, vp]
+        L.tdbem_set_incident_plane.argtypes = [vp, ctypes.c_int32, _dp]
+        L.tdbem_set_rhs.argtypes = [vp, ctypes.c_int32, _dp]
+        L.tdbem_history_eval.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp]
+        L.tdbem_step.argtypes = [vp, _dp, _i32p]
+        L.tdbem_march.argtypes = [vp, ctypes.c_int32, _dp]
+        L.tdbem_march_dev.argtypes = [vp, ctypes.c_int32, vp]
+        L.tdbem_step_v.argtypes = [vp, _dp, _dp, _i32p]
+        L.tdbem_profile_enable.argtypes = [vp, ctypes.c_int32]
+        L.tdbem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), _dp, _i32p]
+        L.tdbem_reset.argtypes = [vp]
+        L.tdbem_alpha.argtypes = [vp, _i32p]
+        L.tdbem_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.tdbem_last_error.argtypes = [vp]
+        L.tdbem_last_error.restype = ctypes.c_char_p
+        L.tdbem_destroy.argtypes = [vp]
+        L.tdbem_destroy.restype = None
+        for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
+                     "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
+                     "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
+                     "tdbem_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+class Solver:
+    """One marching context (a thin owner of a ``tdbem_ctx*``)."""
+
+    def __init__(self, verts, tris, dt: float, Nt: int, **params):
+        L = lib()
+        p = Params()
+        L.tdbem_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        self.verts = np.ascontiguousarray(verts, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        self.Nt = int(Nt)
+        h = ctypes.c_void_p()
+        rc = L.tdbem_create(_ptr(self.verts), len(self.verts), _ptr(self.tris, _i32p), len(self.tris), float(dt),
+                            self.Nt, ctypes.byref(p), ctypes.byref(h))
+        if rc != 0:
+            raise TdbemError(rc, "tdbem_create failed")
+        self._h = h
+        ne = ctypes.c_int64()
+        L.tdbem_num_edges(h, ctypes.byref(ne))
+        self.ne = int(ne.value)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TdbemError(rc, lib().tdbem_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tdbem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def edges(self):
+        ev = np.zeros((self.ne, 2), np.int32)
+        et = np.zeros((self.ne, 2), np.int32)
+        self._check(lib().tdbem_edges(self._h, _ptr(ev, _i32p), _ptr(et, _i32p)))
+        return ev, et
+
+    def set_stream(self, stream_handle: int | None):
+        self._check(lib().tdbem_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def set_incident_plane(self, pulse, rhs: int = 0):
+        a = np.ascontiguousarray(pulse.as_array() if hasattr(pulse, "as_array") else pulse, dtype=np.float64)
+        self._check(lib().tdbem_set_incident_plane(self._h, rhs, _ptr(a)))
+
+    def set_rhs(self, V, rhs: int = 0):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        if V.shape != (self.Nt - 1, self.ne):
+            raise ValueError("V must have shape (Nt-1, ne)")
+        self._check(lib().tdbem_set_rhs(self._h, rhs, _ptr(V)))
+
+    def history_eval(self, alpha: int, J_hist) -> np.ndarray:
+        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.ne)
+        out = np.zeros(self.ne)
+        self._check(lib().tdbem_history_eval(self._h, int(alpha), _ptr(J) if J.size else None, J.shape[0], _ptr(out)))
+        return out
+
+    def step(self):
+        J = np.zeros(self.ne)
+        it = ctypes.c_int32()
+        self._check(lib().tdbem_step(self._h, _ptr(J), ctypes.byref(it)))
+        return J, int(it.value)
+
+    def step_v(self, V, J_out=None):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        it = ctypes.c_int32()
+        self._check(lib().tdbem_step_v(self._h, _ptr(V), _ptr(J_out), ctypes.byref(it)))
+        return int(it.value)
+
+    def profile(self, on: bool = True):
+        self._check(lib().tdbem_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        n = ctypes.c_int32()
+        launches = (ctypes.c_int64 * 16)()
+        ms = np.zeros(16)
+        self._check(lib().tdbem_profile_read(self._h, launches, _ptr(ms), ctypes.byref(n)))
+        k = int(n.value)
+        return np.array(launches[:k]), ms[:k]
+
+    def march(self, n_steps: int, out=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((n_steps, self.ne))
+        self._check(lib().tdbem_march(self._h, int(n_steps), _ptr(out)))
+        return out
+
+    def march_dev(self, n_steps: int, dev_ptr: int | None = None):
+        self._check(lib().tdbem_march_dev(self._h, int(n_steps), ctypes.c_void_p(dev_ptr or 0)))
+
+    def reset(self):
+        self._check(lib().tdbem_reset(self._h))
+
+    @property
+    def alpha(self) -> int:
+        a = ctypes.c_int32()
+        self._check(lib().tdbem_alpha(self._h, ctypes.byref(a)))
+        return int(a.value)
+
+    def info(self) -> Info:
+        inf = Info()
+        self._check(lib().tdbem_get_info(self._h, ctypes.byref(inf)))
+        return inf

@@ -1,0 +1,377 @@
+// capi.cu -- the extern "C" entry points of include/tdbem.h and the marching
+// driver (paper Program 1).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace tdbem;
+
+cudaEvent_t tdbem_ctx::prof_begin(int) {
+  if (!prof_on) return nullptr;
+  if (ev_next >= ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ev_pool.push_back(e);
+  }
+  cudaEvent_t e = ev_pool[ev_next++];
+  cudaEventRecord(e, stream);
+  return e;
+}
+
+void tdbem_ctx::prof_end(int cls, cudaEvent_t b) {
+  if (!prof_on || !b) return;
+  if (ev_next >= ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    ev_pool.push_back(e);
+  }
+  cudaEvent_t e = ev_pool[ev_next++];
+  cudaEventRecord(e, stream);
+  prof_marks.push_back({cls, {b, e}});
+}
+
+extern "C" {
+
+void tdbem_default_params(tdbem_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->d = 2;
+  p->p_s = 4;
+  p->p_t = 4;
+  p->n_leaf = 64;
+  p->theta = 1.0;
+  p->zeta = 1.0;
+  p->eps = 1.0;
+  p->mu = 1.0;
+  p->s_jump = 1.0;
+  p->mode = TDBEM_DIRECT;
+  p->m2l_prec = TDBEM_P_FP32;
+  p->solve_tol = 1e-13;
+  p->solve_maxit = 200;
+  p->warm_start = 1;
+  p->n_rhs = 1;
+}
+
+static void fill_phys(tdbem_ctx* c) {
+  Phys& ph = c->phys;
+  ph.dt = c->dt;
+  ph.eps = c->p.eps;
+  ph.mu = c->p.mu;
+  ph.c = 1.0 / std::sqrt(ph.eps * ph.mu);
+  ph.eta = std::sqrt(ph.mu / ph.eps);
+  ph.a = ph.c * c->dt;
+  ph.theta = c->p.theta;
+  ph.zeta = c->p.zeta;
+  ph.s_jump = c->p.s_jump;
+  // 7-point degree-5 rule on the triangle (Radon): centroid and two orbits of 3
+  const double r15 = std::sqrt(15.0);
+  const double b1 = (6.0 - r15) / 21.0, b2 = (6.0 + r15) / 21.0;
+  const double w0 = 9.0 / 40.0, w1 = (155.0 - r15) / 1200.0, w2 = (155.0 + r15) / 1200.0;
+  const double pts[kNq][3] = {{1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0}, {b1, b1, 1 - 2 * b1}, {b1, 1 - 2 * b1, b1},
+                              {1 - 2 * b1, b1, b1},              {b2, b2, 1 - 2 * b2}, {b2, 1 - 2 * b2, b2},
+                              {1 - 2 * b2, b2, b2}};
+  const double wts[kNq] = {w0, w1, w1, w1, w2, w2, w2};
+  std::memcpy(ph.qb, pts, sizeof(pts));
+  std::memcpy(ph.qw, wts, sizeof(wts));
+}
+
+void tdbem_destroy(tdbem_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+static tdbem_status finish_create(tdbem_ctx* c) {
+  tdbem_status s;
+  int32_t need = c->max_lag + 1;
+  int32_t L = 8;
+  while (L < need) L <<= 1;
+  c->L = L;
+  if ((s = c->dalloc(&c->d_Jring, c->ne * (int64_t)L)) || (s = c->dalloc(&c->d_R, c->ne)) ||
+      (s = c->dalloc(&c->d_J, c->ne)) || (s = c->dalloc(&c->d_pulse, 10)))
+    return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, c->ne * (int64_t)L * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, c->ne * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, int64_t ntri, double dt, int32_t Nt,
+                          const tdbem_params* params, tdbem_ctx** out) {
+  if (!out) return TDBEM_EINVAL;
+  *out = nullptr;
+  if (!verts || !tris || !(dt > 0) || Nt < 2) return TDBEM_EINVAL;
+  tdbem_params p;
+  if (params)
+    p = *params;
+  else
+    tdbem_default_params(&p);
+  if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
+      !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs != 1 ||
+      (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
+    return TDBEM_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  tdbem_ctx* c = new (std::nothrow) tdbem_ctx();
+  if (!c) return TDBEM_ENOMEM;
+  c->p = p;
+  c->dt = dt;
+  c->Nt = Nt;
+  fill_phys(c);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return e == cudaErrorMemoryAllocation ? TDBEM_ENOMEM : TDBEM_ECUDA;
+  }
+  c->stream = c->own_stream;
+  tdbem_status s = tdbem_build_mesh(c, verts, nv, tris, ntri);
+  if (!s) {
+    if (p.mode == TDBEM_DIRECT) {
+      s = tdbem_build_direct(c);
+      if (!s) s = tdbem_build_z0(c);
+    } else {
+      c->set_error("create: fast mode is not available in this build");
+      s = TDBEM_EINVAL;
+    }
+  }
+  if (!s) s = finish_create(c);
+  if (s) {
+    tdbem_destroy(c);
+    return s;
+  }
+  c->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_num_edges(const tdbem_ctx* c, int64_t* ne) {
+  if (!c || !ne) return TDBEM_EINVAL;
+  *ne = c->ne;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_edges(const tdbem_ctx* c, int32_t* edge_vert, int32_t* edge_tri) {
+  if (!c) return TDBEM_EINVAL;
+  if (edge_vert) std::memcpy(edge_vert, c->ev.data(), 2 * c->ne * sizeof(int32_t));
+  if (edge_tri) std::memcpy(edge_tri, c->et.data(), 2 * c->ne * sizeof(int32_t));
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_set_stream(tdbem_ctx* c, void* stream) {
+  if (!c) return TDBEM_EINVAL;
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* pulse) {
+  if (!c || !pulse || rhs != 0) return TDBEM_EINVAL;
+  if (!(pulse[7] > 0)) return TDBEM_EINVAL;
+  std::memcpy(c->pulse, pulse, sizeof(c->pulse));
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse, c->pulse, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->have_pulse = true;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
+  if (!c || !V || rhs != 0) return TDBEM_EINVAL;
+  tdbem_status s;
+  const int64_t n = (int64_t)(c->Nt - 1) * c->ne;
+  if (!c->d_Vall && (s = c->dalloc(&c->d_Vall, n))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_Vall, V, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return TDBEM_OK;
+}
+
+// R^{alpha-1} = V^{alpha-1} - history (eq. R), ring holds the history.
+// skip_rhs: R already holds V^{alpha-1}.
+static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bool skip_rhs = false) {
+  tdbem_status s;
+  if (!skip_rhs) {
+    cudaEvent_t e = c->prof_begin(0);
+    s = tdbem_rhs_into_R(c, alpha);
+    c->prof_end(0, e);
+    if (s) return s;
+  }
+  cudaEvent_t e = c->prof_begin(1);
+  s = tdbem_direct_history(c, alpha, d_ring, 0);
+  c->prof_end(1, e);
+  return s;
+}
+
+tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist, double* R_out) {
+  if (!c || !R_out || alpha < 1 || alpha > c->Nt - 1 || n_hist < 0 || (n_hist > 0 && !J_hist)) return TDBEM_EINVAL;
+  const int64_t ne = c->ne;
+  const int32_t L = c->L;
+  std::vector<double> ring((size_t)ne * L, 0.0);
+  for (int32_t b = std::max(0, alpha - c->max_lag); b <= alpha - 2 && b < n_hist; ++b)
+    for (int64_t j = 0; j < ne; ++j) ring[(size_t)j * L + (b & (L - 1))] = J_hist[(int64_t)b * ne + j];
+  double* d_ring = nullptr;
+  TDBEM_CUDA_TRY(c, cudaMallocAsync(&d_ring, ring.size() * sizeof(double), c->stream));
+  cudaError_t e = cudaMemcpyAsync(d_ring, ring.data(), ring.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  tdbem_status s = TDBEM_OK;
+  if (e == cudaSuccess) s = eval_R(c, alpha, d_ring);
+  if (e == cudaSuccess && !s)
+    e = cudaMemcpyAsync(R_out, c->d_R, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(d_ring, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (s) return s;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    c->set_error(std::string("history_eval: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return TDBEM_ECUDA;
+  }
+  return TDBEM_OK;
+}
+
+static tdbem_status step_async(tdbem_ctx* c, bool have_V = false) {
+  if (c->alpha > c->Nt - 1) {
+    c->set_error("step: all Nt-1 steps already taken");
+    return TDBEM_ESTATE;
+  }
+  tdbem_status s = eval_R(c, c->alpha, c->d_Jring, have_V);
+  if (s) return s;
+  cudaEvent_t e = c->prof_begin(2);
+  s = tdbem_solve_z0(c, c->alpha, nullptr);
+  c->prof_end(2, e);
+  if (s) return s;
+  c->alpha++;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_step(tdbem_ctx* c, double* J_out, int32_t* iters) {
+  if (!c) return TDBEM_EINVAL;
+  tdbem_status s = step_async(c);
+  if (s) return s;
+  int32_t h[2];
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  if (J_out) TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_out, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (iters) *iters = h[0];
+  c->total_iters += h[0];
+  if (!h[1]) {
+    c->set_error("step: Z0 solve missed the tolerance");
+    return TDBEM_ENOCONV;
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t* iters) {
+  if (!c || !V) return TDBEM_EINVAL;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, V, c->ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  tdbem_status s = step_async(c, true);
+  if (s) return s;
+  int32_t h[2];
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  if (J_out) TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_out, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (iters) *iters = h[0];
+  c->total_iters += h[0];
+  if (!h[1]) {
+    c->set_error("step: Z0 solve missed the tolerance");
+    return TDBEM_ENOCONV;
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
+  if (!c) return TDBEM_EINVAL;
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->prof_on = on != 0;
+  c->prof_marks.clear();
+  c->ev_next = 0;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int32_t* n_classes) {
+  if (!c || !launches || !ms) return TDBEM_EINVAL;
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < tdbem_ctx::kClasses; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (auto& m : c->prof_marks) {
+    float t = 0.f;
+    TDBEM_CUDA_TRY(c, cudaEventElapsedTime(&t, m.second.first, m.second.second));
+    launches[m.first] += 1;
+    ms[m.first] += t;
+  }
+  if (n_classes) *n_classes = tdbem_ctx::kClasses;
+  return TDBEM_OK;
+}
+
+static tdbem_status check_misses(tdbem_ctx* c) {
+  int32_t h[4];
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->total_iters = h[3];
+  if (h[2]) {
+    c->set_error("march: " + std::to_string(h[2]) + " Z0 solves missed the tolerance");
+    return TDBEM_ENOCONV;
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_march(tdbem_ctx* c, int32_t n_steps, double* J_all) {
+  if (!c || n_steps < 0) return TDBEM_EINVAL;
+  for (int32_t k = 0; k < n_steps; ++k) {
+    tdbem_status s = step_async(c);
+    if (s) return s;
+    if (J_all)
+      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_all + (int64_t)k * c->ne, c->d_J, c->ne * sizeof(double),
+                                        cudaMemcpyDeviceToHost, c->stream));
+  }
+  return check_misses(c);
+}
+
+tdbem_status tdbem_march_dev(tdbem_ctx* c, int32_t n_steps, double* J_all_dev) {
+  if (!c || n_steps < 0) return TDBEM_EINVAL;
+  for (int32_t k = 0; k < n_steps; ++k) {
+    tdbem_status s = step_async(c);
+    if (s) return s;
+    if (J_all_dev)
+      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_all_dev + (int64_t)k * c->ne, c->d_J, c->ne * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return check_misses(c);
+}
+
+tdbem_status tdbem_reset(tdbem_ctx* c) {
+  if (!c) return TDBEM_EINVAL;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, c->ne * (int64_t)c->L * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, c->ne * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->alpha = 1;
+  c->total_iters = 0;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_alpha(const tdbem_ctx* c, int32_t* alpha) {
+  if (!c || !alpha) return TDBEM_EINVAL;
+  *alpha = c->alpha;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
+  if (!c || !info) return TDBEM_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->ne = c->ne;
+  info->n_tri = c->nt;
+  info->n_near_pairs = c->direct.npairs;
+  info->near_coef_bytes = c->direct.nval * (int64_t)sizeof(double);
+  info->device_bytes = c->device_bytes;
+  info->setup_seconds = c->setup_seconds;
+  info->total_solver_iters = c->total_iters;
+  return TDBEM_OK;
+}
+
+const char* tdbem_last_error(const tdbem_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,429 @@
+// direct.cu -- interaction coefficients of every time lag for a set of edge
+// pairs (paper section 2.4, eq. z_ij), the incident right-hand side (eq. v_i)
+// and the direct FP64 history sum of eq. R.
+//
+// The coefficient of J_j^beta in the tested equation at t_alpha depends on the
+// lag m = alpha - beta only (eq. layer_disc_tmp with the B-spline of eq. J):
+//   Zt^(m)_ij = sum over the triangles S_i^rho of i and S_j^sigma of j of
+//     sum_q w_q A_i^rho [ mu/(4 pi dt^2) f_i(x_q) . int f_j Nddot(tau)/r dS
+//                       + 1/(4 pi eps) div f_i div f_j int N(tau)/r dS
+//                       + theta eta/(4 pi) f_i(x_q) . (n x int f_j x grad_y g dS) ]
+// plus the MFIE identity term s_jump theta eta/2 (f_i, f_j) (Ndot(m)/dt + zeta N(m)).
+// The outer integral uses the 7-point degree-5 rule; the inner integral is
+// exact (integrals.cuh).  One thread owns one (test triangle, source triangle)
+// pair, accumulates its 3x3 local edge pairs over the 7 points and adds them to
+// the edge-pair store with FP64 atomics (each edge pair receives the 4
+// triangle pairs of its two supports).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "integrals.cuh"
+#include "internal.h"
+
+namespace tdbem {
+
+__device__ __forceinline__ double dist3(const double* a, const double* b) {
+  double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+  return sqrt(x * x + y * y + z * z);
+}
+
+// Conservative lag window [m_lo, m_lo + n) of an edge pair from the bounding
+// spheres (centroid, max centroid-vertex distance) of its four triangle pairs.
+__device__ __forceinline__ void edge_pair_window(const TriGeom& g, const int32_t* et, int i, int j, double a,
+                                                 int* m_lo, int* n) {
+  double rlo = 1e300, rhi = 0.0;
+  for (int u = 0; u < 2; ++u)
+    for (int w = 0; w < 2; ++w) {
+      int t = et[2 * i + u], s = et[2 * j + w];
+      double dc = dist3(g.cen + 3 * t, g.cen + 3 * s);
+      double rr = g.rad[t] + g.rad[s];
+      rlo = fmin(rlo, fmax(dc - rr, 0.0));
+      rhi = fmax(rhi, dc + rr);
+    }
+  lag_window(rlo, rhi, a, m_lo, n);
+}
+
+__global__ void k_direct_windows(TriGeom g, const int32_t* et, int64_t ne, double a, int16_t* m_lo, uint8_t* nlag,
+                                 int32_t* err) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ne * ne) return;
+  int i = (int)(p / ne), j = (int)(p % ne);
+  int lo, n;
+  edge_pair_window(g, et, i, j, a, &lo, &n);
+  if (n > 255 || lo > 32767) {
+    atomicExch(err, 1);
+    n = 0;
+  }
+  m_lo[p] = (int16_t)lo;
+  nlag[p] = (uint8_t)n;
+}
+
+// per-row sums of nlag
+__global__ void k_row_totals(const uint8_t* nlag, int64_t ne, int64_t* tot) {
+  int64_t i = blockIdx.x;
+  int64_t s = 0;
+  for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) s += nlag[i * ne + j];
+  __shared__ int64_t red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) tot[i] = s;
+  }
+}
+
+// per-row exclusive scan of nlag into off (row base from the host scan)
+__global__ void k_row_offsets(const uint8_t* nlag, int64_t ne, const int64_t* rowbase, int64_t* off) {
+  int64_t i = blockIdx.x;
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = rowbase[i];
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t j0 = 0; j0 < ne; j0 += blockDim.x) {
+    int64_t j = j0 + threadIdx.x;
+    int64_t v = (j < ne) ? nlag[i * ne + j] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t w = (lane < nw) ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    int64_t excl = x - v + (wid > 0 ? wsum[wid - 1] : 0) + carry;
+    if (j < ne) off[i * ne + j] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+}
+
+// Sink of the direct store: every (i, j) of the mesh.
+struct DirectSink {
+  const int16_t* m_lo;
+  const uint8_t* nlag;
+  const int64_t* off;
+  double* val;
+  int64_t ne;
+  __device__ __forceinline__ double* slot(int i, int j, int m) const {
+    int64_t p = (int64_t)i * ne + j;
+    int w = m - m_lo[p];
+    if (w < 0 || w >= nlag[p]) return nullptr;
+    return val + off[p] + w;
+  }
+};
+
+// One thread per (test triangle t, source triangle s) listed in `pairs` (or
+// all pairs when pairs == nullptr).
+template <class Sink>
+__global__ void __launch_bounds__(128) k_assemble(TriGeom g, Phys ph, int64_t nt, const int2* pairs, int64_t npairs,
+                                                  Sink sink, int32_t* err) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= npairs) return;
+  int t, s;
+  if (pairs) {
+    int2 q = pairs[idx];
+    t = q.x;
+    s = q.y;
+  } else {
+    t = (int)(idx / nt);
+    s = (int)(idx % nt);
+  }
+  const double a = ph.a;
+  // union lag window of the triangle pair
+  double dc = dist3(g.cen + 3 * t, g.cen + 3 * s);
+  int M0, NM;
+  lag_window(fmax(dc - g.rad[t] - g.rad[s], 0.0), dc + g.rad[t] + g.rad[s], a, &M0, &NM);
+  if (NM > kMaxWin) {
+    atomicExch(err, 2);
+    return;
+  }
+  double acc[3][3][kMaxWin];
+  for (int u = 0; u < 3; ++u)
+    for (int w = 0; w < 3; ++w)
+      for (int k = 0; k < NM; ++k) acc[u][w][k] = 0.0;
+  double vt[9], vs[9], ns[3], nin[3];
+  for (int k = 0; k < 9; ++k) {
+    vt[k] = g.v[9 * t + k];
+    vs[k] = g.v[9 * s + k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    ns[k] = g.nrm[3 * s + k];
+    nin[k] = -g.nrm[3 * t + k];  // n points into the conductor (paper section 2.1)
+  }
+  const double At = g.area[t], As = g.area[s];
+  double ci[3], divi[3], oi[3][3], cj[3], divj[3], oj[3][3];
+  for (int k = 0; k < 3; ++k) {
+    double sg = g.sgn[3 * t + k], l = g.elen[3 * t + k];
+    ci[k] = sg * l / (2 * At);
+    divi[k] = sg * l / At;
+    for (int q = 0; q < 3; ++q) oi[k][q] = g.opp[9 * t + 3 * k + q];
+    double sg2 = g.sgn[3 * s + k], l2 = g.elen[3 * s + k];
+    cj[k] = sg2 * l2 / (2 * As);
+    divj[k] = sg2 * l2 / As;
+    for (int q = 0; q < 3; ++q) oj[k][q] = g.opp[9 * s + 3 * k + q];
+  }
+  const double PI = 3.14159265358979323846;
+  const double kA = ph.mu / (4 * PI * ph.dt * ph.dt), kphi = 1.0 / (4 * PI * ph.eps), kP = ph.theta * ph.eta / (4 * PI);
+  InnerOut io;
+  for (int q = 0; q < kNq; ++q) {
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = ph.qb[q][0] * vt[k] + ph.qb[q][1] * vt[3 + k] + ph.qb[q][2] * vt[6 + k];
+    double wq = ph.qw[q] * At;
+    double rhi = fmax(fmax(dist3(x, vs), dist3(x, vs + 3)), dist3(x, vs + 6));
+    double rlo = fmax(dist3(x, g.cen + 3 * s) - g.rad[s], 0.0);
+    int m0, nm;
+    lag_window(rlo, rhi, a, &m0, &nm);
+    if (m0 < M0 || m0 + nm > M0 + NM || nm > kMaxWin) {
+      atomicExch(err, 3);
+      return;
+    }
+    if (!inner_integrals(x, vs, ns, g.lmax[s], a, ph.dt, ph.zeta, m0, nm, io)) {
+      atomicExch(err, 4);
+      return;
+    }
+    double fi[3][3], xo[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int u = 0; u < 3; ++u) {
+        fi[k][u] = ci[k] * (x[u] - oi[k][u]);
+        xo[k][u] = x[u] - oj[k][u];
+      }
+    const double h = io.h;
+    for (int im = 0; im < nm; ++im) {
+      double A1[3], P1[3];
+      for (int u = 0; u < 3; ++u) {
+        A1[u] = io.EA[im][u] - h * ns[u] * io.A0[im];
+        P1[u] = io.EP[im][u] - h * ns[u] * io.Sn[im];
+      }
+      for (int ks = 0; ks < 3; ++ks) {
+        double IA[3], IP[3], nIP[3];
+        for (int u = 0; u < 3; ++u) IA[u] = cj[ks] * (A1[u] + xo[ks][u] * io.A0[im]);
+        IP[0] = cj[ks] * (xo[ks][1] * P1[2] - xo[ks][2] * P1[1]);
+        IP[1] = cj[ks] * (xo[ks][2] * P1[0] - xo[ks][0] * P1[2]);
+        IP[2] = cj[ks] * (xo[ks][0] * P1[1] - xo[ks][1] * P1[0]);
+        nIP[0] = nin[1] * IP[2] - nin[2] * IP[1];
+        nIP[1] = nin[2] * IP[0] - nin[0] * IP[2];
+        nIP[2] = nin[0] * IP[1] - nin[1] * IP[0];
+        for (int kt = 0; kt < 3; ++kt) {
+          double val = kA * (fi[kt][0] * IA[0] + fi[kt][1] * IA[1] + fi[kt][2] * IA[2]) +
+                       kphi * divi[kt] * divj[ks] * io.phi[im] +
+                       kP * (fi[kt][0] * nIP[0] + fi[kt][1] * nIP[1] + fi[kt][2] * nIP[2]);
+          acc[kt][ks][m0 - M0 + im] += wq * val;
+        }
+      }
+    }
+    // MFIE identity term on the test triangle itself (lags 1 and 2)
+    if (s == t && ph.s_jump != 0.0) {
+      const double c1 = 1.0 / ph.dt + 0.5 * ph.zeta, c2 = -1.0 / ph.dt + 0.5 * ph.zeta;
+      for (int kt = 0; kt < 3; ++kt)
+        for (int ks = 0; ks < 3; ++ks) {
+          double fj[3];
+          for (int u = 0; u < 3; ++u) fj[u] = cj[ks] * xo[ks][u];
+          double G = wq * (fi[kt][0] * fj[0] + fi[kt][1] * fj[1] + fi[kt][2] * fj[2]);
+          double sc = ph.s_jump * ph.theta * ph.eta * 0.5 * G;
+          if (1 - M0 >= 0 && 1 - M0 < NM) acc[kt][ks][1 - M0] += sc * c1;
+          if (2 - M0 >= 0 && 2 - M0 < NM) acc[kt][ks][2 - M0] += sc * c2;
+        }
+    }
+  }
+  for (int kt = 0; kt < 3; ++kt) {
+    int i = g.edge[3 * t + kt];
+    for (int ks = 0; ks < 3; ++ks) {
+      int j = g.edge[3 * s + ks];
+      for (int k = 0; k < NM; ++k) {
+        double v = acc[kt][ks][k];
+        if (v == 0.0) continue;
+        double* dst = sink.slot(i, j, M0 + k);
+        if (!dst) {
+          atomicExch(err, 5);
+          continue;
+        }
+        atomicAdd(dst, v);
+      }
+    }
+  }
+}
+
+template __global__ void k_assemble<DirectSink>(TriGeom, Phys, int64_t, const int2*, int64_t, DirectSink, int32_t*);
+
+// ---------------------------------------------------------------------------
+// Incident right-hand side V_i^{alpha-1} (eq. v_i) for a modulated Gaussian
+// plane wave; one thread per edge, 2 triangles x 7 points, FP64.
+__global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, const double* pulse, int32_t alpha,
+                            double* R) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const double PI = 3.14159265358979323846;
+  double kv[3] = {pulse[0], pulse[1], pulse[2]}, pol[3] = {pulse[3], pulse[4], pulse[5]};
+  double f0 = pulse[6], sg = pulse[7], t0 = pulse[8], zmin = pulse[9];
+  double kxp[3] = {kv[1] * pol[2] - kv[2] * pol[1], kv[2] * pol[0] - kv[0] * pol[2], kv[0] * pol[1] - kv[1] * pol[0]};
+  double t = alpha * ph.dt;
+  double sum = 0.0;
+  for (int rho = 0; rho < 2; ++rho) {
+    int tri = et[2 * i + rho];
+    int side = 0;
+    for (int k = 0; k < 3; ++k)
+      if (g.edge[3 * tri + k] == (int)i) side = k;
+    double sgn = g.sgn[3 * tri + side], A = g.area[tri];
+    double ci = sgn * g.elen[3 * tri + side] / (2 * A);
+    const double* o = g.opp + 9 * tri + 3 * side;
+    const double* v = g.v + 9 * tri;
+    double nin[3] = {-g.nrm[3 * tri], -g.nrm[3 * tri + 1], -g.nrm[3 * tri + 2]};
+    for (int q = 0; q < kNq; ++q) {
+      double x[3];
+      for (int u = 0; u < 3; ++u) x[u] = ph.qb[q][0] * v[u] + ph.qb[q][1] * v[3 + u] + ph.qb[q][2] * v[6 + u];
+      double u_ = t - (kv[0] * x[0] + kv[1] * x[1] + kv[2] * x[2] - zmin) / ph.c;
+      double vv = u_ - t0;
+      double e = exp(-vv * vv / (2 * sg * sg));
+      double sw, cw;
+      sincos(2 * PI * f0 * vv, &sw, &cw);
+      double gg = cw * e;
+      double gd = (-2 * PI * f0 * sw - vv / (sg * sg) * cw) * e;
+      // -Edot + theta eta n x (Hdot + zeta H), E = pol g, H = k x pol g / eta
+      double Hm[3], nH[3];
+      for (int u = 0; u < 3; ++u) Hm[u] = kxp[u] * (gd + ph.zeta * gg) / ph.eta;
+      nH[0] = nin[1] * Hm[2] - nin[2] * Hm[1];
+      nH[1] = nin[2] * Hm[0] - nin[0] * Hm[2];
+      nH[2] = nin[0] * Hm[1] - nin[1] * Hm[0];
+      double val = 0.0;
+      for (int u = 0; u < 3; ++u) val += ci * (x[u] - o[u]) * (-pol[u] * gd + ph.theta * ph.eta * nH[u]);
+      sum += ph.qw[q] * A * val;
+    }
+  }
+  R[i] = sum;
+}
+
+// R_i -= sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m}; one block per row.
+// ring[j*L + (beta mod L)] = J_j^beta.
+__global__ void __launch_bounds__(256) k_direct_history(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off,
+                                                       const double* val, int64_t ne, const double* ring, int32_t L,
+                                                       int32_t alpha, double* R) {
+  int64_t i = blockIdx.x;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
+    int64_t p = i * ne + j;
+    int lo = m_lo[p], n = nlag[p];
+    const double* z = val + off[p];
+    const double* Jr = ring + j * L;
+    for (int w = 0; w < n; ++w) {
+      int m = lo + w;
+      int b = alpha - m;
+      if (m < 2 || b < 0) continue;
+      s += __ldg(z + w) * Jr[b & (L - 1)];
+    }
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) R[i] -= s;
+  }
+}
+
+}  // namespace tdbem
+
+using namespace tdbem;
+
+tdbem_status tdbem_build_direct(tdbem_ctx* c) {
+  const int64_t ne = c->ne, npair = ne * ne;
+  PairStore& st = c->direct;
+  st.npairs = npair;
+  tdbem_status s;
+  int32_t* d_err = nullptr;
+  if ((s = c->dalloc(&st.m_lo, npair)) || (s = c->dalloc(&st.nlag, npair)) || (s = c->dalloc(&st.off, npair)) ||
+      (s = c->dalloc(&d_err, 1)))
+    return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_err, 0, sizeof(int32_t), c->stream));
+  k_direct_windows<<<(unsigned)((npair + 255) / 256), 256, 0, c->stream>>>(c->tg, c->d_et, ne, c->phys.a, st.m_lo,
+                                                                           st.nlag, d_err);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  int64_t* d_tot = nullptr;
+  int64_t* d_base = nullptr;
+  if ((s = c->dalloc(&d_tot, ne)) || (s = c->dalloc(&d_base, ne))) return s;
+  k_row_totals<<<(unsigned)ne, 256, 0, c->stream>>>(st.nlag, ne, d_tot);
+  std::vector<int64_t> tot(ne), base(ne);
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(tot.data(), d_tot, ne * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  int32_t herr = 0;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) {
+    c->set_error("direct: lag window out of range (mesh too large relative to c*dt)");
+    return TDBEM_EINVAL;
+  }
+  int64_t acc = 0;
+  for (int64_t i = 0; i < ne; ++i) {
+    base[i] = acc;
+    acc += tot[i];
+  }
+  st.nval = acc;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(d_base, base.data(), ne * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  k_row_offsets<<<(unsigned)ne, 1024, 0, c->stream>>>(st.nlag, ne, d_base, st.off);
+  if ((s = c->dalloc(&st.val, st.nval))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(st.val, 0, st.nval * sizeof(double), c->stream));
+  DirectSink sink{st.m_lo, st.nlag, st.off, st.val, ne};
+  const int64_t ntp = c->nt * c->nt;
+  k_assemble<DirectSink><<<(unsigned)((ntp + 127) / 128), 128, 0, c->stream>>>(c->tg, c->phys, c->nt, nullptr, ntp,
+                                                                               sink, d_err);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) {
+    c->set_error("direct: assembly failed (lag window or light-cone pieces exceed the local buffers), code " +
+                 std::to_string(herr));
+    return TDBEM_EINVAL;
+  }
+  // largest stored lag: every window ends below (bounding-box diagonal + two
+  // triangle radii)/(c dt) + 3
+  int32_t mx = 0;
+  {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, dmax = 0;
+    for (int64_t v = 0; v < c->nv; ++v)
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = std::min(lo[q], c->V[3 * v + q]);
+        hi[q] = std::max(hi[q], c->V[3 * v + q]);
+      }
+    for (int q = 0; q < 3; ++q) dmax += (hi[q] - lo[q]) * (hi[q] - lo[q]);
+    dmax = std::sqrt(dmax) + 2.0 * c->max_tri_rad;
+    mx = (int32_t)std::ceil(dmax / c->phys.a + 3.0) + 1;
+  }
+  c->max_lag = mx;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_rhs_into_R(tdbem_ctx* c, int32_t alpha) {
+  const int64_t ne = c->ne;
+  if (c->d_Vall) {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, c->d_Vall + (int64_t)(alpha - 1) * ne, ne * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, c->stream));
+  } else if (c->have_pulse) {
+    k_rhs_plane<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(c->tg, c->phys, c->d_et, ne, c->d_pulse, alpha,
+                                                                     c->d_R);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  } else {
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_R, 0, ne * sizeof(double), c->stream));
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, int32_t) {
+  const PairStore& st = c->direct;
+  k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
+                                                           alpha, c->d_R);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}

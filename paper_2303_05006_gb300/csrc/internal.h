@@ -1,0 +1,138 @@
+// internal.h -- library-private declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tdbem.h"
+
+#define TDBEM_CUDA_TRY(ctx, call)                                                       \
+  do {                                                                                  \
+    cudaError_t e__ = (call);                                                           \
+    if (e__ != cudaSuccess) {                                                           \
+      (ctx)->set_error(std::string(#call) + ": " + cudaGetErrorString(e__));            \
+      return (e__ == cudaErrorMemoryAllocation) ? TDBEM_ENOMEM : TDBEM_ECUDA;           \
+    }                                                                                   \
+  } while (0)
+
+namespace tdbem {
+
+constexpr int kMaxWin = 16;   // max lags of one (observation point, source triangle) pair
+constexpr int kNq = 7;        // outer quadrature points per test triangle
+
+// Per-triangle geometry in device memory (structure of arrays).
+struct TriGeom {
+  double* v;       // [nt][3][3] vertex coordinates
+  double* nrm;     // [nt][3] unit normal of the winding (outward)
+  double* cen;     // [nt][3] centroid
+  double* area;    // [nt]
+  double* rad;     // [nt] max centroid-vertex distance
+  double* lmax;    // [nt] longest side
+  int32_t* edge;   // [nt][3] edge on side k (vertex k -> k+1)
+  int8_t* sgn;     // [nt][3] +1 if this triangle is the + triangle of that edge
+  double* opp;     // [nt][3][3] vertex opposite side k (the o of that edge's RWG on this triangle)
+  double* elen;    // [nt][3] length of side k
+};
+
+// Physical and discretisation constants passed by value to kernels.
+struct Phys {
+  double dt, a;                // time step, c*dt
+  double c, eta, eps, mu;
+  double theta, zeta, s_jump;
+  double qb[kNq][3], qw[kNq];  // outer rule (barycentric points, weights summing to 1)
+};
+
+// Directly stored coefficients of all lags of a set of edge pairs:
+// for pair p = (i, j): lags m_lo .. m_lo+nlag-1 at val[off .. off+nlag).
+struct PairStore {
+  int64_t npairs = 0;
+  int64_t nval = 0;
+  int16_t* m_lo = nullptr;
+  uint8_t* nlag = nullptr;
+  int64_t* off = nullptr;   // [npairs]
+  double* val = nullptr;    // [nval]
+};
+
+}  // namespace tdbem
+
+struct tdbem_ctx {
+  tdbem_params p;
+  double dt = 0;
+  int32_t Nt = 0;
+  tdbem::Phys phys;
+  int64_t nv = 0, nt = 0, ne = 0;
+  double max_tri_rad = 0;            // max over triangles of centroid-vertex distance
+  // host mesh tables
+  std::vector<double> V;
+  std::vector<int32_t> T;
+  std::vector<int32_t> ev, et, eo;  // [ne][2]
+  std::vector<int32_t> te;          // [nt][3]
+  std::vector<int8_t> ts;           // [nt][3]
+  // device mesh
+  tdbem::TriGeom tg{};
+  int32_t* d_et = nullptr;          // [ne][2]
+  // direct coefficients: rows i, all j (direct mode)
+  tdbem::PairStore direct;
+  int32_t max_lag = 0;
+  // Z0 in CSR
+  int32_t* d_z0_ptr = nullptr;
+  int32_t* d_z0_col = nullptr;
+  double* d_z0_val = nullptr;
+  double* d_z0_inv_diag = nullptr;
+  int64_t z0_nnz = 0;
+  // marching state
+  int32_t L = 0;                    // ring length (power of two)
+  double* d_Jring = nullptr;        // [ne][L]
+  double* d_R = nullptr;            // [ne]
+  double* d_J = nullptr;            // [ne] current solution
+  double* d_Vall = nullptr;         // [Nt-1][ne] or null
+  double* d_pulse = nullptr;        // [10]
+  bool have_pulse = false;
+  double pulse[10];
+  double* d_work = nullptr;         // solver vectors [8][ne]
+  double* d_dots = nullptr;         // solver reductions
+  int32_t* d_status = nullptr;      // solver status / iterations
+  int32_t alpha = 1;
+  int64_t total_iters = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  double setup_seconds = 0;
+  int64_t device_bytes = 0;
+  // kernel-class timing (tdbem_profile_*)
+  static constexpr int kClasses = 8;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
+  size_t ev_next = 0;
+  cudaEvent_t prof_begin(int cls);
+  void prof_end(int cls, cudaEvent_t b);
+  std::string err;
+  void set_error(const std::string& s) { err = s; }
+  template <class T>
+  tdbem_status dalloc(T** ptr, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      *ptr = nullptr;
+      return TDBEM_ENOMEM;
+    }
+    device_bytes += (int64_t)(count * sizeof(T));
+    allocs.push_back((void*)*ptr);
+    return TDBEM_OK;
+  }
+  std::vector<void*> allocs;
+};
+
+// mesh.cu
+tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t ntri);
+// direct.cu
+tdbem_status tdbem_build_direct(tdbem_ctx* c);
+tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, int32_t hist_count);
+tdbem_status tdbem_rhs_into_R(tdbem_ctx* c, int32_t alpha);
+// solve.cu
+tdbem_status tdbem_build_z0(tdbem_ctx* c);
+tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters);
