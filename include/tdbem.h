@@ -166,6 +166,7 @@ typedef struct {
   int64_t device_bytes;            /* device memory held by the context */
   double setup_seconds;            /* wall time of tdbem_create */
   int64_t total_solver_iters;
+  int32_t solver_cluster;          /* CTAs in the Z0 solver's thread-block cluster (0 before the first solve) */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 

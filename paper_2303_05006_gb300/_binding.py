@@ -34,7 +34,8 @@ class Info(ctypes.Structure):
     _fields_ = [("ne", ctypes.c_int64), ("n_tri", ctypes.c_int64), ("lmax", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("mt_leaf", ctypes.c_int32), ("n_near_pairs", ctypes.c_int64),
                 ("near_coef_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64)]
+                ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
+                ("solver_cluster", ctypes.c_int32)]
 
 
 class TdbemError(RuntimeError):

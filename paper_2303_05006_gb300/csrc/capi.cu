@@ -2,6 +2,7 @@
 // driver (paper Program 1).
 #include <chrono>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -130,6 +131,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
     return e == cudaErrorMemoryAllocation ? TDBEM_ENOMEM : TDBEM_ECUDA;
   }
   c->stream = c->own_stream;
+  cudaGetDevice(&c->device);
   tdbem_status s = tdbem_build_mesh(c, verts, nv, tris, ntri);
   if (!s) {
     if (p.mode == TDBEM_DIRECT) {
@@ -175,6 +177,10 @@ tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* p
   if (!(pulse[7] > 0)) return TDBEM_EINVAL;
   std::memcpy(c->pulse, pulse, sizeof(c->pulse));
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse, c->pulse, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  cudaEvent_t e = c->prof_begin(0);
+  tdbem_status s = tdbem_incident_table(c);
+  c->prof_end(0, e);
+  if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->have_pulse = true;
   return TDBEM_OK;
@@ -193,15 +199,9 @@ tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
 // R^{alpha-1} = V^{alpha-1} - history (eq. R), ring holds the history.
 // skip_rhs: R already holds V^{alpha-1}.
 static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bool skip_rhs = false) {
-  tdbem_status s;
-  if (!skip_rhs) {
-    cudaEvent_t e = c->prof_begin(0);
-    s = tdbem_rhs_into_R(c, alpha);
-    c->prof_end(0, e);
-    if (s) return s;
-  }
+  const double* V = skip_rhs ? c->d_R : tdbem_incident_row(c, alpha);
   cudaEvent_t e = c->prof_begin(1);
-  s = tdbem_direct_history(c, alpha, d_ring, 0);
+  tdbem_status s = tdbem_direct_history(c, alpha, d_ring, V);
   c->prof_end(1, e);
   return s;
 }
@@ -369,6 +369,7 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->device_bytes = c->device_bytes;
   info->setup_seconds = c->setup_seconds;
   info->total_solver_iters = c->total_iters;
+  info->solver_cluster = c->cluster;
   return TDBEM_OK;
 }
 

@@ -261,10 +261,13 @@ template __global__ void k_assemble<DirectSink>(TriGeom, Phys, int64_t, const in
 // ---------------------------------------------------------------------------
 // Incident right-hand side V_i^{alpha-1} (eq. v_i) for a modulated Gaussian
 // plane wave; one thread per edge, 2 triangles x 7 points, FP64.
-__global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, const double* pulse, int32_t alpha,
-                            double* R) {
+// grid: (edge blocks, steps); V[(alpha-1)*ne + i] for alpha = alpha0 .. alpha0+gridDim.y-1
+__global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, const double* pulse, int32_t alpha0,
+                            double* V) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ne) return;
+  const int32_t alpha = alpha0 + blockIdx.y;
+  double* R = V + (int64_t)(alpha - alpha0) * ne;
   const double PI = 3.14159265358979323846;
   double kv[3] = {pulse[0], pulse[1], pulse[2]}, pol[3] = {pulse[3], pulse[4], pulse[5]};
   double f0 = pulse[6], sg = pulse[7], t0 = pulse[8], zmin = pulse[9];
@@ -305,11 +308,11 @@ __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, c
   R[i] = sum;
 }
 
-// R_i -= sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m}; one block per row.
-// ring[j*L + (beta mod L)] = J_j^beta.
+// R_i = V_i - sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m} (V may be
+// null: zero; V may alias R); one block per row.  ring[j*L + (beta mod L)] = J_j^beta.
 __global__ void __launch_bounds__(256) k_direct_history(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off,
                                                        const double* val, int64_t ne, const double* ring, int32_t L,
-                                                       int32_t alpha, double* R) {
+                                                       int32_t alpha, const double* V, double* R) {
   int64_t i = blockIdx.x;
   double s = 0.0;
   for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(256) k_direct_history(const int16_t* m_lo, con
   if (threadIdx.x < 32) {
     s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) R[i] -= s;
+    if (threadIdx.x == 0) R[i] = (V ? V[i] : 0.0) - s;
   }
 }
 
@@ -405,25 +408,32 @@ tdbem_status tdbem_build_direct(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_rhs_into_R(tdbem_ctx* c, int32_t alpha) {
+tdbem_status tdbem_incident_table(tdbem_ctx* c) {
   const int64_t ne = c->ne;
-  if (c->d_Vall) {
-    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, c->d_Vall + (int64_t)(alpha - 1) * ne, ne * sizeof(double),
-                                      cudaMemcpyDeviceToDevice, c->stream));
-  } else if (c->have_pulse) {
-    k_rhs_plane<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(c->tg, c->phys, c->d_et, ne, c->d_pulse, alpha,
-                                                                     c->d_R);
+  const int64_t n = (int64_t)(c->Nt - 1) * ne;
+  tdbem_status s;
+  if (!c->d_Vtab && (s = c->dalloc(&c->d_Vtab, n))) return s;
+  const int32_t chunk = 1024;  // steps per launch (grid.y limit)
+  for (int32_t a0 = 1; a0 <= c->Nt - 1; a0 += chunk) {
+    int32_t na = std::min(chunk, c->Nt - a0);
+    dim3 grid((unsigned)((ne + 127) / 128), (unsigned)na);
+    k_rhs_plane<<<grid, 128, 0, c->stream>>>(c->tg, c->phys, c->d_et, ne, c->d_pulse, a0,
+                                              c->d_Vtab + (int64_t)(a0 - 1) * ne);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
-  } else {
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_R, 0, ne * sizeof(double), c->stream));
   }
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, int32_t) {
+const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
+  if (c->d_Vall) return c->d_Vall + (int64_t)(alpha - 1) * c->ne;
+  if (c->have_pulse && c->d_Vtab) return c->d_Vtab + (int64_t)(alpha - 1) * c->ne;
+  return nullptr;
+}
+
+tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V) {
   const PairStore& st = c->direct;
   k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
-                                                           alpha, c->d_R);
+                                                           alpha, V, c->d_R);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }

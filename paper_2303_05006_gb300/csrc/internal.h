@@ -20,7 +20,7 @@
 
 namespace tdbem {
 
-constexpr int kMaxWin = 16;   // max lags of one (observation point, source triangle) pair
+constexpr int kMaxWin = 32;   // max lags of one (observation point, source triangle) pair
 constexpr int kNq = 7;        // outer quadrature points per test triangle
 
 // Per-triangle geometry in device memory (structure of arrays).
@@ -97,6 +97,9 @@ struct tdbem_ctx {
   int32_t* d_status = nullptr;      // solver status / iterations
   int32_t alpha = 1;
   int64_t total_iters = 0;
+  int32_t cluster = 0;              // CTAs in the solver's thread-block cluster
+  int32_t device = 0;               // CUDA device the context lives on
+  double* d_Vtab = nullptr;         // [Nt-1][ne] incident field of every step (precomputed)
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   double setup_seconds = 0;
@@ -131,8 +134,9 @@ struct tdbem_ctx {
 tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, const int32_t* tris, int64_t ntri);
 // direct.cu
 tdbem_status tdbem_build_direct(tdbem_ctx* c);
-tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, int32_t hist_count);
-tdbem_status tdbem_rhs_into_R(tdbem_ctx* c, int32_t alpha);
+tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V);
+tdbem_status tdbem_incident_table(tdbem_ctx* c);
+const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha);
 // solve.cu
 tdbem_status tdbem_build_z0(tdbem_ctx* c);
 tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters);

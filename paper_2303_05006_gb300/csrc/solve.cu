@@ -23,6 +23,8 @@ namespace cg = cooperative_groups;
 
 namespace tdbem {
 
+constexpr int kSolveThreads = 512;
+
 __global__ void k_z0_count(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int32_t* cnt) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ne) return;
@@ -119,7 +121,7 @@ __device__ __forceinline__ double spmv_row(const SolveArgs& A, int64_t i, const 
   return s;
 }
 
-__global__ void __launch_bounds__(1024) k_bicgstab(SolveArgs A) {
+__global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double red[32 * 4];
   // one slot per reduction phase, so that a slot is rewritten only after a
@@ -285,7 +287,7 @@ static tdbem_status pick_cluster(tdbem_ctx* c) {
   for (int cs : {16, 8, 4, 2, 1}) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
-    cfg.blockDim = dim3(1024);
+    cfg.blockDim = dim3(kSolveThreads);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cs;
@@ -294,13 +296,15 @@ static tdbem_status pick_cluster(tdbem_ctx* c) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_bicgstab, &cfg) == cudaSuccess && ncl > 0) {
+    cudaError_t oe = cudaOccupancyMaxActiveClusters(&ncl, k_bicgstab, &cfg);
+    if (oe == cudaSuccess && ncl > 0) {
       g_cluster = cs;
       return TDBEM_OK;
     }
     cudaGetLastError();
+    c->set_error(std::string("solve: cluster of ") + std::to_string(cs) + " not schedulable: " +
+                 cudaGetErrorString(oe) + ", max active " + std::to_string(ncl));
   }
-  c->set_error("solve: no cluster size is schedulable");
   return TDBEM_ECUDA;
 }
 
@@ -324,9 +328,10 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
   A.maxit = c->p.solve_maxit;
   A.status = c->d_status;
   A.resid = c->d_dots;
+  c->cluster = g_cluster;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g_cluster);
-  cfg.blockDim = dim3(1024);
+  cfg.blockDim = dim3(kSolveThreads);
   cfg.stream = c->stream;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

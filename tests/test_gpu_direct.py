@@ -95,7 +95,9 @@ def test_sampled_rows_full_size_sphere7680():
         R_gpu = s.history_eval(alpha, J)[rows]
         R_ref = o.rhs(w.pulses[0], alpha, rows) - o.history(alpha, J, rows, mats=mats)
         scale = np.abs(R_ref).max() + np.abs(o.history(alpha, np.abs(J), rows, mats=mats)).max()
-        assert np.abs(R_gpu - R_ref).max() <= 1e-11 * scale
+        # far pairs reach light-cone knot index j ~ 55 here; the closed-form
+        # primitives lose about j^3 eps ~ 2e-11 of the scale in FP64
+        assert np.abs(R_gpu - R_ref).max() <= 1e-10 * scale
 
 
 def test_errors_are_returned():
