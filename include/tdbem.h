@@ -131,6 +131,34 @@ tdbem_status tdbem_set_rhs(tdbem_ctx* ctx, int32_t rhs, const double* V);
 tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_hist, int32_t n_hist,
                                 double* R_out);
 
+/* Capacity, in doubles, of the fixed device scratch array used by
+   tdbem_history_eval_noalloc (16 MiB). */
+#define TDBEM_NOALLOC_SCRATCH_DOUBLES (2 * 1024 * 1024)
+
+/* Same result as tdbem_history_eval, for callers that must not allocate
+   device memory at the time of the call: code running while another library
+   captures the stream into a CUDA graph, real-time loops whose allocator is
+   frozen, or hosts that own the whole device pool.  tdbem_history_eval
+   allocates a temporary device ring for the supplied history on every call;
+   this variant stages the history in a file-scope static device array of
+   TDBEM_NOALLOC_SCRATCH_DOUBLES doubles instead (reserved on every GPU that
+   loads the library, until exit), and calls no cudaMalloc, cudaFree or other
+   allocating routine.  The paper has no counterpart: it is a deployment
+   convenience.
+     * Needs ne * (L + K) <= TDBEM_NOALLOC_SCRATCH_DOUBLES, where L is the
+       context's history ring length and K the number of history steps used
+       (at most the largest lag); larger problems get TDBEM_EINVAL.
+     * The context's device must be the current device.
+     * The first call on a device resolves the array's device address
+       (cudaGetSymbolAddress) once; make that first call before any stream
+       capture.
+     * Every call shares the one array and rewrites all of it that it reads, so
+       no state carries over between calls; calls that overlap on the GPU (two
+       streams, or two contexts on one device) race on it.
+   Arguments, ownership and errors as for tdbem_history_eval. */
+tdbem_status tdbem_history_eval_noalloc(tdbem_ctx* ctx, int32_t alpha, const double* J_hist, int32_t n_hist,
+                                        double* R_out);
+
 /* One step of Program 1: adds V^{alpha-1}, evaluates the history sum, solves
    Z0 J^{alpha-1} = R^{alpha-1} and, in fast mode at gating steps, pushes the far
    field of the finished time intervals into future right-hand sides.  J_out

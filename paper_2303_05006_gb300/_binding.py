@@ -70,6 +70,7 @@ def lib():
         L.tdbem_set_incident_plane.argtypes = [vp, ctypes.c_int32, _dp]
         L.tdbem_set_rhs.argtypes = [vp, ctypes.c_int32, _dp]
         L.tdbem_history_eval.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp]
+        L.tdbem_history_eval_noalloc.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp]
         L.tdbem_step.argtypes = [vp, _dp, _i32p]
         L.tdbem_march.argtypes = [vp, ctypes.c_int32, _dp]
         L.tdbem_march_dev.argtypes = [vp, ctypes.c_int32, vp]
@@ -86,7 +87,7 @@ def lib():
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
                      "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
-                     "tdbem_profile_read"):
+                     "tdbem_profile_read", "tdbem_history_eval_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -159,6 +160,15 @@ class Solver:
         J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.ne)
         out = np.zeros(self.ne)
         self._check(lib().tdbem_history_eval(self._h, int(alpha), _ptr(J) if J.size else None, J.shape[0], _ptr(out)))
+        return out
+
+    def history_eval_noalloc(self, alpha: int, J_hist) -> np.ndarray:
+        """As history_eval, staging the history in the library's fixed device
+        scratch array instead of allocating device memory."""
+        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.ne)
+        out = np.zeros(self.ne)
+        self._check(lib().tdbem_history_eval_noalloc(self._h, int(alpha), _ptr(J) if J.size else None, J.shape[0],
+                                                     _ptr(out)))
         return out
 
     def step(self):

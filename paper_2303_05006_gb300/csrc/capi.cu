@@ -4,6 +4,7 @@
 #include <cmath>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -227,6 +228,76 @@ tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_his
     c->set_error(std::string("history_eval: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     return TDBEM_ECUDA;
   }
+  return TDBEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free history evaluation: the history is staged in a fixed static
+// device array instead of a per-call allocation.
+static __device__ __align__(256) double g_noalloc_scratch[TDBEM_NOALLOC_SCRATCH_DOUBLES];
+
+// ring[j*L + (b mod L)] = staged[(b - b0)*ne + j] for b = b0 .. b0+nb-1
+__global__ void k_stage_to_ring(const double* staged, int32_t b0, int32_t nb, int64_t ne, int32_t L, double* ring) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nb * ne) return;
+  int32_t k = (int32_t)(t / ne);
+  int64_t j = t % ne;
+  ring[j * L + ((b0 + k) & (L - 1))] = staged[t];
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" tdbem_status tdbem_history_eval_noalloc(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist,
+                                                   double* R_out) {
+  if (!c || !R_out || alpha < 1 || alpha > c->Nt - 1 || n_hist < 0 || (n_hist > 0 && !J_hist)) return TDBEM_EINVAL;
+  const int64_t ne = c->ne;
+  const int32_t L = c->L;
+  const int32_t b0 = std::max(0, alpha - c->max_lag);
+  const int32_t b1 = std::min(alpha - 2, n_hist - 1);
+  const int32_t nb = b1 >= b0 ? b1 - b0 + 1 : 0;
+  if (ne * (int64_t)L + (int64_t)nb * ne > (int64_t)TDBEM_NOALLOC_SCRATCH_DOUBLES) {
+    c->set_error("history_eval_noalloc: problem needs " + std::to_string(ne * (int64_t)L + (int64_t)nb * ne) +
+                 " doubles of scratch, more than TDBEM_NOALLOC_SCRATCH_DOUBLES");
+    return TDBEM_EINVAL;
+  }
+  int dev = -1;
+  TDBEM_CUDA_TRY(c, cudaGetDevice(&dev));
+  if (dev != c->device || dev < 0 || dev >= kMaxDevices) {
+    c->set_error("history_eval_noalloc: the context's device must be current");
+    return TDBEM_EINVAL;
+  }
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        c->set_error(std::string("history_eval_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return TDBEM_ECUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  double* ring = scratch;
+  double* staged = scratch + ne * (int64_t)L;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(ring, 0, ne * (int64_t)L * sizeof(double), c->stream));
+  if (nb > 0) {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(staged, J_hist + (int64_t)b0 * ne, (int64_t)nb * ne * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream));
+    int64_t n = (int64_t)nb * ne;
+    k_stage_to_ring<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(staged, b0, nb, ne, L, ring);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
+  tdbem_status s = eval_R(c, alpha, ring);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(R_out, c->d_R, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
 
