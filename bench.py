@@ -6,7 +6,8 @@ solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
 already resident in HBM.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode fast|direct] [--workload NAME]
+                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3] [--p P]
+                  [--workload NAME] [--no-compare] [--no-cpu-baseline]
 
 N > 1 (torchrun): independent replicas, one per GPU; the march does not shard.
 """
@@ -139,6 +140,43 @@ def run_reference(args, rank, world, dist):
     return 0
 
 
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+KERNELS = ["incident_rhs", "near_history" , "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
+
+
+def roofline(args, info, launches, ms, K):
+    """Roofline of the dominant kernel class of the timed steps, from CUDA-event
+    times on the library's stream: achieved = algorithmic work / device time."""
+    hbm, bf16, src = _peaks()
+    dom = int(np.argmax(ms))
+    name = KERNELS[dom]
+    if name == "m2l" and info.m2l_flops_per_step > 0:
+        flops = info.m2l_flops_per_step * K
+        tflops = flops / (ms[dom] / 1e3) / 1e12
+        if args.prec == "fp32":
+            # FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+            return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": 80.5, "unit": "TFLOP/s",
+                    "frac": tflops / 80.5, "traffic": None, "peak_source": "derived: FP32 lanes x clock",
+                    "flops_per_launch": flops / max(launches[dom], 1)}
+        peak = bf16 if args.prec in ("bf16", "bf16x3") else bf16 * 1.1 / 2.25
+        how = f"{src} bf16_tflops" + ("" if args.prec != "tf32" else " x 1.1/2.25 (nominal TF32/BF16)")
+        return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": tflops / peak, "traffic": None, "peak_source": how,
+                "flops_per_launch": flops / max(launches[dom], 1),
+                "note": "algorithmic flops (split BF16x3 executes three products per flop counted)"
+                if args.prec == "bf16x3" else ""}
+    if name in ("near_history",):
+        if args.mode == "direct":
+            nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8)
+        else:
+            nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8 + 4)
+        gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}
+    return {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -149,15 +187,15 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     w = workload(args.workload)
     mode = {"direct": 0, "fast": 1}[args.mode]
+    W, K = args.warmup, args.steps
+    if W + K > w.Nt - 1:
+        raise SystemExit(f"warmup + steps must be <= {w.Nt - 1}")
     t0 = time.perf_counter()
-    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode)
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec])
     setup_s = time.perf_counter() - t0
     s.set_incident_plane(w.pulses[0])
     stream = torch.cuda.current_stream()
     s.set_stream(stream.cuda_stream)
-    W, K = args.warmup, args.steps
-    if W + K > w.Nt - 1:
-        raise SystemExit(f"warmup + steps must be <= {w.Nt - 1}")
     out = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
     # device-resident march: warm-up, then K timed steps
     s.march_dev(W)
@@ -177,8 +215,7 @@ def run_ours(args, rank, world, dist):
         tt = torch.tensor([t])
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt[0])
-        if dist:
-            dist.barrier()
+        dist.barrier()
     steps_per_s = world * K / t
     # per-kernel timing of the same work (instrumented second pass)
     s.reset()
@@ -211,38 +248,49 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt[0])
     e2e = world * K / te
+    Jfast = out.cpu().numpy()
+    s.close()
     if rank != 0:
         return 0
-    hbm, bf16, src = _peaks()
-    # dominant kernel: class 1 (history / near field)
-    dom = int(np.argmax(ms))
-    names = ["incident_rhs", "history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
-    avg = ms[dom] / max(launches[dom], 1) / 1000.0
-    if args.mode == "direct":
-        algo_bytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8)
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": algo_bytes / avg / 1e9 if dom == 1 else None,
-                "peak": hbm, "unit": "GB/s", "traffic": None,
-                "peak_source": f"{src} hbm_gbs",
-                "bytes_per_launch": algo_bytes}
-        if roof["achieved"] is not None:
-            roof["frac"] = roof["achieved"] / hbm
+    # the plain GPU path on the same steps: speed and the fast path's error
+    cmp = {}
+    if args.mode == "fast" and not args.no_compare:
+        sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0)
+        sd.set_incident_plane(w.pulses[0])
+        sd.set_stream(stream.cuda_stream)
+        outd = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
+        sd.march_dev(W)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sd.march_dev(K, outd.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        td = e0.elapsed_time(e1) / 1000.0
+        Jd = outd.cpu().numpy()
+        cmp = {"direct_steps_per_s": K / td,
+               "fast_over_direct": (K / t) / (K / td),
+               "rel_l2_vs_direct": float(np.linalg.norm(Jfast - Jd) / np.linalg.norm(Jd))}
+        sd.close()
     line = {
         "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1000.0 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode == "direct" else "f32+f64", "data": "synthetic",
+        "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
+                   "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
-                   "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored coefficients)",
+                   "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
+                         + (" + M2L operators" if args.mode == "fast" else "") + ")",
                    "setup_s": setup_s},
         "ns_nt_per_s": steps_per_s * w.n_tri,
-        "roofline": roof,
-        "kernel_ms_per_step": {names[k]: ms[k] / K for k in range(len(ms)) if launches[k]},
+        "roofline": roofline(args, info, launches, ms, K),
+        "kernel_ms_per_step": {KERNELS[k]: ms[k] / K for k in range(len(ms)) if launches[k]},
         "gpu_launches": int(sum(launches)),
         "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.ne, "d2h_bytes_per_step": 8 * s.ne},
         "clocks": ck,
         "solver_iters_per_step": info.total_solver_iters / K if K else None,
     }
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+    line.update(cmp)
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
         res = oracle_sample(w, 16, 16)
         line["cpu_baseline"] = {"value": res["steps_per_s"], "unit": "steps/s", "cores": res["cores"],
                                 "kind": "oracle",
@@ -258,7 +306,10 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["fast", "direct"], default="direct")
+    ap.add_argument("--mode", choices=["fast", "direct"], default="fast")
+    ap.add_argument("--prec", choices=list(PREC), default="bf16x3")
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--workload", default="sphere7680")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

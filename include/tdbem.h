@@ -148,6 +148,7 @@ tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_h
      * Needs ne * (L + K) <= TDBEM_NOALLOC_SCRATCH_DOUBLES, where L is the
        context's history ring length and K the number of history steps used
        (at most the largest lag); larger problems get TDBEM_EINVAL.
+     * Direct mode only (TDBEM_EINVAL otherwise).
      * The context's device must be the current device.
      * The first call on a device resolves the array's device address
        (cudaGetSymbolAddress) once; make that first call before any stream
@@ -195,6 +196,8 @@ typedef struct {
   double setup_seconds;            /* wall time of tdbem_create */
   int64_t total_solver_iters;
   int32_t solver_cluster;          /* CTAs in the Z0 solver's thread-block cluster (0 before the first solve) */
+  int64_t n_far_pairs;             /* interaction-list cluster pairs over all levels (fast mode) */
+  double m2l_flops_per_step;       /* M2L flops per step, averaged over the gating cycle (fast mode) */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 

@@ -35,7 +35,8 @@ class Info(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("mt_leaf", ctypes.c_int32), ("n_near_pairs", ctypes.c_int64),
                 ("near_coef_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
-                ("solver_cluster", ctypes.c_int32)]
+                ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
+                ("m2l_flops_per_step", ctypes.c_double)]
 
 
 class TdbemError(RuntimeError):

@@ -85,6 +85,7 @@ void tdbem_destroy(tdbem_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
+  tdbem_fast_free(c);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
@@ -116,6 +117,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
   else
     tdbem_default_params(&p);
   if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
+      p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_BF16X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs != 1 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
@@ -139,8 +141,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       s = tdbem_build_direct(c);
       if (!s) s = tdbem_build_z0(c);
     } else {
-      c->set_error("create: fast mode is not available in this build");
-      s = TDBEM_EINVAL;
+      s = tdbem_build_fast(c);
+      if (!s) s = tdbem_build_z0_csr(c);
     }
   }
   if (!s) s = finish_create(c);
@@ -199,12 +201,47 @@ tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
 
 // R^{alpha-1} = V^{alpha-1} - history (eq. R), ring holds the history.
 // skip_rhs: R already holds V^{alpha-1}.
-static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bool skip_rhs = false) {
+static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bool skip_rhs = false,
+                           bool eval = false) {
   const double* V = skip_rhs ? c->d_R : tdbem_incident_row(c, alpha);
+  if (c->p.mode == TDBEM_FAST) return tdbem_fast_history(c, alpha, d_ring, V, eval);
   cudaEvent_t e = c->prof_begin(1);
   tdbem_status s = tdbem_direct_history(c, alpha, d_ring, V);
   c->prof_end(1, e);
   return s;
+}
+
+// ring[j*L + slot] = x[j]
+__global__ void k_ring_put(const double* x, int64_t ne, int32_t L, int32_t slot, double* ring) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < ne) ring[j * L + slot] = x[j];
+}
+
+// Fast-mode history evaluation: the far field of target alpha-1 depends on
+// every earlier gating event, so the events of steps 1 .. alpha-1 are replayed
+// on the supplied history in a separate evaluation state, feeding the ring one
+// step at a time exactly as the march does.
+static tdbem_status fast_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist,
+                                      double* d_ring, double* d_buf) {
+  const int64_t ne = c->ne;
+  tdbem_status s = tdbem_fast_eval_reset(c);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_ring, 0, ne * (int64_t)c->L * sizeof(double), c->stream));
+  for (int32_t a = 1; a <= alpha - 1; ++a) {
+    int32_t b = a - 1;  // J^{a-1} becomes known after step a
+    if (b < n_hist) {
+      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(d_buf, J_hist + (int64_t)b * ne, ne * sizeof(double), cudaMemcpyHostToDevice,
+                                        c->stream));
+    } else {
+      TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_buf, 0, ne * sizeof(double), c->stream));
+    }
+    k_ring_put<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(d_buf, ne, c->L, b & (c->L - 1), d_ring);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    // the march consumes (clears) the far slot of target a-1 at step a
+    if ((s = tdbem_fast_consume_eval_slot(c, a))) return s;
+    if ((s = tdbem_fast_replay_step(c, a, d_ring))) return s;
+  }
+  return eval_R(c, alpha, d_ring, false, true);
 }
 
 tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist, double* R_out) {
@@ -215,10 +252,15 @@ tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_his
   for (int32_t b = std::max(0, alpha - c->max_lag); b <= alpha - 2 && b < n_hist; ++b)
     for (int64_t j = 0; j < ne; ++j) ring[(size_t)j * L + (b & (L - 1))] = J_hist[(int64_t)b * ne + j];
   double* d_ring = nullptr;
-  TDBEM_CUDA_TRY(c, cudaMallocAsync(&d_ring, ring.size() * sizeof(double), c->stream));
-  cudaError_t e = cudaMemcpyAsync(d_ring, ring.data(), ring.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  TDBEM_CUDA_TRY(c, cudaMallocAsync(&d_ring, (ring.size() + ne) * sizeof(double), c->stream));
+  cudaError_t e = cudaSuccess;
   tdbem_status s = TDBEM_OK;
-  if (e == cudaSuccess) s = eval_R(c, alpha, d_ring);
+  if (c->p.mode == TDBEM_FAST) {
+    s = fast_history_eval(c, alpha, J_hist, n_hist, d_ring, d_ring + ring.size());
+  } else {
+    e = cudaMemcpyAsync(d_ring, ring.data(), ring.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) s = eval_R(c, alpha, d_ring);
+  }
   if (e == cudaSuccess && !s)
     e = cudaMemcpyAsync(R_out, c->d_R, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   cudaFreeAsync(d_ring, c->stream);
@@ -254,6 +296,10 @@ double* g_noalloc_ptr[kMaxDevices] = {};
 extern "C" tdbem_status tdbem_history_eval_noalloc(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist,
                                                    double* R_out) {
   if (!c || !R_out || alpha < 1 || alpha > c->Nt - 1 || n_hist < 0 || (n_hist > 0 && !J_hist)) return TDBEM_EINVAL;
+  if (c->p.mode != TDBEM_DIRECT) {
+    c->set_error("history_eval_noalloc: direct mode only");
+    return TDBEM_EINVAL;
+  }
   const int64_t ne = c->ne;
   const int32_t L = c->L;
   const int32_t b0 = std::max(0, alpha - c->max_lag);
@@ -312,6 +358,7 @@ static tdbem_status step_async(tdbem_ctx* c, bool have_V = false) {
   s = tdbem_solve_z0(c, c->alpha, nullptr);
   c->prof_end(2, e);
   if (s) return s;
+  if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_after_solve(c, c->alpha))) return s;
   c->alpha++;
   return TDBEM_OK;
 }
@@ -326,6 +373,7 @@ tdbem_status tdbem_step(tdbem_ctx* c, double* J_out, int32_t* iters) {
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (iters) *iters = h[0];
   c->total_iters += h[0];
+  if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
   if (!h[1]) {
     c->set_error("step: Z0 solve missed the tolerance");
     return TDBEM_ENOCONV;
@@ -344,6 +392,7 @@ tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t*
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (iters) *iters = h[0];
   c->total_iters += h[0];
+  if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
   if (!h[1]) {
     c->set_error("step: Z0 solve missed the tolerance");
     return TDBEM_ENOCONV;
@@ -378,6 +427,10 @@ tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int
 }
 
 static tdbem_status check_misses(tdbem_ctx* c) {
+  if (c->p.mode == TDBEM_FAST) {
+    tdbem_status s = tdbem_fast_check(c);
+    if (s) return s;
+  }
   int32_t h[4];
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -418,6 +471,10 @@ tdbem_status tdbem_reset(tdbem_ctx* c) {
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, c->ne * (int64_t)c->L * sizeof(double), c->stream));
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, c->ne * sizeof(double), c->stream));
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
+  if (c->p.mode == TDBEM_FAST) {
+    tdbem_status s = tdbem_fast_reset(c);
+    if (s) return s;
+  }
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->alpha = 1;
   c->total_iters = 0;
@@ -441,6 +498,7 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->setup_seconds = c->setup_seconds;
   info->total_solver_iters = c->total_iters;
   info->solver_cluster = c->cluster;
+  if (c->p.mode == TDBEM_FAST) tdbem_fast_info(c, info);
   return TDBEM_OK;
 }
 

@@ -258,6 +258,49 @@ __global__ void __launch_bounds__(128) k_assemble(TriGeom g, Phys ph, int64_t nt
 
 template __global__ void k_assemble<DirectSink>(TriGeom, Phys, int64_t, const int2*, int64_t, DirectSink, int32_t*);
 
+// Sink of a sparse edge-pair store: CSR over test edges i, sorted source edges j.
+struct CsrSink {
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int16_t* m_lo;
+  const uint8_t* nlag;
+  const int64_t* off;
+  double* val;
+  __device__ __forceinline__ double* slot(int i, int j, int m) const {
+    int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
+    while (lo <= hi) {
+      int64_t mid = (lo + hi) >> 1;
+      int c = col[mid];
+      if (c == j) {
+        int w = m - m_lo[mid];
+        if (w < 0 || w >= nlag[mid]) return nullptr;
+        return val + off[mid] + w;
+      }
+      if (c < j) lo = mid + 1; else hi = mid - 1;
+    }
+    return nullptr;
+  }
+};
+
+template __global__ void k_assemble<CsrSink>(TriGeom, Phys, int64_t, const int2*, int64_t, CsrSink, int32_t*);
+
+// windows of the listed edge pairs (CSR entries)
+__global__ void k_csr_windows(TriGeom g, const int32_t* et, const int64_t* row_ptr, const int32_t* col, int64_t ne,
+                              double a, int16_t* m_lo, uint8_t* nlag, int32_t* err) {
+  int64_t i = blockIdx.x;
+  if (i >= ne) return;
+  for (int64_t p = row_ptr[i] + threadIdx.x; p < row_ptr[i + 1]; p += blockDim.x) {
+    int lo, n;
+    edge_pair_window(g, et, (int)i, col[p], a, &lo, &n);
+    if (n > 255 || lo > 32767) {
+      atomicExch(err, 1);
+      n = 0;
+    }
+    m_lo[p] = (int16_t)lo;
+    nlag[p] = (uint8_t)n;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Incident right-hand side V_i^{alpha-1} (eq. v_i) for a modulated Gaussian
 // plane wave; one thread per edge, 2 triangles x 7 points, FP64.
@@ -435,5 +478,49 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
   k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
                                                            alpha, V, c->d_R);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// Assemble the listed (test triangle, source triangle) pairs into a CSR store
+// of edge pairs (the near field of fast mode).  row_ptr/col must already hold
+// every edge pair touched by the listed triangle pairs.
+tdbem_status tdbem_assemble_csr(tdbem_ctx* c, const int2* d_pairs, int64_t npairs, const int64_t* d_row_ptr,
+                                const int32_t* d_col, int64_t nnz, int16_t** m_lo, uint8_t** nlag, int64_t** off,
+                                double** val, int64_t* nval) {
+  tdbem_status s;
+  int32_t* d_err = nullptr;
+  if ((s = c->dalloc(m_lo, nnz)) || (s = c->dalloc(nlag, nnz)) || (s = c->dalloc(off, nnz)) ||
+      (s = c->dalloc(&d_err, 1)))
+    return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_err, 0, sizeof(int32_t), c->stream));
+  k_csr_windows<<<(unsigned)c->ne, 128, 0, c->stream>>>(c->tg, c->d_et, d_row_ptr, d_col, c->ne, c->phys.a, *m_lo,
+                                                        *nlag, d_err);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  std::vector<uint8_t> hn(nnz);
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(hn.data(), *nlag, nnz, cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<int64_t> ho(nnz);
+  int64_t acc = 0;
+  for (int64_t p = 0; p < nnz; ++p) {
+    ho[p] = acc;
+    acc += hn[p];
+  }
+  *nval = acc;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(*off, ho.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  if ((s = c->dalloc(val, acc))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(*val, 0, acc * sizeof(double), c->stream));
+  CsrSink sink{d_row_ptr, d_col, *m_lo, *nlag, *off, *val};
+  if (npairs > 0) {
+    k_assemble<CsrSink><<<(unsigned)((npairs + 127) / 128), 128, 0, c->stream>>>(c->tg, c->phys, c->nt, d_pairs,
+                                                                                npairs, sink, d_err);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
+  int32_t herr = 0;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) {
+    c->set_error("near field: assembly failed, code " + std::to_string(herr));
+    return TDBEM_EINVAL;
+  }
   return TDBEM_OK;
 }

@@ -1,0 +1,1202 @@
+// fmm.cu -- fast mode: near field directly, far field by the space-time
+// interpolation-based FMM (paper section 3).
+//
+// Clusters.  An adaptive octree over the triangle centroids (section 3.4.1,
+// with triangles as the particles: each triangle carries the parts of its
+// three RWG functions).  A cell is split while it holds more than n_leaf
+// edges (1.5 per triangle) and while its children's time intervals can still
+// hold d+1 = 3 steps (see below).  Cells at level l have size ds_l; the
+// interpolation box of a cell is its cube enlarged by delta = max distance
+// from a triangle centroid to its vertices, so that every quadrature point of
+// its triangles lies inside: half-width H_l = ds_l/2 + delta.
+//
+// Time intervals (eq. Mt).  M_l steps per interval at level l, M_l = 2 M_{l+1}.
+// Causality of one interval requires M_l c dt <= (smallest distance between
+// two non-adjacent boxes) = ds_l - 2 delta, hence
+//     M_lmax = floor((ds_lmax - 2 delta) / (c dt)),
+// with EBREAKDOWN (Remark 1) when it is below d+1 (the window truncation below
+// needs one interval to contain the d+1 first steps of a window).
+//
+// Far field (section 3.3).  With Jh^gamma = sum_k w^k J^{gamma-k} (eq. hat_J)
+// the far interaction of a source cluster (S, J_k) with a target cluster
+// (O, I_{k+q}) uses the truncated-power kernel U^2 of eq. U, interpolated in
+// all eight variables on Chebyshev nodes (first kind):
+//   K_phi = (c(t-s) - r)_+^2 / (r (c dt)^2)              (phi and P terms)
+//   K_A   = d/dt K_phi = 2c (c(t-s) - r)_+ / (r (c dt)^2)  (A term, the second
+//           time derivative goes on the target interpolant, eq. ddotA_fmm)
+// Seven moment components: A (3, kernel K_A), phi (1) and mag (3) (kernel
+// K_phi), eqs. ddotA_M, dotphi_fmm, P_fmm.
+//
+// Window truncation (exact; derived from Appendix A).  The far field of a
+// target interval k' sums the sources of intervals k'-q_hi .. k'-1 only, with
+// the Jh of the first 3 steps of interval k'-q_hi truncated at that interval's
+// start: then sum_{gamma >= G} Jh_G^gamma U(...) = sum_{beta >= G} J^beta N(...)
+// exactly, and every older current contributes N(tau) = 0 provided
+// q_hi M_l >= 1 + r_max/(c dt).  Each source cluster therefore keeps a full and
+// a truncated moment set; the truncated one serves q = q_hi of each pair.
+//
+// M2L operators are translation invariant and, since r depends only on |x-y|
+// and the Chebyshev nodes are symmetric, invariant under the 48 symmetries of
+// the cube: 16 canonical offsets (0 <= c1 <= c2 <= c3, c3 in {2, 3}) per level
+// and lag q, applied to pairs through node-index maps.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace tdbem {
+
+constexpr int kNC = 7;  // moment components: A x,y,z | phi | mag x,y,z
+
+struct FmmLevel {
+  int l = 0, ncell = 0, M = 0, Q = 0;
+  double ds = 0, H = 0;
+  std::vector<double> cen;        // host [ncell][3]
+  std::vector<int> parent, leaf, tri_b, tri_e, icoord;  // icoord [ncell][3]
+  std::vector<int> child;         // [ncell][8]
+  // device
+  double* d_cen = nullptr;
+  int32_t* d_child = nullptr;     // [ncell][8]
+  int32_t* d_leaf_cells = nullptr;  // leaf cell ids at this level
+  int32_t* d_nonleaf_cells = nullptr;
+  int nleaf = 0, nnonleaf = 0;
+  int32_t* d_tri_b = nullptr;
+  int32_t* d_tri_e = nullptr;
+  float* mom = nullptr;           // [ncell][2 slot][2 var][kNC][P]
+  float* loc = nullptr;           // [ncell][Q][kNC][P]
+  // M2L
+  int npairs = 0;
+  int32_t* d_pO = nullptr;
+  int32_t* d_pS = nullptr;
+  int16_t* d_psym = nullptr;
+  float* ops = nullptr;           // [nop][2][P][P]
+  int nop = 0;
+  int4* d_gemm = nullptr;         // {op index, pair base, npairs, kind | q << 8 | qhi << 16}
+  int ngemm = 0;
+  int4* d_tiles = nullptr;        // {gemm, row tile, col tile, 0}: 64 x 64 tiles (CUDA cores)
+  int ntiles = 0;
+  int4* d_tiles_tc = nullptr;     // 128 x 128 tiles (tensor cores)
+  int ntiles_tc = 0;
+  double flops_event = 0;         // M2L flops of one gating event
+  // time tables: source/target factors for offsets i = 0..M-1
+  float* d_tsrc = nullptr;        // [M][pt]  l_n(s_i)
+  float* d_ttgt = nullptr;        // [M][3][pt]  l_m, l_m'/h_t, l_m'/h_t + zeta l_m
+};
+
+struct FmmPlan {
+  int p = 4, pt = 4, PS = 64, P = 256;
+  int lmax = 0, lfar = 2;  // far field at levels lfar..lmax
+  double delta = 0, root[3] = {0, 0, 0}, D = 0;
+  std::vector<FmmLevel> lev;
+  int32_t* d_perm = nullptr;      // triangles in cell order
+  float* d_W = nullptr;           // [nt][3][kNC][PS] P2M tables
+  float* d_T = nullptr;           // [nt][3][kNC][PS] L2P tables
+  int16_t* d_smap = nullptr;      // [48][PS] inverse node maps
+  float* d_Sx = nullptr;          // per level pair (l -> l+1): [lev][2][p][p]
+  float* d_St = nullptr;          // [2][pt][pt] (the same at every level)
+  // near field (CSR over test edges)
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  int16_t* d_mlo = nullptr;
+  uint8_t* d_nlag = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_val64 = nullptr;
+  float* d_val32 = nullptr;
+  int64_t nnz = 0, nval = 0, n_near_tri_pairs = 0;
+  // far right-hand sides (targets ahead of the current step)
+  int Lr = 0;
+  double* d_Rfar = nullptr;       // [Lr][ne]
+  int32_t* d_err = nullptr;       // bounded-wait timeouts of the tensor-core M2L
+  // second far state for history_eval
+  std::vector<float*> mom_eval, loc_eval;
+  double* d_Rfar_eval = nullptr;
+  int32_t max_near_lag = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Lagrange polynomials on Chebyshev nodes of the first kind
+__host__ __device__ inline double cheb_node(int a, int p) { return cos((2.0 * a + 1.0) * 3.14159265358979323846 / (2.0 * p)); }
+
+__host__ __device__ inline void lagrange(int p, double x, double* l, double* dl) {
+  double w[8];
+  for (int a = 0; a < p; ++a) w[a] = cheb_node(a, p);
+  for (int a = 0; a < p; ++a) {
+    double v = 1.0, dv = 0.0;
+    for (int b = 0; b < p; ++b) {
+      if (b == a) continue;
+      double f = 1.0 / (w[a] - w[b]);
+      dv = dv * (x - w[b]) * f + v * f;
+      v *= (x - w[b]) * f;
+    }
+    l[a] = v;
+    if (dl) dl[a] = dv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup kernels
+
+// P2M table W[t][k][c][b] (exact collapsed-Gauss source rule, nq points) and
+// L2P table T[t][k][c][a] (the 7-point outer rule), relative to the leaf box
+// of each triangle.
+__global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* box /*[nt][4] centre, H*/,
+                             const double* qu, const double* qwt, int nq1, float* W, float* T) {
+  int t = blockIdx.x;
+  if (t >= nt) return;
+  const int PS = p * p * p;
+  const double* v = g.v + 9 * t;
+  const double cx = box[4 * t], cy = box[4 * t + 1], cz = box[4 * t + 2], H = box[4 * t + 3];
+  const double A = g.area[t];
+  const double PI = 3.14159265358979323846;
+  double nin[3] = {-g.nrm[3 * t], -g.nrm[3 * t + 1], -g.nrm[3 * t + 2]};
+  for (int e = threadIdx.x; e < 3 * PS; e += blockDim.x) {
+    int k = e / PS, b = e % PS;
+    int b1 = b / (p * p), b2 = (b / p) % p, b3 = b % p;
+    double sg = g.sgn[3 * t + k], l = g.elen[3 * t + k];
+    double cf = sg * l / (2 * A), dv = sg * l / A;
+    const double* o = g.opp + 9 * t + 3 * k;
+    double w[kNC] = {0, 0, 0, 0, 0, 0, 0};
+    // source side: exact integral of f_j l_b, div f_j l_b, f_j x grad l_b
+    for (int iu = 0; iu < nq1; ++iu)
+      for (int iv = 0; iv < nq1; ++iv) {
+        double u = qu[iu], vv = qu[iv];
+        double l0 = u, l1 = (1 - u) * vv, l2 = (1 - u) * (1 - vv);
+        double wt = 2 * A * (1 - u) * qwt[iu] * qwt[iv];
+        double y[3];
+        for (int q = 0; q < 3; ++q) y[q] = l0 * v[q] + l1 * v[3 + q] + l2 * v[6 + q];
+        double L1[8], D1[8], L2[8], D2[8], L3[8], D3[8];
+        lagrange(p, (y[0] - cx) / H, L1, D1);
+        lagrange(p, (y[1] - cy) / H, L2, D2);
+        lagrange(p, (y[2] - cz) / H, L3, D3);
+        double lb = L1[b1] * L2[b2] * L3[b3];
+        double gr[3] = {D1[b1] * L2[b2] * L3[b3] / H, L1[b1] * D2[b2] * L3[b3] / H, L1[b1] * L2[b2] * D3[b3] / H};
+        double f[3] = {cf * (y[0] - o[0]), cf * (y[1] - o[1]), cf * (y[2] - o[2])};
+        w[0] += wt * f[0] * lb;
+        w[1] += wt * f[1] * lb;
+        w[2] += wt * f[2] * lb;
+        w[3] += wt * dv * lb;
+        w[4] += wt * (f[1] * gr[2] - f[2] * gr[1]);
+        w[5] += wt * (f[2] * gr[0] - f[0] * gr[2]);
+        w[6] += wt * (f[0] * gr[1] - f[1] * gr[0]);
+      }
+    // target side: 7-point rule, constants of eq. z_ij folded in
+    double tv[kNC] = {0, 0, 0, 0, 0, 0, 0};
+    const double kA = ph.mu / (4 * PI), kphi = 1.0 / (4 * PI * ph.eps), kP = ph.theta * ph.eta / (4 * PI);
+    for (int q = 0; q < kNq; ++q) {
+      double x[3];
+      for (int u = 0; u < 3; ++u) x[u] = ph.qb[q][0] * v[u] + ph.qb[q][1] * v[3 + u] + ph.qb[q][2] * v[6 + u];
+      double wq = ph.qw[q] * A;
+      double L1[8], L2[8], L3[8];
+      lagrange(p, (x[0] - cx) / H, L1, nullptr);
+      lagrange(p, (x[1] - cy) / H, L2, nullptr);
+      lagrange(p, (x[2] - cz) / H, L3, nullptr);
+      double la = L1[b1] * L2[b2] * L3[b3];
+      double f[3] = {cf * (x[0] - o[0]), cf * (x[1] - o[1]), cf * (x[2] - o[2])};
+      double fxn[3] = {f[1] * nin[2] - f[2] * nin[1], f[2] * nin[0] - f[0] * nin[2], f[0] * nin[1] - f[1] * nin[0]};
+      tv[0] += wq * kA * f[0] * la;
+      tv[1] += wq * kA * f[1] * la;
+      tv[2] += wq * kA * f[2] * la;
+      tv[3] += wq * kphi * dv * la;
+      tv[4] += wq * kP * fxn[0] * la;
+      tv[5] += wq * kP * fxn[1] * la;
+      tv[6] += wq * kP * fxn[2] * la;
+    }
+    for (int c = 0; c < kNC; ++c) {
+      W[(((int64_t)t * 3 + k) * kNC + c) * PS + b] = (float)w[c];
+      T[(((int64_t)t * 3 + k) * kNC + c) * PS + b] = (float)tv[c];
+    }
+  }
+}
+
+// M2L operators of one level: for canonical offset cv[op] and lag qv[op],
+// ops[op][kind][(a,m)][(b,n)], kind 0 = K_A, 1 = K_phi.
+__global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, double dt, double cc, double a,
+                          const int4* opdesc /* {c1,c2,c3,q} */, int nop, float* ops) {
+  const int PS = p * p * p, P = PS * pt;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)nop * P * P;
+  if (e >= total) return;
+  int op = (int)(e / ((int64_t)P * P));
+  int rc = (int)(e % ((int64_t)P * P));
+  int row = rc / P, col = rc % P;
+  int4 d = opdesc[op];
+  int aa = row / pt, m = row % pt, bb = col / pt, n = col % pt;
+  int ai[3] = {aa / (p * p), (aa / p) % p, aa % p}, bi[3] = {bb / (p * p), (bb / p) % p, bb % p};
+  int cv[3] = {d.x, d.y, d.z};
+  double r2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    double dx = cv[k] * ds + H * (cheb_node(ai[k], p) - cheb_node(bi[k], p));
+    r2 += dx * dx;
+  }
+  double r = sqrt(r2);
+  double tau = (d.w * M + 1) * dt + ht * (cheb_node(m, pt) - cheb_node(n, pt));
+  double u = cc * tau - r;
+  double kphi = 0.0, kA = 0.0;
+  if (u > 0.0) {
+    kphi = u * u / (r * a * a);
+    kA = 2.0 * cc * u / (r * a * a);
+  }
+  ops[((int64_t)op * 2 + 0) * P * P + rc] = (float)kA;
+  ops[((int64_t)op * 2 + 1) * P * P + rc] = (float)kphi;
+}
+
+// ---------------------------------------------------------------------------
+// Event kernels
+
+// P2M at the leaves of one level for source interval k: one block per leaf.
+// jh over the interval's M steps (full and truncated at the interval start),
+// contracted with the time factors, then with the W table.
+__global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
+                      const TriGeom g, const float* W, const float* tsrc, const double* ring, int L, int p, int pt,
+                      int M, int k, float* mom) {
+  extern __shared__ float sm[];
+  const int PS = p * p * p, P = PS * pt;
+  int cell = leaf_cells[blockIdx.x];
+  int tb = tri_b[cell], te_ = tri_e[cell];
+  int ntk = 3 * (te_ - tb);
+  float* jt = sm;  // [ntk][2][pt]
+  const double w4[4] = {0.5, -1.5, 1.5, -0.5};
+  const int G = k * M;
+  for (int e = threadIdx.x; e < ntk; e += blockDim.x) {
+    int t = perm[tb + e / 3], kk = e % 3;
+    int j = g.edge[3 * t + kk];
+    const double* Jr = ring + (int64_t)j * L;
+    double acc[2][8];
+    for (int v = 0; v < 2; ++v)
+      for (int n = 0; n < pt; ++n) acc[v][n] = 0.0;
+    for (int i = 0; i < M; ++i) {
+      int gam = G + i;
+      double full = 0.0, trunc = 0.0;
+      for (int kap = 0; kap <= 3; ++kap) {
+        int b = gam - kap;
+        if (b < 0) continue;
+        double jv = w4[kap] * Jr[b & (L - 1)];
+        full += jv;
+        if (kap <= i) trunc += jv;
+      }
+      for (int n = 0; n < pt; ++n) {
+        acc[0][n] += full * tsrc[i * pt + n];
+        acc[1][n] += trunc * tsrc[i * pt + n];
+      }
+    }
+    for (int v = 0; v < 2; ++v)
+      for (int n = 0; n < pt; ++n) jt[(e * 2 + v) * pt + n] = (float)acc[v][n];
+  }
+  __syncthreads();
+  float* out = mom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
+  for (int e = threadIdx.x; e < kNC * PS; e += blockDim.x) {
+    int c = e / PS, b = e % PS;
+    float a0[8], a1[8];
+    for (int n = 0; n < pt; ++n) a0[n] = a1[n] = 0.f;
+    for (int q = 0; q < ntk; ++q) {
+      int t = perm[tb + q / 3], kk = q % 3;
+      float wv = W[(((int64_t)t * 3 + kk) * kNC + c) * PS + b];
+      for (int n = 0; n < pt; ++n) {
+        a0[n] += wv * jt[(q * 2 + 0) * pt + n];
+        a1[n] += wv * jt[(q * 2 + 1) * pt + n];
+      }
+    }
+    for (int n = 0; n < pt; ++n) {
+      out[(0 * kNC + c) * P + b * pt + n] = a0[n];
+      out[(1 * kNC + c) * P + b * pt + n] = a1[n];
+    }
+  }
+}
+
+// M2M: parent moments of source interval k from the children's intervals 2k
+// (slot 0) and 2k+1 (slot 1); the truncated parent set takes the truncated
+// set of child interval 2k and the full set of 2k+1.
+__global__ void k_m2m(const int32_t* cells, const int32_t* child, const float* Sx /*[2][p][p]*/, const float* St,
+                      int p, int pt, int k, const float* cmom, float* pmom) {
+  const int PS = p * p * p, P = PS * pt;
+  int cell = cells[blockIdx.x];
+  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
+  for (int e = threadIdx.x; e < 2 * kNC * P; e += blockDim.x) {
+    int var = e / (kNC * P), r = e % (kNC * P);
+    int c = r / P, bn = r % P;
+    int b = bn / pt, n = bn % pt;
+    int b1 = b / (p * p), b2 = (b / p) % p, b3 = b % p;
+    float s = 0.f;
+    for (int o = 0; o < 8; ++o) {
+      int ch = child[cell * 8 + o];
+      if (ch < 0) continue;
+      int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
+      for (int h = 0; h < 2; ++h) {
+        int cvar = (var == 1 && h == 0) ? 1 : 0;
+        const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * kNC * P + ((int64_t)cvar * kNC + c) * P;
+        for (int n2 = 0; n2 < pt; ++n2) {
+          float tt = St[(h * pt + n) * pt + n2];
+          if (tt == 0.f) continue;
+          for (int c1 = 0; c1 < p; ++c1) {
+            float f1 = Sx[(sx * p + b1) * p + c1] * tt;
+            for (int c2 = 0; c2 < p; ++c2) {
+              float f2 = f1 * Sx[(sy * p + b2) * p + c2];
+              const float* s3 = src + ((c1 * p + c2) * p) * pt + n2;
+              for (int c3 = 0; c3 < p; ++c3) s += f2 * Sx[(sz * p + b3) * p + c3] * s3[c3 * pt];
+            }
+          }
+        }
+      }
+    }
+    out[(int64_t)var * kNC * P + c * P + bn] = s;
+  }
+}
+
+// M2L as a batch of dense GEMMs on CUDA cores (FP32): for every (canonical
+// offset, lag q, kernel kind) the operator (P x P) multiplies the gathered
+// moments of all pairs of that offset class; results are added to the target
+// local coefficients of interval k+q.  Tile 64 x 64, 256 threads, 4 x 4 each.
+__global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* tiles, const float* ops, int P, int pt,
+                                                  int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
+                                                  const int16_t* smap, const float* mom, int k, float* loc, int Q) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  int4 tl = tiles[blockIdx.x];
+  int4 gd = gemm[tl.x];
+  const int kind = gd.w & 0xff, q = (gd.w >> 8) & 0xff, qhi = (gd.w >> 16) & 0xff;
+  const int nk = kind == 0 ? 3 : 4, c0 = kind == 0 ? 0 : 3;
+  const int var = (q == qhi) ? 1 : 0;
+  const float* A = ops + ((int64_t)gd.x * 2 + (kind == 0 ? 0 : 1)) * P * P;
+  const int row0 = tl.y * 64, col0 = tl.z * 64;
+  const int ncol = gd.z * nk;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  // column descriptors of this thread's B loads (column = threadIdx.x & 63)
+  int lc = threadIdx.x & 63;
+  int gcol = col0 + lc;
+  const float* bsrc = nullptr;
+  const int16_t* bmap = nullptr;
+  if (gcol < ncol) {
+    int pr = gd.y + gcol / nk, c = c0 + gcol % nk;
+    bsrc = mom + ((int64_t)pS[pr] * 2 + (k & 1)) * 2 * kNC * P + ((int64_t)var * kNC + c) * P;
+    bmap = smap + (int64_t)psym[pr] * PS;
+  }
+  for (int k0 = 0; k0 < P; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      int rr = e / 16, kk = e % 16;
+      As[kk][rr] = (row0 + rr < P && k0 + kk < P) ? A[(int64_t)(row0 + rr) * P + k0 + kk] : 0.f;
+    }
+    for (int kk = threadIdx.x >> 6; kk < 16; kk += 4) {
+      float v = 0.f;
+      if (bsrc && k0 + kk < P) {
+        int kidx = k0 + kk;
+        int bp = kidx / pt, n = kidx % pt;
+        v = bsrc[bmap[bp] * pt + n];
+      }
+      Bs[kk][lc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < 4; ++j) {
+    int gc = col0 + tx * 4 + j;
+    if (gc >= ncol) continue;
+    int pr = gd.y + gc / nk, c = c0 + gc % nk;
+    const int16_t* map = smap + (int64_t)psym[pr] * PS;
+    float* dst = loc + ((int64_t)pO[pr] * Q + ((k + q) % Q)) * kNC * P + (int64_t)c * P;
+    for (int i = 0; i < 4; ++i) {
+      int row = row0 + ty * 4 + i;
+      if (row >= P) continue;
+      int ap = row / pt, m = row % pt;
+      atomicAdd(dst + map[ap] * pt + m, acc[i][j]);
+    }
+  }
+}
+
+// L2L: children's local coefficients of intervals 2(k+1), 2(k+1)+1 from the
+// parent's (interval k+1); then the parent slot is cleared.
+__global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
+                      int k, float* ploc, int Qp, float* cloc, int Qc) {
+  const int PS = p * p * p, P = PS * pt;
+  int cell = cells[blockIdx.x];
+  float* src = ploc + ((int64_t)cell * Qp + ((k + 1) % Qp)) * kNC * P;
+  for (int o = 0; o < 8; ++o) {
+    int ch = child[cell * 8 + o];
+    if (ch < 0) continue;
+    int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
+    for (int e = threadIdx.x; e < 2 * kNC * P; e += blockDim.x) {
+      int h = e / (kNC * P), r = e % (kNC * P);
+      int c = r / P, an = r % P;
+      int a = an / pt, m2 = an % pt;
+      int a1 = a / (p * p), a2 = (a / p) % p, a3 = a % p;
+      const float* s = src + (int64_t)c * P;
+      float acc = 0.f;
+      for (int m = 0; m < pt; ++m) {
+        float tt = St[(h * pt + m) * pt + m2];
+        if (tt == 0.f) continue;
+        for (int c1 = 0; c1 < p; ++c1) {
+          float f1 = Sx[(sx * p + c1) * p + a1] * tt;
+          for (int c2 = 0; c2 < p; ++c2) {
+            float f2 = f1 * Sx[(sy * p + c2) * p + a2];
+            const float* s3 = s + ((c1 * p + c2) * p) * pt + m;
+            for (int c3 = 0; c3 < p; ++c3) acc += f2 * Sx[(sz * p + c3) * p + a3] * s3[c3 * pt];
+          }
+        }
+      }
+      int slot = (2 * (k + 1) + h) % Qc;
+      cloc[((int64_t)ch * Qc + slot) * kNC * P + (int64_t)c * P + an] += acc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) src[e] = 0.f;
+}
+
+// L2P at the leaves of one level for target interval k+1: every target step
+// rho of the interval receives -(far history) in the far right-hand side ring;
+// the local-coefficient slot is cleared afterwards.
+__global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
+                      const TriGeom g, const float* T, const float* ttgt, int p, int pt, int M, int k, float* loc,
+                      int Q, double* Rfar, int Lr, int64_t ne) {
+  extern __shared__ float sm[];
+  const int PS = p * p * p, P = PS * pt;
+  int cell = leaf_cells[blockIdx.x];
+  float* L = loc + ((int64_t)cell * Q + ((k + 1) % Q)) * kNC * P;
+  float* Le = sm;  // [M][kNC][PS]
+  for (int e = threadIdx.x; e < M * kNC * PS; e += blockDim.x) {
+    int i = e / (kNC * PS), r = e % (kNC * PS);
+    int c = r / PS, a = r % PS;
+    int kind = (c < 3) ? 1 : (c == 3 ? 0 : 2);  // A: l', phi: l, mag: l' + zeta l
+    float s = 0.f;
+    for (int m = 0; m < pt; ++m) s += L[(int64_t)c * P + a * pt + m] * ttgt[(i * 3 + kind) * pt + m];
+    Le[e] = s;
+  }
+  __syncthreads();
+  int tb = tri_b[cell], te_ = tri_e[cell];
+  int ntk = 3 * (te_ - tb);
+  for (int e = threadIdx.x; e < ntk * M; e += blockDim.x) {
+    int q = e / M, i = e % M;
+    int t = perm[tb + q / 3], kk = q % 3;
+    const float* Tt = T + ((int64_t)t * 3 + kk) * kNC * PS;
+    const float* le = Le + (int64_t)i * kNC * PS;
+    float s = 0.f;
+    for (int r = 0; r < kNC * PS; ++r) s += Tt[r] * le[r];
+    int rho = (k + 1) * M + i;
+    atomicAdd(Rfar + (int64_t)(rho & (Lr - 1)) * ne + g.edge[3 * t + kk], -(double)s);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) L[e] = 0.f;
+}
+
+// Near field + assembled right-hand side:
+// R_i = V_i + Rfar_i - sum_{near j} sum_{m>=2} Zt^(m)_ij J_j^{alpha-m}; FP32
+// coefficients and products, per-lane FP32 partial sums, FP64 row total.
+// One warp per row.  The far slot of this step is cleared.
+__global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, const int32_t* col, const int16_t* m_lo,
+                                                     const uint8_t* nlag, const int64_t* off, const float* val,
+                                                     int64_t ne, const double* ring, int L, int alpha,
+                                                     const double* V, double* Rfar_slot, double* R) {
+  int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= ne) return;
+  float s = 0.f;
+  for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
+    int lo = m_lo[p], n = nlag[p];
+    const float* z = val + off[p];
+    const double* Jr = ring + (int64_t)col[p] * L;
+    for (int w = 0; w < n; ++w) {
+      int m = lo + w, b = alpha - m;
+      if (m < 2 || b < 0) continue;
+      s += __ldg(z + w) * (float)Jr[b & (L - 1)];
+    }
+  }
+  double d = s;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  if (lane == 0) {
+    double far = Rfar_slot ? Rfar_slot[i] : 0.0;
+    R[i] = (V ? V[i] : 0.0) + far - d;
+    if (Rfar_slot) Rfar_slot[i] = 0.0;
+  }
+}
+
+__global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+}  // namespace tdbem
+
+using namespace tdbem;
+
+// ---------------------------------------------------------------------------
+// Host planner
+
+namespace {
+
+struct TreeBuild {
+  const std::vector<double>* cen;
+  std::vector<int>* perm;
+  std::vector<FmmLevel>* lev;
+  double root[3];
+  double D;
+  int lcap;
+  int n_leaf;
+};
+
+void build_cell(TreeBuild& tb, int l, int ix, int iy, int iz, int b, int e, int parent) {
+  std::vector<FmmLevel>& lev = *tb.lev;
+  if ((int)lev.size() <= l) lev.resize(l + 1);
+  FmmLevel& L = lev[l];
+  int id = L.ncell++;
+  double ds = tb.D / (1 << l);
+  L.cen.push_back(tb.root[0] + (ix + 0.5) * ds);
+  L.cen.push_back(tb.root[1] + (iy + 0.5) * ds);
+  L.cen.push_back(tb.root[2] + (iz + 0.5) * ds);
+  L.icoord.push_back(ix);
+  L.icoord.push_back(iy);
+  L.icoord.push_back(iz);
+  L.parent.push_back(parent);
+  L.tri_b.push_back(b);
+  L.tri_e.push_back(e);
+  for (int o = 0; o < 8; ++o) L.child.push_back(-1);
+  bool split = 1.5 * (e - b) > tb.n_leaf && l < tb.lcap;
+  L.leaf.push_back(split ? 0 : 1);
+  if (!split) return;
+  // partition [b, e) into octants
+  std::vector<int>& P = *tb.perm;
+  const std::vector<double>& C = *tb.cen;
+  double mid[3] = {tb.root[0] + (ix + 0.5) * ds, tb.root[1] + (iy + 0.5) * ds, tb.root[2] + (iz + 0.5) * ds};
+  std::vector<int> bucket[8];
+  for (int q = b; q < e; ++q) {
+    int t = P[q];
+    int o = ((C[3 * t] >= mid[0]) << 2) | ((C[3 * t + 1] >= mid[1]) << 1) | (C[3 * t + 2] >= mid[2]);
+    bucket[o].push_back(t);
+  }
+  int pos = b;
+  int starts[8];
+  for (int o = 0; o < 8; ++o) {
+    starts[o] = pos;
+    for (int t : bucket[o]) P[pos++] = t;
+  }
+  for (int o = 0; o < 8; ++o) {
+    if (bucket[o].empty()) continue;
+    int cid = (int)((int)lev.size() > l + 1 ? lev[l + 1].ncell : 0);
+    lev[l].child[8 * id + o] = cid;
+    build_cell(tb, l + 1, 2 * ix + ((o >> 2) & 1), 2 * iy + ((o >> 1) & 1), 2 * iz + (o & 1), starts[o],
+               starts[o] + (int)bucket[o].size(), id);
+  }
+}
+
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  const double PI = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1);
+    x[i] = 0.5 * (z + 1);
+    w[i] = 1.0 / ((1 - z * z) * dp * dp);  // (2/((1-z^2)P'^2)) / 2
+  }
+}
+
+}  // namespace
+
+tdbem_status tdbem_build_fast(tdbem_ctx* c) {
+  FmmPlan* F = new (std::nothrow) FmmPlan();
+  if (!F) return TDBEM_ENOMEM;
+  c->fmm = F;
+  const int p = c->p.p_s, pt = c->p.p_t;
+  F->p = p;
+  F->pt = pt;
+  F->PS = p * p * p;
+  F->P = F->PS * pt;
+  const int PS = F->PS, P = F->P;
+  const int64_t nt = c->nt, ne = c->ne;
+  const double a = c->phys.a;
+  // centroids, delta, root cube
+  std::vector<double> cen(3 * nt);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < c->nv; ++v)
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], c->V[3 * v + q]);
+      hi[q] = std::max(hi[q], c->V[3 * v + q]);
+    }
+  for (int64_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 3; ++q)
+      cen[3 * t + q] = (c->V[3 * c->T[3 * t] + q] + c->V[3 * c->T[3 * t + 1] + q] + c->V[3 * c->T[3 * t + 2] + q]) / 3.0;
+  F->delta = c->max_tri_rad;
+  double D = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2])) * (1 + 1e-9);
+  F->D = D;
+  for (int q = 0; q < 3; ++q) F->root[q] = lo[q];
+  // deepest level whose intervals still hold d+1 steps
+  int lcap = 0;
+  for (int l = 0; l < 30; ++l) {
+    double ds = D / (1 << l);
+    if (std::floor((ds - 2 * F->delta) / a) >= 3) lcap = l;
+  }
+  std::vector<int> perm(nt);
+  std::iota(perm.begin(), perm.end(), 0);
+  TreeBuild tb{&cen, &perm, &F->lev, {lo[0], lo[1], lo[2]}, D, lcap, c->p.n_leaf};
+  build_cell(tb, 0, 0, 0, 0, 0, (int)nt, -1);
+  F->lmax = (int)F->lev.size() - 1;
+  const int lmax = F->lmax;
+  for (int l = 0; l <= lmax; ++l) {
+    F->lev[l].l = l;
+    F->lev[l].ds = D / (1 << l);
+    F->lev[l].H = F->lev[l].ds / 2 + F->delta;
+  }
+  bool far = lmax >= 2;
+  int Mlmax = far ? (int)std::floor((F->lev[lmax].ds - 2 * F->delta) / a) : 0;
+  if (far && Mlmax < 3) {
+    c->set_error("fast: time interval of the finest level holds fewer than d+1 steps");
+    return TDBEM_EBREAKDOWN;
+  }
+  for (int l = 0; l <= lmax; ++l) F->lev[l].M = far ? Mlmax << (lmax - l) : 0;
+  // ---- near triangle pairs and interaction lists
+  std::vector<int2> near;
+  int64_t far_count = 0;
+  std::vector<std::vector<int>> il_pairs(lmax + 1);  // flat (O, S, ox, oy, oz)
+  for (int l = 0; l <= lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    // hash of cells by integer coordinates
+    std::vector<std::pair<long long, int>> key(L.ncell);
+    auto K = [](int x, int y, int z) { return ((long long)x << 42) | ((long long)y << 21) | (long long)z; };
+    for (int i = 0; i < L.ncell; ++i) key[i] = {K(L.icoord[3 * i], L.icoord[3 * i + 1], L.icoord[3 * i + 2]), i};
+    std::sort(key.begin(), key.end());
+    auto find = [&](int x, int y, int z) -> int {
+      if (x < 0 || y < 0 || z < 0) return -1;
+      auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(K(x, y, z), -1));
+      if (it != key.end() && it->first == K(x, y, z)) return it->second;
+      return -1;
+    };
+    for (int O = 0; O < L.ncell; ++O) {
+      int ox = L.icoord[3 * O], oy = L.icoord[3 * O + 1], oz = L.icoord[3 * O + 2];
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            int S = find(ox + dx, oy + dy, oz + dz);
+            if (S < 0 || !(L.leaf[O] || L.leaf[S])) continue;
+            for (int u = L.tri_b[O]; u < L.tri_e[O]; ++u)
+              for (int w = L.tri_b[S]; w < L.tri_e[S]; ++w) near.push_back(make_int2(perm[u], perm[w]));
+          }
+      if (l < 2 || !far) continue;
+      // interaction list: children of the parent's neighbours, not adjacent to O
+      const FmmLevel& Lp = F->lev[l - 1];
+      int par = L.parent[O];
+      int px = Lp.icoord[3 * par], py = Lp.icoord[3 * par + 1], pz = Lp.icoord[3 * par + 2];
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            int PN = -1;
+            // parent-level lookup
+            {
+              int x = px + dx, y = py + dy, z = pz + dz;
+              for (int i = 0; i < Lp.ncell; ++i)
+                if (Lp.icoord[3 * i] == x && Lp.icoord[3 * i + 1] == y && Lp.icoord[3 * i + 2] == z) {
+                  PN = i;
+                  break;
+                }
+            }
+            if (PN < 0) continue;
+            for (int o = 0; o < 8; ++o) {
+              int S = Lp.child[8 * PN + o];
+              if (S < 0) continue;
+              int sx = L.icoord[3 * S] - ox, sy = L.icoord[3 * S + 1] - oy, sz = L.icoord[3 * S + 2] - oz;
+              if (std::abs(sx) <= 1 && std::abs(sy) <= 1 && std::abs(sz) <= 1) continue;
+              il_pairs[l].insert(il_pairs[l].end(), {O, S, sx, sy, sz});
+              far_count += (int64_t)(L.tri_e[O] - L.tri_b[O]) * (L.tri_e[S] - L.tri_b[S]);
+            }
+          }
+    }
+  }
+  if ((int64_t)near.size() + far_count != nt * nt) {
+    c->set_error("fast: near and far triangle pairs do not partition all pairs");
+    return TDBEM_EINVAL;
+  }
+  F->n_near_tri_pairs = (int64_t)near.size();
+  // ---- near edge pairs (CSR over test edges)
+  {
+    std::vector<std::vector<int32_t>> rows(ne);
+    for (const int2& q : near)
+      for (int u = 0; u < 3; ++u)
+        for (int w = 0; w < 3; ++w) rows[c->te[3 * q.x + u]].push_back(c->te[3 * q.y + w]);
+    std::vector<int64_t> rp(ne + 1, 0);
+    for (int64_t i = 0; i < ne; ++i) {
+      std::sort(rows[i].begin(), rows[i].end());
+      rows[i].erase(std::unique(rows[i].begin(), rows[i].end()), rows[i].end());
+      rp[i + 1] = rp[i] + (int64_t)rows[i].size();
+    }
+    F->nnz = rp[ne];
+    std::vector<int32_t> col(F->nnz);
+    for (int64_t i = 0; i < ne; ++i) std::copy(rows[i].begin(), rows[i].end(), col.begin() + rp[i]);
+    tdbem_status s;
+    int2* d_near = nullptr;
+    if ((s = c->dalloc(&F->d_row_ptr, ne + 1)) || (s = c->dalloc(&F->d_col, F->nnz)) ||
+        (s = c->dalloc(&d_near, near.size())))
+      return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_row_ptr, rp.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_col, col.data(), F->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(d_near, near.data(), near.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    s = tdbem_assemble_csr(c, d_near, (int64_t)near.size(), F->d_row_ptr, F->d_col, F->nnz, &F->d_mlo, &F->d_nlag,
+                           &F->d_off, &F->d_val64, &F->nval);
+    if (s) return s;
+    if ((s = c->dalloc(&F->d_val32, F->nval))) return s;
+    k_f64_to_f32<<<(unsigned)((F->nval + 255) / 256), 256, 0, c->stream>>>(F->d_val64, F->d_val32, F->nval);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    // largest near lag (ring length)
+    std::vector<int16_t> ml(F->nnz);
+    std::vector<uint8_t> nl(F->nnz);
+    TDBEM_CUDA_TRY(c, cudaMemcpy(ml.data(), F->d_mlo, F->nnz * sizeof(int16_t), cudaMemcpyDeviceToHost));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(nl.data(), F->d_nlag, F->nnz, cudaMemcpyDeviceToHost));
+    int32_t mx = 0;
+    for (int64_t q = 0; q < F->nnz; ++q) mx = std::max<int32_t>(mx, ml[q] + nl[q] - 1);
+    F->max_near_lag = mx;
+  }
+  c->max_lag = std::max(F->max_near_lag, far ? F->lev[2].M + 4 : 0);
+  tdbem_status s;
+  if ((s = c->dalloc(&F->d_perm, nt))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_perm, perm.data(), nt * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!far) return TDBEM_OK;
+  // ---- per-level device data, time tables, M2L operators and work lists
+  const double dt = c->dt, cc = c->phys.c;
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  std::vector<double> tbox(4 * nt);
+  for (int l = 0; l <= lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    std::vector<int> lc, nlc;
+    for (int i = 0; i < L.ncell; ++i) (L.leaf[i] ? lc : nlc).push_back(i);
+    L.nleaf = (int)lc.size();
+    L.nnonleaf = (int)nlc.size();
+    for (int i : lc)
+      for (int u = L.tri_b[i]; u < L.tri_e[i]; ++u) {
+        int t = perm[u];
+        tbox[4 * t] = L.cen[3 * i];
+        tbox[4 * t + 1] = L.cen[3 * i + 1];
+        tbox[4 * t + 2] = L.cen[3 * i + 2];
+        tbox[4 * t + 3] = L.H;
+      }
+    if (l < 2) continue;
+    if ((s = c->dalloc(&L.d_child, 8 * (int64_t)L.ncell)) || (s = c->dalloc(&L.d_tri_b, L.ncell)) ||
+        (s = c->dalloc(&L.d_tri_e, L.ncell)) || (s = c->dalloc(&L.d_leaf_cells, L.nleaf)) ||
+        (s = c->dalloc(&L.d_nonleaf_cells, L.nnonleaf)))
+      return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_child, L.child.data(), 8 * L.ncell * sizeof(int32_t), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tri_b, L.tri_b.data(), L.ncell * sizeof(int32_t), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tri_e, L.tri_e.data(), L.ncell * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (L.nleaf)
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_leaf_cells, lc.data(), L.nleaf * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (L.nnonleaf)
+      TDBEM_CUDA_TRY(
+          c, cudaMemcpy(L.d_nonleaf_cells, nlc.data(), L.nnonleaf * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // time tables
+    std::vector<float> ts(L.M * pt), tt(L.M * 3 * pt);
+    const double ht = 0.5 * L.M * dt;
+    for (int i = 0; i < L.M; ++i) {
+      double xi = (i - 0.5 * (L.M - 1)) / (0.5 * L.M);
+      double lv[8], dv[8];
+      lagrange(pt, xi, lv, dv);
+      for (int n = 0; n < pt; ++n) {
+        ts[i * pt + n] = (float)lv[n];
+        tt[(i * 3 + 0) * pt + n] = (float)lv[n];
+        tt[(i * 3 + 1) * pt + n] = (float)(dv[n] / ht);
+        tt[(i * 3 + 2) * pt + n] = (float)(dv[n] / ht + c->p.zeta * lv[n]);
+      }
+    }
+    if ((s = c->dalloc(&L.d_tsrc, ts.size())) || (s = c->dalloc(&L.d_ttgt, tt.size()))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tsrc, ts.data(), ts.size() * sizeof(float), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_ttgt, tt.data(), tt.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // interaction pairs grouped by canonical offset
+    struct PairRec {
+      int O, S, canon, sym;
+    };
+    std::vector<PairRec> pr;
+    std::vector<std::array<int, 3>> canons;
+    const std::vector<int>& ip = il_pairs[l];
+    for (size_t q = 0; q < ip.size(); q += 5) {
+      // x - y = (c_O - c_S) + H (w_a - w_b): the symmetry is taken on O - S
+      int o[3] = {-ip[q + 2], -ip[q + 3], -ip[q + 4]};
+      int ab[3] = {std::abs(o[0]), std::abs(o[1]), std::abs(o[2])};
+      int ax[3] = {0, 1, 2};
+      std::sort(ax, ax + 3, [&](int u, int w) { return ab[u] != ab[w] ? ab[u] < ab[w] : u < w; });
+      std::array<int, 3> cv = {ab[ax[0]], ab[ax[1]], ab[ax[2]]};
+      int ci = -1;
+      for (size_t z = 0; z < canons.size(); ++z)
+        if (canons[z] == cv) ci = (int)z;
+      if (ci < 0) {
+        canons.push_back(cv);
+        ci = (int)canons.size() - 1;
+      }
+      // symmetry id: permutation (index of ax among the 6) and signs
+      static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+      int pi = 0;
+      for (int z = 0; z < 6; ++z)
+        if (perms[z][0] == ax[0] && perms[z][1] == ax[1] && perms[z][2] == ax[2]) pi = z;
+      int sg = (o[0] < 0 ? 4 : 0) | (o[1] < 0 ? 2 : 0) | (o[2] < 0 ? 1 : 0);
+      pr.push_back({ip[q], ip[q + 1], ci, pi * 8 + sg});
+    }
+    std::stable_sort(pr.begin(), pr.end(), [](const PairRec& x, const PairRec& y) { return x.canon < y.canon; });
+    L.npairs = (int)pr.size();
+    std::vector<int32_t> hO(L.npairs), hS(L.npairs);
+    std::vector<int16_t> hsym(L.npairs);
+    for (int q = 0; q < L.npairs; ++q) {
+      hO[q] = pr[q].O;
+      hS[q] = pr[q].S;
+      hsym[q] = (int16_t)pr[q].sym;
+    }
+    if ((s = c->dalloc(&L.d_pO, L.npairs)) || (s = c->dalloc(&L.d_pS, L.npairs)) ||
+        (s = c->dalloc(&L.d_psym, L.npairs)))
+      return s;
+    if (L.npairs) {
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_pO, hO.data(), L.npairs * sizeof(int32_t), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_pS, hS.data(), L.npairs * sizeof(int32_t), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_psym, hsym.data(), L.npairs * sizeof(int16_t), cudaMemcpyHostToDevice));
+    }
+    // lag ranges per canonical offset; operators; GEMM and tile lists
+    std::vector<int4> opdesc, gemm, tiles, tiles_tc;
+    int qmax = 1;
+    for (size_t ci = 0; ci < canons.size(); ++ci) {
+      int base = -1, cnt = 0;
+      for (int q = 0; q < L.npairs; ++q)
+        if (pr[q].canon == (int)ci) {
+          if (base < 0) base = q;
+          ++cnt;
+        }
+      const std::array<int, 3>& cv = canons[ci];
+      double rmin2 = 0, rmax2 = 0;
+      for (int k = 0; k < 3; ++k) {
+        double g = std::max(0.0, cv[k] * L.ds - 2 * L.H);
+        rmin2 += g * g;
+        double h = cv[k] * L.ds + 2 * L.H;
+        rmax2 += h * h;
+      }
+      double rmin = std::sqrt(rmin2), rmax = std::sqrt(rmax2);
+      int qlo = std::max(1, (int)std::floor(rmin / (L.M * a)));
+      int qhi = (int)std::ceil((1.0 + rmax / a) / L.M);
+      qmax = std::max(qmax, qhi);
+      for (int q = qlo; q <= qhi; ++q) {
+        int op = (int)opdesc.size();
+        opdesc.push_back(make_int4(cv[0], cv[1], cv[2], q));
+        for (int kind = 0; kind < 2; ++kind) {
+          int g = (int)gemm.size();
+          gemm.push_back(make_int4(op, base, cnt, kind | (q << 8) | (qhi << 16)));
+          int ncol = cnt * (kind == 0 ? 3 : 4);
+          for (int rt = 0; rt < (P + 63) / 64; ++rt)
+            for (int ct = 0; ct < (ncol + 63) / 64; ++ct) tiles.push_back(make_int4(g, rt, ct, 0));
+          for (int rt = 0; rt < (P + 127) / 128; ++rt)
+            for (int ct = 0; ct < (ncol + 127) / 128; ++ct) tiles_tc.push_back(make_int4(g, rt, ct, 0));
+          L.flops_event += 2.0 * P * P * ncol;
+        }
+      }
+    }
+    if (qmax >= 255) {
+      c->set_error("fast: too many time intervals per interaction");
+      return TDBEM_EINVAL;
+    }
+    L.Q = qmax + 1;
+    L.nop = (int)opdesc.size();
+    L.ngemm = (int)gemm.size();
+    L.ntiles = (int)tiles.size();
+    L.ntiles_tc = (int)tiles_tc.size();
+    if ((s = c->dalloc(&L.d_tiles_tc, std::max(1, L.ntiles_tc)))) return s;
+    if (L.ntiles_tc)
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles_tc, tiles_tc.data(), L.ntiles_tc * sizeof(int4), cudaMemcpyHostToDevice));
+    int4* d_opdesc = nullptr;
+    if ((s = c->dalloc(&d_opdesc, std::max(1, L.nop))) || (s = c->dalloc(&L.ops, (int64_t)L.nop * 2 * P * P)) ||
+        (s = c->dalloc(&L.d_gemm, std::max(1, L.ngemm))) || (s = c->dalloc(&L.d_tiles, std::max(1, L.ntiles))))
+      return s;
+    if (L.nop) {
+      TDBEM_CUDA_TRY(c, cudaMemcpy(d_opdesc, opdesc.data(), L.nop * sizeof(int4), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_gemm, gemm.data(), L.ngemm * sizeof(int4), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles, tiles.data(), L.ntiles * sizeof(int4), cudaMemcpyHostToDevice));
+      int64_t tot = (int64_t)L.nop * P * P;
+      k_m2l_ops<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p, pt, L.ds, L.H, 0.5 * L.M * dt, L.M, dt, cc, a,
+                                                                      d_opdesc, L.nop, L.ops);
+      TDBEM_CUDA_TRY(c, cudaGetLastError());
+    }
+    // moment and local-coefficient storage (march state and history_eval state)
+    if ((s = c->dalloc(&L.mom, (int64_t)L.ncell * 4 * kNC * P)) ||
+        (s = c->dalloc(&L.loc, (int64_t)L.ncell * L.Q * kNC * P)))
+      return s;
+    TDBEM_CUDA_TRY(c, cudaMemset(L.mom, 0, (int64_t)L.ncell * 4 * kNC * P * sizeof(float)));
+    TDBEM_CUDA_TRY(c, cudaMemset(L.loc, 0, (int64_t)L.ncell * L.Q * kNC * P * sizeof(float)));
+    float *me = nullptr, *le = nullptr;
+    if ((s = c->dalloc(&me, (int64_t)L.ncell * 4 * kNC * P)) || (s = c->dalloc(&le, (int64_t)L.ncell * L.Q * kNC * P)))
+      return s;
+    F->mom_eval.push_back(me);
+    F->loc_eval.push_back(le);
+  }
+  // interpolation matrices between levels (space: child node -> parent
+  // polynomial, per octant sign; time: the same at every level)
+  {
+    std::vector<float> Sx((lmax + 1) * 2 * p * p, 0.f), St(2 * pt * pt);
+    for (int l = 0; l < lmax; ++l) {
+      double Hp = F->lev[l].H, Hc = F->lev[l + 1].H, dsp = F->lev[l].ds;
+      for (int sgn = 0; sgn < 2; ++sgn)
+        for (int cb = 0; cb < p; ++cb) {
+          double xi = ((sgn ? 0.25 : -0.25) * dsp + Hc * cheb_node(cb, p)) / Hp;
+          double lv[8];
+          lagrange(p, xi, lv, nullptr);
+          for (int b = 0; b < p; ++b) Sx[((l * 2 + sgn) * p + b) * p + cb] = (float)lv[b];
+        }
+    }
+    for (int h = 0; h < 2; ++h)
+      for (int cn = 0; cn < pt; ++cn) {
+        double xi = 0.5 * cheb_node(cn, pt) + (h ? 0.5 : -0.5);
+        double lv[8];
+        lagrange(pt, xi, lv, nullptr);
+        for (int n = 0; n < pt; ++n) St[(h * pt + n) * pt + cn] = (float)lv[n];
+      }
+    if ((s = c->dalloc(&F->d_Sx, Sx.size())) || (s = c->dalloc(&F->d_St, St.size()))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_Sx, Sx.data(), Sx.size() * sizeof(float), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_St, St.data(), St.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  // symmetry maps: for symmetry (perm pi, signs sg), canonical node index a'
+  // -> original node index a (a'_k = a~_{i_k}, a~_i = a_i or p-1-a_i)
+  {
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    std::vector<int16_t> sm(48 * PS);
+    for (int pi = 0; pi < 6; ++pi)
+      for (int sg = 0; sg < 8; ++sg)
+        for (int ap = 0; ap < PS; ++ap) {
+          int acan[3] = {ap / (p * p), (ap / p) % p, ap % p};
+          int aorig[3];
+          for (int k = 0; k < 3; ++k) {
+            int i = perms[pi][k];
+            int v = acan[k];
+            bool flip = (sg >> (2 - i)) & 1;
+            aorig[i] = flip ? p - 1 - v : v;
+          }
+          sm[(pi * 8 + sg) * PS + ap] = (int16_t)((aorig[0] * p + aorig[1]) * p + aorig[2]);
+        }
+    if ((s = c->dalloc(&F->d_smap, sm.size()))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_smap, sm.data(), sm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+  }
+  // P2M / L2P tables
+  {
+    int nq1 = std::max(6, (3 * p + 1) / 2 + 1);
+    std::vector<double> qx, qw;
+    gauss_legendre01(nq1, qx, qw);
+    double *d_box = nullptr, *d_qx = nullptr, *d_qw = nullptr;
+    if ((s = c->dalloc(&d_box, 4 * nt)) || (s = c->dalloc(&d_qx, nq1)) || (s = c->dalloc(&d_qw, nq1)) ||
+        (s = c->dalloc(&F->d_W, nt * 3 * kNC * PS)) || (s = c->dalloc(&F->d_T, nt * 3 * kNC * PS)))
+      return s;
+    TDBEM_CUDA_TRY(c, cudaMemcpy(d_box, tbox.data(), 4 * nt * sizeof(double), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(d_qx, qx.data(), nq1 * sizeof(double), cudaMemcpyHostToDevice));
+    TDBEM_CUDA_TRY(c, cudaMemcpy(d_qw, qw.data(), nq1 * sizeof(double), cudaMemcpyHostToDevice));
+    k_far_tables<<<(unsigned)nt, 256, 0, c->stream>>>(c->tg, c->phys, p, (int)nt, d_box, d_qx, d_qw, nq1, F->d_W,
+                                                       F->d_T);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
+  // far right-hand-side rings
+  int Mmax = F->lev[2].M;
+  int Lr = 8;
+  while (Lr < 2 * Mmax) Lr <<= 1;
+  F->Lr = Lr;
+  if ((s = c->dalloc(&F->d_Rfar, (int64_t)Lr * ne)) || (s = c->dalloc(&F->d_Rfar_eval, (int64_t)Lr * ne)) ||
+      (s = c->dalloc(&F->d_err, 1)))
+    return s;
+  TDBEM_CUDA_TRY(c, cudaMemset(F->d_err, 0, sizeof(int32_t)));
+  TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, (int64_t)Lr * ne * sizeof(double)));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return TDBEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Step pieces
+
+static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, bool eval) {
+  FmmPlan* F = c->fmm;
+  if (!F || F->lmax < 2) return TDBEM_OK;
+  const int p = F->p, pt = F->pt, PS = F->PS, P = F->P, lmax = F->lmax;
+  auto MOM = [&](int l) { return eval ? F->mom_eval[l - 2] : F->lev[l].mom; };
+  auto LOC = [&](int l) { return eval ? F->loc_eval[l - 2] : F->lev[l].loc; };
+  double* Rfar = eval ? F->d_Rfar_eval : F->d_Rfar;
+  // upward pass
+  for (int l = lmax; l >= 2; --l) {
+    FmmLevel& L = F->lev[l];
+    if (alpha % L.M) continue;
+    int k = alpha / L.M - 1;
+    if (L.nleaf) {
+      int maxtri = 0;
+      for (int i = 0; i < L.ncell; ++i)
+        if (L.leaf[i]) maxtri = std::max(maxtri, L.tri_e[i] - L.tri_b[i]);
+      size_t smem = (size_t)3 * maxtri * 2 * pt * sizeof(float);
+      cudaEvent_t e = c->prof_begin(3);
+      k_p2m<<<L.nleaf, 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg, F->d_W,
+                                                L.d_tsrc, ring, c->L, p, pt, L.M, k, MOM(l));
+      c->prof_end(3, e);
+      TDBEM_CUDA_TRY(c, cudaGetLastError());
+    }
+    if (L.nnonleaf && l < lmax) {
+      cudaEvent_t e = c->prof_begin(4);
+      k_m2m<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St,
+                                                p, pt, k, MOM(l + 1), MOM(l));
+      c->prof_end(4, e);
+      TDBEM_CUDA_TRY(c, cudaGetLastError());
+    }
+  }
+  // downward pass
+  for (int l = 2; l <= lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    if (alpha % L.M) continue;
+    int k = alpha / L.M - 1;
+    if (L.ntiles) {
+      cudaEvent_t e = c->prof_begin(5);
+      if (c->p.m2l_prec == TDBEM_P_FP32) {
+        k_m2l_fp32<<<L.ntiles, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
+                                                     F->d_smap, MOM(l), k, LOC(l), L.Q);
+        TDBEM_CUDA_TRY(c, cudaGetLastError());
+      } else {
+        tdbem_status s = tdbem_m2l_tc(c, L.d_gemm, L.d_tiles_tc, L.ntiles_tc, L.ops, P, pt, PS, L.d_pO, L.d_pS,
+                                      L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, c->p.m2l_prec, F->d_err);
+        if (s) return s;
+      }
+      c->prof_end(5, e);
+    }
+    if (L.nnonleaf && l < lmax) {
+      cudaEvent_t e = c->prof_begin(6);
+      k_l2l<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St,
+                                                p, pt, k, LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q);
+      c->prof_end(6, e);
+      TDBEM_CUDA_TRY(c, cudaGetLastError());
+    }
+    if (L.nleaf) {
+      size_t smem = (size_t)L.M * kNC * PS * sizeof(float);
+      cudaEvent_t e = c->prof_begin(7);
+      k_l2p<<<L.nleaf, 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg, F->d_T,
+                                                L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr, c->ne);
+      c->prof_end(7, e);
+      TDBEM_CUDA_TRY(c, cudaGetLastError());
+    }
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring, const double* V, bool eval) {
+  FmmPlan* F = c->fmm;
+  double* slot = nullptr;
+  if (F->lmax >= 2) slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne;
+  cudaEvent_t e = c->prof_begin(1);
+  k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag,
+                                                                      F->d_off, F->d_val32, c->ne, ring, c->L, alpha,
+                                                                      V, slot, c->d_R);
+  c->prof_end(1, e);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha) { return far_events(c, alpha, c->d_Jring, false); }
+
+// Evaluation state for history_eval: cleared, then the far events of steps
+// 1 .. alpha-1 are replayed on the supplied history.
+tdbem_status tdbem_fast_eval_reset(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (!F || F->lmax < 2) return TDBEM_OK;
+  for (int l = 2; l <= F->lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->mom_eval[l - 2], 0, (int64_t)L.ncell * 4 * kNC * F->P * sizeof(float),
+                                      c->stream));
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->loc_eval[l - 2], 0, (int64_t)L.ncell * L.Q * kNC * F->P * sizeof(float),
+                                      c->stream));
+  }
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval, 0, (int64_t)F->Lr * c->ne * sizeof(double), c->stream));
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_fast_consume_eval_slot(tdbem_ctx* c, int32_t alpha) {
+  FmmPlan* F = c->fmm;
+  if (!F || F->lmax < 2) return TDBEM_OK;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne, 0,
+                                    c->ne * sizeof(double), c->stream));
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_fast_replay_step(tdbem_ctx* c, int32_t alpha, const double* ring) {
+  return far_events(c, alpha, ring, true);
+}
+
+tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (!F || F->lmax < 2) return TDBEM_OK;
+  for (int l = 2; l <= F->lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.mom, 0, (int64_t)L.ncell * 4 * kNC * F->P * sizeof(float), c->stream));
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.loc, 0, (int64_t)L.ncell * L.Q * kNC * F->P * sizeof(float), c->stream));
+  }
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar, 0, (int64_t)F->Lr * c->ne * sizeof(double), c->stream));
+  return TDBEM_OK;
+}
+
+void tdbem_fast_free(tdbem_ctx* c) {
+  delete c->fmm;
+  c->fmm = nullptr;
+}
+
+void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info) {
+  const FmmPlan* F = c->fmm;
+  if (!F) return;
+  info->lmax = F->lmax;
+  info->n_levels = F->lmax + 1;
+  info->mt_leaf = F->lmax >= 2 ? F->lev[F->lmax].M : 0;
+  info->n_near_pairs = F->nnz;
+  info->near_coef_bytes = F->nval * (int64_t)sizeof(float);
+  int64_t il = 0;
+  double fl = 0;
+  for (int l = 2; l <= F->lmax; ++l) {
+    il += F->lev[l].npairs;
+    if (F->lev[l].M) fl += F->lev[l].flops_event / F->lev[l].M;
+  }
+  info->n_far_pairs = il;
+  info->m2l_flops_per_step = fl;
+}
+
+// CSR of Z0 from the near store
+tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
+                                  const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val) {
+  const FmmPlan* F = c->fmm;
+  *row_ptr = F->d_row_ptr;
+  *col = F->d_col;
+  *m_lo = F->d_mlo;
+  *nlag = F->d_nlag;
+  *off = F->d_off;
+  *val = F->d_val64;
+  return TDBEM_OK;
+}
+
+// timeouts recorded by bounded device waits (0: none)
+tdbem_status tdbem_fast_check(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (!F || !F->d_err) return TDBEM_OK;
+  int32_t h = 0;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&h, F->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    c->set_error("fast: a bounded wait of the tensor-core M2L expired");
+    return TDBEM_ETIMEOUT;
+  }
+  return TDBEM_OK;
+}

@@ -56,6 +56,8 @@ struct PairStore {
   double* val = nullptr;    // [nval]
 };
 
+struct FmmPlan;
+
 }  // namespace tdbem
 
 struct tdbem_ctx {
@@ -76,12 +78,15 @@ struct tdbem_ctx {
   int32_t* d_et = nullptr;          // [ne][2]
   // direct coefficients: rows i, all j (direct mode)
   tdbem::PairStore direct;
+  tdbem::FmmPlan* fmm = nullptr;    // fast mode
   int32_t max_lag = 0;
   // Z0 in CSR
   int32_t* d_z0_ptr = nullptr;
   int32_t* d_z0_col = nullptr;
   double* d_z0_val = nullptr;
   double* d_z0_inv_diag = nullptr;
+  float* d_z0_val32 = nullptr;
+  float* d_z0_inv32 = nullptr;
   int64_t z0_nnz = 0;
   // marching state
   int32_t L = 0;                    // ring length (power of two)
@@ -137,6 +142,27 @@ tdbem_status tdbem_build_direct(tdbem_ctx* c);
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V);
 tdbem_status tdbem_incident_table(tdbem_ctx* c);
 const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha);
+tdbem_status tdbem_assemble_csr(tdbem_ctx* c, const int2* d_pairs, int64_t npairs, const int64_t* d_row_ptr,
+                                const int32_t* d_col, int64_t nnz, int16_t** m_lo, uint8_t** nlag, int64_t** off,
+                                double** val, int64_t* nval);
+// fmm.cu
+tdbem_status tdbem_build_fast(tdbem_ctx* c);
+tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring, const double* V, bool eval);
+tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha);
+tdbem_status tdbem_fast_replay_step(tdbem_ctx* c, int32_t alpha, const double* ring);
+tdbem_status tdbem_fast_consume_eval_slot(tdbem_ctx* c, int32_t alpha);
+tdbem_status tdbem_fast_eval_reset(tdbem_ctx* c);
+tdbem_status tdbem_fast_reset(tdbem_ctx* c);
+void tdbem_fast_free(tdbem_ctx* c);
+tdbem_status tdbem_fast_check(tdbem_ctx* c);
+// m2l_tc.cu
+tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const float* ops, int P,
+                          int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
+                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int prec, int32_t* err);
+void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
+tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
+                                  const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val);
 // solve.cu
 tdbem_status tdbem_build_z0(tdbem_ctx* c);
+tdbem_status tdbem_build_z0_csr(tdbem_ctx* c);
 tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters);

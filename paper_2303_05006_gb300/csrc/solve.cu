@@ -54,28 +54,51 @@ __global__ void k_z0_fill(const int16_t* m_lo, const uint8_t* nlag, const int64_
   inv_diag[i] = (dg != 0.0) ? 1.0 / dg : 1.0;
 }
 
+__global__ void k_z0_csr(const int64_t* row_ptr, const int32_t* col, const int16_t* m_lo, const uint8_t* nlag,
+                         const int64_t* off, const double* val, int64_t ne, const int32_t* ptr, int32_t* zcol, double* z,
+                         double* inv_diag, int32_t* cnt, int fill) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  int k = fill ? ptr[i] : 0;
+  double dg = 0.0;
+  for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+    if (m_lo[p] != 1 || nlag[p] == 0) continue;
+    if (fill) {
+      zcol[k] = col[p];
+      z[k] = val[off[p]];
+      if (col[p] == i) dg = z[k];
+    }
+    ++k;
+  }
+  if (fill)
+    inv_diag[i] = (dg != 0.0) ? 1.0 / dg : 1.0;
+  else
+    cnt[i] = k;
+}
+
 struct SolveArgs {
   const int32_t* ptr;
   const int32_t* col;
-  const double* val;
-  const double* inv_diag;
+  const double* val;      // Z0, FP64 (outer residual)
+  const float* val32;     // Z0, FP32 (inner iterations)
+  const float* inv_diag;  // Jacobi preconditioner
   const double* b;
   double* x;        // solution (also written to the ring)
   double* ring;     // [ne][L]
   int32_t L;
   int32_t alpha;    // solving J^{alpha-1}
   int32_t warm;     // 1: cubic extrapolation of J^{alpha-2..alpha-5}
-  double* w;        // 8 work vectors [8][ne]: r, rh, p, v, s, t, ph, sh
+  double* w;        // FP64 residual [ne], then 9 FP32 vectors [9][ne]
   int64_t ne;
   double tol;
-  int32_t maxit;
-  int32_t* status;  // [0] iterations, [1] converged flag, [2] misses, [3] iteration total
+  int32_t maxit;    // cap on the total inner iterations
+  int32_t* status;  // [0] inner iterations, [1] converged flag, [2] misses, [3] iteration total
   double* resid;    // [0] final relative residual
 };
 
+// Block sums of NV values; the totals end up in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sums(double (&v)[NV], double* sm) {
-  // sm: [32][NV]
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k)
@@ -95,52 +118,78 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* sm) {
   __syncthreads();
 }
 
-// Sum of per-CTA partials `mine` over the cluster: thread 0 of each CTA holds
-// its block total; the totals are published in the CTA's shared slot, the
-// cluster barrier orders them, and every thread reads all slots through DSMEM
-// in rank order (identical result in every CTA).
+// Cluster-wide sums: thread 0 publishes its block totals in this CTA's slot
+// (two alternating slots, so a slot is rewritten only after one more cluster
+// barrier than its readers have passed); after the hardware cluster barrier,
+// lane r of warp 0 reads CTA r's slot through distributed shared memory, the
+// warp sums them in a fixed order and broadcasts through shared memory.
 template <int NV>
-__device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[NV], double* slot) {
+__device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[NV], double (*slots)[4],
+                                             double* bc, int& phase) {
+  double* slot = slots[phase & 1];
+  ++phase;
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < NV; ++k) slot[k] = v[k];
   cl.sync();
-  unsigned nb = cl.num_blocks();
+  if (threadIdx.x < 32) {
+    unsigned nb = cl.num_blocks();
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (unsigned r = 0; r < nb; ++r) {
-    const double* rs = cl.map_shared_rank(slot, r);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += rs[k];
+    for (int k = 0; k < NV; ++k) {
+      double s = threadIdx.x < nb ? cl.map_shared_rank(slot, threadIdx.x)[k] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) bc[k] = s;
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = bc[k];
 }
 
-__device__ __forceinline__ double spmv_row(const SolveArgs& A, int64_t i, const double* xin) {
+__device__ __forceinline__ double spmv_row64(const SolveArgs& A, int64_t i, const double* x) {
   double s = 0.0;
-  for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s += A.val[k] * xin[A.col[k]];
+  for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
   return s;
 }
 
+__device__ __forceinline__ float spmv_row32(const SolveArgs& A, int64_t i, const float* x) {
+  float s0 = 0.f, s1 = 0.f;
+  int k = A.ptr[i], e = A.ptr[i + 1];
+  for (; k + 1 < e; k += 2) {
+    s0 += A.val32[k] * x[A.col[k]];
+    s1 += A.val32[k + 1] * x[A.col[k + 1]];
+  }
+  if (k < e) s0 += A.val32[k] * x[A.col[k]];
+  return s0 + s1;
+}
+
+// Mixed-precision solve of Z0 x = b: FP64 residual r = b - Z0 x (iterative
+// refinement) around an FP32 Jacobi-preconditioned BiCGStab for the
+// correction, inner relative tolerance 1e-5.  Z0 is well conditioned (about 2
+// on the test spheres), so each refinement gains five to six digits and two to
+// three refinements reach 1e-13.
 __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double red[32 * 4];
-  // one slot per reduction phase, so that a slot is rewritten only after a
-  // further cluster barrier that every reader has passed
-  __shared__ double slots[6][4];
+  __shared__ double slots[2][4];
+  __shared__ double bc[4];
+  int phase = 0;
   const int64_t ne = A.ne;
   const unsigned nb = cl.num_blocks(), rk = cl.block_rank();
   const int64_t rows = (ne + nb - 1) / nb;
   const int64_t r0 = rk * rows, r1 = min(ne, r0 + rows);
-  double* r = A.w;
-  double* rh = A.w + ne;
-  double* p = A.w + 2 * ne;
-  double* v = A.w + 3 * ne;
-  double* s = A.w + 4 * ne;
-  double* t = A.w + 5 * ne;
-  double* ph = A.w + 6 * ne;
-  double* sh = A.w + 7 * ne;
+  double* r64 = A.w;
+  float* f = (float*)(A.w + ne);
+  float* r = f;
+  float* rh = f + ne;
+  float* p = f + 2 * ne;
+  float* v = f + 3 * ne;
+  float* s = f + 4 * ne;
+  float* t = f + 5 * ne;
+  float* ph = f + 6 * ne;
+  float* sh = f + 7 * ne;
+  float* d = f + 8 * ne;
   const int L = A.L, msk = A.L - 1;
-  // initial guess
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     double x0 = 0.0;
     if (A.warm) {
@@ -153,99 +202,123 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
     A.x[i] = x0;
   }
   cl.sync();
-  double d3[3];
-  d3[0] = d3[1] = d3[2] = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double ri = A.b[i] - spmv_row(A, i, A.x);
-    r[i] = ri;
-    rh[i] = ri;
-    p[i] = 0.0;
-    v[i] = 0.0;
-    d3[0] += ri * ri;
-    d3[1] += A.b[i] * A.b[i];
-  }
-  block_sums<3>(d3, red);
-  cluster_sums<3>(cl, d3, slots[0]);
-  double rr = d3[0], bb = d3[1];
-  double rho = rr, rho_old = 1.0, alp = 1.0, om = 1.0;
-  const double tol2 = A.tol * A.tol * bb;
-  int it = 0;
-  bool conv = (rr <= tol2);
-  while (!conv && it < A.maxit) {
-    ++it;
-    if (rho == 0.0) break;
-    double beta = (rho / rho_old) * (alp / om);
+  double bb = -1.0, rr = 0.0;
+  int inner_total = 0;
+  bool conv = false;
+  for (int outer = 0; outer < 8; ++outer) {
+    // FP64 residual
+    double q2[2] = {0.0, 0.0};
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double pi = r[i] + beta * (p[i] - om * v[i]);
-      p[i] = pi;
-      ph[i] = pi * A.inv_diag[i];
+      double ri = A.b[i] - spmv_row64(A, i, A.x);
+      r64[i] = ri;
+      q2[0] += ri * ri;
+      q2[1] += A.b[i] * A.b[i];
     }
-    cl.sync();
-    double d1[1] = {0.0};
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double vi = spmv_row(A, i, ph);
-      v[i] = vi;
-      d1[0] += rh[i] * vi;
-    }
-    block_sums<1>(d1, red);
-    cluster_sums<1>(cl, d1, slots[1]);
-    if (d1[0] == 0.0) break;
-    alp = rho / d1[0];
-    double d1b[1] = {0.0};
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double si = r[i] - alp * v[i];
-      s[i] = si;
-      sh[i] = si * A.inv_diag[i];
-      d1b[0] += si * si;
-    }
-    block_sums<1>(d1b, red);
-    cluster_sums<1>(cl, d1b, slots[2]);
-    if (d1b[0] <= tol2) {
-      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        A.x[i] += alp * ph[i];
-        r[i] = s[i];
-      }
-      rr = d1b[0];
+    block_sums<2>(q2, red);
+    cluster_sums<2>(cl, q2, slots, bc, phase);
+    rr = q2[0];
+    if (bb < 0) bb = q2[1];
+    if (rr <= A.tol * A.tol * bb) {
       conv = true;
       break;
     }
-    double d2[2] = {0.0, 0.0};
+    if (inner_total >= A.maxit) break;
+    // FP32 BiCGStab for Z0 d = r64, relative tolerance 1e-5
+    double q1[2] = {0.0, 0.0};
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double ti = spmv_row(A, i, sh);
-      t[i] = ti;
-      d2[0] += ti * s[i];
-      d2[1] += ti * ti;
-    }
-    block_sums<2>(d2, red);
-    cluster_sums<2>(cl, d2, slots[3]);
-    if (d2[1] == 0.0) break;
-    om = d2[0] / d2[1];
-    double d2b[2] = {0.0, 0.0};
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      A.x[i] += alp * ph[i] + om * sh[i];
-      double ri = s[i] - om * t[i];
+      float ri = (float)(r64[i] * (1.0 / sqrt(rr)));  // unit-norm right-hand side
       r[i] = ri;
-      d2b[0] += ri * ri;
-      d2b[1] += rh[i] * ri;
+      rh[i] = ri;
+      p[i] = 0.f;
+      v[i] = 0.f;
+      d[i] = 0.f;
+      q1[0] += (double)ri * ri;
     }
-    block_sums<2>(d2b, red);
-    cluster_sums<2>(cl, d2b, slots[4 + (it & 1)]);
-    rr = d2b[0];
-    rho_old = rho;
-    rho = d2b[1];
-    conv = (rr <= tol2);
-    if (om == 0.0) break;
+    block_sums<1>(*(double(*)[1])q1, red);
+    cluster_sums<1>(cl, *(double(*)[1])q1, slots, bc, phase);
+    double rho = q1[0], rho_old = 1.0, alp = 1.0, om = 1.0;
+    const double tin2 = 1e-10 * q1[0];
+    for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
+      ++inner_total;
+      if (rho == 0.0) break;
+      float beta = (float)((rho / rho_old) * (alp / om));
+      float omf = (float)om;
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        float pi = r[i] + beta * (p[i] - omf * v[i]);
+        p[i] = pi;
+        ph[i] = pi * A.inv_diag[i];
+      }
+      cl.sync();
+      double e1[1] = {0.0};
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        float vi = spmv_row32(A, i, ph);
+        v[i] = vi;
+        e1[0] += (double)(rh[i] * vi);
+      }
+      block_sums<1>(e1, red);
+      cluster_sums<1>(cl, e1, slots, bc, phase);
+      if (e1[0] == 0.0) break;
+      alp = rho / e1[0];
+      float alf = (float)alp;
+      double e2[1] = {0.0};
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        float si = r[i] - alf * v[i];
+        s[i] = si;
+        sh[i] = si * A.inv_diag[i];
+        e2[0] += (double)(si * si);
+      }
+      block_sums<1>(e2, red);
+      cluster_sums<1>(cl, e2, slots, bc, phase);  // also orders sh for the SpMV below
+      if (e2[0] <= tin2) {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] += alf * ph[i];
+        break;
+      }
+      double e3[2] = {0.0, 0.0};
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        float ti = spmv_row32(A, i, sh);
+        t[i] = ti;
+        e3[0] += (double)(ti * s[i]);
+        e3[1] += (double)(ti * ti);
+      }
+      block_sums<2>(e3, red);
+      cluster_sums<2>(cl, e3, slots, bc, phase);
+      if (e3[1] == 0.0) break;
+      om = e3[0] / e3[1];
+      omf = (float)om;
+      double e4[2] = {0.0, 0.0};
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        d[i] += alf * ph[i] + omf * sh[i];
+        float ri = s[i] - omf * t[i];
+        r[i] = ri;
+        e4[0] += (double)(ri * ri);
+        e4[1] += (double)(rh[i] * ri);
+      }
+      block_sums<2>(e4, red);
+      cluster_sums<2>(cl, e4, slots, bc, phase);
+      rho_old = rho;
+      rho = e4[1];
+      if (e4[0] <= tin2 || om == 0.0) break;
+    }
+    // x += |r| d (own rows), then a barrier before the next residual reads x
+    const double sc = sqrt(rr);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.x[i] += sc * (double)d[i];
+    cl.sync();
   }
-  // publish J^{alpha-1}
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.ring[i * L + ((A.alpha - 1) & msk)] = A.x[i];
   if (rk == 0 && threadIdx.x == 0) {
-    A.status[0] = it;
+    A.status[0] = inner_total;
     A.status[1] = conv ? 1 : 0;
     A.status[2] += conv ? 0 : 1;  // solves that missed the tolerance since the last reset
-    A.status[3] += it;            // iterations since the last reset
+    A.status[3] += inner_total;   // iterations since the last reset
     A.resid[0] = bb > 0 ? sqrt(rr / bb) : 0.0;
   }
   cl.sync();  // keep every CTA's shared slots alive until all remote reads are done
+}
+
+__global__ void k_z0_f32(const double* z, const double* inv_diag, int64_t nnz, int64_t ne, float* z32, float* inv32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < nnz) z32[i] = (float)z[i];
+  if (i < ne) inv32[i] = (float)inv_diag[i];
 }
 
 }  // namespace tdbem
@@ -253,6 +326,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
 using namespace tdbem;
 
 static int g_cluster = 0;
+
+static tdbem_status tdbem_z0_f32(tdbem_ctx* c) {
+  tdbem_status s;
+  if ((s = c->dalloc(&c->d_z0_val32, c->z0_nnz)) || (s = c->dalloc(&c->d_z0_inv32, c->ne))) return s;
+  int64_t n = std::max<int64_t>(c->z0_nnz, c->ne);
+  k_z0_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->d_z0_val, c->d_z0_inv_diag, c->z0_nnz, c->ne,
+                                                               c->d_z0_val32, c->d_z0_inv32);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return TDBEM_OK;
+}
 
 tdbem_status tdbem_build_z0(tdbem_ctx* c) {
   const int64_t ne = c->ne;
@@ -278,7 +362,41 @@ tdbem_status tdbem_build_z0(tdbem_ctx* c) {
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   if ((s = c->dalloc(&c->d_work, 8 * ne)) || (s = c->dalloc(&c->d_status, 4)) || (s = c->dalloc(&c->d_dots, 4)))
     return s;
-  return TDBEM_OK;
+  return tdbem_z0_f32(c);
+}
+
+tdbem_status tdbem_build_z0_csr(tdbem_ctx* c) {
+  const int64_t ne = c->ne;
+  const int64_t* rp;
+  const int32_t* col;
+  const int16_t* ml;
+  const uint8_t* nl;
+  const int64_t* off;
+  const double* val;
+  tdbem_fast_z0_source(c, &rp, &col, &ml, &nl, &off, &val);
+  int32_t* d_cnt = nullptr;
+  tdbem_status s;
+  if ((s = c->dalloc(&d_cnt, ne)) || (s = c->dalloc(&c->d_z0_ptr, ne + 1)) ||
+      (s = c->dalloc(&c->d_z0_inv_diag, ne)))
+    return s;
+  k_z0_csr<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(rp, col, ml, nl, off, val, ne, nullptr, nullptr,
+                                                                nullptr, nullptr, d_cnt, 0);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  std::vector<int32_t> cnt(ne), ptr(ne + 1);
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), d_cnt, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  ptr[0] = 0;
+  for (int64_t i = 0; i < ne; ++i) ptr[i + 1] = ptr[i] + cnt[i];
+  c->z0_nnz = ptr[ne];
+  if ((s = c->dalloc(&c->d_z0_col, c->z0_nnz)) || (s = c->dalloc(&c->d_z0_val, c->z0_nnz))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_z0_ptr, ptr.data(), (ne + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    c->stream));
+  k_z0_csr<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(rp, col, ml, nl, off, val, ne, c->d_z0_ptr,
+                                                                c->d_z0_col, c->d_z0_val, c->d_z0_inv_diag, nullptr, 1);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if ((s = c->dalloc(&c->d_work, 8 * ne)) || (s = c->dalloc(&c->d_status, 4)) || (s = c->dalloc(&c->d_dots, 4)))
+    return s;
+  return tdbem_z0_f32(c);
 }
 
 static tdbem_status pick_cluster(tdbem_ctx* c) {
@@ -315,7 +433,8 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
   A.ptr = c->d_z0_ptr;
   A.col = c->d_z0_col;
   A.val = c->d_z0_val;
-  A.inv_diag = c->d_z0_inv_diag;
+  A.val32 = c->d_z0_val32;
+  A.inv_diag = c->d_z0_inv32;
   A.b = c->d_R;
   A.x = c->d_J;
   A.ring = c->d_Jring;
