@@ -71,7 +71,8 @@ typedef enum {
   TDBEM_P_FP32 = 0,   /* FP32 CUDA cores */
   TDBEM_P_TF32 = 1,   /* TF32 tensor cores, FP32 accumulate */
   TDBEM_P_BF16 = 2,   /* BF16 tensor cores, FP32 accumulate */
-  TDBEM_P_BF16X3 = 3  /* split-precision BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  TDBEM_P_BF16X3 = 3, /* split-precision BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  TDBEM_P_TF32X3 = 4  /* split-precision TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
 } tdbem_prec;
 
 typedef struct {

@@ -346,6 +346,94 @@ __global__ void k_m2m(const int32_t* cells, const int32_t* child, const float* S
   }
 }
 
+// One 1-D contraction of nch tensors [p][p][p][pt] (channel stride P) along
+// `axis` (0..2 space, 3 time): out[.., j, ..] = sum_i M(j, i) in[.., i, ..]
+// with M(j, i) = mat[j*n + i] (trans = 0) or mat[i*n + j] (trans = 1).
+__device__ __forceinline__ void contract_axis(const float* in, float* out, const float* mat, bool trans, int axis,
+                                              int p, int pt, int nch) {
+  const int PS = p * p * p, P = PS * pt;
+  const int n = axis == 3 ? pt : p;
+  const int stride = axis == 3 ? 1 : (axis == 2 ? pt : (axis == 1 ? p * pt : p * p * pt));
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
+    int ch = e / P, r = e % P;
+    int j = (r / stride) % n;
+    const float* src = in + (int64_t)ch * P + (r - j * stride);
+    float acc = 0.f;
+    for (int i = 0; i < n; ++i) acc += (trans ? mat[i * n + j] : mat[j * n + i]) * src[i * stride];
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
+// M2M, factorised: for each child and half-interval, the 14 channels (7
+// components x full/truncated) are interpolated one axis at a time and
+// accumulated into the parent moments of source interval k.
+__global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
+                           int k, const float* cmom, float* pmom) {
+  extern __shared__ float sm[];
+  const int PS = p * p * p, P = PS * pt, nch = 2 * kNC;
+  float* b0 = sm;
+  float* b1 = sm + nch * P;
+  float* acc = sm + 2 * nch * P;
+  int cell = cells[blockIdx.x];
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) acc[e] = 0.f;
+  for (int o = 0; o < 8; ++o) {
+    int ch = child[cell * 8 + o];
+    if (ch < 0) continue;
+    int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
+    for (int h = 0; h < 2; ++h) {
+      const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * kNC * P;
+      __syncthreads();
+      for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
+        int var = e / (kNC * P), r = e % (kNC * P);
+        int cvar = (var == 1 && h == 0) ? 1 : 0;  // truncated parent = truncated first half + full second half
+        b0[e] = src[(int64_t)cvar * kNC * P + r];
+      }
+      __syncthreads();
+      contract_axis(b0, b1, St + h * pt * pt, false, 3, p, pt, nch);
+      contract_axis(b1, b0, Sx + sz * p * p, false, 2, p, pt, nch);
+      contract_axis(b0, b1, Sx + sy * p * p, false, 1, p, pt, nch);
+      contract_axis(b1, b0, Sx + sx * p * p, false, 0, p, pt, nch);
+      for (int e = threadIdx.x; e < nch * P; e += blockDim.x) acc[e] += b0[e];
+    }
+  }
+  __syncthreads();
+  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) out[e] = acc[e];
+}
+
+// L2L, factorised (transposed interpolation): the parent's local coefficients
+// of interval k+1 are evaluated at each child's nodes for the child intervals
+// 2(k+1) and 2(k+1)+1 and added there; the parent slot is then cleared.
+__global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
+                           int k, float* ploc, int Qp, float* cloc, int Qc) {
+  extern __shared__ float sm[];
+  const int PS = p * p * p, P = PS * pt, nch = kNC;
+  float* b0 = sm;
+  float* b1 = sm + nch * P;
+  float* par = sm + 2 * nch * P;
+  int cell = cells[blockIdx.x];
+  float* src = ploc + ((int64_t)cell * Qp + ((k + 1) % Qp)) * kNC * P;
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) par[e] = src[e];
+  for (int o = 0; o < 8; ++o) {
+    int ch = child[cell * 8 + o];
+    if (ch < 0) continue;
+    int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
+    for (int h = 0; h < 2; ++h) {
+      __syncthreads();
+      contract_axis(par, b0, St + h * pt * pt, true, 3, p, pt, nch);
+      contract_axis(b0, b1, Sx + sz * p * p, true, 2, p, pt, nch);
+      contract_axis(b1, b0, Sx + sy * p * p, true, 1, p, pt, nch);
+      contract_axis(b0, b1, Sx + sx * p * p, true, 0, p, pt, nch);
+      int slot = (2 * (k + 1) + h) % Qc;
+      float* dst = cloc + ((int64_t)ch * Qc + slot) * kNC * P;
+      for (int e = threadIdx.x; e < nch * P; e += blockDim.x) dst[e] += b1[e];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) src[e] = 0.f;
+}
+
 // M2L as a batch of dense GEMMs on CUDA cores (FP32): for every (canonical
 // offset, lag q, kernel kind) the operator (P x P) multiplies the gathered
 // moments of all pairs of that offset class; results are added to the target
@@ -784,6 +872,9 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
   const double dt = c->dt, cc = c->phys.c;
   TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_l2p, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2m_fact, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_l2l_fact, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+
   std::vector<double> tbox(4 * nt);
   for (int l = 0; l <= lmax; ++l) {
     FmmLevel& L = F->lev[l];
@@ -1053,8 +1144,13 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     }
     if (L.nnonleaf && l < lmax) {
       cudaEvent_t e = c->prof_begin(4);
-      k_m2m<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St,
-                                                p, pt, k, MOM(l + 1), MOM(l));
+      size_t smem = (size_t)3 * 2 * kNC * P * sizeof(float);
+      if (smem <= 227 * 1024)
+        k_m2m_fact<<<L.nnonleaf, 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
+                                                          F->d_St, p, pt, k, MOM(l + 1), MOM(l));
+      else  // large p: direct tensor-product sums from global memory
+        k_m2m<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
+                                                  F->d_St, p, pt, k, MOM(l + 1), MOM(l));
       c->prof_end(4, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
@@ -1079,8 +1175,14 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     }
     if (L.nnonleaf && l < lmax) {
       cudaEvent_t e = c->prof_begin(6);
-      k_l2l<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St,
-                                                p, pt, k, LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q);
+      size_t smem = (size_t)3 * kNC * P * sizeof(float);
+      if (smem <= 227 * 1024)
+        k_l2l_fact<<<L.nnonleaf, 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
+                                                          F->d_St, p, pt, k, LOC(l), L.Q, LOC(l + 1),
+                                                          F->lev[l + 1].Q);
+      else
+        k_l2l<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
+                                                  F->d_St, p, pt, k, LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q);
       c->prof_end(6, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }

@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t tile_off(int row, int kbyte) {
 
 }  // namespace
 
-// prec: 1 = TF32, 2 = BF16, 3 = BF16 x 3 (hi*hi + hi*lo + lo*hi)
+// prec: 1 = TF32, 2 = BF16, 3 = BF16 x 3, 4 = TF32 x 3 (split: hi*hi + hi*lo + lo*hi)
 __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const float* ops, int P,
                                                      int pt, int PS, const int32_t* pO, const int32_t* pS,
                                                      const int16_t* psym, const int16_t* smap, const float* mom,
@@ -128,8 +128,9 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int row0 = tl.y * kTileM, col0 = tl.z * kTileN;
   const int ncol = gd.z * nk;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool split = prec == 3;
-  const int es = prec == 1 ? 4 : 2;  // bytes per element in shared memory
+  const bool split = prec == 3 || prec == 4;
+  const bool tf = prec == 1 || prec == 4;
+  const int es = tf ? 4 : 2;  // bytes per element in shared memory
   const int KC = 128 / es;           // K elements per chunk
 
   if (tid < kTileN) {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = make_idesc(prec == 1 ? 2u : 1u);
+  const uint32_t idesc = make_idesc(tf ? 2u : 1u);
   const uint32_t mb = smem_u32(&mbar);
   bool ok = true;
 
@@ -170,9 +171,14 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       float x[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) x[u] = (row < P && kk + u < P) ? A[(int64_t)row * P + kk + u] : 0.f;
-      if (prec == 1) {
+      if (tf) {
         uint4 w = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]), f32_to_tf32(x[3]));
         *(uint4*)(tA + tile_off(r, 16 * g)) = w;
+        if (split) {
+          uint4 l = make_uint4(f32_to_tf32(x[0] - __uint_as_float(w.x)), f32_to_tf32(x[1] - __uint_as_float(w.y)),
+                               f32_to_tf32(x[2] - __uint_as_float(w.z)), f32_to_tf32(x[3] - __uint_as_float(w.w)));
+          *(uint4*)(tA2 + tile_off(r, 16 * g)) = l;
+        }
       } else {
         __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -200,9 +206,14 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
           }
         }
       }
-      if (prec == 1) {
+      if (tf) {
         uint4 w = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]), f32_to_tf32(x[3]));
         *(uint4*)(tB + tile_off(n, 16 * g)) = w;
+        if (split) {
+          uint4 l = make_uint4(f32_to_tf32(x[0] - __uint_as_float(w.x)), f32_to_tf32(x[1] - __uint_as_float(w.y)),
+                               f32_to_tf32(x[2] - __uint_as_float(w.z)), f32_to_tf32(x[3] - __uint_as_float(w.w)));
+          *(uint4*)(tB2 + tile_off(n, 16 * g)) = l;
+        }
       } else {
         __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -222,8 +233,12 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       for (int s = 0; s < 4; ++s) {
         uint32_t acc = (ch > 0 || s > 0) ? 1u : 0u;
         uint32_t off = 256u * s;  // two core matrices (32 bytes of K) per instruction
-        if (prec == 1) {
+        if (tf) {
           mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
+          if (split) {
+            mma_tf32(tmem, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
+            mma_tf32(tmem, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
+          }
         } else {
           mma_f16(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
           if (split) {

@@ -121,3 +121,20 @@ def test_fast_full_size_sphere7680():
     e = _rel(Jf, Jd)
     assert e < 1.5e-2, e
     assert np.abs(Jf[-50:]).max() < 1e-2 * np.abs(Jd).max()
+
+
+def test_tensor_core_m2l_precisions(sphere1280_direct):
+    """M2L on tcgen05 tensor cores against the FP32 CUDA-core M2L (1920-RWG
+    sphere, 299 steps).  The truncated-power kernel grows quadratically with
+    the lag and the far field of old sources is a telescoping cancellation
+    across lags, so operand rounding is amplified: the split forms (about 16
+    and 22 operand bits) track FP32, the single-pass TF32 and BF16 forms do
+    not (measured: BF16x3 6.8e-4, TF32 4.1e-2, BF16 3.6e-1)."""
+    w, Jd = sphere1280_direct
+    J = {prec: _solver(w, mode=1, m2l_prec=prec).march(w.Nt - 1) for prec in (0, 1, 2, 3, 4)}
+    e = {prec: _rel(J[prec], J[0]) for prec in (1, 2, 3, 4)}
+    assert e[4] < 1e-4, e     # TF32 x 3
+    assert e[3] < 3e-3, e     # BF16 x 3
+    assert e[1] > 10 * e[4] and e[2] > 10 * e[3], e
+    # the accurate tensor-core form keeps the fast path's error at the FP32 level
+    assert abs(_rel(J[4], Jd) - _rel(J[0], Jd)) < 1e-4
