@@ -6,8 +6,12 @@ solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
 already resident in HBM.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3] [--p P]
-                  [--workload NAME] [--no-compare] [--no-cpu-baseline]
+                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3|tf32x3] [--p P]
+                  [--rhs R] [--workload NAME] [--no-compare] [--no-cpu-baseline]
+
+--rhs R marches R incident plane waves on the same scatterer in one batch
+(the reference pulse plus R-1 seeded directions); `value` is then the steps/s
+summed over the R right-hand sides.
 
 N > 1 (torchrun): independent replicas, one per GPU; the march does not shard.
 """
@@ -140,6 +144,14 @@ def run_reference(args, rank, world, dist):
     return 0
 
 
+def batch_pulses(w, n: int, seed: int = 4):
+    """n seeded incident plane waves (direction uniform on the sphere,
+    polarisation at a uniform angle), each with the reference pulse shape."""
+    from workloads.configs import pulse_star, random_plane_waves
+
+    return [pulse_star(w.verts, k=k, pol=pol) for k, pol in random_plane_waves(n, seed)] if n > 0 else []
+
+
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
 KERNELS = ["incident_rhs", "near_history" , "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
 
@@ -190,13 +202,16 @@ def run_ours(args, rank, world, dist):
     W, K = args.warmup, args.steps
     if W + K > w.Nt - 1:
         raise SystemExit(f"warmup + steps must be <= {w.Nt - 1}")
+    R = args.rhs
+    pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
-    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec])
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R)
     setup_s = time.perf_counter() - t0
-    s.set_incident_plane(w.pulses[0])
+    for r, pu in enumerate(pulses):
+        s.set_incident_plane(pu, rhs=r)
     stream = torch.cuda.current_stream()
     s.set_stream(stream.cuda_stream)
-    out = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
+    out = torch.empty((K, R, s.ne), dtype=torch.float64, device="cuda")
     # device-resident march: warm-up, then K timed steps
     s.march_dev(W)
     torch.cuda.synchronize()
@@ -216,7 +231,7 @@ def run_ours(args, rank, world, dist):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt[0])
         dist.barrier()
-    steps_per_s = world * K / t
+    steps_per_s = world * K * R / t
     if args.timed_only:  # for profiler launch lists: nothing but the timed march
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "note": "timed march only"}))
@@ -232,10 +247,10 @@ def run_ours(args, rank, world, dist):
     # end-to-end through the C ABI with host buffers: V^{alpha-1} copied in,
     # J^{alpha-1} copied out every step
     s.reset()
-    Vh = torch.empty((W + K, s.ne), dtype=torch.float64).pin_memory()
-    Jh = torch.empty((s.ne,), dtype=torch.float64).pin_memory()
+    Vh = torch.empty((W + K, R, s.ne), dtype=torch.float64).pin_memory()
+    Jh = torch.empty((R, s.ne), dtype=torch.float64).pin_memory()
     for a in range(1, W + K + 1):
-        Vh[a - 1].copy_(torch.from_numpy(s.history_eval(a, np.zeros((0, s.ne)))))
+        Vh[a - 1].copy_(torch.from_numpy(s.history_eval(a, np.zeros((0, R * s.ne))).reshape(R, s.ne)))
     s.reset()
     for a in range(W):
         s.step_v(Vh[a].numpy(), Jh.numpy())
@@ -251,8 +266,8 @@ def run_ours(args, rank, world, dist):
         tt = torch.tensor([te])
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt[0])
-    e2e = world * K / te
-    Jfast = out.cpu().numpy()
+    e2e = world * K * R / te
+    Jfast = out[:, 0].cpu().numpy()
     s.close()
     if rank != 0:
         return 0
@@ -272,15 +287,33 @@ def run_ours(args, rank, world, dist):
         td = e0.elapsed_time(e1) / 1000.0
         Jd = outd.cpu().numpy()
         cmp = {"direct_steps_per_s": K / td,
-               "fast_over_direct": (K / t) / (K / td),
+               "fast_over_direct": (K * R / t) / (K / td),
                "rel_l2_vs_direct": float(np.linalg.norm(Jfast - Jd) / np.linalg.norm(Jd))}
         sd.close()
+        if R > 1:
+            # the same fast march one right-hand side at a time
+            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec])
+            s1.set_incident_plane(w.pulses[0])
+            s1.set_stream(stream.cuda_stream)
+            s1.march_dev(W)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s1.march_dev(K, outd.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t1 = e0.elapsed_time(e1) / 1000.0
+            cmp["single_rhs_steps_per_s"] = K / t1
+            cmp["batched_over_single"] = (K * R / t) / (K / t1)
+            cmp["rel_l2_rhs0_vs_single"] = float(np.linalg.norm(Jfast - outd.cpu().numpy())
+                                                 / np.linalg.norm(outd.cpu().numpy()))
+            s1.close()
     line = {
-        "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "metric": METRIC, "value": steps_per_s, "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
+        "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1000.0 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
-                   "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None,
+                   "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
                    "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
                          + (" + M2L operators" if args.mode == "fast" else "") + ")",
@@ -289,7 +322,8 @@ def run_ours(args, rank, world, dist):
         "roofline": roofline(args, info, launches, ms, K),
         "kernel_ms_per_step": {KERNELS[k]: ms[k] / K for k in range(len(ms)) if launches[k]},
         "gpu_launches": int(sum(launches)),
-        "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": 8 * s.ne, "d2h_bytes_per_step": 8 * s.ne},
+        "e2e": {"value": e2e, "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
+                "h2d_bytes_per_step": 8 * s.ne * R, "d2h_bytes_per_step": 8 * s.ne * R},
         "clocks": ck,
         "solver_iters_per_step": info.total_solver_iters / K if K else None,
     }
@@ -313,6 +347,7 @@ def main():
     ap.add_argument("--mode", choices=["fast", "direct"], default="fast")
     ap.add_argument("--prec", choices=list(PREC), default="tf32x3")
     ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")
     ap.add_argument("--workload", default="sphere7680")

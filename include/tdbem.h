@@ -87,8 +87,14 @@ typedef struct {
   double solve_tol;     /* relative residual of the Z0 solve */
   int32_t solve_maxit;  /* iteration cap of the Z0 solve */
   int32_t warm_start;   /* 0: zero initial guess, 1: cubic extrapolation of past currents */
-  int32_t n_rhs;        /* number of right-hand sides marched together (>= 1) */
+  int32_t n_rhs;        /* right-hand sides marched together, 1 .. TDBEM_MAX_RHS (batched form) */
 } tdbem_params;
+
+/* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
+   scatterer) share every stored operator: the near field becomes a sparse
+   matrix times an R-column block, the M2L products gain R times more columns
+   per operator, and the R Z0 solves run in one launch. */
+#define TDBEM_MAX_RHS 64
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1. */
@@ -113,22 +119,26 @@ tdbem_status tdbem_edges(const tdbem_ctx* ctx, int32_t* edge_vert, int32_t* edge
    this context is launched; NULL selects the library's own stream. */
 tdbem_status tdbem_set_stream(tdbem_ctx* ctx, void* stream);
 
-/* Incident modulated-Gaussian plane wave for right-hand side `rhs`:
+/* Incident modulated-Gaussian plane wave for right-hand side `rhs`
+   (0 <= rhs < n_rhs; a right-hand side never set has zero incident field):
    pulse = {k[3], pol[3], f0, sigma, t0, z_min}; E = pol g(u), H = k x E / eta,
    u = t - (k.x - z_min)/c, g(u) = cos(2 pi f0 (u - t0)) exp(-(u-t0)^2/(2 sigma^2)).
    V^{alpha-1} (eq. v_i) is then evaluated on the device at every step. */
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* ctx, int32_t rhs, const double* pulse);
 
 /* Use caller-supplied right-hand sides instead: V[(alpha-1)*ne + i] for
-   alpha = 1 .. Nt-1 (host, copied to the device). */
+   alpha = 1 .. Nt-1 (host, copied to the device) is right-hand side `rhs`.
+   Once any caller table exists it replaces the plane-wave tables of every
+   right-hand side (columns never supplied are zero). */
 tdbem_status tdbem_set_rhs(tdbem_ctx* ctx, int32_t rhs, const double* V);
 
 /* History evaluation without solving (eq. R): for a given history
-   J_hist[b*ne + j] = J_j^b (b = 0 .. n_hist-1; J^b = 0 outside) returns
-   R_out[i] = V_i^{alpha-1} - sum_{m >= 2} Zt^(m)_ij J_j^{alpha-m}, evaluated
-   exactly as tdbem_step evaluates it (far field through the FMM in fast mode,
-   with the same time gating).  V is the incident field of rhs 0 if one is
-   set, else zero.  Does not change the marching state. */
+   J_hist[(b*n_rhs + r)*ne + j] = J_j^b of right-hand side r (b = 0 .. n_hist-1;
+   J^b = 0 outside) returns R_out[r*ne + i] = V_i^{alpha-1} - sum_{m >= 2}
+   Zt^(m)_ij J_j^{alpha-m}, evaluated exactly as tdbem_step evaluates it (far
+   field through the FMM in fast mode, with the same time gating).  V is the
+   incident field of each right-hand side (zero where none is set).  Does not
+   change the marching state. */
 tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_hist, int32_t n_hist,
                                 double* R_out);
 
@@ -146,7 +156,7 @@ tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_h
    loads the library, until exit), and calls no cudaMalloc, cudaFree or other
    allocating routine.  The paper has no counterpart: it is a deployment
    convenience.
-     * Needs ne * (L + K) <= TDBEM_NOALLOC_SCRATCH_DOUBLES, where L is the
+     * Needs ne * n_rhs * (L + K) <= TDBEM_NOALLOC_SCRATCH_DOUBLES, where L is the
        context's history ring length and K the number of history steps used
        (at most the largest lag); larger problems get TDBEM_EINVAL.
      * Direct mode only (TDBEM_EINVAL otherwise).
@@ -174,7 +184,10 @@ tdbem_status tdbem_step(tdbem_ctx* ctx, double* J_out, int32_t* iters);
    incident field is produced on the host. */
 tdbem_status tdbem_step_v(tdbem_ctx* ctx, const double* V, double* J_out, int32_t* iters);
 
-/* n_steps steps; J_all ([n_steps][n_rhs][ne], may be NULL) receives every J. */
+/* n_steps steps; J_all ([n_steps][n_rhs][ne], may be NULL) receives every J.
+   Host arrays of every entry point keep the right-hand side index outside
+   the edge index ([n_rhs][ne]); on the device the library stores it innermost
+   ([ne][n_rhs]) and converts on the way in and out. */
 tdbem_status tdbem_march(tdbem_ctx* ctx, int32_t n_steps, double* J_all);
 
 /* Same with the result written to device memory J_all_dev (may be NULL). */

@@ -99,7 +99,13 @@ def _ptr(a, t=_dp):
 
 
 class Solver:
-    """One marching context (a thin owner of a ``tdbem_ctx*``)."""
+    """One marching context (a thin owner of a ``tdbem_ctx*``).
+
+    With ``n_rhs = R > 1`` every per-step array carries the right-hand side
+    index before the edge index: J and R are (R, ne), histories (n, R, ne) and
+    march results (n_steps, R, ne).  With R = 1 they keep the plain (ne,) and
+    (n, ne) shapes.
+    """
 
     def __init__(self, verts, tris, dt: float, Nt: int, **params):
         L = lib()
@@ -122,6 +128,10 @@ class Solver:
         ne = ctypes.c_int64()
         L.tdbem_num_edges(h, ctypes.byref(ne))
         self.ne = int(ne.value)
+        self.R = int(p.n_rhs)
+
+    def _vshape(self, *lead):
+        return (*lead, self.ne) if self.R == 1 else (*lead, self.R, self.ne)
 
     def _check(self, rc):
         if rc != 0:
@@ -158,28 +168,30 @@ class Solver:
         self._check(lib().tdbem_set_rhs(self._h, rhs, _ptr(V)))
 
     def history_eval(self, alpha: int, J_hist) -> np.ndarray:
-        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.ne)
-        out = np.zeros(self.ne)
+        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.R * self.ne)
+        out = np.zeros(self._vshape())
         self._check(lib().tdbem_history_eval(self._h, int(alpha), _ptr(J) if J.size else None, J.shape[0], _ptr(out)))
         return out
 
     def history_eval_noalloc(self, alpha: int, J_hist) -> np.ndarray:
         """As history_eval, staging the history in the library's fixed device
         scratch array instead of allocating device memory."""
-        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.ne)
-        out = np.zeros(self.ne)
+        J = np.ascontiguousarray(J_hist, dtype=np.float64).reshape(-1, self.R * self.ne)
+        out = np.zeros(self._vshape())
         self._check(lib().tdbem_history_eval_noalloc(self._h, int(alpha), _ptr(J) if J.size else None, J.shape[0],
                                                      _ptr(out)))
         return out
 
     def step(self):
-        J = np.zeros(self.ne)
+        J = np.zeros(self._vshape())
         it = ctypes.c_int32()
         self._check(lib().tdbem_step(self._h, _ptr(J), ctypes.byref(it)))
         return J, int(it.value)
 
     def step_v(self, V, J_out=None):
         V = np.ascontiguousarray(V, dtype=np.float64)
+        if V.size != self.R * self.ne:
+            raise ValueError("V must hold n_rhs * ne values")
         it = ctypes.c_int32()
         self._check(lib().tdbem_step_v(self._h, _ptr(V), _ptr(J_out), ctypes.byref(it)))
         return int(it.value)
@@ -197,7 +209,7 @@ class Solver:
 
     def march(self, n_steps: int, out=None) -> np.ndarray:
         if out is None:
-            out = np.zeros((n_steps, self.ne))
+            out = np.zeros(self._vshape(n_steps))
         self._check(lib().tdbem_march(self._h, int(n_steps), _ptr(out)))
         return out
 

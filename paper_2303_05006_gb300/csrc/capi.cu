@@ -96,12 +96,13 @@ static tdbem_status finish_create(tdbem_ctx* c) {
   int32_t L = 8;
   while (L < need) L <<= 1;
   c->L = L;
-  if ((s = c->dalloc(&c->d_Jring, c->ne * (int64_t)L)) || (s = c->dalloc(&c->d_R, c->ne)) ||
-      (s = c->dalloc(&c->d_J, c->ne)) || (s = c->dalloc(&c->d_pulse, 10)))
+  const int64_t NR = c->ne * (int64_t)c->R;
+  if ((s = c->dalloc(&c->d_Jring, NR * L)) || (s = c->dalloc(&c->d_R, NR)) || (s = c->dalloc(&c->d_J, NR)) ||
+      (s = c->dalloc(&c->d_pulse, 10 * (int64_t)c->R)) || (c->R > 1 && (s = c->dalloc(&c->d_stage, NR))))
     return s;
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, c->ne * (int64_t)L * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, c->ne * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * L * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, NR * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 8 * sizeof(int32_t), c->stream));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -118,7 +119,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
     tdbem_default_params(&p);
   if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
-      !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs != 1 ||
+      !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
+      p.n_rhs > TDBEM_MAX_RHS ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -127,6 +129,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
   c->p = p;
   c->dt = dt;
   c->Nt = Nt;
+  c->R = p.n_rhs;
+  c->pulse.assign(10 * (size_t)c->R, 0.0);
   fill_phys(c);
   cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -176,12 +180,13 @@ tdbem_status tdbem_set_stream(tdbem_ctx* c, void* stream) {
 }
 
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* pulse) {
-  if (!c || !pulse || rhs != 0) return TDBEM_EINVAL;
+  if (!c || !pulse || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
   if (!(pulse[7] > 0)) return TDBEM_EINVAL;
-  std::memcpy(c->pulse, pulse, sizeof(c->pulse));
-  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse, c->pulse, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  double* hp = c->pulse.data() + 10 * (size_t)rhs;
+  std::memcpy(hp, pulse, 10 * sizeof(double));
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse + 10 * rhs, hp, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   cudaEvent_t e = c->prof_begin(0);
-  tdbem_status s = tdbem_incident_table(c);
+  tdbem_status s = tdbem_incident_table(c, rhs);
   c->prof_end(0, e);
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -189,12 +194,64 @@ tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* p
   return TDBEM_OK;
 }
 
+// y[i*R + r] = x[i] for i < n (one column of an [n][R] array)
+__global__ void k_put_column(const double* x, int64_t n, int32_t R, int32_t r, double* y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i * R + r] = x[i];
+}
+
+// [ne][R] (device layout) -> [R][ne] (host layout) and back
+__global__ void k_to_host_layout(const double* x, int64_t ne, int32_t R, double* y) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne * R) return;
+  int64_t i = t / R;
+  int32_t r = (int32_t)(t - i * R);
+  y[(int64_t)r * ne + i] = x[t];
+}
+
+__global__ void k_from_host_layout(const double* y, int64_t ne, int32_t R, double* x) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne * R) return;
+  int64_t i = t / R;
+  int32_t r = (int32_t)(t - i * R);
+  x[t] = y[(int64_t)r * ne + i];
+}
+
+static tdbem_status to_host_layout(tdbem_ctx* c, const double* x, double* y) {
+  const int64_t n = c->ne * (int64_t)c->R;
+  k_to_host_layout<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(x, c->ne, c->R, y);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+static tdbem_status from_host_layout(tdbem_ctx* c, const double* y, double* x) {
+  const int64_t n = c->ne * (int64_t)c->R;
+  k_from_host_layout<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(y, c->ne, c->R, x);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
 tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
-  if (!c || !V || rhs != 0) return TDBEM_EINVAL;
+  if (!c || !V || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
   tdbem_status s;
   const int64_t n = (int64_t)(c->Nt - 1) * c->ne;
-  if (!c->d_Vall && (s = c->dalloc(&c->d_Vall, n))) return s;
-  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_Vall, V, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (!c->d_Vall) {
+    if ((s = c->dalloc(&c->d_Vall, n * c->R))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Vall, 0, n * c->R * sizeof(double), c->stream));
+  }
+  if (c->R == 1) {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_Vall, V, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    double* tmp = nullptr;
+    TDBEM_CUDA_TRY(c, cudaMallocAsync(&tmp, n * sizeof(double), c->stream));
+    cudaError_t e = cudaMemcpyAsync(tmp, V, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+      k_put_column<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(tmp, n, c->R, rhs, c->d_Vall);
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(tmp, c->stream);
+    TDBEM_CUDA_TRY(c, e);
+  }
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -211,10 +268,12 @@ static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bo
   return s;
 }
 
-// ring[j*L + slot] = x[j]
-__global__ void k_ring_put(const double* x, int64_t ne, int32_t L, int32_t slot, double* ring) {
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j < ne) ring[j * L + slot] = x[j];
+// ring[(j*L + slot)*R + r] = x[r*ne + j] (x in the host layout [R][ne])
+__global__ void k_ring_put(const double* x, int64_t ne, int32_t R, int32_t L, int32_t slot, double* ring) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne * R) return;
+  int64_t r = t / ne, j = t - r * ne;
+  ring[(j * L + slot) * R + r] = x[t];
 }
 
 // Fast-mode history evaluation: the far field of target alpha-1 depends on
@@ -223,19 +282,21 @@ __global__ void k_ring_put(const double* x, int64_t ne, int32_t L, int32_t slot,
 // step at a time exactly as the march does.
 static tdbem_status fast_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist,
                                       double* d_ring, double* d_buf) {
-  const int64_t ne = c->ne;
+  const int64_t NR = c->ne * (int64_t)c->R;
   tdbem_status s = tdbem_fast_eval_reset(c);
   if (s) return s;
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_ring, 0, ne * (int64_t)c->L * sizeof(double), c->stream));
-  for (int32_t a = 1; a <= alpha - 1; ++a) {
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_ring, 0, NR * c->L * sizeof(double), c->stream));
+  // an empty history leaves every moment zero: nothing to replay
+  const int32_t a_last = n_hist > 0 ? alpha - 1 : 0;
+  for (int32_t a = 1; a <= a_last; ++a) {
     int32_t b = a - 1;  // J^{a-1} becomes known after step a
     if (b < n_hist) {
-      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(d_buf, J_hist + (int64_t)b * ne, ne * sizeof(double), cudaMemcpyHostToDevice,
+      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(d_buf, J_hist + (int64_t)b * NR, NR * sizeof(double), cudaMemcpyHostToDevice,
                                         c->stream));
     } else {
-      TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_buf, 0, ne * sizeof(double), c->stream));
+      TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_buf, 0, NR * sizeof(double), c->stream));
     }
-    k_ring_put<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(d_buf, ne, c->L, b & (c->L - 1), d_ring);
+    k_ring_put<<<(unsigned)((NR + 255) / 256), 256, 0, c->stream>>>(d_buf, c->ne, c->R, c->L, b & (c->L - 1), d_ring);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     // the march consumes (clears) the far slot of target a-1 at step a
     if ((s = tdbem_fast_consume_eval_slot(c, a))) return s;
@@ -244,25 +305,49 @@ static tdbem_status fast_history_eval(tdbem_ctx* c, int32_t alpha, const double*
   return eval_R(c, alpha, d_ring, false, true);
 }
 
+// Copy the device right-hand side d_R ([ne][R]) to the caller's [R][ne] array.
+static cudaError_t copy_out(tdbem_ctx* c, const double* d_x, double* h_out) {
+  const int64_t NR = c->ne * (int64_t)c->R;
+  if (c->R > 1) {
+    if (to_host_layout(c, d_x, c->d_stage)) return cudaErrorLaunchFailure;
+    d_x = c->d_stage;
+  }
+  return cudaMemcpyAsync(h_out, d_x, NR * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+}
+
+__global__ void k_stage_to_ring(const double* staged, int32_t b0, int32_t nb, int64_t ne, int32_t R, int32_t L,
+                                double* ring);
+
 tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_hist, int32_t n_hist, double* R_out) {
   if (!c || !R_out || alpha < 1 || alpha > c->Nt - 1 || n_hist < 0 || (n_hist > 0 && !J_hist)) return TDBEM_EINVAL;
-  const int64_t ne = c->ne;
+  const int64_t NR = c->ne * (int64_t)c->R;
   const int32_t L = c->L;
-  std::vector<double> ring((size_t)ne * L, 0.0);
-  for (int32_t b = std::max(0, alpha - c->max_lag); b <= alpha - 2 && b < n_hist; ++b)
-    for (int64_t j = 0; j < ne; ++j) ring[(size_t)j * L + (b & (L - 1))] = J_hist[(int64_t)b * ne + j];
+  // steps of the history that reach step alpha: b0 .. b1
+  const int32_t b0 = std::max(0, alpha - c->max_lag);
+  const int32_t b1 = std::min(alpha - 2, n_hist - 1);
+  const int32_t nb = b1 >= b0 ? b1 - b0 + 1 : 0;
+  const int64_t nstage = c->p.mode == TDBEM_FAST ? NR : (int64_t)nb * NR;
   double* d_ring = nullptr;
-  TDBEM_CUDA_TRY(c, cudaMallocAsync(&d_ring, (ring.size() + ne) * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMallocAsync(&d_ring, (NR * L + std::max<int64_t>(nstage, 1)) * sizeof(double), c->stream));
+  double* d_stage = d_ring + NR * L;
   cudaError_t e = cudaSuccess;
   tdbem_status s = TDBEM_OK;
   if (c->p.mode == TDBEM_FAST) {
-    s = fast_history_eval(c, alpha, J_hist, n_hist, d_ring, d_ring + ring.size());
+    s = fast_history_eval(c, alpha, J_hist, n_hist, d_ring, d_stage);
   } else {
-    e = cudaMemcpyAsync(d_ring, ring.data(), ring.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    e = cudaMemsetAsync(d_ring, 0, NR * L * sizeof(double), c->stream);
+    if (e == cudaSuccess && nb > 0) {
+      e = cudaMemcpyAsync(d_stage, J_hist + (int64_t)b0 * NR, nstage * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream);
+      if (e == cudaSuccess) {
+        k_stage_to_ring<<<(unsigned)((nstage + 255) / 256), 256, 0, c->stream>>>(d_stage, b0, nb, c->ne, c->R, L,
+                                                                                 d_ring);
+        e = cudaGetLastError();
+      }
+    }
     if (e == cudaSuccess) s = eval_R(c, alpha, d_ring);
   }
-  if (e == cudaSuccess && !s)
-    e = cudaMemcpyAsync(R_out, c->d_R, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !s) e = copy_out(c, c->d_R, R_out);
   cudaFreeAsync(d_ring, c->stream);
   cudaError_t e2 = cudaStreamSynchronize(c->stream);
   if (s) return s;
@@ -278,13 +363,14 @@ tdbem_status tdbem_history_eval(tdbem_ctx* c, int32_t alpha, const double* J_his
 // device array instead of a per-call allocation.
 static __device__ __align__(256) double g_noalloc_scratch[TDBEM_NOALLOC_SCRATCH_DOUBLES];
 
-// ring[j*L + (b mod L)] = staged[(b - b0)*ne + j] for b = b0 .. b0+nb-1
-__global__ void k_stage_to_ring(const double* staged, int32_t b0, int32_t nb, int64_t ne, int32_t L, double* ring) {
+// ring[(j*L + (b mod L))*R + r] = staged[((b - b0)*R + r)*ne + j] for b = b0 .. b0+nb-1
+__global__ void k_stage_to_ring(const double* staged, int32_t b0, int32_t nb, int64_t ne, int32_t R, int32_t L,
+                                double* ring) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nb * ne) return;
-  int32_t k = (int32_t)(t / ne);
-  int64_t j = t % ne;
-  ring[j * L + ((b0 + k) & (L - 1))] = staged[t];
+  if (t >= (int64_t)nb * R * ne) return;
+  int64_t kr = t / ne, j = t - kr * ne;
+  int32_t k = (int32_t)(kr / R), r = (int32_t)(kr - (int64_t)k * R);
+  ring[(j * L + ((b0 + k) & (L - 1))) * R + r] = staged[t];
 }
 
 namespace {
@@ -300,13 +386,13 @@ extern "C" tdbem_status tdbem_history_eval_noalloc(tdbem_ctx* c, int32_t alpha, 
     c->set_error("history_eval_noalloc: direct mode only");
     return TDBEM_EINVAL;
   }
-  const int64_t ne = c->ne;
+  const int64_t ne = c->ne, NR = ne * c->R;
   const int32_t L = c->L;
   const int32_t b0 = std::max(0, alpha - c->max_lag);
   const int32_t b1 = std::min(alpha - 2, n_hist - 1);
   const int32_t nb = b1 >= b0 ? b1 - b0 + 1 : 0;
-  if (ne * (int64_t)L + (int64_t)nb * ne > (int64_t)TDBEM_NOALLOC_SCRATCH_DOUBLES) {
-    c->set_error("history_eval_noalloc: problem needs " + std::to_string(ne * (int64_t)L + (int64_t)nb * ne) +
+  if (NR * L + (int64_t)nb * NR > (int64_t)TDBEM_NOALLOC_SCRATCH_DOUBLES) {
+    c->set_error("history_eval_noalloc: problem needs " + std::to_string(NR * L + (int64_t)nb * NR) +
                  " doubles of scratch, more than TDBEM_NOALLOC_SCRATCH_DOUBLES");
     return TDBEM_EINVAL;
   }
@@ -331,18 +417,18 @@ extern "C" tdbem_status tdbem_history_eval_noalloc(tdbem_ctx* c, int32_t alpha, 
     scratch = g_noalloc_ptr[dev];
   }
   double* ring = scratch;
-  double* staged = scratch + ne * (int64_t)L;
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(ring, 0, ne * (int64_t)L * sizeof(double), c->stream));
+  double* staged = scratch + NR * L;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(ring, 0, NR * L * sizeof(double), c->stream));
   if (nb > 0) {
-    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(staged, J_hist + (int64_t)b0 * ne, (int64_t)nb * ne * sizeof(double),
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(staged, J_hist + (int64_t)b0 * NR, (int64_t)nb * NR * sizeof(double),
                                       cudaMemcpyHostToDevice, c->stream));
-    int64_t n = (int64_t)nb * ne;
-    k_stage_to_ring<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(staged, b0, nb, ne, L, ring);
+    int64_t n = (int64_t)nb * NR;
+    k_stage_to_ring<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(staged, b0, nb, ne, c->R, L, ring);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
   }
   tdbem_status s = eval_R(c, alpha, ring);
   if (s) return s;
-  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(R_out, c->d_R, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, copy_out(c, c->d_R, R_out));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -369,7 +455,7 @@ tdbem_status tdbem_step(tdbem_ctx* c, double* J_out, int32_t* iters) {
   if (s) return s;
   int32_t h[2];
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-  if (J_out) TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_out, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (J_out) TDBEM_CUDA_TRY(c, copy_out(c, c->d_J, J_out));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (iters) *iters = h[0];
   c->total_iters += h[0];
@@ -383,12 +469,19 @@ tdbem_status tdbem_step(tdbem_ctx* c, double* J_out, int32_t* iters) {
 
 tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t* iters) {
   if (!c || !V) return TDBEM_EINVAL;
-  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, V, c->ne * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const int64_t NR = c->ne * (int64_t)c->R;
+  if (c->R == 1) {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, V, NR * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, V, NR * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    tdbem_status s0 = from_host_layout(c, c->d_stage, c->d_R);
+    if (s0) return s0;
+  }
   tdbem_status s = step_async(c, true);
   if (s) return s;
   int32_t h[2];
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-  if (J_out) TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_out, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (J_out) TDBEM_CUDA_TRY(c, copy_out(c, c->d_J, J_out));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (iters) *iters = h[0];
   c->total_iters += h[0];
@@ -447,9 +540,7 @@ tdbem_status tdbem_march(tdbem_ctx* c, int32_t n_steps, double* J_all) {
   for (int32_t k = 0; k < n_steps; ++k) {
     tdbem_status s = step_async(c);
     if (s) return s;
-    if (J_all)
-      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_all + (int64_t)k * c->ne, c->d_J, c->ne * sizeof(double),
-                                        cudaMemcpyDeviceToHost, c->stream));
+    if (J_all) TDBEM_CUDA_TRY(c, copy_out(c, c->d_J, J_all + (int64_t)k * c->ne * c->R));
   }
   return check_misses(c);
 }
@@ -459,18 +550,24 @@ tdbem_status tdbem_march_dev(tdbem_ctx* c, int32_t n_steps, double* J_all_dev) {
   for (int32_t k = 0; k < n_steps; ++k) {
     tdbem_status s = step_async(c);
     if (s) return s;
-    if (J_all_dev)
-      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(J_all_dev + (int64_t)k * c->ne, c->d_J, c->ne * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, c->stream));
+    if (J_all_dev) {
+      double* dst = J_all_dev + (int64_t)k * c->ne * c->R;
+      if (c->R == 1) {
+        TDBEM_CUDA_TRY(c, cudaMemcpyAsync(dst, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      } else if ((s = to_host_layout(c, c->d_J, dst))) {
+        return s;
+      }
+    }
   }
   return check_misses(c);
 }
 
 tdbem_status tdbem_reset(tdbem_ctx* c) {
   if (!c) return TDBEM_EINVAL;
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, c->ne * (int64_t)c->L * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, c->ne * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int32_t), c->stream));
+  const int64_t NR = c->ne * (int64_t)c->R;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * c->L * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, NR * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 8 * sizeof(int32_t), c->stream));
   if (c->p.mode == TDBEM_FAST) {
     tdbem_status s = tdbem_fast_reset(c);
     if (s) return s;

@@ -304,13 +304,14 @@ __global__ void k_csr_windows(TriGeom g, const int32_t* et, const int64_t* row_p
 // ---------------------------------------------------------------------------
 // Incident right-hand side V_i^{alpha-1} (eq. v_i) for a modulated Gaussian
 // plane wave; one thread per edge, 2 triangles x 7 points, FP64.
-// grid: (edge blocks, steps); V[(alpha-1)*ne + i] for alpha = alpha0 .. alpha0+gridDim.y-1
+// grid: (edge blocks, steps); right-hand side r of R:
+// V[((alpha-alpha0)*ne + i)*R + r] for alpha = alpha0 .. alpha0+gridDim.y-1
 __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, const double* pulse, int32_t alpha0,
-                            double* V) {
+                            int32_t R, int32_t r, double* V) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ne) return;
   const int32_t alpha = alpha0 + blockIdx.y;
-  double* R = V + (int64_t)(alpha - alpha0) * ne;
+  double* Rv = V + (int64_t)(alpha - alpha0) * ne * R;
   const double PI = 3.14159265358979323846;
   double kv[3] = {pulse[0], pulse[1], pulse[2]}, pol[3] = {pulse[3], pulse[4], pulse[5]};
   double f0 = pulse[6], sg = pulse[7], t0 = pulse[8], zmin = pulse[9];
@@ -348,7 +349,7 @@ __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, c
       sum += ph.qw[q] * A * val;
     }
   }
-  R[i] = sum;
+  Rv[i * R + r] = sum;
 }
 
 // R_i = V_i - sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m} (V may be
@@ -378,6 +379,51 @@ __global__ void __launch_bounds__(256) k_direct_history(const int16_t* m_lo, con
     s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) R[i] = (V ? V[i] : 0.0) - s;
+  }
+}
+
+// Batched form of k_direct_history for R right-hand sides ([..][ne][R]
+// layouts): one block per row; the block's threads are split into groups of
+// RL lanes (RL = R rounded up to a power of two, at most 32), lane rr of a
+// group takes the right-hand sides rr, rr+RL, ... and the groups take
+// interleaved columns j, so each coefficient is read once per group and
+// broadcast to its lanes while the history vectors are read contiguously.
+__global__ void __launch_bounds__(256) k_direct_history_multi(const int16_t* m_lo, const uint8_t* nlag,
+                                                             const int64_t* off, const double* val, int64_t ne,
+                                                             const double* ring, int32_t L, int32_t alpha,
+                                                             int32_t R, int32_t RL, const double* V, double* Rout) {
+  __shared__ double red[8][32];
+  const int64_t i = blockIdx.x;
+  const int rr = threadIdx.x % RL, sub = threadIdx.x / RL, nsub = blockDim.x / RL;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r0 = 0; r0 < R; r0 += RL) {
+    const int r = r0 + rr;
+    double s = 0.0;
+    if (r < R) {
+      for (int64_t j = sub; j < ne; j += nsub) {
+        int64_t p = i * ne + j;
+        int lo = m_lo[p], n = nlag[p];
+        const double* z = val + off[p];
+        const double* Jr = ring + j * L * R + r;
+        for (int w = 0; w < n; ++w) {
+          int m = lo + w;
+          int b = alpha - m;
+          if (m < 2 || b < 0) continue;
+          s += __ldg(z + w) * Jr[(int64_t)(b & (L - 1)) * R];
+        }
+      }
+    }
+    // lanes rr, rr+RL, ... of a warp hold partial sums of the same r
+    for (int o = 16; o >= RL; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane < RL) red[warp][lane] = s;
+    __syncthreads();
+    if (threadIdx.x < RL && r0 + threadIdx.x < R) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+      int64_t q = i * R + r0 + threadIdx.x;
+      Rout[q] = (V ? V[q] : 0.0) - t;
+    }
+    __syncthreads();
   }
 }
 
@@ -451,32 +497,45 @@ tdbem_status tdbem_build_direct(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_incident_table(tdbem_ctx* c) {
+// Incident field of right-hand side r at every step into column r of the
+// table (the other columns are kept; a column never set stays zero).
+tdbem_status tdbem_incident_table(tdbem_ctx* c, int32_t r) {
   const int64_t ne = c->ne;
-  const int64_t n = (int64_t)(c->Nt - 1) * ne;
+  const int64_t n = (int64_t)(c->Nt - 1) * ne * c->R;
   tdbem_status s;
-  if (!c->d_Vtab && (s = c->dalloc(&c->d_Vtab, n))) return s;
+  if (!c->d_Vtab) {
+    if ((s = c->dalloc(&c->d_Vtab, n))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Vtab, 0, n * sizeof(double), c->stream));
+  }
   const int32_t chunk = 1024;  // steps per launch (grid.y limit)
   for (int32_t a0 = 1; a0 <= c->Nt - 1; a0 += chunk) {
     int32_t na = std::min(chunk, c->Nt - a0);
     dim3 grid((unsigned)((ne + 127) / 128), (unsigned)na);
-    k_rhs_plane<<<grid, 128, 0, c->stream>>>(c->tg, c->phys, c->d_et, ne, c->d_pulse, a0,
-                                              c->d_Vtab + (int64_t)(a0 - 1) * ne);
+    k_rhs_plane<<<grid, 128, 0, c->stream>>>(c->tg, c->phys, c->d_et, ne, c->d_pulse + 10 * r, a0, c->R, r,
+                                              c->d_Vtab + (int64_t)(a0 - 1) * ne * c->R);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
   }
   return TDBEM_OK;
 }
 
 const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
-  if (c->d_Vall) return c->d_Vall + (int64_t)(alpha - 1) * c->ne;
-  if (c->have_pulse && c->d_Vtab) return c->d_Vtab + (int64_t)(alpha - 1) * c->ne;
+  const int64_t stride = c->ne * (int64_t)c->R;
+  if (c->d_Vall) return c->d_Vall + (int64_t)(alpha - 1) * stride;
+  if (c->have_pulse && c->d_Vtab) return c->d_Vtab + (int64_t)(alpha - 1) * stride;
   return nullptr;
 }
 
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V) {
   const PairStore& st = c->direct;
-  k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
-                                                           alpha, V, c->d_R);
+  if (c->R == 1) {
+    k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
+                                                             alpha, V, c->d_R);
+  } else {
+    int RL = 1;
+    while (RL < c->R && RL < 32) RL <<= 1;
+    k_direct_history_multi<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring,
+                                                                   c->L, alpha, c->R, RL, V, c->d_R);
+  }
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }

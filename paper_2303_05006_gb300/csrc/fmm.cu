@@ -74,6 +74,7 @@ struct FmmLevel {
   int32_t* d_pS = nullptr;
   int16_t* d_psym = nullptr;
   float* ops = nullptr;           // [nop][2][P][P]
+  uint4* ops_img = nullptr;       // the same in tensor-core shared-memory images (tensor-core M2L only)
   int nop = 0;
   int4* d_gemm = nullptr;         // {op index, pair base, npairs, kind | q << 8 | qhi << 16}
   int ngemm = 0;
@@ -252,9 +253,10 @@ __global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, 
 // contracted with the time factors, then with the W table.
 __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
                       const TriGeom g, const float* W, const float* tsrc, const double* ring, int L, int p, int pt,
-                      int M, int k, float* mom) {
+                      int M, int k, float* mom, int R) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt;
+  const int rhs = blockIdx.y;  // right-hand side of this block
   int cell = leaf_cells[blockIdx.x];
   int tb = tri_b[cell], te_ = tri_e[cell];
   int ntk = 3 * (te_ - tb);
@@ -264,7 +266,7 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
   for (int e = threadIdx.x; e < ntk; e += blockDim.x) {
     int t = perm[tb + e / 3], kk = e % 3;
     int j = g.edge[3 * t + kk];
-    const double* Jr = ring + (int64_t)j * L;
+    const double* Jr = ring + (int64_t)j * L * R + rhs;
     double acc[2][8];
     for (int v = 0; v < 2; ++v)
       for (int n = 0; n < pt; ++n) acc[v][n] = 0.0;
@@ -274,7 +276,7 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
       for (int kap = 0; kap <= 3; ++kap) {
         int b = gam - kap;
         if (b < 0) continue;
-        double jv = w4[kap] * Jr[b & (L - 1)];
+        double jv = w4[kap] * Jr[(int64_t)(b & (L - 1)) * R];
         full += jv;
         if (kap <= i) trunc += jv;
       }
@@ -287,7 +289,8 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
       for (int n = 0; n < pt; ++n) jt[(e * 2 + v) * pt + n] = (float)acc[v][n];
   }
   __syncthreads();
-  float* out = mom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
+  float* out = mom + (((int64_t)cell * 2 + (k & 1)) * 2 * R + rhs) * kNC * P;  // variant stride R kNC P
+  const int64_t vstr = (int64_t)R * kNC * P;
   for (int e = threadIdx.x; e < kNC * PS; e += blockDim.x) {
     int c = e / PS, b = e % PS;
     float a0[8], a1[8];
@@ -301,8 +304,8 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
       }
     }
     for (int n = 0; n < pt; ++n) {
-      out[(0 * kNC + c) * P + b * pt + n] = a0[n];
-      out[(1 * kNC + c) * P + b * pt + n] = a1[n];
+      out[(int64_t)c * P + b * pt + n] = a0[n];
+      out[vstr + (int64_t)c * P + b * pt + n] = a1[n];
     }
   }
 }
@@ -311,10 +314,11 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
 // (slot 0) and 2k+1 (slot 1); the truncated parent set takes the truncated
 // set of child interval 2k and the full set of 2k+1.
 __global__ void k_m2m(const int32_t* cells, const int32_t* child, const float* Sx /*[2][p][p]*/, const float* St,
-                      int p, int pt, int k, const float* cmom, float* pmom) {
+                      int p, int pt, int k, const float* cmom, float* pmom, int R) {
   const int PS = p * p * p, P = PS * pt;
+  const int rhs = blockIdx.y;
   int cell = cells[blockIdx.x];
-  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
+  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * R * kNC * P;
   for (int e = threadIdx.x; e < 2 * kNC * P; e += blockDim.x) {
     int var = e / (kNC * P), r = e % (kNC * P);
     int c = r / P, bn = r % P;
@@ -327,7 +331,7 @@ __global__ void k_m2m(const int32_t* cells, const int32_t* child, const float* S
       int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
       for (int h = 0; h < 2; ++h) {
         int cvar = (var == 1 && h == 0) ? 1 : 0;
-        const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * kNC * P + ((int64_t)cvar * kNC + c) * P;
+        const float* src = cmom + ((((int64_t)ch * 2 + h) * 2 + cvar) * R + rhs) * kNC * P + (int64_t)c * P;
         for (int n2 = 0; n2 < pt; ++n2) {
           float tt = St[(h * pt + n) * pt + n2];
           if (tt == 0.f) continue;
@@ -342,7 +346,7 @@ __global__ void k_m2m(const int32_t* cells, const int32_t* child, const float* S
         }
       }
     }
-    out[(int64_t)var * kNC * P + c * P + bn] = s;
+    out[((int64_t)var * R + rhs) * kNC * P + c * P + bn] = s;
   }
 }
 
@@ -369,9 +373,11 @@ __device__ __forceinline__ void contract_axis(const float* in, float* out, const
 // components x full/truncated) are interpolated one axis at a time and
 // accumulated into the parent moments of source interval k.
 __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
-                           int k, const float* cmom, float* pmom) {
+                           int k, const float* cmom, float* pmom, int R) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt, nch = 2 * kNC;
+  const int rhs = blockIdx.y;
+  const int64_t vstr = (int64_t)R * kNC * P;  // stride of the full/truncated variant
   float* b0 = sm;
   float* b1 = sm + nch * P;
   float* acc = sm + 2 * nch * P;
@@ -382,12 +388,12 @@ __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const flo
     if (ch < 0) continue;
     int sx = (o >> 2) & 1, sy = (o >> 1) & 1, sz = o & 1;
     for (int h = 0; h < 2; ++h) {
-      const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * kNC * P;
+      const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * vstr + (int64_t)rhs * kNC * P;
       __syncthreads();
       for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
         int var = e / (kNC * P), r = e % (kNC * P);
         int cvar = (var == 1 && h == 0) ? 1 : 0;  // truncated parent = truncated first half + full second half
-        b0[e] = src[(int64_t)cvar * kNC * P + r];
+        b0[e] = src[(int64_t)cvar * vstr + r];
       }
       __syncthreads();
       contract_axis(b0, b1, St + h * pt * pt, false, 3, p, pt, nch);
@@ -398,22 +404,26 @@ __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const flo
     }
   }
   __syncthreads();
-  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * kNC * P;
-  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) out[e] = acc[e];
+  float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * vstr + (int64_t)rhs * kNC * P;
+  for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
+    int var = e / (kNC * P), r = e % (kNC * P);
+    out[(int64_t)var * vstr + r] = acc[e];
+  }
 }
 
 // L2L, factorised (transposed interpolation): the parent's local coefficients
 // of interval k+1 are evaluated at each child's nodes for the child intervals
 // 2(k+1) and 2(k+1)+1 and added there; the parent slot is then cleared.
 __global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
-                           int k, float* ploc, int Qp, float* cloc, int Qc) {
+                           int k, float* ploc, int Qp, float* cloc, int Qc, int R) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt, nch = kNC;
+  const int rhs = blockIdx.y;
   float* b0 = sm;
   float* b1 = sm + nch * P;
   float* par = sm + 2 * nch * P;
   int cell = cells[blockIdx.x];
-  float* src = ploc + ((int64_t)cell * Qp + ((k + 1) % Qp)) * kNC * P;
+  float* src = ploc + (((int64_t)cell * Qp + ((k + 1) % Qp)) * R + rhs) * kNC * P;
   for (int e = threadIdx.x; e < nch * P; e += blockDim.x) par[e] = src[e];
   for (int o = 0; o < 8; ++o) {
     int ch = child[cell * 8 + o];
@@ -426,7 +436,7 @@ __global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const flo
       contract_axis(b1, b0, Sx + sy * p * p, true, 1, p, pt, nch);
       contract_axis(b0, b1, Sx + sx * p * p, true, 0, p, pt, nch);
       int slot = (2 * (k + 1) + h) % Qc;
-      float* dst = cloc + ((int64_t)ch * Qc + slot) * kNC * P;
+      float* dst = cloc + (((int64_t)ch * Qc + slot) * R + rhs) * kNC * P;
       for (int e = threadIdx.x; e < nch * P; e += blockDim.x) dst[e] += b1[e];
     }
   }
@@ -440,7 +450,8 @@ __global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const flo
 // local coefficients of interval k+q.  Tile 64 x 64, 256 threads, 4 x 4 each.
 __global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* tiles, const float* ops, int P, int pt,
                                                   int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                                                  const int16_t* smap, const float* mom, int k, float* loc, int Q) {
+                                                  const int16_t* smap, const float* mom, int k, float* loc, int Q,
+                                                  int R) {
   __shared__ float As[16][64 + 4];
   __shared__ float Bs[16][64 + 4];
   int4 tl = tiles[blockIdx.x];
@@ -450,7 +461,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* 
   const int var = (q == qhi) ? 1 : 0;
   const float* A = ops + ((int64_t)gd.x * 2 + (kind == 0 ? 0 : 1)) * P * P;
   const int row0 = tl.y * 64, col0 = tl.z * 64;
-  const int ncol = gd.z * nk;
+  const int ncol = gd.z * nk * R;  // columns (pair, right-hand side, component)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[4][4] = {};
   // column descriptors of this thread's B loads (column = threadIdx.x & 63)
@@ -459,8 +470,8 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* 
   const float* bsrc = nullptr;
   const int16_t* bmap = nullptr;
   if (gcol < ncol) {
-    int pr = gd.y + gcol / nk, c = c0 + gcol % nk;
-    bsrc = mom + ((int64_t)pS[pr] * 2 + (k & 1)) * 2 * kNC * P + ((int64_t)var * kNC + c) * P;
+    int pr = gd.y + gcol / (nk * R), rem = gcol % (nk * R), rhs = rem / nk, c = c0 + rem % nk;
+    bsrc = mom + (((((int64_t)pS[pr] * 2 + (k & 1)) * 2 + var) * R + rhs) * kNC + c) * P;
     bmap = smap + (int64_t)psym[pr] * PS;
   }
   for (int k0 = 0; k0 < P; k0 += 16) {
@@ -495,9 +506,9 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* 
   for (int j = 0; j < 4; ++j) {
     int gc = col0 + tx * 4 + j;
     if (gc >= ncol) continue;
-    int pr = gd.y + gc / nk, c = c0 + gc % nk;
+    int pr = gd.y + gc / (nk * R), rem = gc % (nk * R), rhs = rem / nk, c = c0 + rem % nk;
     const int16_t* map = smap + (int64_t)psym[pr] * PS;
-    float* dst = loc + ((int64_t)pO[pr] * Q + ((k + q) % Q)) * kNC * P + (int64_t)c * P;
+    float* dst = loc + ((((int64_t)pO[pr] * Q + ((k + q) % Q)) * R + rhs) * kNC + c) * P;
     for (int i = 0; i < 4; ++i) {
       int row = row0 + ty * 4 + i;
       if (row >= P) continue;
@@ -510,10 +521,11 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const int4* gemm, const int4* 
 // L2L: children's local coefficients of intervals 2(k+1), 2(k+1)+1 from the
 // parent's (interval k+1); then the parent slot is cleared.
 __global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
-                      int k, float* ploc, int Qp, float* cloc, int Qc) {
+                      int k, float* ploc, int Qp, float* cloc, int Qc, int R) {
   const int PS = p * p * p, P = PS * pt;
+  const int rhs = blockIdx.y;
   int cell = cells[blockIdx.x];
-  float* src = ploc + ((int64_t)cell * Qp + ((k + 1) % Qp)) * kNC * P;
+  float* src = ploc + (((int64_t)cell * Qp + ((k + 1) % Qp)) * R + rhs) * kNC * P;
   for (int o = 0; o < 8; ++o) {
     int ch = child[cell * 8 + o];
     if (ch < 0) continue;
@@ -538,7 +550,7 @@ __global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* S
         }
       }
       int slot = (2 * (k + 1) + h) % Qc;
-      cloc[((int64_t)ch * Qc + slot) * kNC * P + (int64_t)c * P + an] += acc;
+      cloc[(((int64_t)ch * Qc + slot) * R + rhs) * kNC * P + (int64_t)c * P + an] += acc;
     }
   }
   __syncthreads();
@@ -550,11 +562,12 @@ __global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* S
 // the local-coefficient slot is cleared afterwards.
 __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
                       const TriGeom g, const float* T, const float* ttgt, int p, int pt, int M, int k, float* loc,
-                      int Q, double* Rfar, int Lr, int64_t ne) {
+                      int Q, double* Rfar, int Lr, int64_t ne, int R) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt;
+  const int rhs = blockIdx.y;
   int cell = leaf_cells[blockIdx.x];
-  float* L = loc + ((int64_t)cell * Q + ((k + 1) % Q)) * kNC * P;
+  float* L = loc + (((int64_t)cell * Q + ((k + 1) % Q)) * R + rhs) * kNC * P;
   float* Le = sm;  // [M][kNC][PS]
   for (int e = threadIdx.x; e < M * kNC * PS; e += blockDim.x) {
     int i = e / (kNC * PS), r = e % (kNC * PS);
@@ -575,7 +588,7 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
     float s = 0.f;
     for (int r = 0; r < kNC * PS; ++r) s += Tt[r] * le[r];
     int rho = (k + 1) * M + i;
-    atomicAdd(Rfar + (int64_t)(rho & (Lr - 1)) * ne + g.edge[3 * t + kk], -(double)s);
+    atomicAdd(Rfar + ((int64_t)(rho & (Lr - 1)) * ne + g.edge[3 * t + kk]) * R + rhs, -(double)s);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) L[e] = 0.f;
@@ -609,6 +622,49 @@ __global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, co
     double far = Rfar_slot ? Rfar_slot[i] : 0.0;
     R[i] = (V ? V[i] : 0.0) + far - d;
     if (Rfar_slot) Rfar_slot[i] = 0.0;
+  }
+}
+
+// Batched near field (SpMM over R right-hand sides, [..][ne][R] layouts):
+// one warp per row, split into groups of RL lanes (RL = R rounded up to a
+// power of two, at most 32); lane rr of a group takes the right-hand sides
+// rr, rr+RL, ... and the groups take interleaved nonzeros, so a coefficient is
+// read once per group and the history vectors of a (column, lag) are read
+// contiguously.  Products and the lag sum of a pair are FP32; the sum over
+// the row's pairs is FP64 (with fewer lane groups per RHS than the single
+// kernel has lanes, an FP32 row sum would lose accuracy as R grows).
+__global__ void __launch_bounds__(256) k_near_history_multi(const int64_t* row_ptr, const int32_t* col,
+                                                           const int16_t* m_lo, const uint8_t* nlag,
+                                                           const int64_t* off, const float* val, int64_t ne,
+                                                           const double* ring, int L, int alpha, int R, int RL,
+                                                           const double* V, double* Rfar_slot, double* Rout) {
+  int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, rr = lane % RL, sub = lane / RL, nsub = 32 / RL;
+  if (i >= ne) return;
+  for (int r0 = 0; r0 < R; r0 += RL) {
+    const int r = r0 + rr;
+    double d = 0.0;  // FP32 lag sum per pair, FP64 across pairs: the error does not grow with R
+    if (r < R) {
+      for (int64_t p = row_ptr[i] + sub; p < row_ptr[i + 1]; p += nsub) {
+        int lo = m_lo[p], n = nlag[p];
+        const float* z = val + off[p];
+        const double* Jr = ring + (int64_t)col[p] * L * R + r;
+        float sp = 0.f;
+        for (int w = 0; w < n; ++w) {
+          int m = lo + w, b = alpha - m;
+          if (m < 2 || b < 0) continue;
+          sp += __ldg(z + w) * (float)Jr[(int64_t)(b & (L - 1)) * R];
+        }
+        d += sp;
+      }
+    }
+    for (int o = 16; o >= RL; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (sub == 0 && r < R) {
+      int64_t q = i * R + r;
+      double far = Rfar_slot ? Rfar_slot[q] : 0.0;
+      Rout[q] = (V ? V[q] : 0.0) + far - d;
+      if (Rfar_slot) Rfar_slot[q] = 0.0;
+    }
   }
 }
 
@@ -994,7 +1050,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         for (int kind = 0; kind < 2; ++kind) {
           int g = (int)gemm.size();
           gemm.push_back(make_int4(op, base, cnt, kind | (q << 8) | (qhi << 16)));
-          int ncol = cnt * (kind == 0 ? 3 : 4);
+          int ncol = cnt * (kind == 0 ? 3 : 4) * c->R;  // columns (pair, right-hand side, component)
           for (int rt = 0; rt < (P + 63) / 64; ++rt)
             for (int ct = 0; ct < (ncol + 63) / 64; ++ct) tiles.push_back(make_int4(g, rt, ct, 0));
           for (int rt = 0; rt < (P + 127) / 128; ++rt)
@@ -1027,15 +1083,17 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       k_m2l_ops<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p, pt, L.ds, L.H, 0.5 * L.M * dt, L.M, dt, cc, a,
                                                                       d_opdesc, L.nop, L.ops);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
+      if (c->p.m2l_prec != TDBEM_P_FP32 && (s = tdbem_m2l_tc_images(c, L.ops, L.nop, P, c->p.m2l_prec, &L.ops_img)))
+        return s;
     }
     // moment and local-coefficient storage (march state and history_eval state)
-    if ((s = c->dalloc(&L.mom, (int64_t)L.ncell * 4 * kNC * P)) ||
-        (s = c->dalloc(&L.loc, (int64_t)L.ncell * L.Q * kNC * P)))
+    const int64_t RP = (int64_t)c->R * kNC * P;  // one cluster's coefficients of all right-hand sides
+    if ((s = c->dalloc(&L.mom, (int64_t)L.ncell * 4 * RP)) || (s = c->dalloc(&L.loc, (int64_t)L.ncell * L.Q * RP)))
       return s;
-    TDBEM_CUDA_TRY(c, cudaMemset(L.mom, 0, (int64_t)L.ncell * 4 * kNC * P * sizeof(float)));
-    TDBEM_CUDA_TRY(c, cudaMemset(L.loc, 0, (int64_t)L.ncell * L.Q * kNC * P * sizeof(float)));
+    TDBEM_CUDA_TRY(c, cudaMemset(L.mom, 0, (int64_t)L.ncell * 4 * RP * sizeof(float)));
+    TDBEM_CUDA_TRY(c, cudaMemset(L.loc, 0, (int64_t)L.ncell * L.Q * RP * sizeof(float)));
     float *me = nullptr, *le = nullptr;
-    if ((s = c->dalloc(&me, (int64_t)L.ncell * 4 * kNC * P)) || (s = c->dalloc(&le, (int64_t)L.ncell * L.Q * kNC * P)))
+    if ((s = c->dalloc(&me, (int64_t)L.ncell * 4 * RP)) || (s = c->dalloc(&le, (int64_t)L.ncell * L.Q * RP)))
       return s;
     F->mom_eval.push_back(me);
     F->loc_eval.push_back(le);
@@ -1107,11 +1165,11 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
   int Lr = 8;
   while (Lr < 2 * Mmax) Lr <<= 1;
   F->Lr = Lr;
-  if ((s = c->dalloc(&F->d_Rfar, (int64_t)Lr * ne)) || (s = c->dalloc(&F->d_Rfar_eval, (int64_t)Lr * ne)) ||
-      (s = c->dalloc(&F->d_err, 1)))
+  const int64_t nrf = (int64_t)Lr * ne * c->R;  // [Lr][ne][R]
+  if ((s = c->dalloc(&F->d_Rfar, nrf)) || (s = c->dalloc(&F->d_Rfar_eval, nrf)) || (s = c->dalloc(&F->d_err, 1)))
     return s;
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_err, 0, sizeof(int32_t)));
-  TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, (int64_t)Lr * ne * sizeof(double)));
+  TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, nrf * sizeof(double)));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -1122,7 +1180,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
 static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, bool eval) {
   FmmPlan* F = c->fmm;
   if (!F || F->lmax < 2) return TDBEM_OK;
-  const int p = F->p, pt = F->pt, PS = F->PS, P = F->P, lmax = F->lmax;
+  const int p = F->p, pt = F->pt, PS = F->PS, P = F->P, lmax = F->lmax, R = c->R;
   auto MOM = [&](int l) { return eval ? F->mom_eval[l - 2] : F->lev[l].mom; };
   auto LOC = [&](int l) { return eval ? F->loc_eval[l - 2] : F->lev[l].loc; };
   double* Rfar = eval ? F->d_Rfar_eval : F->d_Rfar;
@@ -1137,8 +1195,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
         if (L.leaf[i]) maxtri = std::max(maxtri, L.tri_e[i] - L.tri_b[i]);
       size_t smem = (size_t)3 * maxtri * 2 * pt * sizeof(float);
       cudaEvent_t e = c->prof_begin(3);
-      k_p2m<<<L.nleaf, 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg, F->d_W,
-                                                L.d_tsrc, ring, c->L, p, pt, L.M, k, MOM(l));
+      k_p2m<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
+                                                         F->d_W, L.d_tsrc, ring, c->L, p, pt, L.M, k, MOM(l), R);
       c->prof_end(3, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
@@ -1146,11 +1204,12 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       cudaEvent_t e = c->prof_begin(4);
       size_t smem = (size_t)3 * 2 * kNC * P * sizeof(float);
       if (smem <= 227 * 1024)
-        k_m2m_fact<<<L.nnonleaf, 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
-                                                          F->d_St, p, pt, k, MOM(l + 1), MOM(l));
+        k_m2m_fact<<<dim3(L.nnonleaf, R), 512, smem, c->stream>>>(
+            L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k, MOM(l + 1), MOM(l), R);
       else  // large p: direct tensor-product sums from global memory
-        k_m2m<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
-                                                  F->d_St, p, pt, k, MOM(l + 1), MOM(l));
+        k_m2m<<<dim3(L.nnonleaf, R), 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child,
+                                                           F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k,
+                                                           MOM(l + 1), MOM(l), R);
       c->prof_end(4, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
@@ -1164,11 +1223,11 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       cudaEvent_t e = c->prof_begin(5);
       if (c->p.m2l_prec == TDBEM_P_FP32) {
         k_m2l_fp32<<<L.ntiles, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
-                                                     F->d_smap, MOM(l), k, LOC(l), L.Q);
+                                                     F->d_smap, MOM(l), k, LOC(l), L.Q, R);
         TDBEM_CUDA_TRY(c, cudaGetLastError());
       } else {
-        tdbem_status s = tdbem_m2l_tc(c, L.d_gemm, L.d_tiles_tc, L.ntiles_tc, L.ops, P, pt, PS, L.d_pO, L.d_pS,
-                                      L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, c->p.m2l_prec, F->d_err);
+        tdbem_status s = tdbem_m2l_tc(c, L.d_gemm, L.d_tiles_tc, L.ntiles_tc, L.ops_img, P, pt, PS, L.d_pO, L.d_pS,
+                                      L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R, c->p.m2l_prec, F->d_err);
         if (s) return s;
       }
       c->prof_end(5, e);
@@ -1177,20 +1236,22 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       cudaEvent_t e = c->prof_begin(6);
       size_t smem = (size_t)3 * kNC * P * sizeof(float);
       if (smem <= 227 * 1024)
-        k_l2l_fact<<<L.nnonleaf, 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
-                                                          F->d_St, p, pt, k, LOC(l), L.Q, LOC(l + 1),
-                                                          F->lev[l + 1].Q);
+        k_l2l_fact<<<dim3(L.nnonleaf, R), 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child,
+                                                                   F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k,
+                                                                   LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q, R);
       else
-        k_l2l<<<L.nnonleaf, 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p,
-                                                  F->d_St, p, pt, k, LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q);
+        k_l2l<<<dim3(L.nnonleaf, R), 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child,
+                                                           F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k, LOC(l),
+                                                           L.Q, LOC(l + 1), F->lev[l + 1].Q, R);
       c->prof_end(6, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
     if (L.nleaf) {
       size_t smem = (size_t)L.M * kNC * PS * sizeof(float);
       cudaEvent_t e = c->prof_begin(7);
-      k_l2p<<<L.nleaf, 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg, F->d_T,
-                                                L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr, c->ne);
+      k_l2p<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
+                                                         F->d_T, L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr,
+                                                         c->ne, R);
       c->prof_end(7, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
@@ -1201,11 +1262,20 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
 tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring, const double* V, bool eval) {
   FmmPlan* F = c->fmm;
   double* slot = nullptr;
-  if (F->lmax >= 2) slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne;
+  if (F->lmax >= 2)
+    slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R;
   cudaEvent_t e = c->prof_begin(1);
-  k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag,
-                                                                      F->d_off, F->d_val32, c->ne, ring, c->L, alpha,
-                                                                      V, slot, c->d_R);
+  if (c->R == 1) {
+    k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag,
+                                                                        F->d_off, F->d_val32, c->ne, ring, c->L,
+                                                                        alpha, V, slot, c->d_R);
+  } else {
+    int RL = 1;
+    while (RL < c->R && RL < 32) RL <<= 1;
+    k_near_history_multi<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(
+        F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag, F->d_off, F->d_val32, c->ne, ring, c->L, alpha, c->R, RL, V,
+        slot, c->d_R);
+  }
   c->prof_end(1, e);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
@@ -1220,20 +1290,19 @@ tdbem_status tdbem_fast_eval_reset(tdbem_ctx* c) {
   if (!F || F->lmax < 2) return TDBEM_OK;
   for (int l = 2; l <= F->lmax; ++l) {
     FmmLevel& L = F->lev[l];
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->mom_eval[l - 2], 0, (int64_t)L.ncell * 4 * kNC * F->P * sizeof(float),
-                                      c->stream));
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->loc_eval[l - 2], 0, (int64_t)L.ncell * L.Q * kNC * F->P * sizeof(float),
-                                      c->stream));
+    const int64_t RP = (int64_t)c->R * kNC * F->P;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->mom_eval[l - 2], 0, (int64_t)L.ncell * 4 * RP * sizeof(float), c->stream));
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->loc_eval[l - 2], 0, (int64_t)L.ncell * L.Q * RP * sizeof(float), c->stream));
   }
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval, 0, (int64_t)F->Lr * c->ne * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval, 0, (int64_t)F->Lr * c->ne * c->R * sizeof(double), c->stream));
   return TDBEM_OK;
 }
 
 tdbem_status tdbem_fast_consume_eval_slot(tdbem_ctx* c, int32_t alpha) {
   FmmPlan* F = c->fmm;
   if (!F || F->lmax < 2) return TDBEM_OK;
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne, 0,
-                                    c->ne * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar_eval + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R, 0,
+                                    c->ne * c->R * sizeof(double), c->stream));
   return TDBEM_OK;
 }
 
@@ -1246,10 +1315,11 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
   if (!F || F->lmax < 2) return TDBEM_OK;
   for (int l = 2; l <= F->lmax; ++l) {
     FmmLevel& L = F->lev[l];
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.mom, 0, (int64_t)L.ncell * 4 * kNC * F->P * sizeof(float), c->stream));
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.loc, 0, (int64_t)L.ncell * L.Q * kNC * F->P * sizeof(float), c->stream));
+    const int64_t RP = (int64_t)c->R * kNC * F->P;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.mom, 0, (int64_t)L.ncell * 4 * RP * sizeof(float), c->stream));
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(L.loc, 0, (int64_t)L.ncell * L.Q * RP * sizeof(float), c->stream));
   }
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar, 0, (int64_t)F->Lr * c->ne * sizeof(double), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(F->d_Rfar, 0, (int64_t)F->Lr * c->ne * c->R * sizeof(double), c->stream));
   return TDBEM_OK;
 }
 

@@ -88,23 +88,27 @@ struct tdbem_ctx {
   float* d_z0_val32 = nullptr;
   float* d_z0_inv32 = nullptr;
   int64_t z0_nnz = 0;
-  // marching state
+  // marching state; R right-hand sides share every operator and the RHS
+  // index is the fastest one in every per-edge array ([..][ne][R]), so that
+  // R = 1 is the plain single-RHS layout
+  int32_t R = 1;                    // right-hand sides (params.n_rhs)
   int32_t L = 0;                    // ring length (power of two)
-  double* d_Jring = nullptr;        // [ne][L]
-  double* d_R = nullptr;            // [ne]
-  double* d_J = nullptr;            // [ne] current solution
-  double* d_Vall = nullptr;         // [Nt-1][ne] or null
-  double* d_pulse = nullptr;        // [10]
+  double* d_Jring = nullptr;        // [ne][L][R]
+  double* d_R = nullptr;            // [ne][R]
+  double* d_J = nullptr;            // [ne][R] current solution
+  double* d_Vall = nullptr;         // [Nt-1][ne][R] or null
+  double* d_pulse = nullptr;        // [R][10]
+  double* d_stage = nullptr;        // [R][ne] host-layout staging (R > 1)
   bool have_pulse = false;
-  double pulse[10];
-  double* d_work = nullptr;         // solver vectors [8][ne]
+  std::vector<double> pulse;        // [R][10]
+  double* d_work = nullptr;         // solver vectors [8][ne][R]
   double* d_dots = nullptr;         // solver reductions
-  int32_t* d_status = nullptr;      // solver status / iterations
+  int32_t* d_status = nullptr;      // solver status / iterations [8]
   int32_t alpha = 1;
   int64_t total_iters = 0;
   int32_t cluster = 0;              // CTAs in the solver's thread-block cluster
   int32_t device = 0;               // CUDA device the context lives on
-  double* d_Vtab = nullptr;         // [Nt-1][ne] incident field of every step (precomputed)
+  double* d_Vtab = nullptr;         // [Nt-1][ne][R] incident field of every step (precomputed)
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   double setup_seconds = 0;
@@ -140,7 +144,7 @@ tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, con
 // direct.cu
 tdbem_status tdbem_build_direct(tdbem_ctx* c);
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V);
-tdbem_status tdbem_incident_table(tdbem_ctx* c);
+tdbem_status tdbem_incident_table(tdbem_ctx* c, int32_t r);
 const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha);
 tdbem_status tdbem_assemble_csr(tdbem_ctx* c, const int2* d_pairs, int64_t npairs, const int64_t* d_row_ptr,
                                 const int32_t* d_col, int64_t nnz, int16_t** m_lo, uint8_t** nlag, int64_t** off,
@@ -156,9 +160,11 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c);
 void tdbem_fast_free(tdbem_ctx* c);
 tdbem_status tdbem_fast_check(tdbem_ctx* c);
 // m2l_tc.cu
-tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const float* ops, int P,
+tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int prec, int32_t* err);
+                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                          int32_t* err);
+tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
                                   const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val);

@@ -7,12 +7,17 @@
 // gathered through the pair's cube-symmetry node map, and the columns of C are
 // added to the target clusters' local coefficients of interval k+q.
 //
-// One CTA computes a 128 x 128 tile of C.  Per K chunk (128 bytes per row)
-// the 256 threads load the operator rows and the gathered moment columns,
-// round them to the tensor-core type (TF32, BF16, or BF16 hi + lo for the
-// split-precision form) and store them in shared memory in the canonical
-// K-major layout without swizzle (8-row x 16-byte core matrices; LBO = 128 B
-// between core matrices along K, SBO = 1024 B between 8-row groups).  One
+// One CTA computes a 128 x 128 tile of C.  Operand tiles live in shared
+// memory in the canonical K-major layout without swizzle: 8-row x 16-byte
+// core matrices, LBO = 128 B between core matrices along K, SBO = 1024 B
+// between 8-row groups.  With 128 bytes of K per row that layout is a linear
+// run of 1024 16-byte units, unit u holding row 8(u >> 6) + (u & 7) and K
+// bytes 16((u >> 3) & 7) .. +15, so thread t writing units t, t+256, ... is
+// free of bank conflicts.  The operators are converted once at setup into
+// exactly these images (TF32, BF16, or hi and lo parts for the split forms,
+// zero-padded past P) and copied in with 16-byte loads; the moment columns
+// are gathered through the symmetry map one spatial node (pt = 4 time
+// coefficients, one 16-byte load) at a time and converted on the fly.  One
 // thread issues tcgen05.mma into a 128-column TMEM accumulator and commits to
 // an mbarrier; every wait on it is bounded and records a timeout in the error
 // word.  The epilogue reads TMEM with tcgen05.ld (32 lanes x 16 columns per
@@ -95,18 +100,74 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-// byte offset of (row, byte-in-row) in a 128-row x 128-byte K-major tile
-__device__ __forceinline__ uint32_t tile_off(int row, int kbyte) {
-  return (uint32_t)((row >> 3) * 1024 + (kbyte >> 4) * 128 + (row & 7) * 16 + (kbyte & 15));
+// 16-byte unit u of a 128-row x 128-byte K-major tile: its row and its
+// 16-byte column along K (the unit's byte offset in the tile is 16 u)
+__device__ __forceinline__ int unit_row(int u) { return ((u >> 6) << 3) | (u & 7); }
+__device__ __forceinline__ int unit_k16(int u) { return (u >> 3) & 7; }
+
+// hi (and lo = residual) parts of E consecutive values in the tensor-core type
+template <bool kTf>
+__device__ __forceinline__ void split_unit(const float* x, uint4& hi, uint4& lo) {
+  if (kTf) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = f32_to_tf32(x[u]);
+      l[u] = f32_to_tf32(x[u] - __uint_as_float(h[u]));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  } else {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      h[u] = __float2bfloat16_rn(x[u]);
+      l[u] = __float2bfloat16_rn(x[u] - __bfloat162float(h[u]));
+    }
+    hi = *(uint4*)h;
+    lo = *(uint4*)l;
+  }
 }
 
 }  // namespace
 
+// Operator images: img[((((op*2 + kind)*nrt + rt)*nch + ch)*nparts + part)*1024 + u]
+// is unit u of row tile rt, K chunk ch, part (0 hi, 1 lo) of operator
+// ops[op][kind] (P x P, row-major FP32).  One thread per unit.
+__global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, int nch, int nparts, int tf,
+                             uint4* img) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nunits) return;
+  const int u = (int)(t & 1023);
+  int64_t rest = t >> 10;
+  const int part = (int)(rest % nparts);
+  rest /= nparts;
+  const int ch = (int)(rest % nch);
+  rest /= nch;
+  const int rt = (int)(rest % nrt);
+  const int64_t opk = rest / nrt;  // op * 2 + kind
+  const int E = tf ? 4 : 8, KC = tf ? 32 : 64;
+  const int row = rt * kTileM + unit_row(u);
+  const int k0 = ch * KC + unit_k16(u) * E;
+  float x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    int kk = k0 + e;
+    x[e] = (e < E && row < P && kk < P) ? ops[(opk * P + row) * P + kk] : 0.f;
+  }
+  uint4 hi, lo;
+  if (tf)
+    split_unit<true>(x, hi, lo);
+  else
+    split_unit<false>(x, hi, lo);
+  img[t] = part == 0 ? hi : lo;
+}
+
 // prec: 1 = TF32, 2 = BF16, 3 = BF16 x 3, 4 = TF32 x 3 (split: hi*hi + hi*lo + lo*hi)
-__global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const float* ops, int P,
+__global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const uint4* img, int P,
                                                      int pt, int PS, const int32_t* pO, const int32_t* pS,
                                                      const int16_t* psym, const int16_t* smap, const float* mom,
-                                                     int k, float* loc, int Q, int prec, int32_t* err) {
+                                                     int k, float* loc, int Q, int R, int prec, int32_t* err) {
   extern __shared__ __align__(1024) uint8_t dsm[];
   __shared__ int64_t src_off[kTileN];
   __shared__ int64_t dst_off[kTileN];
@@ -124,21 +185,20 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int kind = gd.w & 0xff, q = (gd.w >> 8) & 0xff, qhi = (gd.w >> 16) & 0xff;
   const int nk = kind == 0 ? 3 : 4, c0 = kind == 0 ? 0 : 3;
   const int var = (q == qhi) ? 1 : 0;
-  const float* A = ops + ((int64_t)gd.x * 2 + kind) * P * P;
   const int row0 = tl.y * kTileM, col0 = tl.z * kTileN;
-  const int ncol = gd.z * nk;
+  const int ncol = gd.z * nk * R;  // columns (pair, right-hand side, component)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool split = prec == 3 || prec == 4;
   const bool tf = prec == 1 || prec == 4;
-  const int es = tf ? 4 : 2;  // bytes per element in shared memory
-  const int KC = 128 / es;           // K elements per chunk
+  const int E = tf ? 4 : 8;    // K elements per 16-byte unit
+  const int KC = 8 * E;        // K elements per chunk (128 bytes per row)
 
   if (tid < kTileN) {
     int gcol = col0 + tid;
     if (gcol < ncol) {
-      int pr = gd.y + gcol / nk, c = c0 + gcol % nk;
-      src_off[tid] = (((int64_t)pS[pr] * 2 + (k & 1)) * 2 * kNCmp + (int64_t)var * kNCmp + c) * P;
-      dst_off[tid] = (((int64_t)pO[pr] * Q + ((k + q) % Q)) * kNCmp + c) * P;
+      int pr = gd.y + gcol / (nk * R), rem = gcol % (nk * R), rhs = rem / nk, c = c0 + rem % nk;
+      src_off[tid] = (((((int64_t)pS[pr] * 2 + (k & 1)) * 2 + var) * R + rhs) * kNCmp + c) * P;
+      dst_off[tid] = ((((int64_t)pO[pr] * Q + ((k + q) % Q)) * R + rhs) * kNCmp + c) * P;
       map_off[tid] = (int32_t)psym[pr] * PS;
     } else {
       src_off[tid] = -1;
@@ -162,68 +222,55 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   bool ok = true;
 
   const int nchunks = (P + KC - 1) / KC;
+  const int nrt = (P + kTileM - 1) / kTileM;
+  const int nparts = split ? 2 : 1;
+  const uint4* Aimg = img + (((int64_t)gd.x * 2 + kind) * nrt + tl.y) * nchunks * nparts * 1024;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
-    // operator rows: 4 consecutive K values per task
-    for (int e = tid; e < kTileM * (KC / 4); e += kThreads) {
-      int r = e / (KC / 4), g = e % (KC / 4);
-      int row = row0 + r, kk = k0 + 4 * g;
-      float x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = (row < P && kk + u < P) ? A[(int64_t)row * P + kk + u] : 0.f;
-      if (tf) {
-        uint4 w = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]), f32_to_tf32(x[3]));
-        *(uint4*)(tA + tile_off(r, 16 * g)) = w;
-        if (split) {
-          uint4 l = make_uint4(f32_to_tf32(x[0] - __uint_as_float(w.x)), f32_to_tf32(x[1] - __uint_as_float(w.y)),
-                               f32_to_tf32(x[2] - __uint_as_float(w.z)), f32_to_tf32(x[3] - __uint_as_float(w.w)));
-          *(uint4*)(tA2 + tile_off(r, 16 * g)) = l;
-        }
-      } else {
-        __nv_bfloat16 h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          h[u] = __float2bfloat16_rn(x[u]);
-          l[u] = __float2bfloat16_rn(x[u] - __bfloat162float(h[u]));
-        }
-        *(uint2*)(tA + tile_off(r, 8 * g)) = *(uint2*)h;
-        if (split) *(uint2*)(tA2 + tile_off(r, 8 * g)) = *(uint2*)l;
-      }
+    // operator rows: copy of the pre-converted image of this chunk
+    const uint4* src = Aimg + (int64_t)ch * nparts * 1024;
+    for (int u = tid; u < 1024; u += kThreads) {
+      ((uint4*)tA)[u] = __ldg(src + u);
+      if (split) ((uint4*)tA2)[u] = __ldg(src + 1024 + u);
     }
     // moment columns, gathered through the symmetry map
-    for (int e = tid; e < kTileN * (KC / 4); e += kThreads) {
-      int n = e / (KC / 4), g = e % (KC / 4);
-      int kk = k0 + 4 * g;
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      int64_t so = src_off[n];
+    for (int u = tid; u < 1024; u += kThreads) {
+      const int n = unit_row(u);
+      const int kk = k0 + unit_k16(u) * E;
+      float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int64_t so = src_off[n];
       if (so >= 0) {
+        const int16_t* mp = smap + map_off[n];
+        if (pt == 4) {  // E/4 spatial nodes of 4 contiguous time coefficients
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int kq = kk + u;
-          if (kq < P) {
-            int bp = kq / pt, nt = kq - bp * pt;
-            x[u] = mom[so + (int64_t)smap[map_off[n] + bp] * pt + nt];
+          for (int g = 0; g < 2; ++g) {
+            const int kq = kk + 4 * g;
+            if (4 * g < E && kq < P) {
+              float4 v = *(const float4*)(mom + so + (int64_t)mp[kq >> 2] * 4);
+              x[4 * g] = v.x;
+              x[4 * g + 1] = v.y;
+              x[4 * g + 2] = v.z;
+              x[4 * g + 3] = v.w;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int kq = kk + e;
+            if (e < E && kq < P) {
+              const int bp = kq / pt, nt = kq - bp * pt;
+              x[e] = mom[so + (int64_t)mp[bp] * pt + nt];
+            }
           }
         }
       }
-      if (tf) {
-        uint4 w = make_uint4(f32_to_tf32(x[0]), f32_to_tf32(x[1]), f32_to_tf32(x[2]), f32_to_tf32(x[3]));
-        *(uint4*)(tB + tile_off(n, 16 * g)) = w;
-        if (split) {
-          uint4 l = make_uint4(f32_to_tf32(x[0] - __uint_as_float(w.x)), f32_to_tf32(x[1] - __uint_as_float(w.y)),
-                               f32_to_tf32(x[2] - __uint_as_float(w.z)), f32_to_tf32(x[3] - __uint_as_float(w.w)));
-          *(uint4*)(tB2 + tile_off(n, 16 * g)) = l;
-        }
-      } else {
-        __nv_bfloat16 h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          h[u] = __float2bfloat16_rn(x[u]);
-          l[u] = __float2bfloat16_rn(x[u] - __bfloat162float(h[u]));
-        }
-        *(uint2*)(tB + tile_off(n, 8 * g)) = *(uint2*)h;
-        if (split) *(uint2*)(tB2 + tile_off(n, 8 * g)) = *(uint2*)l;
-      }
+      uint4 hi, lo;
+      if (tf)
+        split_unit<true>(x, hi, lo);
+      else
+        split_unit<false>(x, hi, lo);
+      ((uint4*)tB)[u] = hi;
+      if (split) ((uint4*)tB2)[u] = lo;
     }
     fence_async_smem();
     __syncthreads();
@@ -302,9 +349,10 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
 }  // namespace tdbem
 
 // Launch the tensor-core M2L of one level event.
-tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const float* ops, int P,
+tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int prec, int32_t* err) {
+                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                          int32_t* err) {
   using namespace tdbem;
   static bool attr = false;
   if (!attr) {
@@ -312,8 +360,27 @@ tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int
     attr = true;
   }
   if (ntiles == 0) return TDBEM_OK;
-  k_m2l_tc<<<ntiles, kThreads, 65536 + 1024, c->stream>>>(gemm, tiles, ops, P, pt, PS, pO, pS, psym, smap, mom, k,
-                                                          loc, Q, prec, err);
+  k_m2l_tc<<<ntiles, kThreads, 65536 + 1024, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k,
+                                                          loc, Q, R, prec, err);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// Convert the FP32 operators of one level into the tensor-core images read by
+// k_m2l_tc (allocated here, owned by the context).
+tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img) {
+  using namespace tdbem;
+  *img = nullptr;
+  if (nop == 0) return TDBEM_OK;
+  const bool tf = prec == TDBEM_P_TF32 || prec == TDBEM_P_TF32X3;
+  const bool split = prec == TDBEM_P_TF32X3 || prec == TDBEM_P_BF16X3;
+  const int KC = tf ? 32 : 64;
+  const int nrt = (P + kTileM - 1) / kTileM, nch = (P + KC - 1) / KC, nparts = split ? 2 : 1;
+  const int64_t nunits = (int64_t)nop * 2 * nrt * nch * nparts * 1024;
+  tdbem_status s = c->dalloc(img, nunits);
+  if (s) return s;
+  k_m2l_images<<<(unsigned)((nunits + 255) / 256), 256, 0, c->stream>>>(ops, nunits, P, nrt, nch, nparts, tf ? 1 : 0,
+                                                                        *img);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }

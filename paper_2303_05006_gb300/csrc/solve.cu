@@ -315,6 +315,256 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
   cl.sync();  // keep every CTA's shared slots alive until all remote reads are done
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: R right-hand sides at once (vectors [ne][R], RHS fastest).
+// The grid is a row of thread-block clusters; cluster g solves the contiguous
+// RHS slice [g*Rc, min(R, (g+1)*Rc)), Rc = ceil(R / clusters), with the same
+// mixed-precision scheme as k_bicgstab and per-RHS scalars (an RHS that has
+// converged keeps its iterate: its updates are masked).  Reductions are
+// per-RHS: shared-memory atomics per CTA, then CTA slot r of every cluster
+// member is summed through DSMEM in rank order.  The status words are
+// combined over clusters with atomics; the last cluster to finish publishes
+// the step's verdict (status[0] must be zero at launch).
+constexpr int kMaxRhs = 64;
+
+struct MultiArgs {
+  const int32_t* ptr;
+  const int32_t* col;
+  const double* val;
+  const float* val32;
+  const float* inv_diag;
+  const double* b;   // [ne][R]
+  double* x;         // [ne][R]
+  double* ring;      // [ne][L][R]
+  int32_t L, alpha, warm, R;
+  double* w;         // FP64 residual [ne][R], then 9 FP32 vectors [9][ne][R]
+  int64_t ne;
+  double tol;
+  int32_t maxit;
+  int32_t* status;   // [0] max inner iterations, [1] all converged, [2] misses, [3] total, [4..5] scratch
+};
+
+// Sum over the cluster of the per-CTA partial sums part[0..n) into out[];
+// part[] is cleared for the next use.  All threads of every CTA call it.
+__device__ __forceinline__ void multi_reduce(cg::cluster_group& cl, double* part, double (*slot)[kMaxRhs],
+                                             double* out, int n, int& phase) {
+  double* sl = slot[phase & 1];  // alternate slots: a slot is not rewritten before every CTA has read it
+  ++phase;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) sl[r] = part[r];
+  cl.sync();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double sacc = 0.0;
+    for (unsigned k = 0; k < cl.num_blocks(); ++k) sacc += cl.map_shared_rank(sl, k)[r];
+    out[r] = sacc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) part[r] = 0.0;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double part[kMaxRhs], part2[kMaxRhs], red1[kMaxRhs], red2[kMaxRhs];
+  __shared__ double slots[2][kMaxRhs], slots2[2][kMaxRhs];
+  __shared__ double rho[kMaxRhs], rho_old[kMaxRhs], alp[kMaxRhs], om[kMaxRhs], bb[kMaxRhs], nr[kMaxRhs];
+  __shared__ int act[kMaxRhs], conv[kMaxRhs];
+  int phase = 0, phase2 = 0;
+  const int R = A.R;
+  const unsigned nb = cl.num_blocks(), rk = cl.block_rank();
+  const int ncl = gridDim.x / nb, cid = blockIdx.x / nb;
+  const int Rc = (R + ncl - 1) / ncl;
+  const int rb = cid * Rc, Rl = max(0, min(R, rb + Rc) - rb);  // this cluster's RHS slice
+  const int64_t ne = A.ne;
+  const int64_t rows = (ne + nb - 1) / nb;
+  const int64_t r0 = rk * rows, r1 = min(ne, r0 + rows);
+  const int64_t nloc = (r1 > r0 ? r1 - r0 : 0) * Rl;
+  const int64_t NR = ne * R;
+  double* r64 = A.w;
+  float* f = (float*)(A.w + NR);
+  float *rv = f, *rh = f + NR, *pv = f + 2 * NR, *vv = f + 3 * NR, *sv = f + 4 * NR, *tv = f + 5 * NR,
+        *ph = f + 6 * NR, *sh = f + 7 * NR, *dv = f + 8 * NR;
+  const int L = A.L, msk = L - 1;
+  // element e of this CTA: row i = r0 + e / Rl, right-hand side rb + e % Rl, vector index q = i R + r
+#define ELEM(e, i, l, q)            \
+  const int64_t i = r0 + (e) / Rl;  \
+  const int l = (int)((e) % Rl);    \
+  const int64_t q = i * R + rb + l;
+  for (int l = threadIdx.x; l < kMaxRhs; l += blockDim.x) {
+    part[l] = part2[l] = 0.0;
+    bb[l] = -1.0;
+    conv[l] = 0;
+    act[l] = 0;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+    ELEM(e, i, l, q)
+    double x0 = 0.0;
+    if (A.warm) {
+      const double* J = A.ring + i * L * R + rb + l;
+      int b = A.alpha - 2;
+      double j1 = b >= 0 ? J[(int64_t)(b & msk) * R] : 0.0, j2 = b >= 1 ? J[(int64_t)((b - 1) & msk) * R] : 0.0;
+      double j3 = b >= 2 ? J[(int64_t)((b - 2) & msk) * R] : 0.0, j4 = b >= 3 ? J[(int64_t)((b - 3) & msk) * R] : 0.0;
+      x0 = 4.0 * j1 - 6.0 * j2 + 4.0 * j3 - j4;
+    }
+    A.x[q] = x0;
+  }
+  cl.sync();
+  int inner_total = 0;
+  for (int outer = 0;; ++outer) {
+    // FP64 residual of every RHS of the slice
+    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+      ELEM(e, i, l, q)
+      double sacc = 0.0;
+      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val[k] * A.x[(int64_t)A.col[k] * R + rb + l];
+      double bi = A.b[q], ri = bi - sacc;
+      r64[q] = ri;
+      atomicAdd(&part[l], ri * ri);
+      atomicAdd(&part2[l], bi * bi);
+    }
+    __syncthreads();
+    multi_reduce(cl, part, slots, red1, Rl, phase);
+    multi_reduce(cl, part2, slots2, red2, Rl, phase2);
+    for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
+      if (bb[l] < 0) bb[l] = red2[l];
+      nr[l] = red1[l];
+      conv[l] = red1[l] <= A.tol * A.tol * bb[l];
+      act[l] = !conv[l];
+    }
+    __syncthreads();
+    int all = 1;
+    for (int l = 0; l < Rl; ++l) all &= conv[l];
+    if (all || outer == 8 || inner_total >= A.maxit) break;
+    // FP32 Jacobi-preconditioned BiCGStab on the unit-norm residuals, relative tolerance 1e-5
+    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+      ELEM(e, i, l, q)
+      float ri = nr[l] > 0 ? (float)(r64[q] / sqrt(nr[l])) : 0.f;
+      rv[q] = ri;
+      rh[q] = ri;
+      pv[q] = vv[q] = dv[q] = 0.f;
+      atomicAdd(&part[l], (double)ri * ri);
+    }
+    __syncthreads();
+    multi_reduce(cl, part, slots, red1, Rl, phase);
+    for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
+      rho[l] = red1[l];
+      rho_old[l] = alp[l] = om[l] = 1.0;
+      act[l] = act[l] && rho[l] > 0.0;
+    }
+    __syncthreads();
+    for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
+      int any = 0;
+      for (int l = 0; l < Rl; ++l) any |= act[l];
+      if (!any) break;
+      ++inner_total;
+      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+        ELEM(e, i, l, q)
+        if (!act[l]) continue;
+        float beta = (float)((rho[l] / rho_old[l]) * (alp[l] / om[l]));
+        float pi = rv[q] + beta * (pv[q] - (float)om[l] * vv[q]);
+        pv[q] = pi;
+        ph[q] = pi * A.inv_diag[i];
+      }
+      cl.sync();
+      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+        ELEM(e, i, l, q)
+        if (!act[l]) continue;
+        float sacc = 0.f;
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val32[k] * ph[(int64_t)A.col[k] * R + rb + l];
+        vv[q] = sacc;
+        atomicAdd(&part[l], (double)(rh[q] * sacc));
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);
+      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
+        if (act[l] && red1[l] == 0.0) act[l] = 0;
+        if (act[l]) alp[l] = rho[l] / red1[l];
+      }
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+        ELEM(e, i, l, q)
+        if (!act[l]) continue;
+        float si = rv[q] - (float)alp[l] * vv[q];
+        sv[q] = si;
+        sh[q] = si * A.inv_diag[i];
+        atomicAdd(&part[l], (double)(si * si));
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes sh
+      for (int l = threadIdx.x; l < Rl; l += blockDim.x) conv[l] = act[l] && red1[l] <= 1e-10;
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+        ELEM(e, i, l, q)
+        if (!act[l]) continue;
+        if (conv[l]) {
+          dv[q] += (float)alp[l] * ph[q];
+          continue;
+        }
+        float sacc = 0.f;
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val32[k] * sh[(int64_t)A.col[k] * R + rb + l];
+        tv[q] = sacc;
+        atomicAdd(&part[l], (double)(sacc * sv[q]));
+        atomicAdd(&part2[l], (double)(sacc * sacc));
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);
+      multi_reduce(cl, part2, slots2, red2, Rl, phase2);
+      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
+        if (conv[l]) act[l] = 0;
+        if (act[l] && red2[l] == 0.0) act[l] = 0;
+        if (act[l]) om[l] = red1[l] / red2[l];
+      }
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+        ELEM(e, i, l, q)
+        if (!act[l]) continue;
+        dv[q] += (float)alp[l] * ph[q] + (float)om[l] * sh[q];
+        float ri = sv[q] - (float)om[l] * tv[q];
+        rv[q] = ri;
+        atomicAdd(&part[l], (double)(ri * ri));
+        atomicAdd(&part2[l], (double)(rh[q] * ri));
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);
+      multi_reduce(cl, part2, slots2, red2, Rl, phase2);
+      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
+        if (!act[l]) continue;
+        rho_old[l] = rho[l];
+        rho[l] = red2[l];
+        if (red1[l] <= 1e-10 || om[l] == 0.0 || rho[l] == 0.0) act[l] = 0;
+      }
+      __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+      ELEM(e, i, l, q)
+      A.x[q] += sqrt(nr[l]) * (double)dv[q];
+    }
+    cl.sync();
+  }
+  int nconv = 0;
+  for (int l = 0; l < Rl; ++l) nconv += conv[l] ? 1 : 0;
+  for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
+    ELEM(e, i, l, q)
+    A.ring[(i * L + ((A.alpha - 1) & msk)) * R + rb + l] = A.x[q];
+  }
+#undef ELEM
+  if (rk == 0 && threadIdx.x == 0) {
+    atomicMax(&A.status[0], inner_total);
+    if (nconv < Rl) atomicAdd(&A.status[4], 1);
+    __threadfence();
+    if (atomicAdd(&A.status[5], 1) == ncl - 1) {  // last cluster: publish the verdict
+      __threadfence();
+      int miss = atomicAdd(&A.status[4], 0);
+      int it = atomicAdd(&A.status[0], 0);
+      A.status[1] = miss == 0 ? 1 : 0;
+      A.status[2] += miss == 0 ? 0 : 1;
+      A.status[3] += it;
+      A.status[4] = 0;
+      A.status[5] = 0;
+    }
+  }
+  cl.sync();
+}
+
 __global__ void k_z0_f32(const double* z, const double* inv_diag, int64_t nnz, int64_t ne, float* z32, float* inv32) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nnz) z32[i] = (float)z[i];
@@ -360,7 +610,7 @@ tdbem_status tdbem_build_z0(tdbem_ctx* c) {
   k_z0_fill<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, c->d_z0_ptr,
                                                                  c->d_z0_col, c->d_z0_val, c->d_z0_inv_diag);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
-  if ((s = c->dalloc(&c->d_work, 8 * ne)) || (s = c->dalloc(&c->d_status, 4)) || (s = c->dalloc(&c->d_dots, 4)))
+  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 8)) || (s = c->dalloc(&c->d_dots, 4)))
     return s;
   return tdbem_z0_f32(c);
 }
@@ -394,7 +644,7 @@ tdbem_status tdbem_build_z0_csr(tdbem_ctx* c) {
   k_z0_csr<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(rp, col, ml, nl, off, val, ne, c->d_z0_ptr,
                                                                 c->d_z0_col, c->d_z0_val, c->d_z0_inv_diag, nullptr, 1);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
-  if ((s = c->dalloc(&c->d_work, 8 * ne)) || (s = c->dalloc(&c->d_status, 4)) || (s = c->dalloc(&c->d_dots, 4)))
+  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 8)) || (s = c->dalloc(&c->d_dots, 4)))
     return s;
   return tdbem_z0_f32(c);
 }
@@ -426,10 +676,38 @@ static tdbem_status pick_cluster(tdbem_ctx* c) {
   return TDBEM_ECUDA;
 }
 
-tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
+// Batched solver: the cluster size of the single-RHS solver and as many
+// co-resident clusters as there are right-hand sides, up to what fits.
+static int g_multi_ncl = 0;
+static tdbem_status pick_multi(tdbem_ctx* c) {
+  if (g_multi_ncl) return TDBEM_OK;
+  tdbem_status s = pick_cluster(c);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_bicgstab_multi, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g_cluster);
+  cfg.blockDim = dim3(kSolveThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = g_cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int ncl = 0;
+  TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveClusters(&ncl, k_bicgstab_multi, &cfg));
+  if (ncl < 1) {
+    c->set_error("solve: no cluster of the batched solver is schedulable");
+    return TDBEM_ECUDA;
+  }
+  g_multi_ncl = ncl;
+  return TDBEM_OK;
+}
+
+static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha) {
   tdbem_status s;
-  if ((s = pick_cluster(c))) return s;
-  SolveArgs A;
+  if ((s = pick_multi(c))) return s;
+  MultiArgs A;
   A.ptr = c->d_z0_ptr;
   A.col = c->d_z0_col;
   A.val = c->d_z0_val;
@@ -441,15 +719,22 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
   A.L = c->L;
   A.alpha = alpha;
   A.warm = c->p.warm_start ? 1 : 0;
+  A.R = c->R;
   A.w = c->d_work;
   A.ne = c->ne;
   A.tol = c->p.solve_tol;
   A.maxit = c->p.solve_maxit;
   A.status = c->d_status;
-  A.resid = c->d_dots;
+  // every cluster must hold at most kMaxRhs right-hand sides
+  int ncl = std::min(g_multi_ncl, c->R);
+  if ((c->R + ncl - 1) / ncl > kMaxRhs) {
+    c->set_error("solve: too many right-hand sides for the co-resident solver clusters");
+    return TDBEM_EINVAL;
+  }
   c->cluster = g_cluster;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g_cluster);
+  cfg.gridDim = dim3(g_cluster * ncl);
   cfg.blockDim = dim3(kSolveThreads);
   cfg.stream = c->stream;
   cudaLaunchAttribute at[1];
@@ -459,7 +744,48 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  TDBEM_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_bicgstab, A));
+  TDBEM_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_bicgstab_multi, A));
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
+  tdbem_status s;
+  if (c->R > 1) {
+    if ((s = solve_multi(c, alpha))) return s;
+  } else {
+    if ((s = pick_cluster(c))) return s;
+    SolveArgs A;
+    A.ptr = c->d_z0_ptr;
+    A.col = c->d_z0_col;
+    A.val = c->d_z0_val;
+    A.val32 = c->d_z0_val32;
+    A.inv_diag = c->d_z0_inv32;
+    A.b = c->d_R;
+    A.x = c->d_J;
+    A.ring = c->d_Jring;
+    A.L = c->L;
+    A.alpha = alpha;
+    A.warm = c->p.warm_start ? 1 : 0;
+    A.w = c->d_work;
+    A.ne = c->ne;
+    A.tol = c->p.solve_tol;
+    A.maxit = c->p.solve_maxit;
+    A.status = c->d_status;
+    A.resid = c->d_dots;
+    c->cluster = g_cluster;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_cluster);
+    cfg.blockDim = dim3(kSolveThreads);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = g_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TDBEM_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_bicgstab, A));
+  }
   if (iters) {
     int32_t h[2];
     TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
