@@ -205,7 +205,8 @@ def run_ours(args, rank, world, dist):
     R = args.rhs
     pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
-    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R)
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+               jacobi_sweeps=args.jacobi)
     setup_s = time.perf_counter() - t0
     for r, pu in enumerate(pulses):
         s.set_incident_plane(pu, rhs=r)
@@ -292,7 +293,8 @@ def run_ours(args, rank, world, dist):
         sd.close()
         if R > 1:
             # the same fast march one right-hand side at a time
-            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec])
+            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
+                        jacobi_sweeps=args.jacobi)
             s1.set_incident_plane(w.pulses[0])
             s1.set_stream(stream.cuda_stream)
             s1.march_dev(W)
@@ -314,6 +316,7 @@ def run_ours(args, rank, world, dist):
         "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
                    "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
+                   "jacobi_sweeps_max": args.jacobi,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
                    "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
                          + (" + M2L operators" if args.mode == "fast" else "") + ")",
@@ -326,6 +329,7 @@ def run_ours(args, rank, world, dist):
                 "h2d_bytes_per_step": 8 * s.ne * R, "d2h_bytes_per_step": 8 * s.ne * R},
         "clocks": ck,
         "solver_iters_per_step": info.total_solver_iters / K if K else None,
+        "jacobi_sweeps_per_step": info.total_jacobi_sweeps / K if K else None,
     }
     line.update(cmp)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -348,6 +352,7 @@ def main():
     ap.add_argument("--prec", choices=list(PREC), default="tf32x3")
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")
+    ap.add_argument("--jacobi", type=int, default=0, help="FP64 Jacobi sweeps before the Krylov solve (0: none)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")
     ap.add_argument("--workload", default="sphere7680")

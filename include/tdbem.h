@@ -88,6 +88,8 @@ typedef struct {
   int32_t solve_maxit;  /* iteration cap of the Z0 solve */
   int32_t warm_start;   /* 0: zero initial guess, 1: cubic extrapolation of past currents */
   int32_t n_rhs;        /* right-hand sides marched together, 1 .. TDBEM_MAX_RHS (batched form) */
+  int32_t jacobi_sweeps; /* Z0 solve: at most this many FP64 Jacobi sweeps before the Krylov refinement
+                            (0: Krylov only); a sweep that does not cut the residual by 0.7 ends them */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -97,7 +99,8 @@ typedef struct {
 #define TDBEM_MAX_RHS 64
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
-   DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1. */
+   DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1,
+   jacobi_sweeps=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -212,6 +215,7 @@ typedef struct {
   int32_t solver_cluster;          /* CTAs in the Z0 solver's thread-block cluster (0 before the first solve) */
   int64_t n_far_pairs;             /* interaction-list cluster pairs over all levels (fast mode) */
   double m2l_flops_per_step;       /* M2L flops per step, averaged over the gating cycle (fast mode) */
+  int64_t total_jacobi_sweeps;     /* FP64 Jacobi sweeps of the Z0 solves (per-cluster maximum when batched) */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 
@@ -223,6 +227,68 @@ tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
    6 L2L, 7 L2P.  n_classes receives the number of classes (<= 16). */
 tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
 tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
+
+/* ------------------------------------------------------------------------
+   Learned warm start of the Z0 solve.  Not in the paper: the paper solves
+   with GMRES from the previous data (section 2.6).  Here a small network
+   predicts each step's current from local data; the solve to solve_tol
+   still decides the result, so the network changes the work, never the
+   answer.
+
+   Features of edge i at step alpha (TDBEM_MLP_FEATURES = 25):
+     J_i^{alpha-1-k} for k = 1..4 (4 values);
+     sigma_n J_{j_n}^{alpha-1-k} for its 4 RWG neighbours j_n (16 values),
+       where the neighbours are the other two sides of the + triangle, then of
+       the - triangle, in winding order, and sigma_n = (sign of i) x (sign of
+       j_n) in the shared triangle;
+     g_i = b_i / Z0_ii and sigma_n g_{j_n} (5 values), b = R^{alpha-1}.
+   With s_i = RMS of the 25 values and xc_i = 4J^{a-2} - 6J^{a-3} + 4J^{a-4}
+   - J^{a-5} (cubic extrapolation), the prediction is
+     x0_i = xc_i + s_i y(f_i / s_i),
+   y an odd perceptron F -> H -> H -> 1 with tanh and no biases (H =
+   TDBEM_MLP_WIDTH).  Parameters, flattened: W1 [H][F], W2 [H][H], w3 [H].
+   When the network is in use, each solve also forms xc and starts from
+   whichever of x0 and xc has the smaller FP64 residual (the fallback; a
+   non-finite x0 always loses). */
+#define TDBEM_MLP_FEATURES 25
+#define TDBEM_MLP_WIDTH 64
+#define TDBEM_MLP_NPARAM (TDBEM_MLP_WIDTH * TDBEM_MLP_FEATURES + TDBEM_MLP_WIDTH * TDBEM_MLP_WIDTH + TDBEM_MLP_WIDTH)
+
+/* Set (host array of TDBEM_MLP_NPARAM floats, copied) or read the network's
+   parameters.  The first set allocates the network; Adam's moments are reset. */
+tdbem_status tdbem_mlp_set_weights(tdbem_ctx* ctx, const float* theta);
+tdbem_status tdbem_mlp_get_weights(tdbem_ctx* ctx, float* theta);
+
+/* Training samples.  With capacity > 0 every later step appends, for every
+   edge and right-hand side, its scaled features f/s and target
+   (J^{alpha-1} - xc)/s (edges with s = 0 are stored as zeros) to a device
+   buffer of `capacity` samples, until it is full; capacity = 0 stops
+   recording and frees the buffer.  tdbem_mlp_samples reads back samples
+   [first, first+n) (X [n][F], T [n], host; either may be NULL) and the
+   number stored so far (count may be NULL). */
+tdbem_status tdbem_mlp_record(tdbem_ctx* ctx, int64_t capacity);
+tdbem_status tdbem_mlp_samples(tdbem_ctx* ctx, int64_t first, int64_t n, float* X, float* T, int64_t* count);
+
+/* Train on the recorded samples with Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+   step size lr) for `epochs` passes in minibatches of `batch` samples (a
+   multiple of 128), visiting samples in an order shuffled per epoch from
+   `seed`.  Forward, backward and update run in the library's kernels.
+   loss ([epochs], may be NULL) receives each epoch's mean minibatch loss. */
+tdbem_status tdbem_mlp_train(tdbem_ctx* ctx, int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss);
+
+/* Loss and gradient of the current parameters on a caller batch (X [n][F],
+   T [n], host), computed by the training kernels (for gradient checks). */
+tdbem_status tdbem_mlp_grad(tdbem_ctx* ctx, const float* X, const float* T, int64_t n, float* loss, float* grad);
+
+/* Network output y for the rows of X ([n][F], host) by the inference kernel. */
+tdbem_status tdbem_mlp_forward(tdbem_ctx* ctx, const float* X, int64_t n, float* Y);
+
+/* Use the network as the warm start of every later solve (on != 0), or the
+   cubic extrapolation alone (on = 0).  Needs weights.  used / fallback (may
+   be NULL) receive how many solves (per right-hand side) since the last
+   reset started from the network's and from the extrapolation's guess. */
+tdbem_status tdbem_mlp_use(tdbem_ctx* ctx, int32_t on);
+tdbem_status tdbem_mlp_stats(tdbem_ctx* ctx, int64_t* used, int64_t* fallback);
 
 const char* tdbem_last_error(const tdbem_ctx* ctx);
 

@@ -20,6 +20,7 @@ _STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "EBREAKDOWN", 4: "ENOMEM", 5: "E
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 class Params(ctypes.Structure):
@@ -27,7 +28,7 @@ class Params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("zeta", ctypes.c_double), ("eps", ctypes.c_double),
                 ("mu", ctypes.c_double), ("s_jump", ctypes.c_double), ("mode", ctypes.c_int32),
                 ("m2l_prec", ctypes.c_int32), ("solve_tol", ctypes.c_double), ("solve_maxit", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -36,7 +37,7 @@ class Info(ctypes.Structure):
                 ("near_coef_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
                 ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
-                ("m2l_flops_per_step", ctypes.c_double)]
+                ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64)]
 
 
 class TdbemError(RuntimeError):
@@ -85,10 +86,22 @@ def lib():
         L.tdbem_last_error.restype = ctypes.c_char_p
         L.tdbem_destroy.argtypes = [vp]
         L.tdbem_destroy.restype = None
+        i64, i64p = ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)
+        L.tdbem_mlp_set_weights.argtypes = [vp, _fp]
+        L.tdbem_mlp_get_weights.argtypes = [vp, _fp]
+        L.tdbem_mlp_record.argtypes = [vp, i64]
+        L.tdbem_mlp_samples.argtypes = [vp, i64, i64, _fp, _fp, i64p]
+        L.tdbem_mlp_train.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _fp]
+        L.tdbem_mlp_grad.argtypes = [vp, _fp, _fp, i64, ctypes.POINTER(ctypes.c_float), _fp]
+        L.tdbem_mlp_forward.argtypes = [vp, _fp, i64, _fp]
+        L.tdbem_mlp_use.argtypes = [vp, ctypes.c_int32]
+        L.tdbem_mlp_stats.argtypes = [vp, i64p, i64p]
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
                      "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
-                     "tdbem_profile_read", "tdbem_history_eval_noalloc"):
+                     "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_weights",
+                     "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_samples", "tdbem_mlp_train",
+                     "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -224,6 +237,67 @@ class Solver:
         a = ctypes.c_int32()
         self._check(lib().tdbem_alpha(self._h, ctypes.byref(a)))
         return int(a.value)
+
+    # ---- learned warm start (see include/tdbem.h)
+    MLP_FEATURES, MLP_WIDTH = 25, 64
+    MLP_NPARAM = MLP_WIDTH * MLP_FEATURES + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH
+
+    def mlp_set_weights(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.MLP_NPARAM:
+            raise ValueError(f"theta must hold {self.MLP_NPARAM} values")
+        self._check(lib().tdbem_mlp_set_weights(self._h, t.ctypes.data_as(_fp)))
+
+    def mlp_get_weights(self) -> np.ndarray:
+        t = np.zeros(self.MLP_NPARAM, np.float32)
+        self._check(lib().tdbem_mlp_get_weights(self._h, t.ctypes.data_as(_fp)))
+        return t
+
+    def mlp_record(self, capacity: int):
+        self._check(lib().tdbem_mlp_record(self._h, ctypes.c_int64(int(capacity))))
+
+    def mlp_count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(lib().tdbem_mlp_samples(self._h, ctypes.c_int64(0), ctypes.c_int64(0), None, None,
+                                            ctypes.byref(n)))
+        return int(n.value)
+
+    def mlp_samples(self, first: int, n: int):
+        X = np.zeros((n, self.MLP_FEATURES), np.float32)
+        T = np.zeros(n, np.float32)
+        self._check(lib().tdbem_mlp_samples(self._h, ctypes.c_int64(first), ctypes.c_int64(n),
+                                            X.ctypes.data_as(_fp), T.ctypes.data_as(_fp), None))
+        return X, T
+
+    def mlp_train(self, epochs: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
+        loss = np.zeros(max(epochs, 1), np.float32)
+        self._check(lib().tdbem_mlp_train(self._h, int(epochs), int(batch), ctypes.c_float(lr),
+                                          ctypes.c_uint64(seed), loss.ctypes.data_as(_fp)))
+        return loss[:epochs]
+
+    def mlp_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(self.MLP_NPARAM, np.float32)
+        loss = ctypes.c_float()
+        self._check(lib().tdbem_mlp_grad(self._h, X.ctypes.data_as(_fp), T.ctypes.data_as(_fp),
+                                         ctypes.c_int64(len(T)), ctypes.byref(loss), g.ctypes.data_as(_fp)))
+        return float(loss.value), g
+
+    def mlp_forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros(X.shape[0], np.float32)
+        self._check(lib().tdbem_mlp_forward(self._h, X.ctypes.data_as(_fp), ctypes.c_int64(X.shape[0]),
+                                            Y.ctypes.data_as(_fp)))
+        return Y
+
+    def mlp_use(self, on: bool = True):
+        self._check(lib().tdbem_mlp_use(self._h, 1 if on else 0))
+
+    def mlp_stats(self):
+        u, f = ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib().tdbem_mlp_stats(self._h, ctypes.byref(u), ctypes.byref(f)))
+        return int(u.value), int(f.value)
 
     def info(self) -> Info:
         inf = Info()

@@ -55,6 +55,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->solve_maxit = 200;
   p->warm_start = 1;
   p->n_rhs = 1;
+  p->jacobi_sweeps = 0;
 }
 
 static void fill_phys(tdbem_ctx* c) {
@@ -86,6 +87,7 @@ void tdbem_destroy(tdbem_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   tdbem_fast_free(c);
+  tdbem_mlp_free(c);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
@@ -102,7 +104,7 @@ static tdbem_status finish_create(tdbem_ctx* c) {
     return s;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * L * sizeof(double), c->stream));
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, NR * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 8 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 16 * sizeof(int32_t), c->stream));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -120,7 +122,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
   if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
-      p.n_rhs > TDBEM_MAX_RHS ||
+      p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -440,10 +442,13 @@ static tdbem_status step_async(tdbem_ctx* c, bool have_V = false) {
   }
   tdbem_status s = eval_R(c, c->alpha, c->d_Jring, have_V);
   if (s) return s;
+  int32_t warm = c->p.warm_start ? 1 : 0;
+  if ((s = tdbem_mlp_before_solve(c, c->alpha, &warm))) return s;
   cudaEvent_t e = c->prof_begin(2);
-  s = tdbem_solve_z0(c, c->alpha, nullptr);
+  s = tdbem_solve_z0(c, c->alpha, nullptr, warm);
   c->prof_end(2, e);
   if (s) return s;
+  if ((s = tdbem_mlp_after_solve(c, c->alpha))) return s;
   if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_after_solve(c, c->alpha))) return s;
   c->alpha++;
   return TDBEM_OK;
@@ -524,10 +529,11 @@ static tdbem_status check_misses(tdbem_ctx* c) {
     tdbem_status s = tdbem_fast_check(c);
     if (s) return s;
   }
-  int32_t h[4];
-  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  int32_t h[8];
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(h, c->d_status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->total_iters = h[3];
+  c->total_sweeps = h[7];
   if (h[2]) {
     c->set_error("march: " + std::to_string(h[2]) + " Z0 solves missed the tolerance");
     return TDBEM_ENOCONV;
@@ -567,7 +573,7 @@ tdbem_status tdbem_reset(tdbem_ctx* c) {
   const int64_t NR = c->ne * (int64_t)c->R;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * c->L * sizeof(double), c->stream));
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, NR * sizeof(double), c->stream));
-  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 8 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 16 * sizeof(int32_t), c->stream));
   if (c->p.mode == TDBEM_FAST) {
     tdbem_status s = tdbem_fast_reset(c);
     if (s) return s;
@@ -575,6 +581,7 @@ tdbem_status tdbem_reset(tdbem_ctx* c) {
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->alpha = 1;
   c->total_iters = 0;
+  c->total_sweeps = 0;
   return TDBEM_OK;
 }
 
@@ -594,6 +601,7 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->device_bytes = c->device_bytes;
   info->setup_seconds = c->setup_seconds;
   info->total_solver_iters = c->total_iters;
+  info->total_jacobi_sweeps = c->total_sweeps;
   info->solver_cluster = c->cluster;
   if (c->p.mode == TDBEM_FAST) tdbem_fast_info(c, info);
   return TDBEM_OK;

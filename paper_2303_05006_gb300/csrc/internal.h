@@ -88,6 +88,12 @@ struct tdbem_ctx {
   float* d_z0_val32 = nullptr;
   float* d_z0_inv32 = nullptr;
   int64_t z0_nnz = 0;
+  // the same Z0 as column-major ELL for the solver: entry k of row i at [k*ne + i]
+  int32_t z0_ell_w = 0;             // largest row length
+  int32_t* d_ell_len = nullptr;     // [ne]
+  int32_t* d_ell_col = nullptr;     // [w][ne]
+  double* d_ell_val = nullptr;      // [w][ne]
+  float* d_ell_val32 = nullptr;     // [w][ne]
   // marching state; R right-hand sides share every operator and the RHS
   // index is the fastest one in every per-edge array ([..][ne][R]), so that
   // R = 1 is the plain single-RHS layout
@@ -106,6 +112,7 @@ struct tdbem_ctx {
   int32_t* d_status = nullptr;      // solver status / iterations [8]
   int32_t alpha = 1;
   int64_t total_iters = 0;
+  int64_t total_sweeps = 0;
   int32_t cluster = 0;              // CTAs in the solver's thread-block cluster
   int32_t device = 0;               // CUDA device the context lives on
   double* d_Vtab = nullptr;         // [Nt-1][ne][R] incident field of every step (precomputed)
@@ -137,6 +144,8 @@ struct tdbem_ctx {
     return TDBEM_OK;
   }
   std::vector<void*> allocs;
+  // learned warm start (mlp.cu)
+  struct Mlp* mlp = nullptr;
 };
 
 // mesh.cu
@@ -168,7 +177,11 @@ tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P,
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
                                   const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val);
+// mlp.cu
+tdbem_status tdbem_mlp_before_solve(tdbem_ctx* c, int32_t alpha, int32_t* warm);
+tdbem_status tdbem_mlp_after_solve(tdbem_ctx* c, int32_t alpha);
+void tdbem_mlp_free(tdbem_ctx* c);
 // solve.cu
 tdbem_status tdbem_build_z0(tdbem_ctx* c);
 tdbem_status tdbem_build_z0_csr(tdbem_ctx* c);
-tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters);
+tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t warm);

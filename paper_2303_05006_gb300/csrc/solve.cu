@@ -24,6 +24,7 @@ namespace cg = cooperative_groups;
 namespace tdbem {
 
 constexpr int kSolveThreads = 512;
+constexpr double kJacRatio = 0.7;  // largest residual ratio per Jacobi sweep that keeps sweeping
 
 __global__ void k_z0_count(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int32_t* cnt) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -77,9 +78,10 @@ __global__ void k_z0_csr(const int64_t* row_ptr, const int32_t* col, const int16
 }
 
 struct SolveArgs {
-  const int32_t* ptr;
+  // Z0 as column-major ELL: row i has len[i] entries, entry k at [k*ne + i]
+  const int32_t* len;
   const int32_t* col;
-  const double* val;      // Z0, FP64 (outer residual)
+  const double* val;      // Z0, FP64 (residuals, Jacobi sweeps)
   const float* val32;     // Z0, FP32 (inner iterations)
   const float* inv_diag;  // Jacobi preconditioner
   const double* b;
@@ -87,12 +89,15 @@ struct SolveArgs {
   double* ring;     // [ne][L]
   int32_t L;
   int32_t alpha;    // solving J^{alpha-1}
-  int32_t warm;     // 1: cubic extrapolation of J^{alpha-2..alpha-5}
+  int32_t warm;     // 1: cubic extrapolation of J^{alpha-2..alpha-5}; 2: x holds another guess,
+                    //    kept unless the extrapolation has the smaller residual
   double* w;        // FP64 residual [ne], then 9 FP32 vectors [9][ne]
   int64_t ne;
   double tol;
   int32_t maxit;    // cap on the total inner iterations
-  int32_t* status;  // [0] inner iterations, [1] converged flag, [2] misses, [3] iteration total
+  int32_t jacobi;   // max FP64 Jacobi sweeps before the Krylov refinement (0: none)
+  int32_t* status;  // [0] inner iterations, [1] converged flag, [2] misses, [3] iteration total,
+                    // [6] Jacobi sweeps of this solve, [7] Jacobi sweeps since the last reset
   double* resid;    // [0] final relative residual
 };
 
@@ -146,21 +151,37 @@ __device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[
   for (int k = 0; k < NV; ++k) v[k] = bc[k];
 }
 
+// Row i of Z0 times x (x[j*R + rl]: column rl of an [ne][R] block).  With the
+// column-major ELL layout consecutive rows (threads) read consecutive
+// addresses, and four independent products per step keep loads in flight.
+template <class T, class V>
+__device__ __forceinline__ V ell_row(const int32_t* len, const int32_t* col, const T* val, int64_t ne, int64_t i,
+                                     const V* x, int R, int rl) {
+  V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  const int n = len[i];
+  int k = 0;
+  for (; k + 3 < n; k += 4) {
+    const int64_t a = (int64_t)k * ne + i;
+    const int c0 = col[a], c1 = col[a + ne], c2 = col[a + 2 * ne], c3 = col[a + 3 * ne];
+    const V v0 = (V)val[a], v1 = (V)val[a + ne], v2 = (V)val[a + 2 * ne], v3 = (V)val[a + 3 * ne];
+    s0 += v0 * x[(int64_t)c0 * R + rl];
+    s1 += v1 * x[(int64_t)c1 * R + rl];
+    s2 += v2 * x[(int64_t)c2 * R + rl];
+    s3 += v3 * x[(int64_t)c3 * R + rl];
+  }
+  for (; k < n; ++k) {
+    const int64_t a = (int64_t)k * ne + i;
+    s0 += (V)val[a] * x[(int64_t)col[a] * R + rl];
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 __device__ __forceinline__ double spmv_row64(const SolveArgs& A, int64_t i, const double* x) {
-  double s = 0.0;
-  for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s += A.val[k] * x[A.col[k]];
-  return s;
+  return ell_row<double, double>(A.len, A.col, A.val, A.ne, i, x, 1, 0);
 }
 
 __device__ __forceinline__ float spmv_row32(const SolveArgs& A, int64_t i, const float* x) {
-  float s0 = 0.f, s1 = 0.f;
-  int k = A.ptr[i], e = A.ptr[i + 1];
-  for (; k + 1 < e; k += 2) {
-    s0 += A.val32[k] * x[A.col[k]];
-    s1 += A.val32[k + 1] * x[A.col[k + 1]];
-  }
-  if (k < e) s0 += A.val32[k] * x[A.col[k]];
-  return s0 + s1;
+  return ell_row<float, float>(A.len, A.col, A.val32, A.ne, i, x, 1, 0);
 }
 
 // Mixed-precision solve of Z0 x = b: FP64 residual r = b - Z0 x (iterative
@@ -190,6 +211,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
   float* sh = f + 7 * ne;
   float* d = f + 8 * ne;
   const int L = A.L, msk = A.L - 1;
+  // warm 1: the extrapolation goes to x; warm 2: to r64, beside the guess in x
+  double* xc_dst = A.warm == 2 ? r64 : A.x;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     double x0 = 0.0;
     if (A.warm) {
@@ -199,13 +222,68 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       double j3 = b >= 2 ? J[(b - 2) & msk] : 0.0, j4 = b >= 3 ? J[(b - 3) & msk] : 0.0;
       x0 = 4.0 * j1 - 6.0 * j2 + 4.0 * j3 - j4;
     }
-    A.x[i] = x0;
+    xc_dst[i] = x0;
   }
   cl.sync();
+  if (A.warm == 2) {
+    // keep the guess only if its FP64 residual is smaller (a NaN never is)
+    double q2[2] = {0.0, 0.0};
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double rg = A.b[i] - spmv_row64(A, i, A.x), rc = A.b[i] - spmv_row64(A, i, r64);
+      q2[0] += rg * rg;
+      q2[1] += rc * rc;
+    }
+    block_sums<2>(q2, red);
+    cluster_sums<2>(cl, q2, slots, bc, phase);
+    const bool keep = q2[0] < q2[1];
+    if (!keep) {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.x[i] = r64[i];
+    }
+    if (rk == 0 && threadIdx.x == 0) A.status[keep ? 8 : 9] += 1;
+    cl.sync();
+  }
   double bb = -1.0, rr = 0.0;
   int inner_total = 0;
   bool conv = false;
-  for (int outer = 0; outer < 8; ++outer) {
+  // Stage 1: FP64 Jacobi sweeps x <- x + D^{-1}(b - Z0 x).  Z0 is strongly
+  // diagonal (spectral radius of I - D^{-1} Z0 about 0.27 on the test
+  // meshes), so each sweep gains about half a digit for one SpMV and one
+  // cluster reduction.  The sweep that finds a residual norm above kJacRatio
+  // times the previous one hands the iterate to the Krylov stage instead.
+  int sweeps = 0;
+  {
+    double* cur = A.x;
+    double* nxt = r64;  // the residual buffer is free until the Krylov stage
+    double rr_prev = -1.0;
+    for (int k = 0; k < A.jacobi; ++k) {
+      double q2[2] = {0.0, 0.0};
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        double ri = A.b[i] - spmv_row64(A, i, cur);
+        nxt[i] = cur[i] + ri * (double)A.inv_diag[i];
+        q2[0] += ri * ri;
+        q2[1] += A.b[i] * A.b[i];
+      }
+      block_sums<2>(q2, red);
+      cluster_sums<2>(cl, q2, slots, bc, phase);  // its cluster barrier also publishes nxt
+      if (bb < 0) bb = q2[1];
+      rr = q2[0];
+      if (rr <= A.tol * A.tol * bb) {  // cur is the solution
+        conv = true;
+        break;
+      }
+      if (rr_prev >= 0.0 && rr > kJacRatio * kJacRatio * rr_prev) break;  // not contracting: keep cur
+      rr_prev = rr;
+      double* t = cur;
+      cur = nxt;
+      nxt = t;
+      ++sweeps;
+    }
+    if (cur != A.x) {
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.x[i] = cur[i];
+      cl.sync();
+    }
+  }
+  for (int outer = 0; outer < 8 && !conv; ++outer) {
     // FP64 residual
     double q2[2] = {0.0, 0.0};
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -307,6 +385,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.ring[i * L + ((A.alpha - 1) & msk)] = A.x[i];
   if (rk == 0 && threadIdx.x == 0) {
     A.status[0] = inner_total;
+    A.status[6] = sweeps;
+    A.status[7] += sweeps;
     A.status[1] = conv ? 1 : 0;
     A.status[2] += conv ? 0 : 1;  // solves that missed the tolerance since the last reset
     A.status[3] += inner_total;   // iterations since the last reset
@@ -328,7 +408,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
 constexpr int kMaxRhs = 64;
 
 struct MultiArgs {
-  const int32_t* ptr;
+  const int32_t* len;  // Z0 as column-major ELL (see SolveArgs)
   const int32_t* col;
   const double* val;
   const float* val32;
@@ -341,7 +421,9 @@ struct MultiArgs {
   int64_t ne;
   double tol;
   int32_t maxit;
-  int32_t* status;   // [0] max inner iterations, [1] all converged, [2] misses, [3] total, [4..5] scratch
+  int32_t jacobi;    // max FP64 Jacobi sweeps before the Krylov refinement
+  int32_t* status;   // [0] max inner iterations, [1] all converged, [2] misses, [3] total, [4..5] scratch,
+                     // [6] max Jacobi sweeps of this solve, [7] their running total
 };
 
 // Sum over the cluster of the per-CTA partial sums part[0..n) into out[];
@@ -362,193 +444,330 @@ __device__ __forceinline__ void multi_reduce(cg::cluster_group& cl, double* part
   __syncthreads();
 }
 
+// Add a thread's partial sum v (of right-hand side l = lane mod Rp) into
+// part[l]: lanes of one RHS are combined by shuffles first, so each warp
+// issues at most 32 shared atomics per reduction.
+__device__ __forceinline__ void seg_add(double v, int Rp, bool act, double* part, int l) {
+  for (int o = 16; o >= Rp; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (act && (threadIdx.x & 31) < Rp) atomicAdd(&part[l], v);
+}
+
+// Element map: the cluster's RHS slice (Rl right-hand sides) is padded to
+// Rp = a power of two <= kMaxRhs; thread t always takes RHS l = t mod Rp
+// (active when l < Rl) and rows r0 + t / Rp, stepping by blockDim / Rp, so
+// its partial sums are per-RHS registers.
 __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double part[kMaxRhs], part2[kMaxRhs], red1[kMaxRhs], red2[kMaxRhs];
   __shared__ double slots[2][kMaxRhs], slots2[2][kMaxRhs];
   __shared__ double rho[kMaxRhs], rho_old[kMaxRhs], alp[kMaxRhs], om[kMaxRhs], bb[kMaxRhs], nr[kMaxRhs];
-  __shared__ int act[kMaxRhs], conv[kMaxRhs];
+  __shared__ double rprev[kMaxRhs];
+  __shared__ int act[kMaxRhs], conv[kMaxRhs], jac[kMaxRhs];
   int phase = 0, phase2 = 0;
   const int R = A.R;
   const unsigned nb = cl.num_blocks(), rk = cl.block_rank();
   const int ncl = gridDim.x / nb, cid = blockIdx.x / nb;
   const int Rc = (R + ncl - 1) / ncl;
   const int rb = cid * Rc, Rl = max(0, min(R, rb + Rc) - rb);  // this cluster's RHS slice
+  int sh = 0;
+  while ((1 << sh) < Rl) ++sh;
+  const int Rp = 1 << sh;
+  const int l = threadIdx.x & (Rp - 1);
+  const bool lane_on = l < Rl;
+  const int rstep = blockDim.x >> sh;
   const int64_t ne = A.ne;
   const int64_t rows = (ne + nb - 1) / nb;
   const int64_t r0 = rk * rows, r1 = min(ne, r0 + rows);
-  const int64_t nloc = (r1 > r0 ? r1 - r0 : 0) * Rl;
+  const int64_t i0 = r0 + (threadIdx.x >> sh);
   const int64_t NR = ne * R;
   double* r64 = A.w;
   float* f = (float*)(A.w + NR);
   float *rv = f, *rh = f + NR, *pv = f + 2 * NR, *vv = f + 3 * NR, *sv = f + 4 * NR, *tv = f + 5 * NR,
-        *ph = f + 6 * NR, *sh = f + 7 * NR, *dv = f + 8 * NR;
+        *ph = f + 6 * NR, *shv = f + 7 * NR, *dv = f + 8 * NR;
   const int L = A.L, msk = L - 1;
-  // element e of this CTA: row i = r0 + e / Rl, right-hand side rb + e % Rl, vector index q = i R + r
-#define ELEM(e, i, l, q)            \
-  const int64_t i = r0 + (e) / Rl;  \
-  const int l = (int)((e) % Rl);    \
-  const int64_t q = i * R + rb + l;
-  for (int l = threadIdx.x; l < kMaxRhs; l += blockDim.x) {
-    part[l] = part2[l] = 0.0;
-    bb[l] = -1.0;
-    conv[l] = 0;
-    act[l] = 0;
+  const int rl = rb + l;  // this thread's right-hand side (valid when lane_on)
+#define ROWS for (int64_t i = lane_on ? i0 : r1; i < r1; i += rstep)
+  for (int k = threadIdx.x; k < kMaxRhs; k += blockDim.x) {
+    part[k] = part2[k] = 0.0;
+    bb[k] = -1.0;
+    rprev[k] = -1.0;
+    conv[k] = act[k] = 0;
+    jac[k] = 1;
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-    ELEM(e, i, l, q)
+  double* xc_dst = A.warm == 2 ? r64 : A.x;  // as in k_bicgstab
+  ROWS {
     double x0 = 0.0;
     if (A.warm) {
-      const double* J = A.ring + i * L * R + rb + l;
+      const double* J = A.ring + i * L * R + rl;
       int b = A.alpha - 2;
       double j1 = b >= 0 ? J[(int64_t)(b & msk) * R] : 0.0, j2 = b >= 1 ? J[(int64_t)((b - 1) & msk) * R] : 0.0;
       double j3 = b >= 2 ? J[(int64_t)((b - 2) & msk) * R] : 0.0, j4 = b >= 3 ? J[(int64_t)((b - 3) & msk) * R] : 0.0;
       x0 = 4.0 * j1 - 6.0 * j2 + 4.0 * j3 - j4;
     }
-    A.x[q] = x0;
+    xc_dst[i * R + rl] = x0;
   }
   cl.sync();
-  int inner_total = 0;
+  if (A.warm == 2) {
+    double q1 = 0.0, q2 = 0.0;
+    ROWS {
+      const double bi = A.b[i * R + rl];
+      const double rg = bi - ell_row<double, double>(A.len, A.col, A.val, A.ne, i, A.x, R, rl);
+      const double rc = bi - ell_row<double, double>(A.len, A.col, A.val, A.ne, i, r64, R, rl);
+      q1 += rg * rg;
+      q2 += rc * rc;
+    }
+    seg_add(q1, Rp, lane_on, part, l);
+    seg_add(q2, Rp, lane_on, part2, l);
+    __syncthreads();
+    multi_reduce(cl, part, slots, red1, Rl, phase);
+    multi_reduce(cl, part2, slots2, red2, Rl, phase2);
+    if (lane_on && !(red1[l] < red2[l])) {
+      ROWS A.x[i * R + rl] = r64[i * R + rl];
+    }
+    if (rk == 0 && threadIdx.x == 0) {
+      int kept = 0;
+      for (int m = 0; m < Rl; ++m) kept += red1[m] < red2[m] ? 1 : 0;
+      atomicAdd(&A.status[8], kept);
+      atomicAdd(&A.status[9], Rl - kept);
+    }
+    cl.sync();
+  }
+  int inner_total = 0, sweeps = 0;
+  // Stage 1: FP64 Jacobi sweeps per RHS (as in k_bicgstab).  An RHS leaves
+  // the stage when it converges or stops contracting; its iterate is then
+  // carried along unchanged (jac: 1 sweeping, 2 stopping now, 0 stopped).
+  {
+    double* cur = A.x;
+    double* nxt = r64;
+    for (int k = 0; k < A.jacobi; ++k) {
+      int any = 0;
+      for (int m = 0; m < Rl; ++m) any |= (jac[m] == 1);
+      if (!any) break;
+      double q1 = 0.0, q2 = 0.0;
+      const bool on = lane_on && jac[l] == 1;
+      ROWS {
+        const int64_t q = i * R + rl;
+        if (!on) {
+          nxt[q] = cur[q];
+          continue;
+        }
+        double sacc = 0.0;
+        sacc = ell_row<double, double>(A.len, A.col, A.val, A.ne, i, cur, R, rl);
+        const double bi = A.b[q], ri = bi - sacc;
+        nxt[q] = cur[q] + ri * (double)A.inv_diag[i];
+        q1 += ri * ri;
+        q2 += bi * bi;
+      }
+      seg_add(q1, Rp, on, part, l);
+      seg_add(q2, Rp, on, part2, l);
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes nxt
+      multi_reduce(cl, part2, slots2, red2, Rl, phase2);
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+        if (jac[m] != 1) continue;
+        if (bb[m] < 0) bb[m] = red2[m];
+        const bool done = red1[m] <= A.tol * A.tol * bb[m];
+        const bool slow = rprev[m] >= 0.0 && red1[m] > kJacRatio * kJacRatio * rprev[m];
+        rprev[m] = red1[m];
+        if (done || slow) jac[m] = 2;  // keeps cur: its nxt is reset below
+      }
+      __syncthreads();
+      if (lane_on && jac[l] == 2) {
+        ROWS nxt[i * R + rl] = cur[i * R + rl];
+      }
+      __syncthreads();
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x)
+        if (jac[m] == 2) jac[m] = 0;
+      cl.sync();  // reverted values and flags visible before the next sweep
+      double* t = cur;
+      cur = nxt;
+      nxt = t;
+      ++sweeps;
+    }
+    if (cur != A.x) {
+      ROWS A.x[i * R + rl] = cur[i * R + rl];
+    }
+    for (int m = threadIdx.x; m < kMaxRhs; m += blockDim.x) bb[m] = -1.0;
+    cl.sync();
+  }
+  // Stage 2: mixed-precision refinement as in k_bicgstab, per RHS.
   for (int outer = 0;; ++outer) {
-    // FP64 residual of every RHS of the slice
-    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-      ELEM(e, i, l, q)
-      double sacc = 0.0;
-      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val[k] * A.x[(int64_t)A.col[k] * R + rb + l];
-      double bi = A.b[q], ri = bi - sacc;
-      r64[q] = ri;
-      atomicAdd(&part[l], ri * ri);
-      atomicAdd(&part2[l], bi * bi);
+    {
+      double q1 = 0.0, q2 = 0.0;
+      ROWS {
+        const int64_t q = i * R + rl;
+        double sacc = 0.0;
+        sacc = ell_row<double, double>(A.len, A.col, A.val, A.ne, i, A.x, R, rl);
+        const double bi = A.b[q], ri = bi - sacc;
+        r64[q] = ri;
+        q1 += ri * ri;
+        q2 += bi * bi;
+      }
+      seg_add(q1, Rp, lane_on, part, l);
+      seg_add(q2, Rp, lane_on, part2, l);
     }
     __syncthreads();
     multi_reduce(cl, part, slots, red1, Rl, phase);
     multi_reduce(cl, part2, slots2, red2, Rl, phase2);
-    for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
-      if (bb[l] < 0) bb[l] = red2[l];
-      nr[l] = red1[l];
-      conv[l] = red1[l] <= A.tol * A.tol * bb[l];
-      act[l] = !conv[l];
+    for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+      if (bb[m] < 0) bb[m] = red2[m];
+      nr[m] = red1[m];
+      conv[m] = red1[m] <= A.tol * A.tol * bb[m];
+      act[m] = !conv[m];
     }
     __syncthreads();
     int all = 1;
-    for (int l = 0; l < Rl; ++l) all &= conv[l];
+    for (int m = 0; m < Rl; ++m) all &= conv[m];
     if (all || outer == 8 || inner_total >= A.maxit) break;
     // FP32 Jacobi-preconditioned BiCGStab on the unit-norm residuals, relative tolerance 1e-5
-    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-      ELEM(e, i, l, q)
-      float ri = nr[l] > 0 ? (float)(r64[q] / sqrt(nr[l])) : 0.f;
-      rv[q] = ri;
-      rh[q] = ri;
-      pv[q] = vv[q] = dv[q] = 0.f;
-      atomicAdd(&part[l], (double)ri * ri);
+    {
+      double q1 = 0.0;
+      const double inv = (lane_on && nr[l] > 0) ? 1.0 / sqrt(nr[l]) : 0.0;
+      ROWS {
+        const int64_t q = i * R + rl;
+        const float ri = (float)(r64[q] * inv);
+        rv[q] = ri;
+        rh[q] = ri;
+        pv[q] = vv[q] = dv[q] = 0.f;
+        q1 += (double)ri * ri;
+      }
+      seg_add(q1, Rp, lane_on, part, l);
     }
     __syncthreads();
     multi_reduce(cl, part, slots, red1, Rl, phase);
-    for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
-      rho[l] = red1[l];
-      rho_old[l] = alp[l] = om[l] = 1.0;
-      act[l] = act[l] && rho[l] > 0.0;
+    for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+      rho[m] = red1[m];
+      rho_old[m] = alp[m] = om[m] = 1.0;
+      act[m] = act[m] && rho[m] > 0.0;
     }
     __syncthreads();
     for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
       int any = 0;
-      for (int l = 0; l < Rl; ++l) any |= act[l];
+      for (int m = 0; m < Rl; ++m) any |= act[m];
       if (!any) break;
       ++inner_total;
-      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-        ELEM(e, i, l, q)
-        if (!act[l]) continue;
-        float beta = (float)((rho[l] / rho_old[l]) * (alp[l] / om[l]));
-        float pi = rv[q] + beta * (pv[q] - (float)om[l] * vv[q]);
-        pv[q] = pi;
-        ph[q] = pi * A.inv_diag[i];
+      bool on = lane_on && act[l];
+      if (on) {
+        const float beta = (float)((rho[l] / rho_old[l]) * (alp[l] / om[l])), omf = (float)om[l];
+        ROWS {
+          const int64_t q = i * R + rl;
+          const float pi = rv[q] + beta * (pv[q] - omf * vv[q]);
+          pv[q] = pi;
+          ph[q] = pi * A.inv_diag[i];
+        }
       }
       cl.sync();
-      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-        ELEM(e, i, l, q)
-        if (!act[l]) continue;
-        float sacc = 0.f;
-        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val32[k] * ph[(int64_t)A.col[k] * R + rb + l];
-        vv[q] = sacc;
-        atomicAdd(&part[l], (double)(rh[q] * sacc));
-      }
-      __syncthreads();
-      multi_reduce(cl, part, slots, red1, Rl, phase);
-      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
-        if (act[l] && red1[l] == 0.0) act[l] = 0;
-        if (act[l]) alp[l] = rho[l] / red1[l];
-      }
-      __syncthreads();
-      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-        ELEM(e, i, l, q)
-        if (!act[l]) continue;
-        float si = rv[q] - (float)alp[l] * vv[q];
-        sv[q] = si;
-        sh[q] = si * A.inv_diag[i];
-        atomicAdd(&part[l], (double)(si * si));
-      }
-      __syncthreads();
-      multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes sh
-      for (int l = threadIdx.x; l < Rl; l += blockDim.x) conv[l] = act[l] && red1[l] <= 1e-10;
-      __syncthreads();
-      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-        ELEM(e, i, l, q)
-        if (!act[l]) continue;
-        if (conv[l]) {
-          dv[q] += (float)alp[l] * ph[q];
-          continue;
+      {
+        double e1 = 0.0;
+        if (on) {
+          ROWS {
+            const int64_t q = i * R + rl;
+            float sacc = 0.f;
+            sacc = ell_row<float, float>(A.len, A.col, A.val32, A.ne, i, ph, R, rl);
+            vv[q] = sacc;
+            e1 += (double)(rh[q] * sacc);
+          }
         }
-        float sacc = 0.f;
-        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) sacc += A.val32[k] * sh[(int64_t)A.col[k] * R + rb + l];
-        tv[q] = sacc;
-        atomicAdd(&part[l], (double)(sacc * sv[q]));
-        atomicAdd(&part2[l], (double)(sacc * sacc));
+        seg_add(e1, Rp, on, part, l);
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+        if (act[m] && red1[m] == 0.0) act[m] = 0;
+        if (act[m]) alp[m] = rho[m] / red1[m];
+      }
+      __syncthreads();
+      on = lane_on && act[l];
+      {
+        double e2 = 0.0;
+        if (on) {
+          const float alf = (float)alp[l];
+          ROWS {
+            const int64_t q = i * R + rl;
+            const float si = rv[q] - alf * vv[q];
+            sv[q] = si;
+            shv[q] = si * A.inv_diag[i];
+            e2 += (double)(si * si);
+          }
+        }
+        seg_add(e2, Rp, on, part, l);
+      }
+      __syncthreads();
+      multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes shv
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) conv[m] = act[m] && red1[m] <= 1e-10;
+      __syncthreads();
+      {
+        double e3 = 0.0, e4 = 0.0;
+        if (on) {
+          const float alf = (float)alp[l];
+          if (conv[l]) {
+            ROWS dv[i * R + rl] += alf * ph[i * R + rl];
+          } else {
+            ROWS {
+              const int64_t q = i * R + rl;
+              float sacc = 0.f;
+              sacc = ell_row<float, float>(A.len, A.col, A.val32, A.ne, i, shv, R, rl);
+              tv[q] = sacc;
+              e3 += (double)(sacc * sv[q]);
+              e4 += (double)(sacc * sacc);
+            }
+          }
+        }
+        const bool on2 = on && !conv[l];
+        seg_add(e3, Rp, on2, part, l);
+        seg_add(e4, Rp, on2, part2, l);
       }
       __syncthreads();
       multi_reduce(cl, part, slots, red1, Rl, phase);
       multi_reduce(cl, part2, slots2, red2, Rl, phase2);
-      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
-        if (conv[l]) act[l] = 0;
-        if (act[l] && red2[l] == 0.0) act[l] = 0;
-        if (act[l]) om[l] = red1[l] / red2[l];
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+        if (conv[m]) act[m] = 0;
+        if (act[m] && red2[m] == 0.0) act[m] = 0;
+        if (act[m]) om[m] = red1[m] / red2[m];
       }
       __syncthreads();
-      for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-        ELEM(e, i, l, q)
-        if (!act[l]) continue;
-        dv[q] += (float)alp[l] * ph[q] + (float)om[l] * sh[q];
-        float ri = sv[q] - (float)om[l] * tv[q];
-        rv[q] = ri;
-        atomicAdd(&part[l], (double)(ri * ri));
-        atomicAdd(&part2[l], (double)(rh[q] * ri));
+      on = lane_on && act[l];
+      {
+        double e5 = 0.0, e6 = 0.0;
+        if (on) {
+          const float alf = (float)alp[l], omf = (float)om[l];
+          ROWS {
+            const int64_t q = i * R + rl;
+            dv[q] += alf * ph[q] + omf * shv[q];
+            const float ri = sv[q] - omf * tv[q];
+            rv[q] = ri;
+            e5 += (double)(ri * ri);
+            e6 += (double)(rh[q] * ri);
+          }
+        }
+        seg_add(e5, Rp, on, part, l);
+        seg_add(e6, Rp, on, part2, l);
       }
       __syncthreads();
       multi_reduce(cl, part, slots, red1, Rl, phase);
       multi_reduce(cl, part2, slots2, red2, Rl, phase2);
-      for (int l = threadIdx.x; l < Rl; l += blockDim.x) {
-        if (!act[l]) continue;
-        rho_old[l] = rho[l];
-        rho[l] = red2[l];
-        if (red1[l] <= 1e-10 || om[l] == 0.0 || rho[l] == 0.0) act[l] = 0;
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) {
+        if (!act[m]) continue;
+        rho_old[m] = rho[m];
+        rho[m] = red2[m];
+        if (red1[m] <= 1e-10 || om[m] == 0.0 || rho[m] == 0.0) act[m] = 0;
       }
       __syncthreads();
     }
-    for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-      ELEM(e, i, l, q)
-      A.x[q] += sqrt(nr[l]) * (double)dv[q];
+    if (lane_on) {
+      const double sc = sqrt(nr[l]);
+      ROWS A.x[i * R + rl] += sc * (double)dv[i * R + rl];
     }
     cl.sync();
   }
   int nconv = 0;
-  for (int l = 0; l < Rl; ++l) nconv += conv[l] ? 1 : 0;
-  for (int64_t e = threadIdx.x; e < nloc; e += blockDim.x) {
-    ELEM(e, i, l, q)
-    A.ring[(i * L + ((A.alpha - 1) & msk)) * R + rb + l] = A.x[q];
-  }
-#undef ELEM
+  for (int m = 0; m < Rl; ++m) nconv += conv[m] ? 1 : 0;
+  ROWS A.ring[(i * L + ((A.alpha - 1) & msk)) * R + rl] = A.x[i * R + rl];
+#undef ROWS
   if (rk == 0 && threadIdx.x == 0) {
     atomicMax(&A.status[0], inner_total);
+    atomicMax(&A.status[6], sweeps);
     if (nconv < Rl) atomicAdd(&A.status[4], 1);
     __threadfence();
     if (atomicAdd(&A.status[5], 1) == ncl - 1) {  // last cluster: publish the verdict
@@ -558,11 +777,26 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
       A.status[1] = miss == 0 ? 1 : 0;
       A.status[2] += miss == 0 ? 0 : 1;
       A.status[3] += it;
+      A.status[7] += atomicAdd(&A.status[6], 0);
       A.status[4] = 0;
       A.status[5] = 0;
     }
   }
   cl.sync();
+}
+
+// CSR -> column-major ELL (padding entries are never read: len[i] bounds them)
+__global__ void k_csr_to_ell(const int32_t* ptr, const int32_t* col, const double* val, int64_t ne, int32_t* len,
+                             int32_t* ecol, double* eval, float* eval32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const int b = ptr[i], n = ptr[i + 1] - b;
+  len[i] = n;
+  for (int k = 0; k < n; ++k) {
+    ecol[(int64_t)k * ne + i] = col[b + k];
+    eval[(int64_t)k * ne + i] = val[b + k];
+    eval32[(int64_t)k * ne + i] = (float)val[b + k];
+  }
 }
 
 __global__ void k_z0_f32(const double* z, const double* inv_diag, int64_t nnz, int64_t ne, float* z32, float* inv32) {
@@ -583,6 +817,22 @@ static tdbem_status tdbem_z0_f32(tdbem_ctx* c) {
   int64_t n = std::max<int64_t>(c->z0_nnz, c->ne);
   k_z0_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->d_z0_val, c->d_z0_inv_diag, c->z0_nnz, c->ne,
                                                                c->d_z0_val32, c->d_z0_inv32);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  // ELL width: the longest row
+  std::vector<int32_t> hp(c->ne + 1);
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(hp.data(), c->d_z0_ptr, (c->ne + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int32_t w = 1;
+  for (int64_t i = 0; i < c->ne; ++i) w = std::max(w, hp[i + 1] - hp[i]);
+  c->z0_ell_w = w;
+  const int64_t ew = (int64_t)w * c->ne;
+  if ((s = c->dalloc(&c->d_ell_len, c->ne)) || (s = c->dalloc(&c->d_ell_col, ew)) ||
+      (s = c->dalloc(&c->d_ell_val, ew)) || (s = c->dalloc(&c->d_ell_val32, ew)))
+    return s;
+  k_csr_to_ell<<<(unsigned)((c->ne + 255) / 256), 256, 0, c->stream>>>(c->d_z0_ptr, c->d_z0_col, c->d_z0_val, c->ne,
+                                                                       c->d_ell_len, c->d_ell_col, c->d_ell_val,
+                                                                       c->d_ell_val32);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
@@ -610,7 +860,7 @@ tdbem_status tdbem_build_z0(tdbem_ctx* c) {
   k_z0_fill<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, c->d_z0_ptr,
                                                                  c->d_z0_col, c->d_z0_val, c->d_z0_inv_diag);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
-  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 8)) || (s = c->dalloc(&c->d_dots, 4)))
+  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 16)) || (s = c->dalloc(&c->d_dots, 4)))
     return s;
   return tdbem_z0_f32(c);
 }
@@ -644,7 +894,7 @@ tdbem_status tdbem_build_z0_csr(tdbem_ctx* c) {
   k_z0_csr<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(rp, col, ml, nl, off, val, ne, c->d_z0_ptr,
                                                                 c->d_z0_col, c->d_z0_val, c->d_z0_inv_diag, nullptr, 1);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
-  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 8)) || (s = c->dalloc(&c->d_dots, 4)))
+  if ((s = c->dalloc(&c->d_work, 8 * ne * c->R)) || (s = c->dalloc(&c->d_status, 16)) || (s = c->dalloc(&c->d_dots, 4)))
     return s;
   return tdbem_z0_f32(c);
 }
@@ -704,26 +954,27 @@ static tdbem_status pick_multi(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
-static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha) {
+static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha, int32_t warm) {
   tdbem_status s;
   if ((s = pick_multi(c))) return s;
   MultiArgs A;
-  A.ptr = c->d_z0_ptr;
-  A.col = c->d_z0_col;
-  A.val = c->d_z0_val;
-  A.val32 = c->d_z0_val32;
+  A.len = c->d_ell_len;
+  A.col = c->d_ell_col;
+  A.val = c->d_ell_val;
+  A.val32 = c->d_ell_val32;
   A.inv_diag = c->d_z0_inv32;
   A.b = c->d_R;
   A.x = c->d_J;
   A.ring = c->d_Jring;
   A.L = c->L;
   A.alpha = alpha;
-  A.warm = c->p.warm_start ? 1 : 0;
+  A.warm = warm;
   A.R = c->R;
   A.w = c->d_work;
   A.ne = c->ne;
   A.tol = c->p.solve_tol;
   A.maxit = c->p.solve_maxit;
+  A.jacobi = c->p.jacobi_sweeps;
   A.status = c->d_status;
   // every cluster must hold at most kMaxRhs right-hand sides
   int ncl = std::min(g_multi_ncl, c->R);
@@ -733,6 +984,7 @@ static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha) {
   }
   c->cluster = g_cluster;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status + 6, 0, sizeof(int32_t), c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(g_cluster * ncl);
   cfg.blockDim = dim3(kSolveThreads);
@@ -748,28 +1000,29 @@ static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha) {
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters) {
+tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t warm) {
   tdbem_status s;
   if (c->R > 1) {
-    if ((s = solve_multi(c, alpha))) return s;
+    if ((s = solve_multi(c, alpha, warm))) return s;
   } else {
     if ((s = pick_cluster(c))) return s;
     SolveArgs A;
-    A.ptr = c->d_z0_ptr;
-    A.col = c->d_z0_col;
-    A.val = c->d_z0_val;
-    A.val32 = c->d_z0_val32;
+    A.len = c->d_ell_len;
+    A.col = c->d_ell_col;
+    A.val = c->d_ell_val;
+    A.val32 = c->d_ell_val32;
     A.inv_diag = c->d_z0_inv32;
     A.b = c->d_R;
     A.x = c->d_J;
     A.ring = c->d_Jring;
     A.L = c->L;
     A.alpha = alpha;
-    A.warm = c->p.warm_start ? 1 : 0;
+    A.warm = warm;
     A.w = c->d_work;
     A.ne = c->ne;
     A.tol = c->p.solve_tol;
     A.maxit = c->p.solve_maxit;
+    A.jacobi = c->p.jacobi_sweeps;
     A.status = c->d_status;
     A.resid = c->d_dots;
     c->cluster = g_cluster;

@@ -1,0 +1,176 @@
+"""Learned warm start on the GPU.
+
+* The inference and training kernels against the FP64 reference network
+  (oracle/mlp.py, itself pinned by finite differences): forward outputs,
+  loss and every gradient entry, on a ragged batch (not a multiple of the
+  128-sample training block).
+* The features recorded during a march against their definition, written
+  out here in numpy from the mesh, the marched currents and the oracle's Z0.
+* Training lowers the loss; on a held-out incident wave the trained network
+  cuts the solver's work while the currents stay those of the plain solve
+  (the solve to its tolerance decides them); a useless network is rejected by
+  the residual fallback and changes nothing.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+F, H = 25, 64
+
+
+def _theta(rng, scale=1.0, zero_out=False):
+    W1 = rng.standard_normal((H, F)) * scale / np.sqrt(F)
+    W2 = rng.standard_normal((H, H)) * scale / np.sqrt(H)
+    w3 = np.zeros(H) if zero_out else rng.standard_normal(H) * scale / np.sqrt(H)
+    return np.concatenate([W1.ravel(), W2.ravel(), w3]).astype(np.float32)
+
+
+def _solver(w, **kw):
+    from paper_2303_05006_gb300 import Solver
+
+    return Solver(w.verts, w.tris, w.dt, w.Nt, **kw)
+
+
+def _pulses(w, n, seed):
+    from workloads.configs import pulse_star, random_plane_waves
+
+    return [pulse_star(w.verts, k=k, pol=pol) for k, pol in random_plane_waves(n, seed)]
+
+
+def test_forward_and_gradient_match_reference():
+    from workloads import workload
+
+    w = workload("sphere80")
+    s = _solver(w)
+    rng = np.random.default_rng(7)
+    th = _theta(rng)
+    s.mlp_set_weights(th)
+    assert np.array_equal(s.mlp_get_weights(), th)
+    n = 1000
+    X = rng.standard_normal((n, F)).astype(np.float32)
+    T = rng.standard_normal(n).astype(np.float32)
+    th64 = th.astype(np.float64)
+    y_ref = ref.forward(th64, X.astype(np.float64), F, H)
+    y = s.mlp_forward(X)
+    assert np.abs(y - y_ref).max() <= 1e-5 * max(1.0, np.abs(y_ref).max())
+    loss, g = s.mlp_grad(X, T)
+    loss_ref, g_ref = ref.loss_and_grad(th64, X.astype(np.float64), T.astype(np.float64), F, H)
+    assert abs(loss - loss_ref) <= 1e-5 * loss_ref
+    # FP32 sums over 1000 samples: relative l2 of the whole gradient and per block of parameters
+    assert np.linalg.norm(g - g_ref) <= 1e-5 * np.linalg.norm(g_ref)
+    for a, b in ((0, H * F), (H * F, H * F + H * H), (H * F + H * H, H * F + H * H + H)):
+        assert np.linalg.norm(g[a:b] - g_ref[a:b]) <= 1e-5 * np.linalg.norm(g_ref[a:b])
+
+
+def _neighbours(w, s):
+    """Edge neighbours and signs from the definition: for edge i, the other
+    two sides of its + triangle, then of its - triangle, in winding order;
+    sign = (sign of i) x (sign of the neighbour) in that triangle."""
+    ev, et = s.edges()
+    key = {(int(a), int(b)): e for e, (a, b) in enumerate(ev)}
+    tris = np.asarray(w.tris)
+
+    def edge_on_side(t, k):
+        a, b = int(tris[t][k]), int(tris[t][(k + 1) % 3])
+        return key[(min(a, b), max(a, b))]
+
+    def sign(e, t):
+        return 1.0 if et[e][0] == t else -1.0
+
+    nb = np.zeros((s.ne, 4), np.int64)
+    sg = np.zeros((s.ne, 4))
+    for i in range(s.ne):
+        for rho in range(2):
+            t = int(et[i][rho])
+            k = [edge_on_side(t, q) for q in range(3)].index(i)
+            for u in (1, 2):
+                j = edge_on_side(t, (k + u) % 3)
+                nb[i, 2 * rho + u - 1] = j
+                sg[i, 2 * rho + u - 1] = sign(i, t) * sign(j, t)
+    return nb, sg
+
+
+def test_recorded_features_match_definition(sphere320_oracle):
+    w, o = sphere320_oracle
+    s = _solver(w)
+    s.set_incident_plane(w.pulses[0])
+    n_steps = 60
+    s.mlp_record(n_steps * s.ne)
+    J = s.march(n_steps)
+    assert s.mlp_count() == n_steps * s.ne
+    X, T = s.mlp_samples(0, n_steps * s.ne)
+    nb, sg = _neighbours(w, s)
+    Z0 = o.z_lag(1)
+    dinv = 1.0 / np.diag(Z0)
+
+    def Jb(beta):
+        return J[beta] if beta >= 0 else np.zeros(s.ne)
+
+    for alpha in (5, 20, 40, 60):  # step alpha solved J^{alpha-1}
+        b = Z0 @ J[alpha - 1]
+        hist = np.stack([Jb(alpha - 2 - k) for k in range(4)], axis=1)  # ne x 4
+        f = np.zeros((s.ne, F))
+        f[:, 0:4] = hist
+        for n in range(4):
+            f[:, 4 + 4 * n: 8 + 4 * n] = sg[:, n:n + 1] * hist[nb[:, n]]
+        g = b * dinv
+        f[:, 20] = g
+        f[:, 21:25] = sg * g[nb]
+        sc = np.sqrt(np.mean(f ** 2, axis=1))
+        xc = 4 * hist[:, 0] - 6 * hist[:, 1] + 4 * hist[:, 2] - hist[:, 3]
+        ok = sc > 0
+        Xd = np.zeros_like(f)
+        Xd[ok] = f[ok] / sc[ok, None]
+        Td = np.zeros(s.ne)
+        Td[ok] = (J[alpha - 1][ok] - xc[ok]) / sc[ok]
+        rows = slice((alpha - 1) * s.ne, alpha * s.ne)
+        assert np.abs(X[rows] - Xd).max() <= 1e-5, alpha
+        assert np.abs(T[rows] - Td).max() <= 1e-4 * max(1.0, np.abs(Td).max()), alpha
+
+
+def test_training_gain_and_fallback():
+    """1920-RWG sphere, direct FP64 path: record 3 seeded incident waves,
+    train on the GPU, then march a held-out wave with and without the network."""
+    from workloads import workload
+
+    w = workload("sphere1280")
+    train_p = _pulses(w, 3, seed=21)
+    test_p = _pulses(w, 1, seed=99)[0]
+    s = _solver(w, jacobi_sweeps=60)
+    rng = np.random.default_rng(5)
+    s.mlp_set_weights(_theta(rng, zero_out=True))  # zero output layer: starts as the extrapolation
+    nsteps = w.Nt - 1
+    s.mlp_record(len(train_p) * nsteps * s.ne)
+    for pu in train_p:
+        s.set_incident_plane(pu)
+        s.reset()
+        s.march(nsteps)
+    X, T = s.mlp_samples(0, s.mlp_count())
+    base = float(np.mean(T.astype(np.float64) ** 2))  # loss of the plain extrapolation (y = 0)
+    loss = s.mlp_train(epochs=6, batch=1024, lr=1e-3, seed=3)
+    assert loss[-1] < loss[0] and loss[-1] < 0.5 * base, (base, loss)
+    s.mlp_record(0)
+
+    def run(use):
+        s.set_incident_plane(test_p)
+        s.reset()
+        s.mlp_use(use)
+        J = s.march(nsteps)
+        inf = s.info()
+        return J, inf.total_jacobi_sweeps, inf.total_solver_iters, s.mlp_stats()
+
+    J0, sw0, it0, _ = run(False)
+    J1, sw1, it1, (used, fb) = run(True)
+    assert np.linalg.norm(J1 - J0) <= 1e-11 * np.linalg.norm(J0)
+    assert used > 0.5 * nsteps, (used, fb)
+    # the solver's work: FP64 Jacobi sweeps plus two SpMV per Krylov iteration
+    work0, work1 = sw0 + 2 * it0, sw1 + 2 * it1
+    assert work1 < 0.95 * work0, (sw0, it0, sw1, it1)
+    # a useless network (large random weights) is rejected and changes nothing
+    s.mlp_set_weights(_theta(np.random.default_rng(8), scale=30.0))
+    J2, _, _, (used2, fb2) = run(True)
+    assert fb2 > 0.5 * nsteps, (used2, fb2)
+    assert np.linalg.norm(J2 - J0) <= 1e-11 * np.linalg.norm(J0)
