@@ -260,25 +260,32 @@ tdbem_status tdbem_mlp_set_weights(tdbem_ctx* ctx, const float* theta);
 tdbem_status tdbem_mlp_get_weights(tdbem_ctx* ctx, float* theta);
 
 /* Training samples.  With capacity > 0 every later step appends, for every
-   edge and right-hand side, its scaled features f/s and target
-   (J^{alpha-1} - xc)/s (edges with s = 0 are stored as zeros) to a device
-   buffer of `capacity` samples, until it is full; capacity = 0 stops
-   recording and frees the buffer.  tdbem_mlp_samples reads back samples
-   [first, first+n) (X [n][F], T [n], host; either may be NULL) and the
-   number stored so far (count may be NULL). */
+   edge and right-hand side, its scaled features f/s, target
+   t = (J^{alpha-1} - xc)/s (edges with s = 0 are stored as zeros) and weight
+   w = s^2 / (mean over that step's samples of s^2 t^2) to a device buffer
+   of `capacity` samples, until it is full; capacity = 0 stops recording and
+   frees the buffer.  A step's mean of w (y - t)^2 is the squared error of
+   the network's guess divided by that of the plain extrapolation (1 for
+   y = 0; steps whose extrapolation is exact get zero weight).
+   tdbem_mlp_samples reads back samples [first, first+n) (X [n][F], T [n],
+   W [n], host; any may be NULL) and the number stored so far (count may be
+   NULL). */
 tdbem_status tdbem_mlp_record(tdbem_ctx* ctx, int64_t capacity);
-tdbem_status tdbem_mlp_samples(tdbem_ctx* ctx, int64_t first, int64_t n, float* X, float* T, int64_t* count);
+tdbem_status tdbem_mlp_samples(tdbem_ctx* ctx, int64_t first, int64_t n, float* X, float* T, float* W,
+                               int64_t* count);
 
-/* Train on the recorded samples with Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+/* Train on the recorded samples (weighted loss) with Adam (beta1 0.9, beta2 0.999, eps 1e-8,
    step size lr) for `epochs` passes in minibatches of `batch` samples (a
    multiple of 128), visiting samples in an order shuffled per epoch from
    `seed`.  Forward, backward and update run in the library's kernels.
    loss ([epochs], may be NULL) receives each epoch's mean minibatch loss. */
 tdbem_status tdbem_mlp_train(tdbem_ctx* ctx, int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss);
 
-/* Loss and gradient of the current parameters on a caller batch (X [n][F],
-   T [n], host), computed by the training kernels (for gradient checks). */
-tdbem_status tdbem_mlp_grad(tdbem_ctx* ctx, const float* X, const float* T, int64_t n, float* loss, float* grad);
+/* Loss (1/n) sum w (y - t)^2 and its gradient for the current parameters
+   on a caller batch (X [n][F], T [n], W [n] or NULL for unit weights, host),
+   computed by the training kernels (for gradient checks). */
+tdbem_status tdbem_mlp_grad(tdbem_ctx* ctx, const float* X, const float* T, const float* W, int64_t n, float* loss,
+                            float* grad);
 
 /* Network output y for the rows of X ([n][F], host) by the inference kernel. */
 tdbem_status tdbem_mlp_forward(tdbem_ctx* ctx, const float* X, int64_t n, float* Y);

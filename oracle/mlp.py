@@ -9,7 +9,8 @@ biases,
     z1 = W1 x,  h1 = tanh(z1),  z2 = W2 h1,  h2 = tanh(z2),  y = w3 . h2,
 
 so that flipping every input flips the output (the march is linear in the
-incident field).  Loss of a batch: mean of (y - t)^2.
+incident field).  Loss of a batch: mean of w (y - t)^2, with sample weights w
+(1 when none are given).
 
 This module is the CPU check of the GPU forward and backward kernels: plain
 numpy in float64, one formula per line, no batching tricks beyond matrix
@@ -37,18 +38,19 @@ def forward(theta: np.ndarray, X: np.ndarray, F: int, H: int) -> np.ndarray:
     return h2 @ w3
 
 
-def loss_and_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray, F: int, H: int):
-    """Mean squared error over the batch and its gradient (chain rule, one
-    layer at a time)."""
+def loss_and_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray, F: int, H: int, W=None):
+    """Weighted mean squared error over the batch and its gradient (chain
+    rule, one layer at a time)."""
     X = np.asarray(X, dtype=np.float64)
     T = np.asarray(T, dtype=np.float64)
+    w = np.ones(len(T)) if W is None else np.asarray(W, dtype=np.float64)
     W1, W2, w3 = unpack(theta, F, H)
     n = X.shape[0]
     h1 = np.tanh(X @ W1.T)          # n x H
     h2 = np.tanh(h1 @ W2.T)         # n x H
     y = h2 @ w3                     # n
-    loss = float(np.mean((y - T) ** 2))
-    dy = 2.0 * (y - T) / n          # n
+    loss = float(np.mean(w * (y - T) ** 2))
+    dy = 2.0 * w * (y - T) / n      # n
     g3 = h2.T @ dy                  # H
     dz2 = np.outer(dy, w3) * (1.0 - h2 ** 2)   # n x H
     g2 = dz2.T @ h1                 # H x H

@@ -90,9 +90,9 @@ def lib():
         L.tdbem_mlp_set_weights.argtypes = [vp, _fp]
         L.tdbem_mlp_get_weights.argtypes = [vp, _fp]
         L.tdbem_mlp_record.argtypes = [vp, i64]
-        L.tdbem_mlp_samples.argtypes = [vp, i64, i64, _fp, _fp, i64p]
+        L.tdbem_mlp_samples.argtypes = [vp, i64, i64, _fp, _fp, _fp, i64p]
         L.tdbem_mlp_train.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _fp]
-        L.tdbem_mlp_grad.argtypes = [vp, _fp, _fp, i64, ctypes.POINTER(ctypes.c_float), _fp]
+        L.tdbem_mlp_grad.argtypes = [vp, _fp, _fp, _fp, i64, ctypes.POINTER(ctypes.c_float), _fp]
         L.tdbem_mlp_forward.argtypes = [vp, _fp, i64, _fp]
         L.tdbem_mlp_use.argtypes = [vp, ctypes.c_int32]
         L.tdbem_mlp_stats.argtypes = [vp, i64p, i64p]
@@ -258,16 +258,18 @@ class Solver:
 
     def mlp_count(self) -> int:
         n = ctypes.c_int64()
-        self._check(lib().tdbem_mlp_samples(self._h, ctypes.c_int64(0), ctypes.c_int64(0), None, None,
+        self._check(lib().tdbem_mlp_samples(self._h, ctypes.c_int64(0), ctypes.c_int64(0), None, None, None,
                                             ctypes.byref(n)))
         return int(n.value)
 
     def mlp_samples(self, first: int, n: int):
         X = np.zeros((n, self.MLP_FEATURES), np.float32)
         T = np.zeros(n, np.float32)
+        W = np.zeros(n, np.float32)
         self._check(lib().tdbem_mlp_samples(self._h, ctypes.c_int64(first), ctypes.c_int64(n),
-                                            X.ctypes.data_as(_fp), T.ctypes.data_as(_fp), None))
-        return X, T
+                                            X.ctypes.data_as(_fp), T.ctypes.data_as(_fp), W.ctypes.data_as(_fp),
+                                            None))
+        return X, T, W
 
     def mlp_train(self, epochs: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
         loss = np.zeros(max(epochs, 1), np.float32)
@@ -275,13 +277,15 @@ class Solver:
                                           ctypes.c_uint64(seed), loss.ctypes.data_as(_fp)))
         return loss[:epochs]
 
-    def mlp_grad(self, X, T):
+    def mlp_grad(self, X, T, W=None):
         X = np.ascontiguousarray(X, dtype=np.float32)
         T = np.ascontiguousarray(T, dtype=np.float32)
+        Wp = None if W is None else np.ascontiguousarray(W, dtype=np.float32)
         g = np.zeros(self.MLP_NPARAM, np.float32)
         loss = ctypes.c_float()
         self._check(lib().tdbem_mlp_grad(self._h, X.ctypes.data_as(_fp), T.ctypes.data_as(_fp),
-                                         ctypes.c_int64(len(T)), ctypes.byref(loss), g.ctypes.data_as(_fp)))
+                                         None if Wp is None else Wp.ctypes.data_as(_fp), ctypes.c_int64(len(T)),
+                                         ctypes.byref(loss), g.ctypes.data_as(_fp)))
         return float(loss.value), g
 
     def mlp_forward(self, X) -> np.ndarray:

@@ -129,9 +129,9 @@ __global__ void __launch_bounds__(128) k_mlp_forward_rows(const float* X, int64_
   Y[t] = mlp_forward(Ws, x);
 }
 
-// training sample of (edge, RHS) for the step just solved: x = f / s and
-// t = (J^{alpha-1} - xc) / s, zeros where s = 0
-__global__ void k_mlp_record(FeatArgs a, const double* J, int64_t base, float* X, float* T) {
+// training sample of (edge, RHS) for the step just solved: x = f / s,
+// t = (J^{alpha-1} - xc) / s (zeros where s = 0) and the raw weight s^2
+__global__ void k_mlp_record(FeatArgs a, const double* J, int64_t base, float* X, float* T, float* Wt) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.ne * a.R) return;
   const int64_t i = t / a.R;
@@ -142,12 +142,39 @@ __global__ void k_mlp_record(FeatArgs a, const double* J, int64_t base, float* X
   float* xo = X + (base + t) * kF;
   for (int f = 0; f < kF; ++f) xo[f] = x[f];
   T[base + t] = s > 0.0 ? (float)((J[t] - xc) / s) : 0.f;
+  Wt[base + t] = (float)(s * s);
+}
+
+// Weights of one step's samples: s^2 divided by the step's mean of s^2 t^2.
+// The weighted loss w (y - t)^2 of a step then is the squared error of the
+// guess divided by that of the plain extrapolation (1 for y = 0): each step
+// counts by how much the network improves on the extrapolation there, which
+// is what the solve's fallback compares.  A step whose extrapolation is exact
+// gets weight zero.
+__global__ void k_mlp_weight_norm(float* Wt, const float* T, int64_t n) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc += (double)Wt[k] * (double)T[k] * (double)T[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[0] = t;
+  }
+  __syncthreads();
+  const double mean = red[0] / (double)n;
+  const float sc = mean > 0.0 ? (float)(1.0 / mean) : 0.f;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) Wt[k] *= sc;
 }
 
 // One minibatch: samples perm[b0 + k] for k < nb (nb <= gridDim.x * kTB).
-// Loss (1/nb) sum (y - t)^2 is added to *loss; gradients are added to G.
-__global__ void __launch_bounds__(kTB) k_mlp_train(const float* X, const float* T, const int32_t* perm, int64_t b0,
-                                                   int32_t nb, const float* Wg, float* G, double* loss) {
+// Loss (1/nb) sum w (y - t)^2 (w = 1 when Wt is null) is added to *loss;
+// gradients are added to G.
+__global__ void __launch_bounds__(kTB) k_mlp_train(const float* X, const float* T, const float* Wt,
+                                                   const int32_t* perm, int64_t b0, int32_t nb, const float* Wg,
+                                                   float* G, double* loss) {
   extern __shared__ float sm[];
   float* Ws = sm;                    // kNP
   float* xs = Ws + kNP;              // [kTB][kF]
@@ -183,7 +210,8 @@ __global__ void __launch_bounds__(kTB) k_mlp_train(const float* X, const float* 
     y += w3[j] * h2[j];
   }
   const float e = valid ? y - T[idx] : 0.f;
-  const float dy = 2.f * e / (float)nb;
+  const float wt = valid ? (Wt ? Wt[idx] : 1.f) : 0.f;
+  const float dy = 2.f * wt * e / (float)nb;
   dys[s] = dy;
   // backward through the two hidden layers
   float* d2 = d2s + s * kHS;
@@ -195,7 +223,7 @@ __global__ void __launch_bounds__(kTB) k_mlp_train(const float* X, const float* 
     d1[q] = acc * (1.f - h1[q] * h1[q]);
   }
   // loss
-  double l = valid ? (double)e * (double)e / (double)nb : 0.0;
+  double l = valid ? (double)wt * (double)e * (double)e / (double)nb : 0.0;
   for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
   if ((s & 31) == 0) lsum[s >> 5] = l;
   __syncthreads();
@@ -251,6 +279,7 @@ struct Mlp {
   int8_t* nbs = nullptr;   // [ne][4]
   float* X = nullptr;      // training samples [cap][kF]
   float* T = nullptr;      // [cap]
+  float* Wt = nullptr;     // [cap] sample weights
   int64_t cap = 0, count = 0;
   bool use = false;
   bool have_w = false;     // parameters set by the caller
@@ -260,7 +289,7 @@ struct Mlp {
 
 static void mlp_free_buffers(Mlp* M) {
   for (void* p : {(void*)M->w, (void*)M->g, (void*)M->m, (void*)M->v, (void*)M->nb, (void*)M->nbs, (void*)M->X,
-                  (void*)M->T, (void*)M->loss, (void*)M->perm})
+                  (void*)M->T, (void*)M->Wt, (void*)M->loss, (void*)M->perm})
     if (p) cudaFree(p);
 }
 
@@ -349,7 +378,9 @@ tdbem_status tdbem_mlp_after_solve(tdbem_ctx* c, int32_t alpha) {
   const int64_t n = c->ne * (int64_t)c->R;
   if (M->count + n > M->cap) return TDBEM_OK;
   k_mlp_record<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(feat_args(c, alpha), c->d_J, M->count, M->X,
-                                                                   M->T);
+                                                                   M->T, M->Wt);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  k_mlp_weight_norm<<<1, 1024, 0, c->stream>>>(M->Wt + M->count, M->T + M->count, n);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   M->count += n;
   return TDBEM_OK;
@@ -397,21 +428,24 @@ tdbem_status tdbem_mlp_record(tdbem_ctx* c, int64_t capacity) {
   if (s) return s;
   Mlp* M = c->mlp;
   MLP_TRY(cudaStreamSynchronize(c->stream));
-  for (void* p : {(void*)M->X, (void*)M->T, (void*)M->perm})
+  for (void* p : {(void*)M->X, (void*)M->T, (void*)M->Wt, (void*)M->perm})
     if (p) cudaFree(p);
   M->X = nullptr;
   M->T = nullptr;
+  M->Wt = nullptr;
   M->perm = nullptr;
   M->cap = M->count = 0;
   if (capacity == 0) return TDBEM_OK;
   MLP_TRY(cudaMalloc(&M->X, capacity * kF * sizeof(float)));
   MLP_TRY(cudaMalloc(&M->T, capacity * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->Wt, capacity * sizeof(float)));
   MLP_TRY(cudaMalloc(&M->perm, capacity * sizeof(int32_t)));
   M->cap = capacity;
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_mlp_samples(tdbem_ctx* c, int64_t first, int64_t n, float* X, float* T, int64_t* count) {
+tdbem_status tdbem_mlp_samples(tdbem_ctx* c, int64_t first, int64_t n, float* X, float* T, float* Wt,
+                               int64_t* count) {
   if (!c || first < 0 || n < 0) return TDBEM_EINVAL;
   Mlp* M = c->mlp;
   if (count) *count = M ? M->count : 0;
@@ -419,6 +453,7 @@ tdbem_status tdbem_mlp_samples(tdbem_ctx* c, int64_t first, int64_t n, float* X,
   if (!M || first + n > M->count) return TDBEM_EINVAL;
   if (X) MLP_TRY(cudaMemcpyAsync(X, M->X + first * kF, n * kF * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   if (T) MLP_TRY(cudaMemcpyAsync(T, M->T + first, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (Wt) MLP_TRY(cudaMemcpyAsync(Wt, M->Wt + first, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   MLP_TRY(cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -445,8 +480,8 @@ tdbem_status tdbem_mlp_train(tdbem_ctx* c, int32_t epochs, int32_t batch, float 
     int64_t nbatch = 0;
     for (int64_t b0 = 0; b0 < n; b0 += batch) {
       const int32_t nb = (int32_t)std::min<int64_t>(batch, n - b0);
-      k_mlp_train<<<(unsigned)((nb + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(M->X, M->T, M->perm, b0, nb,
-                                                                                       M->w, M->g, M->loss);
+      k_mlp_train<<<(unsigned)((nb + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(M->X, M->T, M->Wt, M->perm, b0,
+                                                                                       nb, M->w, M->g, M->loss);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
       ++M->adam_t;
       const float c1 = 1.f - powf(0.9f, (float)M->adam_t), c2 = 1.f - powf(0.999f, (float)M->adam_t);
@@ -463,22 +498,27 @@ tdbem_status tdbem_mlp_train(tdbem_ctx* c, int32_t epochs, int32_t batch, float 
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_mlp_grad(tdbem_ctx* c, const float* X, const float* T, int64_t n, float* loss, float* grad) {
+tdbem_status tdbem_mlp_grad(tdbem_ctx* c, const float* X, const float* T, const float* Wt, int64_t n, float* loss,
+                            float* grad) {
   if (!c || !X || !T || n < 1 || n > INT32_MAX || !grad) return TDBEM_EINVAL;
   Mlp* M = c->mlp;
   if (!M || !M->have_w) {
     c->set_error("mlp: no weights set");
     return TDBEM_ESTATE;
   }
-  float *dX = nullptr, *dT = nullptr;
+  float *dX = nullptr, *dT = nullptr, *dW = nullptr;
   MLP_TRY(cudaMallocAsync(&dX, n * kF * sizeof(float), c->stream));
   MLP_TRY(cudaMallocAsync(&dT, n * sizeof(float), c->stream));
   MLP_TRY(cudaMemcpyAsync(dX, X, n * kF * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   MLP_TRY(cudaMemcpyAsync(dT, T, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  if (Wt) {
+    MLP_TRY(cudaMallocAsync(&dW, n * sizeof(float), c->stream));
+    MLP_TRY(cudaMemcpyAsync(dW, Wt, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  }
   MLP_TRY(cudaMemsetAsync(M->g, 0, kNP * sizeof(float), c->stream));
   MLP_TRY(cudaMemsetAsync(M->loss, 0, sizeof(double), c->stream));
-  k_mlp_train<<<(unsigned)((n + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(dX, dT, nullptr, 0, (int32_t)n, M->w,
-                                                                                M->g, M->loss);
+  k_mlp_train<<<(unsigned)((n + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(dX, dT, dW, nullptr, 0, (int32_t)n,
+                                                                                M->w, M->g, M->loss);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   double l = 0.0;
   MLP_TRY(cudaMemcpyAsync(grad, M->g, kNP * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -486,6 +526,7 @@ tdbem_status tdbem_mlp_grad(tdbem_ctx* c, const float* X, const float* T, int64_
   MLP_TRY(cudaMemsetAsync(M->g, 0, kNP * sizeof(float), c->stream));
   cudaFreeAsync(dX, c->stream);
   cudaFreeAsync(dT, c->stream);
+  if (dW) cudaFreeAsync(dW, c->stream);
   MLP_TRY(cudaStreamSynchronize(c->stream));
   if (loss) *loss = (float)l;
   return TDBEM_OK;

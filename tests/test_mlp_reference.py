@@ -21,7 +21,8 @@ def test_gradient_matches_finite_differences():
     th = _theta(rng)
     X = rng.standard_normal((37, F))
     T = rng.standard_normal(37)
-    _, g = mlp.loss_and_grad(th, X, T, F, H)
+    Wt = rng.uniform(0.1, 3.0, 37)
+    _, g = mlp.loss_and_grad(th, X, T, F, H, Wt)
     # every w3 entry, and a seeded sample of W1 and W2 entries
     idx = np.concatenate([np.arange(H * F + H * H, H * F + H * H + H),
                           rng.choice(H * F, 40, replace=False),
@@ -30,7 +31,7 @@ def test_gradient_matches_finite_differences():
     for k in idx:
         e = np.zeros_like(th)
         e[k] = h
-        fd = (mlp.loss_and_grad(th + e, X, T, F, H)[0] - mlp.loss_and_grad(th - e, X, T, F, H)[0]) / (2 * h)
+        fd = (mlp.loss_and_grad(th + e, X, T, F, H, Wt)[0] - mlp.loss_and_grad(th - e, X, T, F, H, Wt)[0]) / (2 * h)
         assert abs(fd - g[k]) <= 1e-7 * max(1.0, abs(g[k])) + 1e-9, (k, fd, g[k])
 
 
