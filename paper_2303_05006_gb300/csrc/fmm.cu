@@ -80,8 +80,8 @@ struct FmmLevel {
   int ngemm = 0;
   int4* d_tiles = nullptr;        // {gemm, row tile, col tile, 0}: 64 x 64 tiles (CUDA cores)
   int ntiles = 0;
-  int4* d_items_tc = nullptr;     // tensor cores: {gemm, row tile, first chunk, first col tile | count << 20}
-  int nitems_tc = 0;
+  int4* d_tiles_tc = nullptr;     // 128 x 128 tiles (tensor cores)
+  int ntiles_tc = 0;
   double flops_event = 0;         // M2L flops of one gating event
   // time tables: source/target factors for offsets i = 0..M-1
   float* d_tsrc = nullptr;        // [M][pt]  l_n(s_i)
@@ -1054,6 +1054,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           for (int rt = 0; rt < (P + 63) / 64; ++rt)
             for (int ct = 0; ct < (ncol + 63) / 64; ++ct) tiles.push_back(make_int4(g, rt, ct, 0));
           for (int rt = 0; rt < (P + 127) / 128; ++rt)
+            for (int ct = 0; ct < (ncol + 127) / 128; ++ct) tiles_tc.push_back(make_int4(g, rt, ct, 0));
           L.flops_event += 2.0 * P * P * ncol;
         }
       }
@@ -1066,28 +1067,10 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     L.nop = (int)opdesc.size();
     L.ngemm = (int)gemm.size();
     L.ntiles = (int)tiles.size();
-    // tensor-core work items: one K slice of one operator row tile and a run
-    // of 128-column tiles of its GEMM, runs sized so that a gating event has
-    // a few items per SM
-    if (c->p.m2l_prec != TDBEM_P_FP32) {
-      const bool tf = c->p.m2l_prec == TDBEM_P_TF32 || c->p.m2l_prec == TDBEM_P_TF32X3;
-      const int KC = tf ? 32 : 64, nchunks = (P + KC - 1) / KC, slice = tdbem_m2l_tcs_slice_chunks();
-      const int nrt = (P + 127) / 128, nsl = (nchunks + slice - 1) / slice;
-      int64_t total = 0;
-      for (const int4& gd : gemm) total += (int64_t)((gd.z * ((gd.w & 0xff) == 0 ? 3 : 4) * c->R + 127) / 128) * nrt * nsl;
-      const int per = (int)std::max<int64_t>(1, std::min<int64_t>(32, total / (4 * 152)));
-      for (size_t g = 0; g < gemm.size(); ++g) {
-        const int nct = (gemm[g].z * ((gemm[g].w & 0xff) == 0 ? 3 : 4) * c->R + 127) / 128;
-        for (int rt = 0; rt < nrt; ++rt)
-          for (int ch = 0; ch < nchunks; ch += slice)
-            for (int ct = 0; ct < nct; ct += per)
-              tiles_tc.push_back(make_int4((int)g, rt, ch, ct | (std::min(per, nct - ct) << 20)));
-      }
-    }
-    L.nitems_tc = (int)tiles_tc.size();
-    if ((s = c->dalloc(&L.d_items_tc, std::max(1, L.nitems_tc)))) return s;
-    if (L.nitems_tc)
-      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_items_tc, tiles_tc.data(), L.nitems_tc * sizeof(int4), cudaMemcpyHostToDevice));
+    L.ntiles_tc = (int)tiles_tc.size();
+    if ((s = c->dalloc(&L.d_tiles_tc, std::max(1, L.ntiles_tc)))) return s;
+    if (L.ntiles_tc)
+      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles_tc, tiles_tc.data(), L.ntiles_tc * sizeof(int4), cudaMemcpyHostToDevice));
     int4* d_opdesc = nullptr;
     if ((s = c->dalloc(&d_opdesc, std::max(1, L.nop))) || (s = c->dalloc(&L.ops, (int64_t)L.nop * 2 * P * P)) ||
         (s = c->dalloc(&L.d_gemm, std::max(1, L.ngemm))) || (s = c->dalloc(&L.d_tiles, std::max(1, L.ntiles))))
@@ -1243,9 +1226,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
                                                      F->d_smap, MOM(l), k, LOC(l), L.Q, R);
         TDBEM_CUDA_TRY(c, cudaGetLastError());
       } else {
-        tdbem_status s = tdbem_m2l_tcs(c, L.d_gemm, L.d_items_tc, L.nitems_tc, L.ops_img, P, pt, PS, L.d_pO,
-                                       L.d_pS, L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R, c->p.m2l_prec,
-                                       F->d_err);
+        tdbem_status s = tdbem_m2l_tc(c, L.d_gemm, L.d_tiles_tc, L.ntiles_tc, L.ops_img, P, pt, PS, L.d_pO, L.d_pS,
+                                      L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R, c->p.m2l_prec, F->d_err);
         if (s) return s;
       }
       c->prof_end(5, e);

@@ -173,11 +173,6 @@ tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int
                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
                           const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
                           int32_t* err);
-tdbem_status tdbem_m2l_tcs(tdbem_ctx* c, const int4* gemm, const int4* items, int nitems, const uint4* img, int P,
-                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                           const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
-                           int32_t* err);
-int tdbem_m2l_tcs_slice_chunks();
 tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,

@@ -37,6 +37,7 @@ namespace {
 constexpr int kTileM = 128, kTileN = 128, kThreads = 256;
 constexpr uint32_t kTmemCols = 128;
 constexpr int kNCmp = 7;
+constexpr int kSmapSmem = 24 * 1024;  // largest symmetry-map table staged in shared memory
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -180,6 +181,13 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   uint8_t* tA2 = dsm + 32768;
   uint8_t* tB2 = dsm + 49152;
 
+  // the symmetry node maps, staged in shared memory when they fit
+  const int16_t* smp = smap;
+  if (48 * PS * 2 <= kSmapSmem) {
+    int16_t* st = (int16_t*)(dsm + 65536);
+    for (int u = threadIdx.x; u < 48 * PS; u += kThreads) st[u] = smap[u];
+    smp = st;
+  }
   const int4 tl = tiles[blockIdx.x];
   const int4 gd = gemm[tl.x];
   const int kind = gd.w & 0xff, q = (gd.w >> 8) & 0xff, qhi = (gd.w >> 16) & 0xff;
@@ -233,44 +241,68 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       ((uint4*)tA)[u] = __ldg(src + u);
       if (split) ((uint4*)tA2)[u] = __ldg(src + 1024 + u);
     }
-    // moment columns, gathered through the symmetry map
-    for (int u = tid; u < 1024; u += kThreads) {
-      const int n = unit_row(u);
-      const int kk = k0 + unit_k16(u) * E;
-      float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      const int64_t so = src_off[n];
-      if (so >= 0) {
-        const int16_t* mp = smap + map_off[n];
-        if (pt == 4) {  // E/4 spatial nodes of 4 contiguous time coefficients
+    // moment columns, gathered through the symmetry map.  With pt = 4 a
+    // 16-byte unit is one (TF32) or two (BF16) spatial nodes: every thread
+    // first looks up the nodes of all its units, then issues all their
+    // 16-byte moment loads, so that its loads are in flight together.
+    if (pt == 4) {
+      constexpr int kU = 1024 / kThreads;
+      int64_t so[kU];
+      int nd[kU][2];
+      float4 v[kU][2];
 #pragma unroll
-          for (int g = 0; g < 2; ++g) {
-            const int kq = kk + 4 * g;
-            if (4 * g < E && kq < P) {
-              float4 v = *(const float4*)(mom + so + (int64_t)mp[kq >> 2] * 4);
-              x[4 * g] = v.x;
-              x[4 * g + 1] = v.y;
-              x[4 * g + 2] = v.z;
-              x[4 * g + 3] = v.w;
-            }
-          }
-        } else {
+      for (int j = 0; j < kU; ++j) {
+        const int u = tid + j * kThreads, n = unit_row(u);
+        const int kk = k0 + unit_k16(u) * E;
+        so[j] = src_off[n];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int kq = kk + 4 * g;
+          nd[j][g] = (so[j] >= 0 && 4 * g < E && kq < P) ? smp[map_off[n] + (kq >> 2)] : -1;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kU; ++j)
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+          v[j][g] = nd[j][g] >= 0 ? *(const float4*)(mom + so[j] + (int64_t)nd[j][g] * 4)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kU; ++j) {
+        const int u = tid + j * kThreads;
+        const float x[8] = {v[j][0].x, v[j][0].y, v[j][0].z, v[j][0].w, v[j][1].x, v[j][1].y, v[j][1].z, v[j][1].w};
+        uint4 hi, lo;
+        if (tf)
+          split_unit<true>(x, hi, lo);
+        else
+          split_unit<false>(x, hi, lo);
+        ((uint4*)tB)[u] = hi;
+        if (split) ((uint4*)tB2)[u] = lo;
+      }
+    } else {
+      for (int u = tid; u < 1024; u += kThreads) {
+        const int n = unit_row(u);
+        const int kk = k0 + unit_k16(u) * E;
+        float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int64_t so = src_off[n];
+        if (so >= 0) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int kq = kk + e;
             if (e < E && kq < P) {
               const int bp = kq / pt, nt = kq - bp * pt;
-              x[e] = mom[so + (int64_t)mp[bp] * pt + nt];
+              x[e] = mom[so + (int64_t)smp[map_off[n] + bp] * pt + nt];
             }
           }
         }
+        uint4 hi, lo;
+        if (tf)
+          split_unit<true>(x, hi, lo);
+        else
+          split_unit<false>(x, hi, lo);
+        ((uint4*)tB)[u] = hi;
+        if (split) ((uint4*)tB2)[u] = lo;
       }
-      uint4 hi, lo;
-      if (tf)
-        split_unit<true>(x, hi, lo);
-      else
-        split_unit<false>(x, hi, lo);
-      ((uint4*)tB)[u] = hi;
-      if (split) ((uint4*)tB2)[u] = lo;
     }
     fence_async_smem();
     __syncthreads();
@@ -331,250 +363,15 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
           float v3 = __shfl_down_sync(0xffffffffu, val, 3);
           if (col_ok && (lane & 3) == 0 && r < P) {
             int ap = r >> 2;
-            float* dst = loc + dst_off[n] + (int64_t)smap[map_off[n] + ap] * 4;
+            float* dst = loc + dst_off[n] + (int64_t)smp[map_off[n] + ap] * 4;
             atomicAdd((float4*)dst, make_float4(val, v1, v2, v3));
           }
         } else if (col_ok && r < P) {
           int ap = r / pt, m = r - ap * pt;
-          atomicAdd(loc + dst_off[n] + (int64_t)smap[map_off[n] + ap] * pt + m, val);
+          atomicAdd(loc + dst_off[n] + (int64_t)smp[map_off[n] + ap] * pt + m, val);
         }
       }
     }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
-}
-
-// ---------------------------------------------------------------------------
-// Operator-stationary form.  A work item is one K slice (at most kSliceCh
-// chunks) of one 128-row tile of one operator, and a run of 128-column tiles
-// of its GEMM.  The CTA copies the slice's operator image into shared memory
-// once and streams the column tiles through it: per chunk the moment columns
-// are gathered into one of two buffers while the tensor core works on the
-// other (one mbarrier per buffer, every wait bounded); after the last chunk
-// of a column tile the accumulator is added to the targets.  Partial sums of
-// the K slices of one tile meet in those atomic adds.
-constexpr int kSliceCh = 4;
-
-struct TcsArgs {
-  const int4* gemm;   // {op, pair base, npairs, kind | q << 8 | qhi << 16}
-  const int4* items;  // {gemm, row tile, first chunk, first column tile | count << 20}
-  const uint4* img;   // operator images
-  int P, pt, PS;
-  const int32_t* pO;
-  const int32_t* pS;
-  const int16_t* psym;
-  const int16_t* smap;
-  const float* mom;
-  float* loc;
-  int k, Q, R, prec;
-  int32_t* err;
-};
-
-__device__ __forceinline__ bool wait_uniform(uint32_t mb, uint32_t parity) {
-  bool mine = mbar_wait(mb, parity);
-  return __syncthreads_and(mine) != 0;
-}
-
-__global__ void __launch_bounds__(kThreads) k_m2l_tcs(TcsArgs a) {
-  extern __shared__ __align__(1024) uint8_t dsm[];
-  __shared__ int64_t src_off[kTileN];
-  __shared__ int64_t dst_off[kTileN];
-  __shared__ int32_t map_off[kTileN];
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool split = a.prec == 3 || a.prec == 4;
-  const bool tf = a.prec == 1 || a.prec == 4;
-  const int E = tf ? 4 : 8, KC = 8 * E;
-  const int nparts = split ? 2 : 1;
-  const int P = a.P, pt = a.pt;
-  const int nchunks = (P + KC - 1) / KC;
-  const int nrt = (P + kTileM - 1) / kTileM;
-  const int4 it = a.items[blockIdx.x];
-  const int4 gd = a.gemm[it.x];
-  const int kind = gd.w & 0xff, q = (gd.w >> 8) & 0xff, qhi = (gd.w >> 16) & 0xff;
-  const int nk = kind == 0 ? 3 : 4, c0 = kind == 0 ? 0 : 3;
-  const int var = (q == qhi) ? 1 : 0;
-  const int row0 = it.y * kTileM;
-  const int ch0 = it.z, nch = min(kSliceCh, nchunks - ch0);
-  const int ct0 = it.w & 0xFFFFF, nct = it.w >> 20;
-  const int ncol = gd.z * nk * a.R;
-  // shared memory: operator slice [nch][nparts][16 KB], then two B buffers [nparts][16 KB]
-  uint8_t* tAs = dsm;
-  uint8_t* tBb[2] = {dsm + (size_t)kSliceCh * nparts * 16384, dsm + (size_t)(kSliceCh + 1) * nparts * 16384};
-  // the operator slice, once
-  {
-    const uint4* src = a.img + ((((int64_t)gd.x * 2 + kind) * nrt + it.y) * nchunks + ch0) * nparts * 1024;
-    const int nu = nch * nparts * 1024;
-    for (int u = tid; u < nu; u += kThreads) ((uint4*)tAs)[u] = __ldg(src + u);
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = make_idesc(tf ? 2u : 1u);
-  const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-  uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};  // commits and completed waits per buffer
-  bool ok = true;
-  int gidx = 0;  // chunks issued by this CTA
-  for (int t = 0; t < nct && ok; ++t) {
-    const int col0 = (ct0 + t) * kTileN;
-    if (tid < kTileN) {
-      const int gcol = col0 + tid;
-      if (gcol < ncol) {
-        const int pr = gd.y + gcol / (nk * a.R), rem = gcol % (nk * a.R), rhs = rem / nk, c = c0 + rem % nk;
-        src_off[tid] = (((((int64_t)a.pS[pr] * 2 + (a.k & 1)) * 2 + var) * a.R + rhs) * kNCmp + c) * P;
-        dst_off[tid] = ((((int64_t)a.pO[pr] * a.Q + ((a.k + q) % a.Q)) * a.R + rhs) * kNCmp + c) * P;
-        map_off[tid] = (int32_t)a.psym[pr] * a.PS;
-      } else {
-        src_off[tid] = -1;
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < nch && ok; ++j, ++gidx) {
-      const int b = gidx & 1;
-      // the buffer's previous MMAs must be done before it is overwritten
-      while (ok && waited[b] < issued[b]) {
-        ok = wait_uniform(mb[b], waited[b] & 1u);
-        ++waited[b];
-      }
-      if (!ok) break;
-      uint8_t* tB = tBb[b];
-      uint8_t* tB2 = tB + 16384;
-      const int k0 = (ch0 + j) * KC;
-      for (int u = tid; u < 1024; u += kThreads) {
-        const int n = unit_row(u);
-        const int kk = k0 + unit_k16(u) * E;
-        float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int64_t so = src_off[n];
-        if (so >= 0) {
-          const int16_t* mp = a.smap + map_off[n];
-          if (pt == 4) {
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-              const int kq = kk + 4 * g;
-              if (4 * g < E && kq < P) {
-                float4 v = *(const float4*)(a.mom + so + (int64_t)mp[kq >> 2] * 4);
-                x[4 * g] = v.x;
-                x[4 * g + 1] = v.y;
-                x[4 * g + 2] = v.z;
-                x[4 * g + 3] = v.w;
-              }
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int kq = kk + e;
-              if (e < E && kq < P) {
-                const int bp = kq / pt, nt = kq - bp * pt;
-                x[e] = a.mom[so + (int64_t)mp[bp] * pt + nt];
-              }
-            }
-          }
-        }
-        uint4 hi, lo;
-        if (tf)
-          split_unit<true>(x, hi, lo);
-        else
-          split_unit<false>(x, hi, lo);
-        ((uint4*)tB)[u] = hi;
-        if (split) ((uint4*)tB2)[u] = lo;
-      }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(tAs + (size_t)j * nparts * 16384);
-        const uint32_t a1 = a0 + 16384, b0 = smem_u32(tB), b1 = smem_u32(tB2);
-        for (int s = 0; s < 4; ++s) {
-          const uint32_t acc = (j > 0 || s > 0) ? 1u : 0u;
-          const uint32_t off = 256u * s;
-          if (tf) {
-            mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
-            if (split) {
-              mma_tf32(tmem, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
-              mma_tf32(tmem, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
-            }
-          } else {
-            mma_f16(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
-            if (split) {
-              mma_f16(tmem, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
-              mma_f16(tmem, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
-            }
-          }
-        }
-        mma_commit(mb[b]);
-      }
-      ++issued[b];
-    }
-    // the tile's MMAs complete before its accumulator is read
-    for (int b = 0; b < 2 && ok; ++b)
-      while (ok && waited[b] < issued[b]) {
-        ok = wait_uniform(mb[b], waited[b] & 1u);
-        ++waited[b];
-      }
-    if (!ok) break;
-    tc_fence_after();
-    {
-      const int q4 = warp & 3, cb = (warp >> 2) * (kTileN / 2);
-      const int r = row0 + q4 * 32 + lane;
-      for (int j0 = 0; j0 < kTileN / 2; j0 += 16) {
-        uint32_t v[16];
-        uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cb + j0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int n = cb + j0 + jj;
-          float val = __uint_as_float(v[jj]);
-          const bool col_ok = col0 + n < ncol;
-          if (pt == 4) {
-            float v1 = __shfl_down_sync(0xffffffffu, val, 1);
-            float v2 = __shfl_down_sync(0xffffffffu, val, 2);
-            float v3 = __shfl_down_sync(0xffffffffu, val, 3);
-            if (col_ok && (lane & 3) == 0 && r < P) {
-              int ap = r >> 2;
-              float* dst = a.loc + dst_off[n] + (int64_t)a.smap[map_off[n] + ap] * 4;
-              atomicAdd((float4*)dst, make_float4(val, v1, v2, v3));
-            }
-          } else if (col_ok && r < P) {
-            int ap = r / pt, m = r - ap * pt;
-            atomicAdd(a.loc + dst_off[n] + (int64_t)a.smap[map_off[n] + ap] * pt + m, val);
-          }
-        }
-      }
-    }
-    // accumulator read and descriptors used: the next tile may overwrite both
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-  }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
-    // a last bounded chance for issued work to drain before TMEM is freed
-    for (int b = 0; b < 2; ++b)
-      while (waited[b] < issued[b]) {
-        mbar_wait(mb[b], waited[b] & 1u);
-        ++waited[b];
-      }
   }
   tc_fence_before();
   __syncthreads();
@@ -591,11 +388,13 @@ tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int
   using namespace tdbem;
   static bool attr = false;
   if (!attr) {
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536 + 1024));
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           65536 + kSmapSmem + 1024));
     attr = true;
   }
   if (ntiles == 0) return TDBEM_OK;
-  k_m2l_tc<<<ntiles, kThreads, 65536 + 1024, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k,
+  const size_t smem = 65536 + (48 * PS * 2 <= kSmapSmem ? 48 * PS * 2 : 0) + 1024;
+  k_m2l_tc<<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k,
                                                           loc, Q, R, prec, err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
@@ -616,34 +415,6 @@ tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P,
   if (s) return s;
   k_m2l_images<<<(unsigned)((nunits + 255) / 256), 256, 0, c->stream>>>(ops, nunits, P, nrt, nch, nparts, tf ? 1 : 0,
                                                                         *img);
-  TDBEM_CUDA_TRY(c, cudaGetLastError());
-  return TDBEM_OK;
-}
-
-// Dynamic shared memory of the operator-stationary M2L for a precision.
-size_t tdbem_m2l_tcs_smem(int prec) {
-  using namespace tdbem;
-  const int nparts = (prec == TDBEM_P_TF32X3 || prec == TDBEM_P_BF16X3) ? 2 : 1;
-  return (size_t)(kSliceCh + 2) * nparts * 16384 + 1024;
-}
-
-int tdbem_m2l_tcs_slice_chunks() { return tdbem::kSliceCh; }
-
-// Launch the operator-stationary tensor-core M2L of one level event.
-tdbem_status tdbem_m2l_tcs(tdbem_ctx* c, const int4* gemm, const int4* items, int nitems, const uint4* img, int P,
-                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                           const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
-                           int32_t* err) {
-  using namespace tdbem;
-  const size_t smem = tdbem_m2l_tcs_smem(prec);
-  static size_t attr = 0;
-  if (attr < smem) {
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
-  if (nitems == 0) return TDBEM_OK;
-  TcsArgs a{gemm, items, img, P, pt, PS, pO, pS, psym, smap, mom, loc, k, Q, R, prec, err};
-  k_m2l_tcs<<<nitems, kThreads, smem, c->stream>>>(a);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
