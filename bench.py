@@ -152,6 +152,9 @@ def batch_pulses(w, n: int, seed: int = 4):
     return [pulse_star(w.verts, k=k, pol=pol) for k, pol in random_plane_waves(n, seed)] if n > 0 else []
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_m2l_tc launch (TF32x3, p = 4, 7680 RWG)
+M2L_TRAFFIC_TF32X3 = 141975808 + 3774976
+
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
 KERNELS = ["incident_rhs", "near_history" , "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
 
@@ -172,8 +175,13 @@ def roofline(args, info, launches, ms, K):
                     "flops_per_launch": flops / max(launches[dom], 1)}
         peak = bf16 if args.prec in ("bf16", "bf16x3") else bf16 * 1.1 / 2.25
         how = f"{src} bf16_tflops" + ("" if not args.prec.startswith("tf32") else " x 1.1/2.25 (nominal TF32/BF16)")
+        # DRAM bytes of one launch from the committed ncu capture of this kernel and configuration
+        traffic = (M2L_TRAFFIC_TF32X3 if (args.prec == "tf32x3" and args.p == 4 and args.rhs == 1
+                                          and args.workload == "sphere7680") else None)
         return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": tflops / peak, "traffic": None, "peak_source": how,
+                "frac": tflops / peak, "traffic": traffic,
+                "traffic_source": "profiles/m2l_tc_sphere7680_tf32x3.md (one launch)" if traffic else None,
+                "peak_source": how,
                 "flops_per_launch": flops / max(launches[dom], 1),
                 "note": "algorithmic flops (a split form executes three products per flop counted)"
                 if args.prec.endswith("x3") else ""}
