@@ -338,6 +338,7 @@ def run_ours(args, rank, world, dist):
         "clocks": ck,
         "solver_iters_per_step": info.total_solver_iters / K if K else None,
         "jacobi_sweeps_per_step": info.total_jacobi_sweeps / K if K else None,
+        "m2l_tile_rows_per_level": list(info.m2l_tile_rows),
     }
     line.update(cmp)
     if not args.no_cpu_baseline and rank == 0 and world == 1:

@@ -90,6 +90,8 @@ typedef struct {
   int32_t n_rhs;        /* right-hand sides marched together, 1 .. TDBEM_MAX_RHS (batched form) */
   int32_t jacobi_sweeps; /* Z0 solve: at most this many FP64 Jacobi sweeps before the Krylov refinement
                             (0: Krylov only); a sweep that does not cut the residual by 0.7 ends them */
+  int32_t m2l_tile_rows; /* tensor-core M2L: rows of the product per CTA, 128 or 256; 0 (default) times
+                            both at setup on each level and keeps the faster */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -100,7 +102,7 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0. */
+   jacobi_sweeps=0, m2l_tile_rows=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -216,6 +218,8 @@ typedef struct {
   int64_t n_far_pairs;             /* interaction-list cluster pairs over all levels (fast mode) */
   double m2l_flops_per_step;       /* M2L flops per step, averaged over the gating cycle (fast mode) */
   int64_t total_jacobi_sweeps;     /* FP64 Jacobi sweeps of the Z0 solves (per-cluster maximum when batched) */
+  int32_t m2l_tile_rows[8];        /* per octree level: rows of the M2L product per tensor-core CTA (128 or
+                                      256), chosen at setup by timing both shapes; 0 where no tensor-core M2L runs */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 

@@ -28,7 +28,8 @@ class Params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("zeta", ctypes.c_double), ("eps", ctypes.c_double),
                 ("mu", ctypes.c_double), ("s_jump", ctypes.c_double), ("mode", ctypes.c_int32),
                 ("m2l_prec", ctypes.c_int32), ("solve_tol", ctypes.c_double), ("solve_maxit", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
+                ("m2l_tile_rows", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -37,7 +38,8 @@ class Info(ctypes.Structure):
                 ("near_coef_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
                 ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
-                ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64)]
+                ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64),
+                ("m2l_tile_rows", ctypes.c_int32 * 8)]
 
 
 class TdbemError(RuntimeError):

@@ -123,6 +123,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
+      (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();

@@ -80,8 +80,13 @@ struct FmmLevel {
   int ngemm = 0;
   int4* d_tiles = nullptr;        // {gemm, row tile, col tile, 0}: 64 x 64 tiles (CUDA cores)
   int ntiles = 0;
-  int4* d_tiles_tc = nullptr;     // 128 x 128 tiles (tensor cores)
-  int ntiles_tc = 0;
+  // tensor cores: {gemm, row-tile group, 128-column tile, 0} for groups of
+  // mt = 1 or 2 128-row operator tiles per CTA; tc_mt is the shape the setup
+  // autotuner measured faster for this level
+  int4* d_tiles_tc[2] = {nullptr, nullptr};
+  int ntiles_tc[2] = {0, 0};
+  int tc_mt = 1;
+  float tc_ms[2] = {0.f, 0.f};     // autotuner: mean time of one M2L event per shape
   double flops_event = 0;         // M2L flops of one gating event
   // time tables: source/target factors for offsets i = 0..M-1
   float* d_tsrc = nullptr;        // [M][pt]  l_n(s_i)
@@ -107,6 +112,7 @@ struct FmmPlan {
   int64_t* d_off = nullptr;
   double* d_val64 = nullptr;
   float* d_val32 = nullptr;
+  int4* d_npack = nullptr;        // per near pair: {col, first lag >= 2, lag count, offset of that lag's value}
   int64_t nnz = 0, nval = 0, n_near_tri_pairs = 0;
   // far right-hand sides (targets ahead of the current step)
   int Lr = 0;
@@ -598,8 +604,7 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
 // R_i = V_i + Rfar_i - sum_{near j} sum_{m>=2} Zt^(m)_ij J_j^{alpha-m}; FP32
 // coefficients and products, per-lane FP32 partial sums, FP64 row total.
 // One warp per row.  The far slot of this step is cleared.
-__global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, const int32_t* col, const int16_t* m_lo,
-                                                     const uint8_t* nlag, const int64_t* off, const float* val,
+__global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, const int4* pack, const float* val,
                                                      int64_t ne, const double* ring, int L, int alpha,
                                                      const double* V, double* Rfar_slot, double* R) {
   int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -607,14 +612,12 @@ __global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, co
   if (i >= ne) return;
   float s = 0.f;
   for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
-    int lo = m_lo[p], n = nlag[p];
-    const float* z = val + off[p];
-    const double* Jr = ring + (int64_t)col[p] * L;
-    for (int w = 0; w < n; ++w) {
-      int m = lo + w, b = alpha - m;
-      if (m < 2 || b < 0) continue;
-      s += __ldg(z + w) * (float)Jr[b & (L - 1)];
-    }
+    const int4 pk = __ldg(pack + p);  // one 16-byte record per pair
+    const int lo = pk.y & 0xffff;
+    const int n = min(pk.y >> 16, alpha - lo + 1);  // lags with J^{alpha-m}, m >= lo >= 2, known
+    const float* z = val + ((int64_t)(uint32_t)pk.z | ((int64_t)pk.w << 32));
+    const double* Jr = ring + (int64_t)pk.x * L;
+    for (int w = 0; w < n; ++w) s += __ldg(z + w) * (float)Jr[(alpha - lo - w) & (L - 1)];
   }
   double d = s;
   for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
@@ -666,6 +669,23 @@ __global__ void __launch_bounds__(256) k_near_history_multi(const int64_t* row_p
       if (Rfar_slot) Rfar_slot[q] = 0.0;
     }
   }
+}
+
+// Near-pair records for the history sum: the lag m = 1 belongs to Z0 (it is
+// solved for, never summed), so each window starts at lag max(m_lo, 2).
+__global__ void k_pack_near(const int32_t* col, const int16_t* m_lo, const uint8_t* nlag, const int64_t* off,
+                            int64_t nnz, int4* pack) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  int lo = m_lo[p], n = nlag[p];
+  int64_t o = off[p];
+  if (lo < 2) {
+    const int d = min(2 - lo, n);
+    lo += d;
+    n -= d;
+    o += d;
+  }
+  pack[p] = make_int4(col[p], (lo & 0xffff) | (n << 16), (int)(uint32_t)(o & 0xffffffffll), (int)(o >> 32));
 }
 
 __global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
@@ -910,6 +930,10 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     if ((s = c->dalloc(&F->d_val32, F->nval))) return s;
     k_f64_to_f32<<<(unsigned)((F->nval + 255) / 256), 256, 0, c->stream>>>(F->d_val64, F->d_val32, F->nval);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if ((s = c->dalloc(&F->d_npack, F->nnz))) return s;
+    k_pack_near<<<(unsigned)((F->nnz + 255) / 256), 256, 0, c->stream>>>(F->d_col, F->d_mlo, F->d_nlag, F->d_off,
+                                                                          F->nnz, F->d_npack);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
     // largest near lag (ring length)
     std::vector<int16_t> ml(F->nnz);
     std::vector<uint8_t> nl(F->nnz);
@@ -1023,7 +1047,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_psym, hsym.data(), L.npairs * sizeof(int16_t), cudaMemcpyHostToDevice));
     }
     // lag ranges per canonical offset; operators; GEMM and tile lists
-    std::vector<int4> opdesc, gemm, tiles, tiles_tc;
+    std::vector<int4> opdesc, gemm, tiles, tiles_tc, tiles_tc2;
     int qmax = 1;
     for (size_t ci = 0; ci < canons.size(); ++ci) {
       int base = -1, cnt = 0;
@@ -1053,8 +1077,10 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           int ncol = cnt * (kind == 0 ? 3 : 4) * c->R;  // columns (pair, right-hand side, component)
           for (int rt = 0; rt < (P + 63) / 64; ++rt)
             for (int ct = 0; ct < (ncol + 63) / 64; ++ct) tiles.push_back(make_int4(g, rt, ct, 0));
-          for (int rt = 0; rt < (P + 127) / 128; ++rt)
+          for (int rt = 0; rt < (P + 127) / 128; ++rt)  // single 128-row tiles
             for (int ct = 0; ct < (ncol + 127) / 128; ++ct) tiles_tc.push_back(make_int4(g, rt, ct, 0));
+          for (int rt = 0; rt < (P + 255) / 256; ++rt)  // pairs of 128-row tiles
+            for (int ct = 0; ct < (ncol + 127) / 128; ++ct) tiles_tc2.push_back(make_int4(g, rt, ct, 0));
           L.flops_event += 2.0 * P * P * ncol;
         }
       }
@@ -1067,10 +1093,13 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     L.nop = (int)opdesc.size();
     L.ngemm = (int)gemm.size();
     L.ntiles = (int)tiles.size();
-    L.ntiles_tc = (int)tiles_tc.size();
-    if ((s = c->dalloc(&L.d_tiles_tc, std::max(1, L.ntiles_tc)))) return s;
-    if (L.ntiles_tc)
-      TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles_tc, tiles_tc.data(), L.ntiles_tc * sizeof(int4), cudaMemcpyHostToDevice));
+    for (int v = 0; v < 2; ++v) {
+      const std::vector<int4>& tl = v == 0 ? tiles_tc : tiles_tc2;
+      L.ntiles_tc[v] = (int)tl.size();
+      if ((s = c->dalloc(&L.d_tiles_tc[v], std::max(1, L.ntiles_tc[v])))) return s;
+      if (L.ntiles_tc[v])
+        TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles_tc[v], tl.data(), L.ntiles_tc[v] * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     int4* d_opdesc = nullptr;
     if ((s = c->dalloc(&d_opdesc, std::max(1, L.nop))) || (s = c->dalloc(&L.ops, (int64_t)L.nop * 2 * P * P)) ||
         (s = c->dalloc(&L.d_gemm, std::max(1, L.ngemm))) || (s = c->dalloc(&L.d_tiles, std::max(1, L.ntiles))))
@@ -1171,6 +1200,39 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_err, 0, sizeof(int32_t)));
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, nrf * sizeof(double)));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // M2L tile autotuner: time one gating event of each level in both CTA
+  // shapes (one or two 128-row operator tiles per CTA) on this context's own
+  // operators, pairs and right-hand sides, and keep the faster.  The moments
+  // are still zero, so the trial launches add nothing to the local coefficients.
+  if (c->p.m2l_prec != TDBEM_P_FP32 && c->p.m2l_tile_rows != 0) {
+    for (int l = 2; l <= F->lmax; ++l) F->lev[l].tc_mt = c->p.m2l_tile_rows / 128;
+  } else if (c->p.m2l_prec != TDBEM_P_FP32) {
+    cudaEvent_t e0, e1;
+    TDBEM_CUDA_TRY(c, cudaEventCreate(&e0));
+    TDBEM_CUDA_TRY(c, cudaEventCreate(&e1));
+    for (int l = 2; l <= F->lmax; ++l) {
+      FmmLevel& L = F->lev[l];
+      if (!L.ntiles_tc[0]) continue;
+      for (int v = 0; v < 2; ++v) {
+        const int reps = 3;
+        for (int it = -1; it < reps; ++it) {  // one untimed launch first
+          if (it == 0) TDBEM_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+          if ((s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
+                                L.d_pS, L.d_psym, F->d_smap, L.mom, 0, L.loc, L.Q, c->R, c->p.m2l_prec, F->d_err)))
+            return s;
+        }
+        TDBEM_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        TDBEM_CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TDBEM_CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+        L.tc_ms[v] = ms / reps;
+      }
+      L.tc_mt = L.tc_ms[1] < L.tc_ms[0] ? 2 : 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((s = tdbem_fast_check(c))) return s;
+  }
   return TDBEM_OK;
 }
 
@@ -1226,8 +1288,10 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
                                                      F->d_smap, MOM(l), k, LOC(l), L.Q, R);
         TDBEM_CUDA_TRY(c, cudaGetLastError());
       } else {
-        tdbem_status s = tdbem_m2l_tc(c, L.d_gemm, L.d_tiles_tc, L.ntiles_tc, L.ops_img, P, pt, PS, L.d_pO, L.d_pS,
-                                      L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R, c->p.m2l_prec, F->d_err);
+        const int v = L.tc_mt - 1;
+        tdbem_status s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS,
+                                      L.d_pO, L.d_pS, L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R,
+                                      c->p.m2l_prec, F->d_err);
         if (s) return s;
       }
       c->prof_end(5, e);
@@ -1266,9 +1330,8 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
     slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R;
   cudaEvent_t e = c->prof_begin(1);
   if (c->R == 1) {
-    k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag,
-                                                                        F->d_off, F->d_val32, c->ne, ring, c->L,
-                                                                        alpha, V, slot, c->d_R);
+    k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_npack, F->d_val32, c->ne,
+                                                                        ring, c->L, alpha, V, slot, c->d_R);
   } else {
     int RL = 1;
     while (RL < c->R && RL < 32) RL <<= 1;
@@ -1344,6 +1407,8 @@ void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info) {
   }
   info->n_far_pairs = il;
   info->m2l_flops_per_step = fl;
+  for (int l = 2; l <= F->lmax && l < 8; ++l)
+    info->m2l_tile_rows[l] = (c->p.m2l_prec != TDBEM_P_FP32 && F->lev[l].ntiles_tc[0]) ? 128 * F->lev[l].tc_mt : 0;
 }
 
 // CSR of Z0 from the near store

@@ -169,7 +169,7 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c);
 void tdbem_fast_free(tdbem_ctx* c);
 tdbem_status tdbem_fast_check(tdbem_ctx* c);
 // m2l_tc.cu
-tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
+tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
                           int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
                           const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
                           int32_t* err);

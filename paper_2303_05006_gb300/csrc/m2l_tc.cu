@@ -7,7 +7,10 @@
 // gathered through the pair's cube-symmetry node map, and the columns of C are
 // added to the target clusters' local coefficients of interval k+q.
 //
-// One CTA computes a 128 x 128 tile of C.  Operand tiles live in shared
+// One CTA computes two 128 x 128 tiles of C that share their columns (the
+// two 128-row halves of a 256-row operator), so each gathered moment chunk
+// feeds both: the gathers, which bound the kernel, are halved per output.
+// Operand tiles live in shared
 // memory in the canonical K-major layout without swizzle: 8-row x 16-byte
 // core matrices, LBO = 128 B between core matrices along K, SBO = 1024 B
 // between 8-row groups.  With 128 bytes of K per row that layout is a linear
@@ -18,7 +21,7 @@
 // zero-padded past P) and copied in with 16-byte loads; the moment columns
 // are gathered through the symmetry map one spatial node (pt = 4 time
 // coefficients, one 16-byte load) at a time and converted on the fly.  One
-// thread issues tcgen05.mma into a 128-column TMEM accumulator and commits to
+// thread issues tcgen05.mma into a 128-column TMEM accumulator per row tile and commits to
 // an mbarrier; every wait on it is bounded and records a timeout in the error
 // word.  The epilogue reads TMEM with tcgen05.ld (32 lanes x 16 columns per
 // warp and call) and adds each group of pt = 4 consecutive rows -- the four
@@ -35,7 +38,11 @@ namespace tdbem {
 namespace {
 
 constexpr int kTileM = 128, kTileN = 128, kThreads = 256;
-constexpr uint32_t kTmemCols = 128;
+constexpr int kTileBytes = 16384;  // one 128 x 128-byte operand tile
+// per CTA: kMT 128-row operator tiles sharing one gathered B, one 128-column
+// TMEM accumulator each; shared memory A hi/lo per row tile, then B hi/lo
+template <int kMT>
+constexpr int smem_tiles() { return (2 * kMT + 2) * kTileBytes; }
 constexpr int kNCmp = 7;
 constexpr int kSmapSmem = 24 * 1024;  // largest symmetry-map table staged in shared memory
 
@@ -165,26 +172,26 @@ __global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, i
 }
 
 // prec: 1 = TF32, 2 = BF16, 3 = BF16 x 3, 4 = TF32 x 3 (split: hi*hi + hi*lo + lo*hi)
+template <int kMT>
 __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const uint4* img, int P,
                                                      int pt, int PS, const int32_t* pO, const int32_t* pS,
                                                      const int16_t* psym, const int16_t* smap, const float* mom,
                                                      int k, float* loc, int Q, int R, int prec, int32_t* err) {
+  constexpr uint32_t kTmemCols = 128 * kMT;
   extern __shared__ __align__(1024) uint8_t dsm[];
   __shared__ int64_t src_off[kTileN];
   __shared__ int64_t dst_off[kTileN];
   __shared__ int32_t map_off[kTileN];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  // shared tiles (16 KB each): A hi, B hi, A lo, B lo
-  uint8_t* tA = dsm;
-  uint8_t* tB = dsm + 16384;
-  uint8_t* tA2 = dsm + 32768;
-  uint8_t* tB2 = dsm + 49152;
+  // shared tiles (16 KB each): A hi, A lo of each row tile, then B hi, B lo
+  uint8_t* tB = dsm + 2 * kMT * kTileBytes;
+  uint8_t* tB2 = tB + kTileBytes;
 
   // the symmetry node maps, staged in shared memory when they fit
   const int16_t* smp = smap;
   if (48 * PS * 2 <= kSmapSmem) {
-    int16_t* st = (int16_t*)(dsm + 65536);
+    int16_t* st = (int16_t*)(dsm + smem_tiles<kMT>());
     for (int u = threadIdx.x; u < 48 * PS; u += kThreads) st[u] = smap[u];
     smp = st;
   }
@@ -193,7 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int kind = gd.w & 0xff, q = (gd.w >> 8) & 0xff, qhi = (gd.w >> 16) & 0xff;
   const int nk = kind == 0 ? 3 : 4, c0 = kind == 0 ? 0 : 3;
   const int var = (q == qhi) ? 1 : 0;
-  const int row0 = tl.y * kTileM, col0 = tl.z * kTileN;
+  // row tiles kMT*tl.y .. +kMT-1 (those below P)
+  const int rt0 = tl.y * kMT, col0 = tl.z * kTileN;
+  const int row0 = rt0 * kTileM;
   const int ncol = gd.z * nk * R;  // columns (pair, right-hand side, component)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool split = prec == 3 || prec == 4;
@@ -231,15 +240,18 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
 
   const int nchunks = (P + KC - 1) / KC;
   const int nrt = (P + kTileM - 1) / kTileM;
+  const int nmt = min(kMT, nrt - rt0);  // row tiles of this CTA
   const int nparts = split ? 2 : 1;
-  const uint4* Aimg = img + (((int64_t)gd.x * 2 + kind) * nrt + tl.y) * nchunks * nparts * 1024;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
-    // operator rows: copy of the pre-converted image of this chunk
-    const uint4* src = Aimg + (int64_t)ch * nparts * 1024;
-    for (int u = tid; u < 1024; u += kThreads) {
-      ((uint4*)tA)[u] = __ldg(src + u);
-      if (split) ((uint4*)tA2)[u] = __ldg(src + 1024 + u);
+    // operator rows: copies of the pre-converted images of this chunk
+    for (int mt = 0; mt < nmt; ++mt) {
+      const uint4* src = img + ((((int64_t)gd.x * 2 + kind) * nrt + rt0 + mt) * nchunks + ch) * nparts * 1024;
+      uint4* dA = (uint4*)(dsm + 2 * mt * kTileBytes);
+      for (int u = tid; u < 1024; u += kThreads) {
+        dA[u] = __ldg(src + u);
+        if (split) dA[1024 + u] = __ldg(src + 1024 + u);
+      }
     }
     // moment columns, gathered through the symmetry map.  With pt = 4 a
     // 16-byte unit is one (TF32) or two (BF16) spatial nodes: every thread
@@ -308,21 +320,25 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB), a1 = smem_u32(tA2), b1 = smem_u32(tB2);
-      for (int s = 0; s < 4; ++s) {
-        uint32_t acc = (ch > 0 || s > 0) ? 1u : 0u;
-        uint32_t off = 256u * s;  // two core matrices (32 bytes of K) per instruction
-        if (tf) {
-          mma_tf32(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
-          if (split) {
-            mma_tf32(tmem, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
-            mma_tf32(tmem, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
-          }
-        } else {
-          mma_f16(tmem, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
-          if (split) {
-            mma_f16(tmem, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
-            mma_f16(tmem, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
+      const uint32_t b0 = smem_u32(tB), b1 = smem_u32(tB2);
+      for (int mt = 0; mt < nmt; ++mt) {
+        const uint32_t a0 = smem_u32(dsm + 2 * mt * kTileBytes), a1 = a0 + kTileBytes;
+        const uint32_t d = tmem + (uint32_t)(mt * kTileN);  // this row tile's accumulator columns
+        for (int s = 0; s < 4; ++s) {
+          uint32_t acc = (ch > 0 || s > 0) ? 1u : 0u;
+          uint32_t off = 256u * s;  // two core matrices (32 bytes of K) per instruction
+          if (tf) {
+            mma_tf32(d, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
+            if (split) {
+              mma_tf32(d, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
+              mma_tf32(d, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
+            }
+          } else {
+            mma_f16(d, make_desc(a0 + off), make_desc(b0 + off), idesc, acc);
+            if (split) {
+              mma_f16(d, make_desc(a0 + off), make_desc(b1 + off), idesc, 1u);
+              mma_f16(d, make_desc(a1 + off), make_desc(b0 + off), idesc, 1u);
+            }
           }
         }
       }
@@ -339,12 +355,12 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     mbar_wait(mb, (uint32_t)((nchunks - 1) & 1));
   }
   tc_fence_after();
-  if (ok) {
+  for (int mt = 0; ok && mt < nmt; ++mt) {
     const int q4 = warp & 3, cb = (warp >> 2) * 64;
-    const int r = row0 + q4 * 32 + lane;
+    const int r = row0 + mt * kTileM + q4 * 32 + lane;
     for (int j0 = 0; j0 < 64; j0 += 16) {
       uint32_t v[16];
-      uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cb + j0);
+      uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mt * kTileN + cb + j0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
           "%15}, [%16];"
@@ -380,24 +396,35 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
 
 }  // namespace tdbem
 
-// Launch the tensor-core M2L of one level event.
-tdbem_status tdbem_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
-                          int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
-                          int32_t* err) {
+// Launch the tensor-core M2L of one level event with mt (1 or 2) 128-row
+// operator tiles per CTA; tiles must be the list planned for that mt.
+template <int kMT>
+static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
+                                  int P, int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
+                                  const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                                  int32_t* err) {
   using namespace tdbem;
   static bool attr = false;
   if (!attr) {
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           65536 + kSmapSmem + 1024));
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_tc<kMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_tiles<kMT>() + kSmapSmem + 1024));
     attr = true;
   }
   if (ntiles == 0) return TDBEM_OK;
-  const size_t smem = 65536 + (48 * PS * 2 <= kSmapSmem ? 48 * PS * 2 : 0) + 1024;
-  k_m2l_tc<<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k,
-                                                          loc, Q, R, prec, err);
+  const size_t smem = smem_tiles<kMT>() + (48 * PS * 2 <= kSmapSmem ? 48 * PS * 2 : 0) + 1024;
+  k_m2l_tc<kMT><<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc,
+                                                        Q, R, prec, err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
+}
+
+tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
+                          int P, int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
+                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                          int32_t* err) {
+  if (mt == 2)
+    return launch_m2l_tc<2>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc, Q, R, prec, err);
+  return launch_m2l_tc<1>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc, Q, R, prec, err);
 }
 
 // Convert the FP32 operators of one level into the tensor-core images read by

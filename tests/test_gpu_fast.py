@@ -138,3 +138,19 @@ def test_tensor_core_m2l_precisions(sphere1280_direct):
     assert e[1] > 10 * e[4] and e[2] > 10 * e[3], e
     # the accurate tensor-core form keeps the fast path's error at the FP32 level
     assert abs(_rel(J[4], Jd) - _rel(J[0], Jd)) < 1e-4
+
+
+def test_m2l_tile_shapes_and_autotuner(sphere1280_direct):
+    """Both tensor-core M2L shapes (one or two 128-row operator tiles per CTA)
+    give the same march up to the order of FP32 atomic additions, and the
+    setup autotuner reports the shape it measured faster on every far level."""
+    w, Jd = sphere1280_direct
+    J = {rows: _solver(w, mode=1, m2l_prec=4, m2l_tile_rows=rows).march(w.Nt - 1) for rows in (128, 256)}
+    # measured 2.4e-5: the far field's FP32 atomics add in a different order
+    # (an indexing fault in either shape gives an O(1) difference)
+    assert _rel(J[256], J[128]) < 1e-4
+    assert abs(_rel(J[256], Jd) - _rel(J[128], Jd)) < 1e-4
+    s = _solver(w, mode=1, m2l_prec=4)
+    inf = s.info()
+    chosen = [inf.m2l_tile_rows[l] for l in range(2, inf.lmax + 1)]
+    assert chosen and all(r in (128, 256) for r in chosen), chosen
