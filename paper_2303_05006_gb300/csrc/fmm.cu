@@ -113,6 +113,11 @@ struct FmmPlan {
   double* d_val64 = nullptr;
   float* d_val32 = nullptr;
   int4* d_npack = nullptr;        // per near pair: {col, first lag >= 2, lag count, offset of that lag's value}
+  // the near history flattened per test edge: for row i, entries hrow[i] ..
+  // hrow[i+1]-1 hold a coefficient (FP32) and (column << 8) | lag, lags >= 2
+  int64_t* d_hrow = nullptr;
+  float* d_hval = nullptr;
+  int32_t* d_hmeta = nullptr;
   int64_t nnz = 0, nval = 0, n_near_tri_pairs = 0;
   // far right-hand sides (targets ahead of the current step)
   int Lr = 0;
@@ -628,6 +633,40 @@ __global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, co
   }
 }
 
+// Near field, flattened form: a warp streams its row's (coefficient,
+// column << 8 | lag) entries with coalesced loads; every lane does the same
+// work, and the lags of one column are neighbours in the history ring.
+// R_i = V_i + Rfar_i - sum over the row's entries of z J_col^{alpha-m}.
+__global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, const float* hval, const int32_t* hmeta,
+                                                          int64_t ne, const double* ring, int L, int alpha,
+                                                          const double* V, double* Rfar_slot, double* R) {
+  int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (i >= ne) return;
+  const int64_t e0 = hrow[i], e1 = hrow[i + 1];
+  float s0 = 0.f, s1 = 0.f;
+  int64_t e = e0 + lane;
+  for (; e + 32 < e1; e += 64) {
+    const float z0 = __ldg(hval + e), z1 = __ldg(hval + e + 32);
+    const int q0 = __ldg(hmeta + e), q1 = __ldg(hmeta + e + 32);
+    const int b0 = alpha - (q0 & 0xff), b1 = alpha - (q1 & 0xff);
+    if (b0 >= 0) s0 += z0 * (float)ring[(int64_t)(q0 >> 8) * L + (b0 & (L - 1))];
+    if (b1 >= 0) s1 += z1 * (float)ring[(int64_t)(q1 >> 8) * L + (b1 & (L - 1))];
+  }
+  if (e < e1) {
+    const int q0 = __ldg(hmeta + e);
+    const int b0 = alpha - (q0 & 0xff);
+    if (b0 >= 0) s0 += __ldg(hval + e) * (float)ring[(int64_t)(q0 >> 8) * L + (b0 & (L - 1))];
+  }
+  double d = (double)s0 + (double)s1;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  if (lane == 0) {
+    double far = Rfar_slot ? Rfar_slot[i] : 0.0;
+    R[i] = (V ? V[i] : 0.0) + far - d;
+    if (Rfar_slot) Rfar_slot[i] = 0.0;
+  }
+}
+
 // Batched near field (SpMM over R right-hand sides, [..][ne][R] layouts):
 // one warp per row, split into groups of RL lanes (RL = R rounded up to a
 // power of two, at most 32); lane rr of a group takes the right-hand sides
@@ -942,6 +981,39 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     int32_t mx = 0;
     for (int64_t q = 0; q < F->nnz; ++q) mx = std::max<int32_t>(mx, ml[q] + nl[q] - 1);
     F->max_near_lag = mx;
+    // flattened history entries (lags >= 2) per test edge
+    if (mx > 255 || ne >= ((int64_t)1 << 23)) {
+      c->set_error("fast: near window or edge count beyond the flattened near-field encoding");
+      return TDBEM_EINVAL;
+    }
+    {
+      std::vector<int64_t> off(F->nnz);
+      std::vector<float> v32(F->nval);
+      TDBEM_CUDA_TRY(c, cudaMemcpy(off.data(), F->d_off, F->nnz * sizeof(int64_t), cudaMemcpyDeviceToHost));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(v32.data(), F->d_val32, F->nval * sizeof(float), cudaMemcpyDeviceToHost));
+      std::vector<int64_t> hrow(ne + 1, 0);
+      std::vector<float> hval;
+      std::vector<int32_t> hmeta;
+      hval.reserve(F->nval);
+      hmeta.reserve(F->nval);
+      for (int64_t i = 0; i < ne; ++i) {
+        hrow[i] = (int64_t)hval.size();
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+          for (int w = 0; w < nl[q]; ++w) {
+            const int m = ml[q] + w;
+            if (m < 2) continue;
+            hval.push_back(v32[off[q] + w]);
+            hmeta.push_back((col[q] << 8) | m);
+          }
+      }
+      hrow[ne] = (int64_t)hval.size();
+      if ((s = c->dalloc(&F->d_hrow, ne + 1)) || (s = c->dalloc(&F->d_hval, hval.size())) ||
+          (s = c->dalloc(&F->d_hmeta, hmeta.size())))
+        return s;
+      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow, hrow.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval, hval.data(), hval.size() * sizeof(float), cudaMemcpyHostToDevice));
+      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta, hmeta.data(), hmeta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
   }
   c->max_lag = std::max(F->max_near_lag, far ? F->lev[2].M + 4 : 0);
   tdbem_status s;
@@ -1330,8 +1402,8 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
     slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R;
   cudaEvent_t e = c->prof_begin(1);
   if (c->R == 1) {
-    k_near_history<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_row_ptr, F->d_npack, F->d_val32, c->ne,
-                                                                        ring, c->L, alpha, V, slot, c->d_R);
+    k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_hrow, F->d_hval, F->d_hmeta, c->ne,
+                                                                             ring, c->L, alpha, V, slot, c->d_R);
   } else {
     int RL = 1;
     while (RL < c->R && RL < 32) RL <<= 1;

@@ -2,7 +2,8 @@
 //
 // Z0 = Zt^(1) couples only edges whose supports come within c dt of each other
 // (tau = 1 - r/(c dt) > 0), so it is sparse and close to diagonal (section
-// 2.6).  It is stored in CSR and solved with Jacobi-preconditioned BiCGStab to
+// 2.6).  It is built in CSR, kept for the solver in column-major ELL, and
+// solved with Jacobi-preconditioned BiCGStab to
 // a relative residual solve_tol, starting from the cubic extrapolation of the
 // last four currents.
 //
@@ -24,6 +25,10 @@ namespace cg = cooperative_groups;
 namespace tdbem {
 
 constexpr int kSolveThreads = 512;
+// squared relative residual at which an inner FP32 BiCGStab stops: 1e-6 in
+// norm, about what FP32 SpMVs with Z0 (condition ~2) resolve, so that two
+// refinements from a cubic extrapolation reach 1e-13
+constexpr double kInner2 = 1e-12;
 constexpr double kJacRatio = 0.7;  // largest residual ratio per Jacobi sweep that keeps sweeping
 
 __global__ void k_z0_count(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int32_t* cnt) {
@@ -186,7 +191,7 @@ __device__ __forceinline__ float spmv_row32(const SolveArgs& A, int64_t i, const
 
 // Mixed-precision solve of Z0 x = b: FP64 residual r = b - Z0 x (iterative
 // refinement) around an FP32 Jacobi-preconditioned BiCGStab for the
-// correction, inner relative tolerance 1e-5.  Z0 is well conditioned (about 2
+// correction, inner relative tolerance 1e-6 (kInner2).  Z0 is well conditioned (about 2
 // on the test spheres), so each refinement gains five to six digits and two to
 // three refinements reach 1e-13.
 __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       break;
     }
     if (inner_total >= A.maxit) break;
-    // FP32 BiCGStab for Z0 d = r64, relative tolerance 1e-5
+    // FP32 BiCGStab for Z0 d = r64, relative tolerance 1e-6
     double q1[2] = {0.0, 0.0};
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       float ri = (float)(r64[i] * (1.0 / sqrt(rr)));  // unit-norm right-hand side
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
     block_sums<1>(*(double(*)[1])q1, red);
     cluster_sums<1>(cl, *(double(*)[1])q1, slots, bc, phase);
     double rho = q1[0], rho_old = 1.0, alp = 1.0, om = 1.0;
-    const double tin2 = 1e-10 * q1[0];
+    const double tin2 = kInner2 * q1[0];
     for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
       ++inner_total;
       if (rho == 0.0) break;
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
     int all = 1;
     for (int m = 0; m < Rl; ++m) all &= conv[m];
     if (all || outer == 8 || inner_total >= A.maxit) break;
-    // FP32 Jacobi-preconditioned BiCGStab on the unit-norm residuals, relative tolerance 1e-5
+    // FP32 Jacobi-preconditioned BiCGStab on the unit-norm residuals, relative tolerance 1e-6
     {
       double q1 = 0.0;
       const double inv = (lane_on && nr[l] > 0) ? 1.0 / sqrt(nr[l]) : 0.0;
@@ -695,7 +700,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
       }
       __syncthreads();
       multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes shv
-      for (int m = threadIdx.x; m < Rl; m += blockDim.x) conv[m] = act[m] && red1[m] <= 1e-10;
+      for (int m = threadIdx.x; m < Rl; m += blockDim.x) conv[m] = act[m] && red1[m] <= kInner2;
       __syncthreads();
       {
         double e3 = 0.0, e4 = 0.0;
@@ -751,7 +756,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
         if (!act[m]) continue;
         rho_old[m] = rho[m];
         rho[m] = red2[m];
-        if (red1[m] <= 1e-10 || om[m] == 0.0 || rho[m] == 0.0) act[m] = 0;
+        if (red1[m] <= kInner2 || om[m] == 0.0 || rho[m] == 0.0) act[m] = 0;
       }
       __syncthreads();
     }
