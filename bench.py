@@ -188,8 +188,8 @@ def roofline(args, info, launches, ms, K):
     if name in ("near_history",):
         if args.mode == "direct":
             nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8)
-        else:
-            nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1 + 8 + 4)
+        else:  # flattened entries: FP32 coefficient + (column << 8 | lag), 8 B per stored lag
+            nbytes = 2 * info.near_coef_bytes
         gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}

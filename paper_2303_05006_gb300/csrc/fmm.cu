@@ -112,7 +112,6 @@ struct FmmPlan {
   int64_t* d_off = nullptr;
   double* d_val64 = nullptr;
   float* d_val32 = nullptr;
-  int4* d_npack = nullptr;        // per near pair: {col, first lag >= 2, lag count, offset of that lag's value}
   // the near history flattened per test edge: for row i, entries hrow[i] ..
   // hrow[i+1]-1 hold a coefficient (FP32) and (column << 8) | lag, lags >= 2
   int64_t* d_hrow = nullptr;
@@ -605,34 +604,6 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
   for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) L[e] = 0.f;
 }
 
-// Near field + assembled right-hand side:
-// R_i = V_i + Rfar_i - sum_{near j} sum_{m>=2} Zt^(m)_ij J_j^{alpha-m}; FP32
-// coefficients and products, per-lane FP32 partial sums, FP64 row total.
-// One warp per row.  The far slot of this step is cleared.
-__global__ void __launch_bounds__(256) k_near_history(const int64_t* row_ptr, const int4* pack, const float* val,
-                                                     int64_t ne, const double* ring, int L, int alpha,
-                                                     const double* V, double* Rfar_slot, double* R) {
-  int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (i >= ne) return;
-  float s = 0.f;
-  for (int64_t p = row_ptr[i] + lane; p < row_ptr[i + 1]; p += 32) {
-    const int4 pk = __ldg(pack + p);  // one 16-byte record per pair
-    const int lo = pk.y & 0xffff;
-    const int n = min(pk.y >> 16, alpha - lo + 1);  // lags with J^{alpha-m}, m >= lo >= 2, known
-    const float* z = val + ((int64_t)(uint32_t)pk.z | ((int64_t)pk.w << 32));
-    const double* Jr = ring + (int64_t)pk.x * L;
-    for (int w = 0; w < n; ++w) s += __ldg(z + w) * (float)Jr[(alpha - lo - w) & (L - 1)];
-  }
-  double d = s;
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-  if (lane == 0) {
-    double far = Rfar_slot ? Rfar_slot[i] : 0.0;
-    R[i] = (V ? V[i] : 0.0) + far - d;
-    if (Rfar_slot) Rfar_slot[i] = 0.0;
-  }
-}
-
 // Near field, flattened form: a warp streams its row's (coefficient,
 // column << 8 | lag) entries with coalesced loads; every lane does the same
 // work, and the lags of one column are neighbours in the history ring.
@@ -667,64 +638,44 @@ __global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, 
   }
 }
 
-// Batched near field (SpMM over R right-hand sides, [..][ne][R] layouts):
-// one warp per row, split into groups of RL lanes (RL = R rounded up to a
-// power of two, at most 32); lane rr of a group takes the right-hand sides
-// rr, rr+RL, ... and the groups take interleaved nonzeros, so a coefficient is
-// read once per group and the history vectors of a (column, lag) are read
-// contiguously.  Products and the lag sum of a pair are FP32; the sum over
-// the row's pairs is FP64 (with fewer lane groups per RHS than the single
-// kernel has lanes, an FP32 row sum would lose accuracy as R grows).
-__global__ void __launch_bounds__(256) k_near_history_multi(const int64_t* row_ptr, const int32_t* col,
-                                                           const int16_t* m_lo, const uint8_t* nlag,
-                                                           const int64_t* off, const float* val, int64_t ne,
-                                                           const double* ring, int L, int alpha, int R, int RL,
-                                                           const double* V, double* Rfar_slot, double* Rout) {
-  int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31, rr = lane % RL, sub = lane / RL, nsub = 32 / RL;
-  if (i >= ne) return;
+// Batched near field on the flattened entries: one block per row; thread t
+// takes right-hand side r0 + t mod RL (RL = R rounded up to a power of two,
+// at most 32) and the row's entries sub, sub + nsub, ... (sub = t / RL), so
+// each entry's coefficient is read once per lane group and its history
+// R-vector contiguously; partial sums meet in shared memory.
+__global__ void __launch_bounds__(256) k_near_history_flat_multi(const int64_t* hrow, const float* hval,
+                                                                const int32_t* hmeta, int64_t ne, const double* ring,
+                                                                int L, int alpha, int R, int RL, const double* V,
+                                                                double* Rfar_slot, double* Rout) {
+  __shared__ double red[8][32];
+  const int64_t i = blockIdx.x;
+  const int rr = threadIdx.x % RL, sub = threadIdx.x / RL, nsub = blockDim.x / RL;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e0 = hrow[i], e1 = hrow[i + 1];
   for (int r0 = 0; r0 < R; r0 += RL) {
     const int r = r0 + rr;
-    double d = 0.0;  // FP32 lag sum per pair, FP64 across pairs: the error does not grow with R
+    float s = 0.f;
     if (r < R) {
-      for (int64_t p = row_ptr[i] + sub; p < row_ptr[i + 1]; p += nsub) {
-        int lo = m_lo[p], n = nlag[p];
-        const float* z = val + off[p];
-        const double* Jr = ring + (int64_t)col[p] * L * R + r;
-        float sp = 0.f;
-        for (int w = 0; w < n; ++w) {
-          int m = lo + w, b = alpha - m;
-          if (m < 2 || b < 0) continue;
-          sp += __ldg(z + w) * (float)Jr[(int64_t)(b & (L - 1)) * R];
-        }
-        d += sp;
+      for (int64_t e = e0 + sub; e < e1; e += nsub) {
+        const int q = __ldg(hmeta + e);
+        const int b = alpha - (q & 0xff);
+        if (b >= 0) s += __ldg(hval + e) * (float)ring[((int64_t)(q >> 8) * L + (b & (L - 1))) * R + r];
       }
     }
+    double d = s;
     for (int o = 16; o >= RL; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (sub == 0 && r < R) {
-      int64_t q = i * R + r;
-      double far = Rfar_slot ? Rfar_slot[q] : 0.0;
-      Rout[q] = (V ? V[q] : 0.0) + far - d;
+    if (lane < RL) red[warp][lane] = d;
+    __syncthreads();
+    if (threadIdx.x < RL && r0 + (int)threadIdx.x < R) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+      const int64_t q = i * R + r0 + threadIdx.x;
+      const double far = Rfar_slot ? Rfar_slot[q] : 0.0;
+      Rout[q] = (V ? V[q] : 0.0) + far - t;
       if (Rfar_slot) Rfar_slot[q] = 0.0;
     }
+    __syncthreads();
   }
-}
-
-// Near-pair records for the history sum: the lag m = 1 belongs to Z0 (it is
-// solved for, never summed), so each window starts at lag max(m_lo, 2).
-__global__ void k_pack_near(const int32_t* col, const int16_t* m_lo, const uint8_t* nlag, const int64_t* off,
-                            int64_t nnz, int4* pack) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= nnz) return;
-  int lo = m_lo[p], n = nlag[p];
-  int64_t o = off[p];
-  if (lo < 2) {
-    const int d = min(2 - lo, n);
-    lo += d;
-    n -= d;
-    o += d;
-  }
-  pack[p] = make_int4(col[p], (lo & 0xffff) | (n << 16), (int)(uint32_t)(o & 0xffffffffll), (int)(o >> 32));
 }
 
 __global__ void k_f64_to_f32(const double* a, float* b, int64_t n) {
@@ -968,10 +919,6 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     if (s) return s;
     if ((s = c->dalloc(&F->d_val32, F->nval))) return s;
     k_f64_to_f32<<<(unsigned)((F->nval + 255) / 256), 256, 0, c->stream>>>(F->d_val64, F->d_val32, F->nval);
-    TDBEM_CUDA_TRY(c, cudaGetLastError());
-    if ((s = c->dalloc(&F->d_npack, F->nnz))) return s;
-    k_pack_near<<<(unsigned)((F->nnz + 255) / 256), 256, 0, c->stream>>>(F->d_col, F->d_mlo, F->d_nlag, F->d_off,
-                                                                          F->nnz, F->d_npack);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     // largest near lag (ring length)
     std::vector<int16_t> ml(F->nnz);
@@ -1407,9 +1354,8 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
   } else {
     int RL = 1;
     while (RL < c->R && RL < 32) RL <<= 1;
-    k_near_history_multi<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(
-        F->d_row_ptr, F->d_col, F->d_mlo, F->d_nlag, F->d_off, F->d_val32, c->ne, ring, c->L, alpha, c->R, RL, V,
-        slot, c->d_R);
+    k_near_history_flat_multi<<<(unsigned)c->ne, 256, 0, c->stream>>>(F->d_hrow, F->d_hval, F->d_hmeta, c->ne, ring,
+                                                                        c->L, alpha, c->R, RL, V, slot, c->d_R);
   }
   c->prof_end(1, e);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
