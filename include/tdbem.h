@@ -198,6 +198,23 @@ tdbem_status tdbem_march(tdbem_ctx* ctx, int32_t n_steps, double* J_all);
 /* Same with the result written to device memory J_all_dev (may be NULL). */
 tdbem_status tdbem_march_dev(tdbem_ctx* ctx, int32_t n_steps, double* J_all_dev);
 
+/* March several scatterers together.  Context i (its own mesh, dt, tree and
+   right-hand sides) takes n_steps[i] steps; the steps are issued in rounds,
+   one step of every context that still has steps in each round, each context
+   on its own stream (tdbem_set_stream, or the library's stream per context),
+   so that the kernels of different scatterers overlap on the GPU where one
+   scatterer alone leaves SMs idle (the Z0 solve of one context occupies one
+   16-SM cluster).  This is the batched form of the survey's configuration of
+   several scatterers; it is an interleave issued from the host, not a single
+   persistent launch.  J_all_dev (array of n device pointers, each
+   [n_steps[i]][n_rhs][ne] or NULL; the array itself may be NULL) receives
+   every current, as in tdbem_march_dev.  All contexts must live on the current
+   device and be distinct.  On an error, failed (may be NULL) receives the
+   index of the context that reported it (-1 for invalid arguments) and the
+   others may have taken some of their steps. */
+tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* n_steps, double* const* J_all_dev,
+                              int32_t* failed);
+
 /* Restart the march at alpha = 1 (history and future right-hand sides cleared). */
 tdbem_status tdbem_reset(tdbem_ctx* ctx);
 

@@ -7,7 +7,7 @@ Importing it loads the library and fails loudly when it has not been built.
 """
 from ._binding import (TDBEM_DIRECT, TDBEM_FAST, TDBEM_P_BF16, TDBEM_P_BF16X3, TDBEM_P_FP32, TDBEM_P_TF32,
                        TDBEM_P_TF32X3,
-                       Info, Params, Solver, TdbemError, lib, library_path)
+                       Info, Params, Solver, TdbemError, lib, library_path, march_many)
 
-__all__ = ["Solver", "Params", "Info", "TdbemError", "lib", "library_path", "TDBEM_DIRECT", "TDBEM_FAST",
+__all__ = ["Solver", "march_many", "Params", "Info", "TdbemError", "lib", "library_path", "TDBEM_DIRECT", "TDBEM_FAST",
            "TDBEM_P_FP32", "TDBEM_P_TF32", "TDBEM_P_BF16", "TDBEM_P_BF16X3", "TDBEM_P_TF32X3"]

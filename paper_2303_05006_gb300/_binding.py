@@ -98,12 +98,13 @@ def lib():
         L.tdbem_mlp_forward.argtypes = [vp, _fp, i64, _fp]
         L.tdbem_mlp_use.argtypes = [vp, ctypes.c_int32]
         L.tdbem_mlp_stats.argtypes = [vp, i64p, i64p]
+        L.tdbem_march_many.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, _i32p, ctypes.POINTER(vp), _i32p]
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
                      "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
                      "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_weights",
                      "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_samples", "tdbem_mlp_train",
-                     "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats"):
+                     "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats", "tdbem_march_many"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -309,3 +310,19 @@ class Solver:
         inf = Info()
         self._check(lib().tdbem_get_info(self._h, ctypes.byref(inf)))
         return inf
+
+
+def march_many(solvers, n_steps, dev_ptrs=None) -> None:
+    """March several Solver contexts together (tdbem_march_many): steps are
+    issued in rounds, each context on its own stream.  n_steps: one count per
+    solver; dev_ptrs: optional device pointers (ints) receiving each
+    context's currents, [n_steps][n_rhs][ne] float64."""
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s._h.value if hasattr(s._h, "value") else s._h for s in solvers])
+    ns = np.ascontiguousarray(n_steps, dtype=np.int32)
+    dp = None if dev_ptrs is None else (ctypes.c_void_p * n)(*[p or 0 for p in dev_ptrs])
+    failed = ctypes.c_int32(-1)
+    rc = lib().tdbem_march_many(hs, n, ns.ctypes.data_as(_i32p), dp, ctypes.byref(failed))
+    if rc != 0:
+        who = solvers[failed.value] if 0 <= failed.value < n else None
+        raise TdbemError(rc, lib().tdbem_last_error(who._h).decode() if who else "tdbem_march_many failed")

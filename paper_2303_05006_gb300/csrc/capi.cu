@@ -552,21 +552,58 @@ tdbem_status tdbem_march(tdbem_ctx* c, int32_t n_steps, double* J_all) {
   return check_misses(c);
 }
 
+// One step of the march, its current stored at step k of J_all_dev (device, may be null).
+static tdbem_status step_dev(tdbem_ctx* c, int32_t k, double* J_all_dev) {
+  tdbem_status s = step_async(c);
+  if (s) return s;
+  if (J_all_dev) {
+    double* dst = J_all_dev + (int64_t)k * c->ne * c->R;
+    if (c->R == 1) {
+      TDBEM_CUDA_TRY(c, cudaMemcpyAsync(dst, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else if ((s = to_host_layout(c, c->d_J, dst))) {
+      return s;
+    }
+  }
+  return TDBEM_OK;
+}
+
 tdbem_status tdbem_march_dev(tdbem_ctx* c, int32_t n_steps, double* J_all_dev) {
   if (!c || n_steps < 0) return TDBEM_EINVAL;
   for (int32_t k = 0; k < n_steps; ++k) {
-    tdbem_status s = step_async(c);
+    tdbem_status s = step_dev(c, k, J_all_dev);
     if (s) return s;
-    if (J_all_dev) {
-      double* dst = J_all_dev + (int64_t)k * c->ne * c->R;
-      if (c->R == 1) {
-        TDBEM_CUDA_TRY(c, cudaMemcpyAsync(dst, c->d_J, c->ne * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      } else if ((s = to_host_layout(c, c->d_J, dst))) {
+  }
+  return check_misses(c);
+}
+
+tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* n_steps, double* const* J_all_dev,
+                              int32_t* failed) {
+  if (failed) *failed = -1;
+  if (!ctxs || n < 1 || !n_steps) return TDBEM_EINVAL;
+  int32_t rounds = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!ctxs[i] || n_steps[i] < 0) return TDBEM_EINVAL;
+    for (int32_t j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return TDBEM_EINVAL;
+    rounds = std::max(rounds, n_steps[i]);
+  }
+  for (int32_t k = 0; k < rounds; ++k)
+    for (int32_t i = 0; i < n; ++i) {
+      if (k >= n_steps[i]) continue;
+      tdbem_status s = step_dev(ctxs[i], k, J_all_dev ? J_all_dev[i] : nullptr);
+      if (s) {
+        if (failed) *failed = i;
         return s;
       }
     }
+  for (int32_t i = 0; i < n; ++i) {
+    tdbem_status s = check_misses(ctxs[i]);
+    if (s) {
+      if (failed) *failed = i;
+      return s;
+    }
   }
-  return check_misses(c);
+  return TDBEM_OK;
 }
 
 tdbem_status tdbem_reset(tdbem_ctx* c) {

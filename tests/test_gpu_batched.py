@@ -140,3 +140,37 @@ def test_batched_argument_errors():
     s = Solver(w.verts, w.tris, w.dt, w.Nt, n_rhs=2)
     with pytest.raises(TdbemError):
         s.set_incident_plane(w.pulses[0], rhs=2)
+
+
+def test_march_many_matches_separate_marches():
+    """Several scatterers marched together (steps issued in rounds, one stream
+    per context) give the currents of their separate marches: two direct
+    FP64 contexts exactly to rounding, one fast context to the order of its
+    FP32 atomics."""
+    import torch
+
+    from paper_2303_05006_gb300 import Solver, march_many
+    from workloads import workload
+
+    specs = [("sphere80", dict(mode=0), 1e-12), ("sphere320", dict(mode=0), 1e-12),
+             ("sphere1280", dict(mode=1, m2l_prec=4), 1e-4)]
+    ws = [workload(n) for n, _, _ in specs]
+    steps = [min(w.Nt - 1, 120) for w in ws]
+    ref = []
+    for w, (_, kw, _), n in zip(ws, specs, steps):
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, **kw)
+        s.set_incident_plane(w.pulses[0])
+        ref.append(s.march(n))
+        s.close()
+    solvers = []
+    for w, (_, kw, _) in zip(ws, specs):
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, **kw)
+        s.set_incident_plane(w.pulses[0])
+        solvers.append(s)
+    outs = [torch.zeros((n, s.ne), dtype=torch.float64, device="cuda") for n, s in zip(steps, solvers)]
+    march_many(solvers, steps, [o.data_ptr() for o in outs])
+    torch.cuda.synchronize()
+    for o, r, (name, _, tol) in zip(outs, ref, specs):
+        assert _rel(o.cpu().numpy(), r) < tol, name
+    with pytest.raises(Exception):
+        march_many([solvers[0], solvers[0]], [1, 1])
