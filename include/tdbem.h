@@ -101,7 +101,7 @@ typedef struct {
 #define TDBEM_MAX_RHS 64
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
-   DIRECT, FP32, solve_tol=1e-13, solve_maxit=200, warm_start=1, n_rhs=1,
+   DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
    jacobi_sweeps=0, m2l_tile_rows=0. */
 void tdbem_default_params(tdbem_params* p);
 

@@ -52,7 +52,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->mode = TDBEM_DIRECT;
   p->m2l_prec = TDBEM_P_FP32;
   p->solve_tol = 1e-13;
-  p->solve_maxit = 200;
+  p->solve_maxit = 1000;
   p->warm_start = 1;
   p->n_rhs = 1;
   p->jacobi_sweeps = 0;

@@ -29,6 +29,9 @@ constexpr int kSolveThreads = 512;
 // norm; 1e-6 measured 4% fewer iterations and no faster solve, the batched
 // solve slower)
 constexpr double kInner2 = 1e-10;
+// iterations of one inner FP32 solve: a few on well-shaped meshes, ~100 where
+// slivers (a cone tip, the poles of a UV mesh) worsen the conditioning of Z0
+constexpr int kInnerMax = 80;
 constexpr double kJacRatio = 0.7;  // largest residual ratio per Jacobi sweep that keeps sweeping
 
 __global__ void k_z0_count(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int32_t* cnt) {
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
     cluster_sums<1>(cl, *(double(*)[1])q1, slots, bc, phase);
     double rho = q1[0], rho_old = 1.0, alp = 1.0, om = 1.0;
     const double tin2 = kInner2 * q1[0];
-    for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
+    for (int it = 0; it < kInnerMax && inner_total < A.maxit; ++it) {
       ++inner_total;
       if (rho == 0.0) break;
       float beta = (float)((rho / rho_old) * (alp / om));
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
       act[m] = act[m] && rho[m] > 0.0;
     }
     __syncthreads();
-    for (int it = 0; it < 40 && inner_total < A.maxit; ++it) {
+    for (int it = 0; it < kInnerMax && inner_total < A.maxit; ++it) {
       int any = 0;
       for (int m = 0; m < Rl; ++m) any |= act[m];
       if (!any) break;
