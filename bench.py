@@ -214,7 +214,8 @@ def run_many(args, rank, world, dist):
     steps = [min(K, w.Nt - 1 - W) for w in ws]
     solvers = []
     for w in ws:
-        s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R)
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+                   precond=args.precond)
         for r, pu in enumerate([w.pulses[0]] + batch_pulses(w, R - 1)):
             s.set_incident_plane(pu, rhs=r)
         solvers.append(s)
@@ -278,7 +279,7 @@ def run_ours(args, rank, world, dist):
     pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
     s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
-               jacobi_sweeps=args.jacobi)
+               jacobi_sweeps=args.jacobi, precond=args.precond)
     setup_s = time.perf_counter() - t0
     for r, pu in enumerate(pulses):
         s.set_incident_plane(pu, rhs=r)
@@ -388,7 +389,7 @@ def run_ours(args, rank, world, dist):
         "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
                    "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
-                   "jacobi_sweeps_max": args.jacobi,
+                   "jacobi_sweeps_max": args.jacobi, "precond": args.precond,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
                    "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
                          + (" + M2L operators" if args.mode == "fast" else "") + ")",
@@ -426,6 +427,7 @@ def main():
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")
     ap.add_argument("--jacobi", type=int, default=0, help="FP64 Jacobi sweeps before the Krylov solve (0: none)")
+    ap.add_argument("--precond", type=int, default=1, help="Z0 preconditioner: 0 Jacobi, 1 triangle blocks")
     ap.add_argument("--scatterers", default="", help="comma-separated workloads marched together (tdbem_march_many)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")

@@ -92,6 +92,9 @@ typedef struct {
                             (0: Krylov only); a sweep that does not cut the residual by 0.7 ends them */
   int32_t m2l_tile_rows; /* tensor-core M2L: rows of the product per CTA, 128 or 256; 0 (default) times
                             both at setup on each level and keeps the faster */
+  int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
+                            blocks of Z0 among the RWG functions of each triangle, summed; single-RHS
+                            solves only, the batched solver keeps Jacobi) */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -102,7 +105,7 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0, m2l_tile_rows=0. */
+   jacobi_sweeps=0, m2l_tile_rows=0, precond=1. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),

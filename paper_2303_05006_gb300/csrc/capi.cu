@@ -56,6 +56,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->warm_start = 1;
   p->n_rhs = 1;
   p->jacobi_sweeps = 0;
+  p->precond = 1;
 }
 
 static void fill_phys(tdbem_ctx* c) {
@@ -123,7 +124,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
-      (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) ||
+      (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
+      p.precond > 1 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();

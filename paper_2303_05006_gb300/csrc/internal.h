@@ -94,6 +94,8 @@ struct tdbem_ctx {
   int32_t* d_ell_col = nullptr;     // [w][ne]
   double* d_ell_val = nullptr;      // [w][ne]
   float* d_ell_val32 = nullptr;     // [w][ne]
+  int32_t* d_pc_col = nullptr;      // triangle-block preconditioner [5][ne] (precond = 1), else null
+  float* d_pc_val = nullptr;
   // marching state; R right-hand sides share every operator and the RHS
   // index is the fastest one in every per-edge array ([..][ne][R]), so that
   // R = 1 is the plain single-RHS layout

@@ -25,6 +25,7 @@ namespace cg = cooperative_groups;
 namespace tdbem {
 
 constexpr int kSolveThreads = 512;
+constexpr int kPc = 5;  // entries per row of the triangle-block preconditioner
 // squared relative residual at which an inner FP32 BiCGStab stops (1e-5 in
 // norm; 1e-6 measured 4% fewer iterations and no faster solve, the batched
 // solve slower)
@@ -92,6 +93,8 @@ struct SolveArgs {
   const double* val;      // Z0, FP64 (residuals, Jacobi sweeps)
   const float* val32;     // Z0, FP32 (inner iterations)
   const float* inv_diag;  // Jacobi preconditioner
+  const int32_t* pc_col;  // triangle-block preconditioner P as ELL [kPc][ne] (null: Jacobi)
+  const float* pc_val;
   const double* b;
   double* x;        // solution (also written to the ring)
   double* ring;     // [ne][L]
@@ -190,6 +193,15 @@ __device__ __forceinline__ double spmv_row64(const SolveArgs& A, int64_t i, cons
 
 __device__ __forceinline__ float spmv_row32(const SolveArgs& A, int64_t i, const float* x) {
   return ell_row<float, float>(A.len, A.col, A.val32, A.ne, i, x, 1, 0);
+}
+
+// Row i of the triangle-block preconditioner times x (kPc entries: the edge
+// and its four RWG neighbours; unused slots hold a zero value).
+__device__ __forceinline__ float precond_row(const SolveArgs& A, int64_t i, const float* x) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPc; ++k) s += A.pc_val[k * A.ne + i] * x[A.pc_col[k * A.ne + i]];
+  return s;
 }
 
 // Mixed-precision solve of Z0 x = b: FP64 residual r = b - Z0 x (iterative
@@ -332,9 +344,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         float pi = r[i] + beta * (p[i] - omf * v[i]);
         p[i] = pi;
-        ph[i] = pi * A.inv_diag[i];
+        if (!A.pc_val) ph[i] = pi * A.inv_diag[i];
       }
       cl.sync();
+      if (A.pc_val) {  // ph = P p needs the neighbours' p: published by the barrier above
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) ph[i] = precond_row(A, i, p);
+        cl.sync();
+      }
       double e1[1] = {0.0};
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         float vi = spmv_row32(A, i, ph);
@@ -350,14 +366,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         float si = r[i] - alf * v[i];
         s[i] = si;
-        sh[i] = si * A.inv_diag[i];
+        if (!A.pc_val) sh[i] = si * A.inv_diag[i];
         e2[0] += (double)(si * si);
       }
       block_sums<1>(e2, red);
-      cluster_sums<1>(cl, e2, slots, bc, phase);  // also orders sh for the SpMV below
+      cluster_sums<1>(cl, e2, slots, bc, phase);  // also orders sh (or s) for what follows
       if (e2[0] <= tin2) {
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] += alf * ph[i];
         break;
+      }
+      if (A.pc_val) {
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) sh[i] = precond_row(A, i, s);
+        cl.sync();
       }
       double e3[2] = {0.0, 0.0};
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -819,6 +839,69 @@ using namespace tdbem;
 
 static int g_cluster = 0;
 
+// Triangle-block (additive Schwarz) preconditioner: for every triangle the
+// 3 x 3 block of Z0 among the RWG functions of its three sides is inverted,
+// and P = sum over triangles of the inverses scattered to their rows and
+// columns.  Row i of P couples edge i with the other sides of its two
+// triangles (at most kPc entries).  A triangle whose block is singular adds
+// its diagonal reciprocals instead.
+static tdbem_status build_triangle_precond(tdbem_ctx* c, const std::vector<int32_t>& hp) {
+  const int64_t ne = c->ne, nnz = hp[ne];
+  std::vector<int32_t> hc(nnz);
+  std::vector<double> hv(nnz);
+  TDBEM_CUDA_TRY(c, cudaMemcpy(hc.data(), c->d_z0_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  TDBEM_CUDA_TRY(c, cudaMemcpy(hv.data(), c->d_z0_val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+  auto z = [&](int32_t i, int32_t j) {
+    for (int32_t k = hp[i]; k < hp[i + 1]; ++k)
+      if (hc[k] == j) return hv[k];
+    return 0.0;
+  };
+  std::vector<int32_t> pcol(kPc * ne, 0);
+  std::vector<double> pval(kPc * ne, 0.0);
+  std::vector<int> used(ne, 0);
+  auto add = [&](int32_t i, int32_t j, double v) {
+    for (int k = 0; k < used[i]; ++k)
+      if (pcol[k * ne + i] == j) {
+        pval[k * ne + i] += v;
+        return true;
+      }
+    if (used[i] == kPc) return false;
+    pcol[used[i] * ne + i] = j;
+    pval[used[i] * ne + i] = v;
+    ++used[i];
+    return true;
+  };
+  for (int64_t t = 0; t < c->nt; ++t) {
+    const int32_t e[3] = {c->te[3 * t], c->te[3 * t + 1], c->te[3 * t + 2]};
+    double B[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) B[a][b] = z(e[a], e[b]);
+    double C[3][3];  // cofactors
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3, b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+        C[a][b] = B[a1][b1] * B[a2][b2] - B[a1][b2] * B[a2][b1];
+      }
+    const double det = B[0][0] * C[0][0] + B[0][1] * C[0][1] + B[0][2] * C[0][2];
+    double nb = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) nb = std::max(nb, std::fabs(B[a][b]));
+    bool ok = std::fabs(det) > 1e-12 * nb * nb * nb;
+    for (int a = 0; a < 3 && ok; ++a)
+      for (int b = 0; b < 3 && ok; ++b) ok = add(e[a], e[b], C[b][a] / det);  // inverse = adjugate / det
+    if (!ok)
+      for (int a = 0; a < 3; ++a)
+        if (B[a][a] != 0.0) add(e[a], e[a], 1.0 / B[a][a]);
+  }
+  std::vector<float> pv32(kPc * ne);
+  for (int64_t k = 0; k < kPc * ne; ++k) pv32[k] = (float)pval[k];
+  tdbem_status s;
+  if ((s = c->dalloc(&c->d_pc_col, kPc * ne)) || (s = c->dalloc(&c->d_pc_val, kPc * ne))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpy(c->d_pc_col, pcol.data(), kPc * ne * sizeof(int32_t), cudaMemcpyHostToDevice));
+  TDBEM_CUDA_TRY(c, cudaMemcpy(c->d_pc_val, pv32.data(), kPc * ne * sizeof(float), cudaMemcpyHostToDevice));
+  return TDBEM_OK;
+}
+
 static tdbem_status tdbem_z0_f32(tdbem_ctx* c) {
   tdbem_status s;
   if ((s = c->dalloc(&c->d_z0_val32, c->z0_nnz)) || (s = c->dalloc(&c->d_z0_inv32, c->ne))) return s;
@@ -843,6 +926,7 @@ static tdbem_status tdbem_z0_f32(tdbem_ctx* c) {
                                                                        c->d_ell_val32);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->p.precond == 1) return build_triangle_precond(c, hp);
   return TDBEM_OK;
 }
 
@@ -1020,6 +1104,8 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t
     A.val = c->d_ell_val;
     A.val32 = c->d_ell_val32;
     A.inv_diag = c->d_z0_inv32;
+    A.pc_col = c->d_pc_col;
+    A.pc_val = c->d_pc_val;
     A.b = c->d_R;
     A.x = c->d_J;
     A.ring = c->d_Jring;

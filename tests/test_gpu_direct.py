@@ -116,3 +116,14 @@ def test_errors_are_returned():
     with pytest.raises(TdbemError) as e:
         s.step()  # beyond Nt-1
     assert e.value.code == 7
+
+
+def test_jacobi_preconditioner_march(sphere320_oracle, sphere320_march):
+    """The Z0 solve with the plain Jacobi preconditioner reaches the same
+    currents as the oracle's LU march (bar 1e-10), like the triangle-block
+    default."""
+    w, o = sphere320_oracle
+    s = _solver(w, precond=0)
+    J = s.march(w.Nt - 1)
+    assert np.linalg.norm(J - sphere320_march) / np.linalg.norm(sphere320_march) < 1e-10
+    assert s.info().total_solver_iters > 0
