@@ -93,8 +93,7 @@ typedef struct {
   int32_t m2l_tile_rows; /* tensor-core M2L: rows of the product per CTA, 128 or 256; 0 (default) times
                             both at setup on each level and keeps the faster */
   int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
-                            blocks of Z0 among the RWG functions of each triangle, summed; single-RHS
-                            solves only, the batched solver keeps Jacobi) */
+                            blocks of Z0 among the RWG functions of each triangle, summed) */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one

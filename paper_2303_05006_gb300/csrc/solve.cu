@@ -195,6 +195,15 @@ __device__ __forceinline__ float spmv_row32(const SolveArgs& A, int64_t i, const
   return ell_row<float, float>(A.len, A.col, A.val32, A.ne, i, x, 1, 0);
 }
 
+// The same for column rl of an [ne][R] block
+__device__ __forceinline__ float precond_row_r(const int32_t* pcol, const float* pval, int64_t ne, int64_t i,
+                                               const float* x, int R, int rl) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPc; ++k) s += pval[k * ne + i] * x[(int64_t)pcol[k * ne + i] * R + rl];
+  return s;
+}
+
 // Row i of the triangle-block preconditioner times x (kPc entries: the edge
 // and its four RWG neighbours; unused slots hold a zero value).
 __device__ __forceinline__ float precond_row(const SolveArgs& A, int64_t i, const float* x) {
@@ -437,6 +446,8 @@ constexpr int kMaxRhs = 64;
 
 struct MultiArgs {
   const int32_t* len;  // Z0 as column-major ELL (see SolveArgs)
+  const int32_t* pc_col;  // triangle-block preconditioner (see SolveArgs; null: Jacobi)
+  const float* pc_val;
   const int32_t* col;
   const double* val;
   const float* val32;
@@ -682,10 +693,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
           const int64_t q = i * R + rl;
           const float pi = rv[q] + beta * (pv[q] - omf * vv[q]);
           pv[q] = pi;
-          ph[q] = pi * A.inv_diag[i];
+          if (!A.pc_val) ph[q] = pi * A.inv_diag[i];
         }
       }
       cl.sync();
+      if (A.pc_val) {  // ph = P p: the neighbours' p were published by the barrier above
+        if (on) {
+          ROWS ph[i * R + rl] = precond_row_r(A.pc_col, A.pc_val, A.ne, i, pv, R, rl);
+        }
+        cl.sync();
+      }
       {
         double e1 = 0.0;
         if (on) {
@@ -715,7 +732,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
             const int64_t q = i * R + rl;
             const float si = rv[q] - alf * vv[q];
             sv[q] = si;
-            shv[q] = si * A.inv_diag[i];
+            if (!A.pc_val) shv[q] = si * A.inv_diag[i];
             e2 += (double)(si * si);
           }
         }
@@ -725,6 +742,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab_multi(MultiArgs A) {
       multi_reduce(cl, part, slots, red1, Rl, phase);  // its cluster barrier also publishes shv
       for (int m = threadIdx.x; m < Rl; m += blockDim.x) conv[m] = act[m] && red1[m] <= kInner2;
       __syncthreads();
+      if (A.pc_val) {  // shv = P s for the right-hand sides still iterating
+        if (on && !conv[l]) {
+          ROWS shv[i * R + rl] = precond_row_r(A.pc_col, A.pc_val, A.ne, i, sv, R, rl);
+        }
+        cl.sync();
+      }
       {
         double e3 = 0.0, e4 = 0.0;
         if (on) {
@@ -1055,6 +1078,8 @@ static tdbem_status solve_multi(tdbem_ctx* c, int32_t alpha, int32_t warm) {
   A.val = c->d_ell_val;
   A.val32 = c->d_ell_val32;
   A.inv_diag = c->d_z0_inv32;
+  A.pc_col = c->d_pc_col;
+  A.pc_val = c->d_pc_val;
   A.b = c->d_R;
   A.x = c->d_J;
   A.ring = c->d_Jring;
