@@ -18,7 +18,8 @@
 // bytes 16((u >> 3) & 7) .. +15, so thread t writing units t, t+256, ... is
 // free of bank conflicts.  The operators are converted once at setup into
 // exactly these images (TF32, BF16, or hi and lo parts for the split forms,
-// zero-padded past P) and copied in with 16-byte loads; the moment columns
+// zero-padded past P) and brought in by TMA bulk copies (cp.async.bulk, one
+// per row tile and chunk, completing on an mbarrier); the moment columns
 // are gathered through the symmetry map one spatial node (pt = 4 time
 // coefficients, one 16-byte load) at a time and converted on the fly.  One
 // thread issues tcgen05.mma into a 128-column TMEM accumulator per row tile and commits to
@@ -96,6 +97,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   for (uint32_t i = 0; i < (1u << 20); ++i)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
+}
+
+// arrive on mbar (one of its expected arrivals) and add bytes to the
+// transaction count the current phase waits for
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk copy (TMA, no tensor map) of bytes from global to this CTA's shared
+// memory, counted on mbar; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -182,7 +197,8 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   __shared__ int64_t src_off[kTileN];
   __shared__ int64_t dst_off[kTileN];
   __shared__ int32_t map_off[kTileN];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar;   // MMA completion
+  __shared__ __align__(8) uint64_t abar;   // operator tiles landed
   __shared__ uint32_t tmem_base;
   // shared tiles (16 KB each): A hi, A lo of each row tile, then B hi, B lo
   uint8_t* tB = dsm + 2 * kMT * kTileBytes;
@@ -228,6 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&abar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -235,8 +252,9 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = make_idesc(tf ? 2u : 1u);
-  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t mb = smem_u32(&mbar), ab = smem_u32(&abar);
   bool ok = true;
+  bool a_pending = false;  // thread 0: an operator copy not yet seen complete
 
   const int nchunks = (P + KC - 1) / KC;
   const int nrt = (P + kTileM - 1) / kTileM;
@@ -244,14 +262,17 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int nparts = split ? 2 : 1;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
-    // operator rows: copies of the pre-converted images of this chunk
-    for (int mt = 0; mt < nmt; ++mt) {
-      const uint4* src = img + ((((int64_t)gd.x * 2 + kind) * nrt + rt0 + mt) * nchunks + ch) * nparts * 1024;
-      uint4* dA = (uint4*)(dsm + 2 * mt * kTileBytes);
-      for (int u = tid; u < 1024; u += kThreads) {
-        dA[u] = __ldg(src + u);
-        if (split) dA[1024 + u] = __ldg(src + 1024 + u);
+    // operator rows: the pre-converted images of this chunk (hi and lo parts
+    // contiguous, nparts x 16 KB per row tile) brought in by the TMA bulk-copy
+    // engine while the threads gather the moments; the previous chunk's MMAs
+    // have completed, so the tiles are free
+    if (tid == 0) {
+      mbar_expect_tx(ab, (uint32_t)(nmt * nparts * kTileBytes));
+      for (int mt = 0; mt < nmt; ++mt) {
+        const uint4* src = img + ((((int64_t)gd.x * 2 + kind) * nrt + rt0 + mt) * nchunks + ch) * nparts * 1024;
+        bulk_g2s(smem_u32(dsm + 2 * mt * kTileBytes), src, (uint32_t)(nparts * kTileBytes), ab);
       }
+      a_pending = true;
     }
     // moment columns, gathered through the symmetry map.  With pt = 4 a
     // 16-byte unit is one (TF32) or two (BF16) spatial nodes: every thread
@@ -318,10 +339,13 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     }
     fence_async_smem();
     __syncthreads();
+    bool a_ok = true;
     if (tid == 0) {
+      a_ok = mbar_wait(ab, (uint32_t)(ch & 1));
+      a_pending = !a_ok;
       tc_fence_after();
       const uint32_t b0 = smem_u32(tB), b1 = smem_u32(tB2);
-      for (int mt = 0; mt < nmt; ++mt) {
+      for (int mt = 0; a_ok && mt < nmt; ++mt) {
         const uint32_t a0 = smem_u32(dsm + 2 * mt * kTileBytes), a1 = a0 + kTileBytes;
         const uint32_t d = tmem + (uint32_t)(mt * kTileN);  // this row tile's accumulator columns
         for (int s = 0; s < 4; ++s) {
@@ -346,13 +370,16 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     }
     // the next chunk overwrites the tiles: wait for the MMAs to finish; the
     // verdict is made uniform across the CTA before anyone acts on it
-    bool mine = mbar_wait(mb, (uint32_t)(ch & 1));
+    // (with no MMA issued the commit arrives at once)
+    bool mine = mbar_wait(mb, (uint32_t)(ch & 1)) && a_ok;
     ok = __syncthreads_and(mine) != 0;
-    if (!ok && tid == 0) atomicExch(err, 1);
-  }
-  if (!ok) {
-    // give the tensor core a last bounded chance to drain before TMEM is freed
-    mbar_wait(mb, (uint32_t)((nchunks - 1) & 1));
+    if (!ok) {
+      if (tid == 0) atomicExch(err, 1);
+      // give the tensor core and the copy engine a last bounded chance to
+      // drain this chunk before TMEM is freed and the CTA exits
+      mbar_wait(mb, (uint32_t)(ch & 1));
+      if (tid == 0 && a_pending) mbar_wait(ab, (uint32_t)(ch & 1));
+    }
   }
   tc_fence_after();
   for (int mt = 0; ok && mt < nmt; ++mt) {
