@@ -152,14 +152,15 @@ def batch_pulses(w, n: int, seed: int = 4):
     return [pulse_star(w.verts, k=k, pol=pol) for k, pol in random_plane_waves(n, seed)] if n > 0 else []
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_m2l_tc launch (TF32x3, p = 4, 7680 RWG)
-M2L_TRAFFIC_TF32X3 = 141975808 + 3774976
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_m2l_tc launch (TF32x3, p = 4, 7680 RWG);
+# None until the current kernel has been captured
+M2L_TRAFFIC_TF32X3 = None
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
-KERNELS = ["incident_rhs", "near_history" , "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p"]
+KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack"]
 
 
-def roofline(args, info, launches, ms, K):
+def roofline(args, info, launches, ms, K, W):
     """Roofline of the dominant kernel class of the timed steps, from CUDA-event
     times on the library's stream: achieved = algorithmic work / device time."""
     hbm, bf16, src = _peaks()
@@ -176,8 +177,8 @@ def roofline(args, info, launches, ms, K):
         peak = bf16 if args.prec in ("bf16", "bf16x3") else bf16 * 1.1 / 2.25
         how = f"{src} bf16_tflops" + ("" if not args.prec.startswith("tf32") else " x 1.1/2.25 (nominal TF32/BF16)")
         # DRAM bytes of one launch from the committed ncu capture of this kernel and configuration
-        traffic = (M2L_TRAFFIC_TF32X3 if (args.prec == "tf32x3" and args.p == 4 and args.rhs == 1
-                                          and args.workload == "sphere7680") else None)
+        traffic = (M2L_TRAFFIC_TF32X3 if (M2L_TRAFFIC_TF32X3 and args.prec == "tf32x3" and args.p == 4
+                                          and args.rhs == 1 and args.workload == "sphere7680") else None)
         return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": tflops / peak, "traffic": traffic,
                 "traffic_source": "profiles/m2l_tc_sphere7680_tf32x3.md (one launch)" if traffic else None,
@@ -193,6 +194,20 @@ def roofline(args, info, launches, ms, K):
         gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}
+    if name == "z0_solve" and info.z0_nnz > 0:
+        # algorithmic operand bytes of one solve: per BiCGStab iteration two FP32
+        # ELL SpMVs (value + column, 8 B per non-zero) and 4-byte vector passes
+        # (21 + 2 x 12 with the 5-entry triangle-block preconditioner, 21 + 2 x 2
+        # with the diagonal one); two FP64 residuals (12 B per non-zero, 3 vectors)
+        R = args.rhs
+        its = info.total_solver_iters / max(W + K, 1)
+        vec = 21 + 2 * (12 if args.precond else 2)
+        nbytes = its * (16 * info.z0_nnz + 4 * vec * info.ne * R) + 2 * (12 * info.z0_nnz + 24 * info.ne * R)
+        gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes,
+                "note": "latency-bound: one 16-CTA cluster runs about 8 dependent BiCGStab iterations per solve, "
+                        "each with 6 cluster-wide barriers; Z0 (FP32 ELL) and the vectors stay in L2"}
     return {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None}
 
@@ -215,7 +230,7 @@ def run_many(args, rank, world, dist):
     solvers = []
     for w in ws:
         s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
-                   precond=args.precond)
+                   precond=args.precond, solve_tol=args.solve_tol)
         for r, pu in enumerate([w.pulses[0]] + batch_pulses(w, R - 1)):
             s.set_incident_plane(pu, rhs=r)
         solvers.append(s)
@@ -279,7 +294,7 @@ def run_ours(args, rank, world, dist):
     pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
     s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
-               jacobi_sweeps=args.jacobi, precond=args.precond)
+               jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol)
     setup_s = time.perf_counter() - t0
     for r, pu in enumerate(pulses):
         s.set_incident_plane(pu, rhs=r)
@@ -348,7 +363,7 @@ def run_ours(args, rank, world, dist):
     # the plain GPU path on the same steps: speed and the fast path's error
     cmp = {}
     if args.mode == "fast" and not args.no_compare:
-        sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0)
+        sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0, precond=args.precond, solve_tol=args.solve_tol)
         sd.set_incident_plane(w.pulses[0])
         sd.set_stream(stream.cuda_stream)
         outd = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
@@ -367,7 +382,7 @@ def run_ours(args, rank, world, dist):
         if R > 1:
             # the same fast march one right-hand side at a time
             s1 = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
-                        jacobi_sweeps=args.jacobi)
+                        jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol)
             s1.set_incident_plane(w.pulses[0])
             s1.set_stream(stream.cuda_stream)
             s1.march_dev(W)
@@ -389,20 +404,20 @@ def run_ours(args, rank, world, dist):
         "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
                    "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
-                   "jacobi_sweeps_max": args.jacobi, "precond": args.precond,
+                   "jacobi_sweeps_max": args.jacobi, "precond": args.precond, "solve_tol": args.solve_tol,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
                    "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
                          + (" + M2L operators" if args.mode == "fast" else "") + ")",
                    "setup_s": setup_s},
         "ns_nt_per_s": steps_per_s * w.n_tri,
-        "roofline": roofline(args, info, launches, ms, K),
+        "roofline": roofline(args, info, launches, ms, K, W),
         "kernel_ms_per_step": {KERNELS[k]: ms[k] / K for k in range(len(ms)) if launches[k]},
         "gpu_launches": int(sum(launches)),
         "e2e": {"value": e2e, "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
                 "h2d_bytes_per_step": 8 * s.ne * R, "d2h_bytes_per_step": 8 * s.ne * R},
         "clocks": ck,
-        "solver_iters_per_step": info.total_solver_iters / K if K else None,
-        "jacobi_sweeps_per_step": info.total_jacobi_sweeps / K if K else None,
+        "solver_iters_per_step": info.total_solver_iters / (W + K),
+        "jacobi_sweeps_per_step": info.total_jacobi_sweeps / (W + K),
         "m2l_tile_rows_per_level": list(info.m2l_tile_rows),
     }
     line.update(cmp)
@@ -428,6 +443,8 @@ def main():
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")
     ap.add_argument("--jacobi", type=int, default=0, help="FP64 Jacobi sweeps before the Krylov solve (0: none)")
     ap.add_argument("--precond", type=int, default=1, help="Z0 preconditioner: 0 Jacobi, 1 triangle blocks")
+    ap.add_argument("--solve-tol", type=float, default=1e-8,
+                    help="relative residual of every Z0 solve (1e-8: the paper's GMRES drop tolerance, section 2.6)")
     ap.add_argument("--scatterers", default="", help="comma-separated workloads marched together (tdbem_march_many)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")

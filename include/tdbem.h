@@ -239,6 +239,7 @@ typedef struct {
   int64_t total_jacobi_sweeps;     /* FP64 Jacobi sweeps of the Z0 solves (per-cluster maximum when batched) */
   int32_t m2l_tile_rows[8];        /* per octree level: rows of the M2L product per tensor-core CTA (128 or
                                       256), chosen at setup by timing both shapes; 0 where no tensor-core M2L runs */
+  int64_t z0_nnz;                  /* stored non-zeros of Z0 (the solver's sparse matrix) */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 
@@ -247,7 +248,9 @@ tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
    synchronises and returns, per class, the number of launches and the summed
    device time in milliseconds since the last enable.  Classes (index):
    0 incident RHS, 1 history/near field, 2 Z0 solve, 3 P2M, 4 M2M, 5 M2L,
-   6 L2L, 7 L2P.  n_classes receives the number of classes (<= 16). */
+   6 L2L, 7 L2P, 8 M2L moment packing (the symmetry-permuted copy of the
+   moments that the tensor-core M2L reads).  n_classes receives the number of
+   classes (<= 16). */
 tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
 tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
 

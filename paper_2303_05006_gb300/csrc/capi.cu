@@ -642,6 +642,7 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->setup_seconds = c->setup_seconds;
   info->total_solver_iters = c->total_iters;
   info->total_jacobi_sweeps = c->total_sweeps;
+  info->z0_nnz = c->z0_nnz;
   info->solver_cluster = c->cluster;
   if (c->p.mode == TDBEM_FAST) tdbem_fast_info(c, info);
   return TDBEM_OK;

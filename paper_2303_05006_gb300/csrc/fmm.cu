@@ -43,6 +43,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -73,6 +74,12 @@ struct FmmLevel {
   int32_t* d_pO = nullptr;
   int32_t* d_pS = nullptr;
   int16_t* d_psym = nullptr;
+  // distinct (source cell, symmetry) combinations of the pairs, in source
+  // order, and each pair's combination (tensor-core M2L packing)
+  int ncombo = 0;
+  int32_t* d_pC = nullptr;
+  int32_t* d_cS = nullptr;
+  int16_t* d_csym = nullptr;
   float* ops = nullptr;           // [nop][2][P][P]
   uint4* ops_img = nullptr;       // the same in tensor-core shared-memory images (tensor-core M2L only)
   int nop = 0;
@@ -122,6 +129,7 @@ struct FmmPlan {
   int Lr = 0;
   double* d_Rfar = nullptr;       // [Lr][ne]
   int32_t* d_err = nullptr;       // bounded-wait timeouts of the tensor-core M2L
+  float* d_pack = nullptr;        // packed moments of one level event (tensor-core M2L), largest level
   // second far state for history_eval
   std::vector<float*> mom_eval, loc_eval;
   double* d_Rfar_eval = nullptr;
@@ -1065,6 +1073,29 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_pS, hS.data(), L.npairs * sizeof(int32_t), cudaMemcpyHostToDevice));
       TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_psym, hsym.data(), L.npairs * sizeof(int16_t), cudaMemcpyHostToDevice));
     }
+    // (source cell, symmetry) combinations: the tensor-core M2L permutes each
+    // source moment once per symmetry in use instead of once per pair and lag
+    {
+      std::map<std::pair<int, int>, int> cid;
+      for (int q = 0; q < L.npairs; ++q) cid.emplace(std::make_pair(pr[q].S, pr[q].sym), 0);
+      std::vector<int32_t> cS, hC(L.npairs);
+      std::vector<int16_t> csym;
+      for (auto& e : cid) {
+        e.second = (int)cS.size();
+        cS.push_back(e.first.first);
+        csym.push_back((int16_t)e.first.second);
+      }
+      for (int q = 0; q < L.npairs; ++q) hC[q] = cid[std::make_pair(pr[q].S, pr[q].sym)];
+      L.ncombo = (int)cS.size();
+      if ((s = c->dalloc(&L.d_pC, std::max(1, L.npairs))) || (s = c->dalloc(&L.d_cS, std::max(1, L.ncombo))) ||
+          (s = c->dalloc(&L.d_csym, std::max(1, L.ncombo))))
+        return s;
+      if (L.npairs) {
+        TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_pC, hC.data(), L.npairs * sizeof(int32_t), cudaMemcpyHostToDevice));
+        TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_cS, cS.data(), L.ncombo * sizeof(int32_t), cudaMemcpyHostToDevice));
+        TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_csym, csym.data(), L.ncombo * sizeof(int16_t), cudaMemcpyHostToDevice));
+      }
+    }
     // lag ranges per canonical offset; operators; GEMM and tile lists
     std::vector<int4> opdesc, gemm, tiles, tiles_tc, tiles_tc2;
     int qmax = 1;
@@ -1218,11 +1249,20 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     return s;
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_err, 0, sizeof(int32_t)));
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, nrf * sizeof(double)));
+  if (c->p.m2l_prec != TDBEM_P_FP32) {
+    // packed moments of the largest level event, zeroed so that the
+    // autotuner's trial launches below add nothing
+    int64_t npk = 0;
+    for (int l = 2; l <= F->lmax; ++l) npk = std::max(npk, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC * P);
+    if ((s = c->dalloc(&F->d_pack, std::max<int64_t>(1, npk)))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemset(F->d_pack, 0, std::max<int64_t>(1, npk) * sizeof(float)));
+  }
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // M2L tile autotuner: time one gating event of each level in both CTA
   // shapes (one or two 128-row operator tiles per CTA) on this context's own
-  // operators, pairs and right-hand sides, and keep the faster.  The moments
-  // are still zero, so the trial launches add nothing to the local coefficients.
+  // operators, pairs and right-hand sides, and keep the faster.  The packed
+  // moments are still zero, so the trial launches add nothing to the local
+  // coefficients.
   if (c->p.m2l_prec != TDBEM_P_FP32 && c->p.m2l_tile_rows != 0) {
     for (int l = 2; l <= F->lmax; ++l) F->lev[l].tc_mt = c->p.m2l_tile_rows / 128;
   } else if (c->p.m2l_prec != TDBEM_P_FP32) {
@@ -1237,7 +1277,8 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         for (int it = -1; it < reps; ++it) {  // one untimed launch first
           if (it == 0) TDBEM_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
           if ((s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
-                                L.d_pS, L.d_psym, F->d_smap, L.mom, 0, L.loc, L.Q, c->R, c->p.m2l_prec, F->d_err)))
+                                L.d_pC, L.d_psym, F->d_smap, F->d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec,
+                                F->d_err)))
             return s;
         }
         TDBEM_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
@@ -1301,19 +1342,24 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     if (alpha % L.M) continue;
     int k = alpha / L.M - 1;
     if (L.ntiles) {
-      cudaEvent_t e = c->prof_begin(5);
       if (c->p.m2l_prec == TDBEM_P_FP32) {
+        cudaEvent_t e = c->prof_begin(5);
         k_m2l_fp32<<<L.ntiles, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
                                                      F->d_smap, MOM(l), k, LOC(l), L.Q, R);
         TDBEM_CUDA_TRY(c, cudaGetLastError());
+        c->prof_end(5, e);
       } else {
-        const int v = L.tc_mt - 1;
-        tdbem_status s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS,
-                                      L.d_pO, L.d_pS, L.d_psym, F->d_smap, MOM(l), k, LOC(l), L.Q, R,
-                                      c->p.m2l_prec, F->d_err);
+        cudaEvent_t e = c->prof_begin(8);
+        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, F->d_pack);
         if (s) return s;
+        c->prof_end(8, e);
+        e = c->prof_begin(5);
+        const int v = L.tc_mt - 1;
+        s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO, L.d_pC,
+                         L.d_psym, F->d_smap, F->d_pack, k, LOC(l), L.Q, R, c->p.m2l_prec, F->d_err);
+        if (s) return s;
+        c->prof_end(5, e);
       }
-      c->prof_end(5, e);
     }
     if (L.nnonleaf && l < lmax) {
       cudaEvent_t e = c->prof_begin(6);

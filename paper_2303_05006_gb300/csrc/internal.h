@@ -123,7 +123,7 @@ struct tdbem_ctx {
   double setup_seconds = 0;
   int64_t device_bytes = 0;
   // kernel-class timing (tdbem_profile_*)
-  static constexpr int kClasses = 8;
+  static constexpr int kClasses = 9;
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
@@ -171,10 +171,14 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c);
 void tdbem_fast_free(tdbem_ctx* c);
 tdbem_status tdbem_fast_check(tdbem_ctx* c);
 // m2l_tc.cu
+// pC: each pair's (source cell, symmetry) combination; pk: the packed
+// moments of tdbem_m2l_pack for this event
 tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
-                          int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                          int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
+                          const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
                           int32_t* err);
+tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo, const int16_t* smap,
+                            const float* mom, int k, int R, int PS, int pt, float* pk);
 tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,

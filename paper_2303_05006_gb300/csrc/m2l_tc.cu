@@ -189,8 +189,8 @@ __global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, i
 // prec: 1 = TF32, 2 = BF16, 3 = BF16 x 3, 4 = TF32 x 3 (split: hi*hi + hi*lo + lo*hi)
 template <int kMT>
 __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const uint4* img, int P,
-                                                     int pt, int PS, const int32_t* pO, const int32_t* pS,
-                                                     const int16_t* psym, const int16_t* smap, const float* mom,
+                                                     int pt, int PS, const int32_t* pO, const int32_t* pC,
+                                                     const int16_t* psym, const int16_t* smap, const float* pk,
                                                      int k, float* loc, int Q, int R, int prec, int32_t* err) {
   constexpr uint32_t kTmemCols = 128 * kMT;
   extern __shared__ __align__(1024) uint8_t dsm[];
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     int gcol = col0 + tid;
     if (gcol < ncol) {
       int pr = gd.y + gcol / (nk * R), rem = gcol % (nk * R), rhs = rem / nk, c = c0 + rem % nk;
-      src_off[tid] = (((((int64_t)pS[pr] * 2 + (k & 1)) * 2 + var) * R + rhs) * kNCmp + c) * P;
+      src_off[tid] = ((((int64_t)pC[pr] * 2 + var) * R + rhs) * kNCmp + c) * P;  // packed row
       dst_off[tid] = ((((int64_t)pO[pr] * Q + ((k + q) % Q)) * R + rhs) * kNCmp + c) * P;
       map_off[tid] = (int32_t)psym[pr] * PS;
     } else {
@@ -274,32 +274,24 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       }
       a_pending = true;
     }
-    // moment columns, gathered through the symmetry map.  With pt = 4 a
-    // 16-byte unit is one (TF32) or two (BF16) spatial nodes: every thread
-    // first looks up the nodes of all its units, then issues all their
-    // 16-byte moment loads, so that its loads are in flight together.
-    if (pt == 4) {
+    // moment columns: rows of the packed, already permuted moments, so each
+    // column's chunk is a contiguous run.  Every thread first issues the
+    // 16-byte loads of all its units, then converts and stores them.
+    if ((P & 3) == 0) {
       constexpr int kU = 1024 / kThreads;
-      int64_t so[kU];
-      int nd[kU][2];
       float4 v[kU][2];
 #pragma unroll
       for (int j = 0; j < kU; ++j) {
-        const int u = tid + j * kThreads, n = unit_row(u);
+        const int u = tid + j * kThreads;
+        const int64_t so = src_off[unit_row(u)];
         const int kk = k0 + unit_k16(u) * E;
-        so[j] = src_off[n];
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           const int kq = kk + 4 * g;
-          nd[j][g] = (so[j] >= 0 && 4 * g < E && kq < P) ? smp[map_off[n] + (kq >> 2)] : -1;
+          v[j][g] = (so >= 0 && 4 * g < E && kq < P) ? __ldg((const float4*)(pk + so + kq))
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
-#pragma unroll
-      for (int j = 0; j < kU; ++j)
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-          v[j][g] = nd[j][g] >= 0 ? *(const float4*)(mom + so[j] + (int64_t)nd[j][g] * 4)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < kU; ++j) {
         const int u = tid + j * kThreads;
@@ -314,20 +306,11 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       }
     } else {
       for (int u = tid; u < 1024; u += kThreads) {
-        const int n = unit_row(u);
+        const int64_t so = src_off[unit_row(u)];
         const int kk = k0 + unit_k16(u) * E;
-        float x[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int64_t so = src_off[n];
-        if (so >= 0) {
+        float x[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int kq = kk + e;
-            if (e < E && kq < P) {
-              const int bp = kq / pt, nt = kq - bp * pt;
-              x[e] = mom[so + (int64_t)smp[map_off[n] + bp] * pt + nt];
-            }
-          }
-        }
+        for (int e = 0; e < 8; ++e) x[e] = (so >= 0 && e < E && kk + e < P) ? pk[so + kk + e] : 0.f;
         uint4 hi, lo;
         if (tf)
           split_unit<true>(x, hi, lo);
@@ -421,14 +404,38 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// Symmetry-permuted moments of one gating event.  Row
+// ((combo * 2 + var) * R + rhs) * kNC + c of pk is the B column shared by
+// every interaction pair whose source cell and cube symmetry are those of
+// combo: pk[row][node * pt + t] = mom[S][k & 1][var][rhs][c][smap[sym][node] * pt + t].
+// One thread per (row, spatial node); the writes of a warp are contiguous.
+__global__ void k_m2l_pack(const int32_t* cS, const int16_t* csym, int64_t nrows, const int16_t* smap,
+                           const float* mom, int k, int R, int PS, int pt, float* pk) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nrows * PS) return;
+  const int64_t row = g / PS;
+  const int node = (int)(g - row * PS);
+  const int64_t per = 2LL * R * kNCmp;  // rows per combo: (var, rhs, component)
+  const int64_t combo = row / per, rem = row - combo * per;
+  const int P = PS * pt;
+  const float* src =
+      mom + (((int64_t)cS[combo] * 2 + (k & 1)) * per + rem) * P + (int64_t)smap[csym[combo] * PS + node] * pt;
+  float* dst = pk + row * P + (int64_t)node * pt;
+  if (pt == 4) {
+    *(float4*)dst = __ldg((const float4*)src);
+  } else {
+    for (int t = 0; t < pt; ++t) dst[t] = src[t];
+  }
+}
+
 }  // namespace tdbem
 
 // Launch the tensor-core M2L of one level event with mt (1 or 2) 128-row
 // operator tiles per CTA; tiles must be the list planned for that mt.
 template <int kMT>
 static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
-                                  int P, int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                                  const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                                  int P, int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
+                                  const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
                                   int32_t* err) {
   using namespace tdbem;
   static bool attr = false;
@@ -439,19 +446,19 @@ static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* ti
   }
   if (ntiles == 0) return TDBEM_OK;
   const size_t smem = smem_tiles<kMT>() + (48 * PS * 2 <= kSmapSmem ? 48 * PS * 2 : 0) + 1024;
-  k_m2l_tc<kMT><<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc,
+  k_m2l_tc<kMT><<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc,
                                                         Q, R, prec, err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
 
 tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
-                          int P, int pt, int PS, const int32_t* pO, const int32_t* pS, const int16_t* psym,
-                          const int16_t* smap, const float* mom, int k, float* loc, int Q, int R, int prec,
+                          int P, int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
+                          const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
                           int32_t* err) {
   if (mt == 2)
-    return launch_m2l_tc<2>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc, Q, R, prec, err);
-  return launch_m2l_tc<1>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pS, psym, smap, mom, k, loc, Q, R, prec, err);
+    return launch_m2l_tc<2>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, err);
+  return launch_m2l_tc<1>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, err);
 }
 
 // Convert the FP32 operators of one level into the tensor-core images read by
@@ -469,6 +476,19 @@ tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P,
   if (s) return s;
   k_m2l_images<<<(unsigned)((nunits + 255) / 256), 256, 0, c->stream>>>(ops, nunits, P, nrt, nch, nparts, tf ? 1 : 0,
                                                                         *img);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// Pack the moments of one level event for k_m2l_tc: ncombo (source cell,
+// symmetry) combinations, rows of P floats each (see k_m2l_pack).
+tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo, const int16_t* smap,
+                            const float* mom, int k, int R, int PS, int pt, float* pk) {
+  using namespace tdbem;
+  const int64_t nrows = (int64_t)ncombo * 2 * R * kNCmp;
+  if (nrows == 0) return TDBEM_OK;
+  const int64_t nth = nrows * PS;
+  k_m2l_pack<<<(unsigned)((nth + 255) / 256), 256, 0, c->stream>>>(cS, csym, nrows, smap, mom, k, R, PS, pt, pk);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
