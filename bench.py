@@ -277,6 +277,66 @@ def run_many(args, rank, world, dist):
     return 0
 
 
+def run_sweep(args, rank, world, dist):
+    """Error and speed of the fast march per (interpolation order, M2L form),
+    against the FP64 direct march of the same workload and steps.  One JSON
+    line, the settings under "sweep"."""
+    import torch
+
+    from paper_2303_05006_gb300 import Solver
+    from workloads import workload
+
+    if rank != 0:
+        return 0
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    K = min(args.steps, w.Nt - 1)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def march(s):
+        s.set_incident_plane(w.pulses[0])
+        s.set_stream(stream.cuda_stream)
+        out = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.march_dev(K, out.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), K / (e0.elapsed_time(e1) / 1000.0)
+
+    t0 = time.perf_counter()
+    sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0, precond=args.precond, solve_tol=args.solve_tol)
+    setup_direct = time.perf_counter() - t0
+    Jd, sps_d = march(sd)
+    ne = sd.ne
+    sd.close()
+    nJd = np.linalg.norm(Jd)
+    rows = []
+    for item in args.sweep.split(","):
+        p, prec = item.split(":")
+        t0 = time.perf_counter()
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=int(p), p_t=int(p), m2l_prec=PREC[prec],
+                   precond=args.precond, solve_tol=args.solve_tol)
+        setup = time.perf_counter() - t0
+        J, sps = march(s)
+        s.close()
+        err = np.linalg.norm(J - Jd, axis=1) / np.maximum(np.linalg.norm(Jd, axis=1), 1e-300)
+        rows.append({"p_s": int(p), "p_t": int(p), "m2l": prec, "steps_per_s": sps, "setup_s": setup,
+                     "rel_l2_vs_direct": float(np.linalg.norm(J - Jd) / nJd),
+                     "rel_l2_last_100_steps": float(np.linalg.norm(J[-100:] - Jd[-100:]) / np.linalg.norm(Jd[-100:])),
+                     "finite": bool(np.isfinite(J).all()), "max_step_rel_err": float(err.max())})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": METRIC, "value": max(r["steps_per_s"] for r in rows), "unit": "steps/s",
+                      "n_gpus": 1, "steps": K, "warmup": 0, "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": args.workload, "n_rwg": ne, "n_tri": w.n_tri, "Nt": w.Nt,
+                                 "solve_tol": args.solve_tol, "precond": args.precond,
+                                 "reference": "FP64 direct march on the GPU (equal to the oracle to 1e-10)"},
+                      "direct_steps_per_s": sps_d, "direct_setup_s": setup_direct, "sweep": rows}), flush=True)
+    return 0
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -450,12 +510,16 @@ def main():
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")
     ap.add_argument("--workload", default="sphere7680")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", default="",
+                    help="comma-separated p:form settings (e.g. 3:fp32,4:tf32x3); prints error vs the FP64 march per setting")
     args = ap.parse_args()
     rank, world, dist = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world, dist)
     if args.scatterers:
         return run_many(args, rank, world, dist)
+    if args.sweep:
+        return run_sweep(args, rank, world, dist)
     return run_ours(args, rank, world, dist)
 
 
