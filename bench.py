@@ -103,7 +103,7 @@ def oracle_sample(w, rows_n: int, steps: int, seed: int = 11):
     from oracle.oracle import Oracle, threads
     from workloads import random_history
 
-    o = Oracle(w.verts, w.tris, w.dt)
+    o = Oracle(w.verts, w.tris, w.dt, theta=w.theta, zeta=w.zeta)
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(o.ne, rows_n, replace=False))
     t0 = time.perf_counter()
@@ -229,7 +229,7 @@ def run_many(args, rank, world, dist):
     steps = [min(K, w.Nt - 1 - W) for w in ws]
     solvers = []
     for w in ws:
-        s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
                    precond=args.precond, solve_tol=args.solve_tol)
         for r, pu in enumerate([w.pulses[0]] + batch_pulses(w, R - 1)):
             s.set_incident_plane(pu, rhs=r)
@@ -292,7 +292,7 @@ def run_sweep(args, rank, world, dist):
     torch.cuda.set_device(dev)
     w = workload(args.workload)
     K = min(args.steps, w.Nt - 1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(priority=-100) if args.high_priority else torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def march(s):
@@ -307,7 +307,7 @@ def run_sweep(args, rank, world, dist):
         return out.cpu().numpy(), K / (e0.elapsed_time(e1) / 1000.0)
 
     t0 = time.perf_counter()
-    sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0, precond=args.precond, solve_tol=args.solve_tol)
+    sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=0, precond=args.precond, solve_tol=args.solve_tol)
     setup_direct = time.perf_counter() - t0
     Jd, sps_d = march(sd)
     ne = sd.ne
@@ -317,7 +317,7 @@ def run_sweep(args, rank, world, dist):
     for item in args.sweep.split(","):
         p, prec = item.split(":")
         t0 = time.perf_counter()
-        s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, p_s=int(p), p_t=int(p), m2l_prec=PREC[prec],
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=1, p_s=int(p), p_t=int(p), m2l_prec=PREC[prec],
                    precond=args.precond, solve_tol=args.solve_tol)
         setup = time.perf_counter() - t0
         J, sps = march(s)
@@ -332,6 +332,7 @@ def run_sweep(args, rank, world, dist):
                       "n_gpus": 1, "steps": K, "warmup": 0, "higher_is_better": True, "data": "synthetic",
                       "config": {"workload": args.workload, "n_rwg": ne, "n_tri": w.n_tri, "Nt": w.Nt,
                                  "solve_tol": args.solve_tol, "precond": args.precond,
+                                 "theta": w.theta, "zeta": w.zeta,
                                  "reference": "FP64 direct march on the GPU (equal to the oracle to 1e-10)"},
                       "direct_steps_per_s": sps_d, "direct_setup_s": setup_direct, "sweep": rows}), flush=True)
     return 0
@@ -353,12 +354,13 @@ def run_ours(args, rank, world, dist):
     R = args.rhs
     pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
-    s = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
-               jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol)
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+               jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol,
+               m2l_tile_rows=args.m2l_tile_rows, far_overlap=args.far_overlap)
     setup_s = time.perf_counter() - t0
     for r, pu in enumerate(pulses):
         s.set_incident_plane(pu, rhs=r)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(priority=-100) if args.high_priority else torch.cuda.current_stream()
     s.set_stream(stream.cuda_stream)
     out = torch.empty((K, R, s.ne), dtype=torch.float64, device="cuda")
     # device-resident march: warm-up, then K timed steps
@@ -423,7 +425,7 @@ def run_ours(args, rank, world, dist):
     # the plain GPU path on the same steps: speed and the fast path's error
     cmp = {}
     if args.mode == "fast" and not args.no_compare:
-        sd = Solver(w.verts, w.tris, w.dt, w.Nt, mode=0, precond=args.precond, solve_tol=args.solve_tol)
+        sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=0, precond=args.precond, solve_tol=args.solve_tol)
         sd.set_incident_plane(w.pulses[0])
         sd.set_stream(stream.cuda_stream)
         outd = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
@@ -441,7 +443,7 @@ def run_ours(args, rank, world, dist):
         sd.close()
         if R > 1:
             # the same fast march one right-hand side at a time
-            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
+            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
                         jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol)
             s1.set_incident_plane(w.pulses[0])
             s1.set_stream(stream.cuda_stream)
@@ -465,6 +467,8 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
                    "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
                    "jacobi_sweeps_max": args.jacobi, "precond": args.precond, "solve_tol": args.solve_tol,
+                   "theta": w.theta, "zeta": w.zeta,
+                   "m2l_tile_rows": args.m2l_tile_rows or "autotuned", "far_overlap": args.far_overlap,
                    "steps_timed": f"alpha {W + 1}..{W + K}",
                    "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored near coefficients"
                          + (" + M2L operators" if args.mode == "fast" else "") + ")",
@@ -510,6 +514,12 @@ def main():
     ap.add_argument("--timed-only", action="store_true", help="stop after the timed march (profiling)")
     ap.add_argument("--workload", default="sphere7680")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--high-priority", type=int, default=1, choices=(0, 1),
+                    help="1: march on a highest-priority CUDA stream (the deferred far-field products run at the lowest)")
+    ap.add_argument("--far-overlap", type=int, default=1, choices=(0, 1),
+                    help="1: M2L products of lag >= 2 on a second stream, overlapping the next steps; 0: serial")
+    ap.add_argument("--m2l-tile-rows", type=int, default=0, choices=(0, 128, 256),
+                    help="tensor-core M2L CTA shape: 0 = autotuned at setup, 128 or 256 operator rows per CTA")
     ap.add_argument("--sweep", default="",
                     help="comma-separated p:form settings (e.g. 3:fp32,4:tf32x3); prints error vs the FP64 march per setting")
     args = ap.parse_args()

@@ -94,6 +94,12 @@ typedef struct {
                             both at setup on each level and keeps the faster */
   int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
                             blocks of Z0 among the RWG functions of each triangle, summed) */
+  int32_t far_overlap;   /* fast mode, 1 (default): the M2L products of a gating event with lag q >= 2, whose
+                            local coefficients are first read one interval later, run on a second stream of
+                            the context while the next steps' near field and solves proceed; 0: every product
+                            on the context's stream, in the step that fires it (program 1's order).  The second
+                            stream has the lowest priority; the library's own stream the highest (a caller's
+                            stream keeps its own priority) */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -104,7 +110,7 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0, m2l_tile_rows=0, precond=1. */
+   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -123,7 +129,11 @@ tdbem_status tdbem_num_edges(const tdbem_ctx* ctx, int64_t* ne);
 tdbem_status tdbem_edges(const tdbem_ctx* ctx, int32_t* edge_vert, int32_t* edge_tri);
 
 /* CUDA stream (a cudaStream_t passed as void*) on which every later kernel of
-   this context is launched; NULL selects the library's own stream. */
+   this context is launched; NULL selects the library's own stream.  With
+   far_overlap on, the deferred M2L products run on a second stream owned by
+   the context, ordered after this one by events; every call that marches to
+   completion (march, march_dev, march_many), resets, evaluates a history or
+   reads the profile makes this stream wait for them. */
 tdbem_status tdbem_set_stream(tdbem_ctx* ctx, void* stream);
 
 /* Incident modulated-Gaussian plane wave for right-hand side `rhs`

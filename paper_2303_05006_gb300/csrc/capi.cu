@@ -57,6 +57,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->n_rhs = 1;
   p->jacobi_sweeps = 0;
   p->precond = 1;
+  p->far_overlap = 1;
 }
 
 static void fill_phys(tdbem_ctx* c) {
@@ -84,6 +85,7 @@ static void fill_phys(tdbem_ctx* c) {
 
 void tdbem_destroy(tdbem_ctx* c) {
   if (!c) return;
+  tdbem_fast_join(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
@@ -125,7 +127,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
-      p.precond > 1 ||
+      p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -137,7 +139,12 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
   c->R = p.n_rhs;
   c->pulse.assign(10 * (size_t)c->R, 0.0);
   fill_phys(c);
-  cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  // the library's own stream takes the highest priority, so that the steps'
+  // kernels are dispatched ahead of the deferred far-field products (which
+  // run on a lowest-priority stream) whenever both wait for an SM
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  cudaError_t e = cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, prio_hi);
   if (e != cudaSuccess) {
     delete c;
     return e == cudaErrorMemoryAllocation ? TDBEM_ENOMEM : TDBEM_ECUDA;
@@ -503,6 +510,8 @@ tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t*
 
 tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
   if (!c) return TDBEM_EINVAL;
+  tdbem_status s = tdbem_fast_join(c);
+  if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->prof_on = on != 0;
   c->prof_marks.clear();
@@ -512,6 +521,8 @@ tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
 
 tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int32_t* n_classes) {
   if (!c || !launches || !ms) return TDBEM_EINVAL;
+  tdbem_status s = tdbem_fast_join(c);
+  if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (int k = 0; k < tdbem_ctx::kClasses; ++k) {
     launches[k] = 0;
@@ -529,7 +540,9 @@ tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int
 
 static tdbem_status check_misses(tdbem_ctx* c) {
   if (c->p.mode == TDBEM_FAST) {
-    tdbem_status s = tdbem_fast_check(c);
+    tdbem_status s = tdbem_fast_join(c);
+    if (s) return s;
+    s = tdbem_fast_check(c);
     if (s) return s;
   }
   int32_t h[8];

@@ -92,6 +92,14 @@ struct FmmLevel {
   // autotuner measured faster for this level
   int4* d_tiles_tc[2] = {nullptr, nullptr};
   int ntiles_tc[2] = {0, 0};
+  // every tile list holds first the tiles of lag q = 1 (their local
+  // coefficients are read in the event that fires them), then those of
+  // q >= 2 (read one interval later or after), which may be deferred
+  int ntiles_urgent = 0;
+  int ntiles_tc_urgent[2] = {0, 0};
+  float* d_pack = nullptr;          // packed moments of this level's event (tensor-core M2L)
+  cudaEvent_t ev_defer = nullptr;   // recorded on the side stream after a deferred M2L
+  bool defer_pending = false;       // host: a deferred M2L not yet waited for
   int tc_mt = 1;
   float tc_ms[2] = {0.f, 0.f};     // autotuner: mean time of one M2L event per shape
   double flops_event = 0;         // M2L flops of one gating event
@@ -129,7 +137,10 @@ struct FmmPlan {
   int Lr = 0;
   double* d_Rfar = nullptr;       // [Lr][ne]
   int32_t* d_err = nullptr;       // bounded-wait timeouts of the tensor-core M2L
-  float* d_pack = nullptr;        // packed moments of one level event (tensor-core M2L), largest level
+  // second stream for the deferred (q >= 2) M2L products, and the event that
+  // orders it after the context's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr;
   // second far state for history_eval
   std::vector<float*> mom_eval, loc_eval;
   double* d_Rfar_eval = nullptr;
@@ -1135,6 +1146,16 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         }
       }
     }
+    // lag-1 tiles first in every list (see FmmLevel): only they feed the
+    // interval the event's own L2L and L2P read
+    auto lag1_first = [&](std::vector<int4>& tl) {
+      auto it = std::stable_partition(tl.begin(), tl.end(),
+                                      [&](const int4& t) { return ((gemm[t.x].w >> 8) & 0xff) == 1; });
+      return (int)(it - tl.begin());
+    };
+    L.ntiles_urgent = lag1_first(tiles);
+    L.ntiles_tc_urgent[0] = lag1_first(tiles_tc);
+    L.ntiles_tc_urgent[1] = lag1_first(tiles_tc2);
     if (qmax >= 255) {
       c->set_error("fast: too many time intervals per interaction");
       return TDBEM_EINVAL;
@@ -1250,12 +1271,22 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_err, 0, sizeof(int32_t)));
   TDBEM_CUDA_TRY(c, cudaMemset(F->d_Rfar, 0, nrf * sizeof(double)));
   if (c->p.m2l_prec != TDBEM_P_FP32) {
-    // packed moments of the largest level event, zeroed so that the
-    // autotuner's trial launches below add nothing
-    int64_t npk = 0;
-    for (int l = 2; l <= F->lmax; ++l) npk = std::max(npk, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC * P);
-    if ((s = c->dalloc(&F->d_pack, std::max<int64_t>(1, npk)))) return s;
-    TDBEM_CUDA_TRY(c, cudaMemset(F->d_pack, 0, std::max<int64_t>(1, npk) * sizeof(float)));
+    // packed moments of each level's event (one buffer per level: a deferred
+    // M2L of one level may still read its buffer while another level packs),
+    // zeroed so that the autotuner's trial launches below add nothing
+    for (int l = 2; l <= F->lmax; ++l) {
+      const int64_t npk = std::max<int64_t>(1, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC * P);
+      if ((s = c->dalloc(&F->lev[l].d_pack, npk))) return s;
+      TDBEM_CUDA_TRY(c, cudaMemset(F->lev[l].d_pack, 0, npk * sizeof(float)));
+    }
+  }
+  if (c->p.far_overlap) {
+    int prio_lo = 0, prio_hi = 0;
+    TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->side, cudaStreamNonBlocking, prio_lo));
+    TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_fork, cudaEventDisableTiming));
+    for (int l = 2; l <= F->lmax; ++l)
+      TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->lev[l].ev_defer, cudaEventDisableTiming));
   }
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // M2L tile autotuner: time one gating event of each level in both CTA
@@ -1277,7 +1308,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         for (int it = -1; it < reps; ++it) {  // one untimed launch first
           if (it == 0) TDBEM_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
           if ((s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
-                                L.d_pC, L.d_psym, F->d_smap, F->d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec,
+                                L.d_pC, L.d_psym, F->d_smap, L.d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec,
                                 F->d_err)))
             return s;
         }
@@ -1306,6 +1337,17 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
   auto MOM = [&](int l) { return eval ? F->mom_eval[l - 2] : F->lev[l].mom; };
   auto LOC = [&](int l) { return eval ? F->loc_eval[l - 2] : F->lev[l].loc; };
   double* Rfar = eval ? F->d_Rfar_eval : F->d_Rfar;
+  // The deferred M2L of a level's previous event adds to local coefficients
+  // that this event reads (and reads the packed moments it rewrites): order it
+  // before any work of a level that fires now.  History evaluation packs into
+  // the same buffers, so it waits for every level.
+  for (int l = 2; l <= lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    if (L.defer_pending && (eval || alpha % L.M == 0)) {
+      TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, L.ev_defer, 0));
+      L.defer_pending = false;
+    }
+  }
   // upward pass
   for (int l = lmax; l >= 2; --l) {
     FmmLevel& L = F->lev[l];
@@ -1342,23 +1384,51 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     if (alpha % L.M) continue;
     int k = alpha / L.M - 1;
     if (L.ntiles) {
-      if (c->p.m2l_prec == TDBEM_P_FP32) {
-        cudaEvent_t e = c->prof_begin(5);
-        k_m2l_fp32<<<L.ntiles, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
-                                                     F->d_smap, MOM(l), k, LOC(l), L.Q, R);
-        TDBEM_CUDA_TRY(c, cudaGetLastError());
-        c->prof_end(5, e);
-      } else {
+      const bool tc = c->p.m2l_prec != TDBEM_P_FP32;
+      const int v = L.tc_mt - 1;
+      if (tc) {
         cudaEvent_t e = c->prof_begin(8);
-        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, F->d_pack);
+        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, L.d_pack);
         if (s) return s;
         c->prof_end(8, e);
-        e = c->prof_begin(5);
-        const int v = L.tc_mt - 1;
-        s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO, L.d_pC,
-                         L.d_psym, F->d_smap, F->d_pack, k, LOC(l), L.Q, R, c->p.m2l_prec, F->d_err);
-        if (s) return s;
+      }
+      // tiles [t0, t0 + n) of this level's list, on c->stream
+      auto m2l_range = [&](int t0, int n) -> tdbem_status {
+        if (n <= 0) return TDBEM_OK;
+        cudaEvent_t e = c->prof_begin(5);
+        if (!tc) {
+          k_m2l_fp32<<<n, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles + t0, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
+                                               F->d_smap, MOM(l), k, LOC(l), L.Q, R);
+          TDBEM_CUDA_TRY(c, cudaGetLastError());
+        } else {
+          tdbem_status s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v] + t0, n, L.ops_img, P, pt, PS, L.d_pO,
+                                        L.d_pC, L.d_psym, F->d_smap, L.d_pack, k, LOC(l), L.Q, R, c->p.m2l_prec,
+                                        F->d_err);
+          if (s) return s;
+        }
         c->prof_end(5, e);
+        return TDBEM_OK;
+      };
+      const int nall = tc ? L.ntiles_tc[v] : L.ntiles;
+      const int nu = tc ? L.ntiles_tc_urgent[v] : L.ntiles_urgent;
+      tdbem_status s;
+      if (!F->side || eval) {
+        if ((s = m2l_range(0, nall))) return s;
+      } else {
+        // lag 1 now; lags >= 2 on the side stream, overlapping the next
+        // steps, waited for when this level fires again
+        if ((s = m2l_range(0, nu))) return s;
+        if (nall > nu) {
+          TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_fork, c->stream));
+          TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(F->side, F->ev_fork, 0));
+          cudaStream_t main = c->stream;
+          c->stream = F->side;
+          s = m2l_range(nu, nall - nu);
+          c->stream = main;
+          if (s) return s;
+          TDBEM_CUDA_TRY(c, cudaEventRecord(L.ev_defer, F->side));
+          L.defer_pending = true;
+        }
       }
     }
     if (L.nnonleaf && l < lmax) {
@@ -1440,6 +1510,8 @@ tdbem_status tdbem_fast_replay_step(tdbem_ctx* c, int32_t alpha, const double* r
 tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
   FmmPlan* F = c->fmm;
   if (!F || F->lmax < 2) return TDBEM_OK;
+  tdbem_status s0 = tdbem_fast_join(c);
+  if (s0) return s0;
   for (int l = 2; l <= F->lmax; ++l) {
     FmmLevel& L = F->lev[l];
     const int64_t RP = (int64_t)c->R * kNC * F->P;
@@ -1450,7 +1522,29 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
+// The context's stream waits for every deferred M2L still in flight.
+tdbem_status tdbem_fast_join(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (!F) return TDBEM_OK;
+  for (int l = 2; l <= F->lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    if (L.defer_pending) {
+      TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, L.ev_defer, 0));
+      L.defer_pending = false;
+    }
+  }
+  return TDBEM_OK;
+}
+
 void tdbem_fast_free(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (F) {
+    if (F->side) cudaStreamSynchronize(F->side);
+    for (size_t l = 2; l < F->lev.size(); ++l)
+      if (F->lev[l].ev_defer) cudaEventDestroy(F->lev[l].ev_defer);
+    if (F->ev_fork) cudaEventDestroy(F->ev_fork);
+    if (F->side) cudaStreamDestroy(F->side);
+  }
   delete c->fmm;
   c->fmm = nullptr;
 }

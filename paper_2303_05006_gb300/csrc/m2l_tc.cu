@@ -260,6 +260,30 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int nrt = (P + kTileM - 1) / kTileM;
   const int nmt = min(kMT, nrt - rt0);  // row tiles of this CTA
   const int nparts = split ? 2 : 1;
+  // moment columns: rows of the packed, already permuted moments, so each
+  // column's chunk is a contiguous run.  With P a multiple of 4 every thread
+  // loads its four 16-byte units of a chunk into registers; the loads of
+  // chunk ch + 1 are issued as soon as the MMAs of chunk ch are, so their
+  // latency overlaps the tensor-core work.
+  constexpr int kU = 1024 / kThreads;
+  const bool vec = (P & 3) == 0;
+  float4 v[kU][2];
+  auto load_b = [&](int chunk) {
+    const int kb = chunk * KC;
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      const int u = tid + j * kThreads;
+      const int64_t so = src_off[unit_row(u)];
+      const int kk = kb + unit_k16(u) * E;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int kq = kk + 4 * g;
+        v[j][g] = (so >= 0 && 4 * g < E && kq < P) ? __ldg((const float4*)(pk + so + kq))
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  if (vec) load_b(0);
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * KC;
     // operator rows: the pre-converted images of this chunk (hi and lo parts
@@ -274,24 +298,9 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       }
       a_pending = true;
     }
-    // moment columns: rows of the packed, already permuted moments, so each
-    // column's chunk is a contiguous run.  Every thread first issues the
-    // 16-byte loads of all its units, then converts and stores them.
-    if ((P & 3) == 0) {
-      constexpr int kU = 1024 / kThreads;
-      float4 v[kU][2];
-#pragma unroll
-      for (int j = 0; j < kU; ++j) {
-        const int u = tid + j * kThreads;
-        const int64_t so = src_off[unit_row(u)];
-        const int kk = k0 + unit_k16(u) * E;
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const int kq = kk + 4 * g;
-          v[j][g] = (so >= 0 && 4 * g < E && kq < P) ? __ldg((const float4*)(pk + so + kq))
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
+    // convert and store this chunk's moment columns (already in registers
+    // when P is a multiple of 4)
+    if (vec) {
 #pragma unroll
       for (int j = 0; j < kU; ++j) {
         const int u = tid + j * kThreads;
@@ -351,6 +360,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       }
       mma_commit(mb);
     }
+    if (vec && ch + 1 < nchunks) load_b(ch + 1);
     // the next chunk overwrites the tiles: wait for the MMAs to finish; the
     // verdict is made uniform across the CTA before anyone acts on it
     // (with no MMA issued the commit arrives at once)
