@@ -152,9 +152,9 @@ def batch_pulses(w, n: int, seed: int = 4):
     return [pulse_star(w.verts, k=k, pol=pol) for k, pol in random_plane_waves(n, seed)] if n > 0 else []
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_m2l_tc launch (TF32x3, p = 4, 7680 RWG);
-# None until the current kernel has been captured
-M2L_TRAFFIC_TF32X3 = None
+# dram__bytes_read.sum + dram__bytes_write.sum per k_m2l_tc launch (TF32x3, p = 4, 7680 RWG, two
+# 128-row tiles per CTA, lag >= 2 products deferred): one gating period of six launches, 769.8 MB
+M2L_TRAFFIC_TF32X3 = 769.8e6 / 6
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack"]
@@ -178,10 +178,12 @@ def roofline(args, info, launches, ms, K, W):
         how = f"{src} bf16_tflops" + ("" if not args.prec.startswith("tf32") else " x 1.1/2.25 (nominal TF32/BF16)")
         # DRAM bytes of one launch from the committed ncu capture of this kernel and configuration
         traffic = (M2L_TRAFFIC_TF32X3 if (M2L_TRAFFIC_TF32X3 and args.prec == "tf32x3" and args.p == 4
-                                          and args.rhs == 1 and args.workload == "sphere7680") else None)
+                                          and args.rhs == 1 and args.workload == "sphere7680" and args.far_overlap
+                                          and list(info.m2l_tile_rows)[2:4] == [256, 256]) else None)
         return {"kernel": name, "bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": tflops / peak, "traffic": traffic,
-                "traffic_source": "profiles/m2l_tc_sphere7680_tf32x3.md (one launch)" if traffic else None,
+                "traffic_source": "profiles/m2l_tc_sphere7680_tf32x3.md (mean of one gating period's launches)"
+                if traffic else None,
                 "peak_source": how,
                 "flops_per_launch": flops / max(launches[dom], 1),
                 "note": "algorithmic flops (a split form executes three products per flop counted)"

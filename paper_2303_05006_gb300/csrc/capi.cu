@@ -194,6 +194,8 @@ tdbem_status tdbem_set_stream(tdbem_ctx* c, void* stream) {
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* pulse) {
   if (!c || !pulse || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
   if (!(pulse[7] > 0)) return TDBEM_EINVAL;
+  tdbem_status s0 = tdbem_fast_invalidate(c);  // sums launched ahead used the old field
+  if (s0) return s0;
   double* hp = c->pulse.data() + 10 * (size_t)rhs;
   std::memcpy(hp, pulse, 10 * sizeof(double));
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse + 10 * rhs, hp, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -245,7 +247,8 @@ static tdbem_status from_host_layout(tdbem_ctx* c, const double* y, double* x) {
 
 tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
   if (!c || !V || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
-  tdbem_status s;
+  tdbem_status s = tdbem_fast_invalidate(c);  // sums launched ahead used the old right-hand side
+  if (s) return s;
   const int64_t n = (int64_t)(c->Nt - 1) * c->ne;
   if (!c->d_Vall) {
     if ((s = c->dalloc(&c->d_Vall, n * c->R))) return s;
@@ -623,6 +626,8 @@ tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* 
 
 tdbem_status tdbem_reset(tdbem_ctx* c) {
   if (!c) return TDBEM_EINVAL;
+  tdbem_status s0 = tdbem_fast_invalidate(c);
+  if (s0) return s0;
   const int64_t NR = c->ne * (int64_t)c->R;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * c->L * sizeof(double), c->stream));
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_J, 0, NR * sizeof(double), c->stream));

@@ -132,6 +132,23 @@ struct FmmPlan {
   int64_t* d_hrow = nullptr;
   float* d_hval = nullptr;
   int32_t* d_hmeta = nullptr;
+  // the same entries split by lag for the pipelined single-RHS march: the
+  // lags >= 3 of step alpha + 2 need the currents up to J^{alpha-1} only, so
+  // they are summed on the near stream while step alpha's solve runs; the
+  // lag-2 entries (and the far field) are added once J^{alpha} is known
+  int64_t* d_hrow2 = nullptr;
+  float* d_hval2 = nullptr;
+  int32_t* d_hmeta2 = nullptr;
+  int64_t* d_hrow3 = nullptr;
+  float* d_hval3 = nullptr;
+  int32_t* d_hmeta3 = nullptr;
+  double* d_Rp = nullptr;          // [2][ne] V - (lags >= 3) of the step alpha in buffer alpha & 1
+  cudaStream_t nstream = nullptr;  // near stream (null: no pipelining)
+  cudaEvent_t ev_solved = nullptr; // context stream: a solve has been enqueued
+  cudaEvent_t ev_near[2] = {nullptr, nullptr};  // near stream: buffer b is written
+  int32_t ahead[2] = {0, 0};       // step whose partial sum is in buffer b, launched ahead (0: none)
+  const double* ahead_V[2] = {nullptr, nullptr};  // incident row it was computed with
+  bool v_from_table = false;       // the last step took V from the incident table (not from the caller)
   int64_t nnz = 0, nval = 0, n_near_tri_pairs = 0;
   // far right-hand sides (targets ahead of the current step)
   int Lr = 0;
@@ -979,6 +996,44 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow, hrow.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
       TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval, hval.data(), hval.size() * sizeof(float), cudaMemcpyHostToDevice));
       TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta, hmeta.data(), hmeta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+      if (c->R == 1 && c->p.far_overlap) {
+        // lag 2 / lags >= 3 (see FmmPlan), each row's entries in the same order
+        std::vector<int64_t> r2(ne + 1, 0), r3(ne + 1, 0);
+        std::vector<float> v2, v3;
+        std::vector<int32_t> m2, m3;
+        for (int64_t i = 0; i < ne; ++i) {
+          r2[i] = (int64_t)v2.size();
+          r3[i] = (int64_t)v3.size();
+          for (int64_t e = hrow[i]; e < hrow[i + 1]; ++e) {
+            const bool two = (hmeta[e] & 0xff) == 2;
+            (two ? v2 : v3).push_back(hval[e]);
+            (two ? m2 : m3).push_back(hmeta[e]);
+          }
+        }
+        r2[ne] = (int64_t)v2.size();
+        r3[ne] = (int64_t)v3.size();
+        if ((s = c->dalloc(&F->d_hrow2, ne + 1)) || (s = c->dalloc(&F->d_hval2, v2.size())) ||
+            (s = c->dalloc(&F->d_hmeta2, m2.size())) || (s = c->dalloc(&F->d_hrow3, ne + 1)) ||
+            (s = c->dalloc(&F->d_hval3, v3.size())) || (s = c->dalloc(&F->d_hmeta3, m3.size())) ||
+            (s = c->dalloc(&F->d_Rp, 2 * ne)))
+          return s;
+        TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow2, r2.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow3, r3.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        if (!v2.empty()) {
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval2, v2.data(), v2.size() * sizeof(float), cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta2, m2.data(), m2.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        if (!v3.empty()) {
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval3, v3.data(), v3.size() * sizeof(float), cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta3, m3.data(), m3.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        int prio_lo = 0, prio_hi = 0;
+        TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->nstream, cudaStreamNonBlocking, prio_hi));
+        TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_solved, cudaEventDisableTiming));
+        for (int b = 0; b < 2; ++b)
+          TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_near[b], cudaEventDisableTiming));
+      }
     }
   }
   c->max_lag = std::max(F->max_near_lag, far ? F->lev[2].M + 4 : 0);
@@ -1463,6 +1518,27 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
   double* slot = nullptr;
   if (F->lmax >= 2)
     slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R;
+  if (!eval && F->nstream) {
+    // pipelined march: V - (lags >= 3) was summed ahead on the near stream
+    // when the incident row it used is still this step's; otherwise now
+    const int b = alpha & 1;
+    double* Rp = F->d_Rp + (int64_t)b * c->ne;
+    const unsigned grid = (unsigned)((c->ne + 7) / 8);
+    if (F->ahead[b]) TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, F->ev_near[b], 0));
+    const bool have = F->ahead[b] == alpha && F->ahead_V[b] == V && V != c->d_R;
+    F->ahead[b] = 0;
+    F->v_from_table = V != c->d_R;
+    cudaEvent_t e = c->prof_begin(1);
+    if (!have)
+      k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring, c->L, alpha,
+                                                       V, nullptr, Rp);
+    // lag 2 (the currents of the step just solved) and the far field
+    k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow2, F->d_hval2, F->d_hmeta2, c->ne, ring, c->L, alpha,
+                                                     Rp, slot, c->d_R);
+    c->prof_end(1, e);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    return TDBEM_OK;
+  }
   cudaEvent_t e = c->prof_begin(1);
   if (c->R == 1) {
     k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_hrow, F->d_hval, F->d_hmeta, c->ne,
@@ -1478,7 +1554,32 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
   return TDBEM_OK;
 }
 
-tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha) { return far_events(c, alpha, c->d_Jring, false); }
+tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha) {
+  FmmPlan* F = c->fmm;
+  if (F->nstream && F->v_from_table && alpha + 2 <= c->Nt - 1) {
+    // V - (lags >= 3) of step alpha + 2 needs the currents up to J^{alpha-1},
+    // which this solve completes; its buffer was last read by the lag-2 pass
+    // of step alpha, before the solve.  It runs on the near stream while the
+    // far field of this step and the next step proceed.
+    const int32_t a2 = alpha + 2;
+    const int b = a2 & 1;
+    const double* V = tdbem_incident_row(c, a2);
+    TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_solved, c->stream));
+    TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(F->nstream, F->ev_solved, 0));
+    cudaStream_t main = c->stream;
+    c->stream = F->nstream;
+    cudaEvent_t e = c->prof_begin(1);
+    k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, F->nstream>>>(
+        F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, c->d_Jring, c->L, a2, V, nullptr, F->d_Rp + (int64_t)b * c->ne);
+    c->prof_end(1, e);
+    c->stream = main;
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_near[b], F->nstream));
+    F->ahead[b] = a2;
+    F->ahead_V[b] = V;
+  }
+  return far_events(c, alpha, c->d_Jring, false);
+}
 
 // Evaluation state for history_eval: cleared, then the far events of steps
 // 1 .. alpha-1 are replayed on the supplied history.
@@ -1509,9 +1610,9 @@ tdbem_status tdbem_fast_replay_step(tdbem_ctx* c, int32_t alpha, const double* r
 
 tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
   FmmPlan* F = c->fmm;
-  if (!F || F->lmax < 2) return TDBEM_OK;
-  tdbem_status s0 = tdbem_fast_join(c);
-  if (s0) return s0;
+  if (!F) return TDBEM_OK;
+  tdbem_status s0 = tdbem_fast_invalidate(c);
+  if (s0 || F->lmax < 2) return s0;
   for (int l = 2; l <= F->lmax; ++l) {
     FmmLevel& L = F->lev[l];
     const int64_t RP = (int64_t)c->R * kNC * F->P;
@@ -1522,10 +1623,13 @@ tdbem_status tdbem_fast_reset(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
-// The context's stream waits for every deferred M2L still in flight.
+// The context's stream waits for every deferred M2L and every near-field
+// sum launched ahead that is still in flight (the sums stay usable).
 tdbem_status tdbem_fast_join(tdbem_ctx* c) {
   FmmPlan* F = c->fmm;
   if (!F) return TDBEM_OK;
+  for (int b = 0; b < 2; ++b)
+    if (F->ahead[b]) TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, F->ev_near[b], 0));
   for (int l = 2; l <= F->lmax; ++l) {
     FmmLevel& L = F->lev[l];
     if (L.defer_pending) {
@@ -1536,9 +1640,24 @@ tdbem_status tdbem_fast_join(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
+// As tdbem_fast_join, and the sums launched ahead are discarded (the
+// incident field or the march state is about to change).
+tdbem_status tdbem_fast_invalidate(tdbem_ctx* c) {
+  FmmPlan* F = c->fmm;
+  if (!F) return TDBEM_OK;
+  tdbem_status s = tdbem_fast_join(c);
+  F->ahead[0] = F->ahead[1] = 0;
+  return s;
+}
+
 void tdbem_fast_free(tdbem_ctx* c) {
   FmmPlan* F = c->fmm;
   if (F) {
+    if (F->nstream) cudaStreamSynchronize(F->nstream);
+    for (int b = 0; b < 2; ++b)
+      if (F->ev_near[b]) cudaEventDestroy(F->ev_near[b]);
+    if (F->ev_solved) cudaEventDestroy(F->ev_solved);
+    if (F->nstream) cudaStreamDestroy(F->nstream);
     if (F->side) cudaStreamSynchronize(F->side);
     for (size_t l = 2; l < F->lev.size(); ++l)
       if (F->lev[l].ev_defer) cudaEventDestroy(F->lev[l].ev_defer);

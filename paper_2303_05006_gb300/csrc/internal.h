@@ -170,6 +170,7 @@ tdbem_status tdbem_fast_eval_reset(tdbem_ctx* c);
 tdbem_status tdbem_fast_reset(tdbem_ctx* c);
 void tdbem_fast_free(tdbem_ctx* c);
 tdbem_status tdbem_fast_join(tdbem_ctx* c);
+tdbem_status tdbem_fast_invalidate(tdbem_ctx* c);
 tdbem_status tdbem_fast_check(tdbem_ctx* c);
 // m2l_tc.cu
 // pC: each pair's (source cell, symmetry) combination; pk: the packed

@@ -190,6 +190,14 @@ def test_far_overlap_matches_program_order():
     s.reset()
     Jr = s.march(n)
     assert _rel(Jr, Jb) < max(4 * floor, 1e-6)
+    # caller-supplied right-hand sides (step_v) take no sums launched ahead
+    m = 180
+    V = [s.history_eval(a, np.zeros((0, s.ne))) for a in range(1, m + 1)]
+    s.reset()
+    Jv = np.zeros((m, s.ne))
+    for a in range(m):
+        s.step_v(V[a], Jv[a])
+    assert _rel(Jv, Jb[:m]) < max(4 * floor, 1e-6)
     alpha = 200
     Rm = s.history_eval(alpha, Jb[: alpha - 1])
     R0 = _solver(w, mode=1, m2l_prec=4, far_overlap=0).history_eval(alpha, Jb[: alpha - 1])
