@@ -94,12 +94,16 @@ typedef struct {
                             both at setup on each level and keeps the faster */
   int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
                             blocks of Z0 among the RWG functions of each triangle, summed) */
-  int32_t far_overlap;   /* fast mode, 1 (default): the M2L products of a gating event with lag q >= 2, whose
-                            local coefficients are first read one interval later, run on a second stream of
-                            the context while the next steps' near field and solves proceed; 0: every product
-                            on the context's stream, in the step that fires it (program 1's order).  The second
-                            stream has the lowest priority; the library's own stream the highest (a caller's
-                            stream keeps its own priority) */
+  int32_t far_overlap;   /* fast mode, 1 (default): the steps overlap.  The M2L products of a gating event with
+                            lag q >= 2, whose local coefficients are first read one interval later, run on a
+                            lowest-priority second stream of the context while the next steps proceed; with
+                            one right-hand side, the near-field lags >= 3 of step alpha + 2 are summed on a
+                            highest-priority third stream while step alpha's solve runs.  0: every kernel on
+                            the context's stream in program 1's order.  The library's own stream has the
+                            highest priority (a caller's stream keeps its own) */
+  int32_t solve_grid;    /* single-RHS Z0 solve: 0 (default) one thread-block cluster below 49152 RWG functions
+                            and a cooperative grid of every SM from there on; 1 always the cluster; 2 always
+                            the grid */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -110,7 +114,7 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1. */
+   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -243,7 +247,9 @@ typedef struct {
   int64_t device_bytes;            /* device memory held by the context */
   double setup_seconds;            /* wall time of tdbem_create */
   int64_t total_solver_iters;
-  int32_t solver_cluster;          /* CTAs in the Z0 solver's thread-block cluster (0 before the first solve) */
+  int32_t solver_cluster;          /* CTAs of the single-RHS Z0 solve: one thread-block cluster, or for meshes of
+                                      49152 RWG functions or more a cooperative grid of every SM (0 before the
+                                      first solve) */
   int64_t n_far_pairs;             /* interaction-list cluster pairs over all levels (fast mode) */
   double m2l_flops_per_step;       /* M2L flops per step, averaged over the gating cycle (fast mode) */
   int64_t total_jacobi_sweeps;     /* FP64 Jacobi sweeps of the Z0 solves (per-cluster maximum when batched) */

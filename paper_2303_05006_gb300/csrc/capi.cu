@@ -58,6 +58,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->jacobi_sweeps = 0;
   p->precond = 1;
   p->far_overlap = 1;
+  p->solve_grid = 0;
 }
 
 static void fill_phys(tdbem_ctx* c) {
@@ -127,7 +128,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
-      p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) ||
+      p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -194,8 +195,6 @@ tdbem_status tdbem_set_stream(tdbem_ctx* c, void* stream) {
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* pulse) {
   if (!c || !pulse || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
   if (!(pulse[7] > 0)) return TDBEM_EINVAL;
-  tdbem_status s0 = tdbem_fast_invalidate(c);  // sums launched ahead used the old field
-  if (s0) return s0;
   double* hp = c->pulse.data() + 10 * (size_t)rhs;
   std::memcpy(hp, pulse, 10 * sizeof(double));
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse + 10 * rhs, hp, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -247,8 +246,7 @@ static tdbem_status from_host_layout(tdbem_ctx* c, const double* y, double* x) {
 
 tdbem_status tdbem_set_rhs(tdbem_ctx* c, int32_t rhs, const double* V) {
   if (!c || !V || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
-  tdbem_status s = tdbem_fast_invalidate(c);  // sums launched ahead used the old right-hand side
-  if (s) return s;
+  tdbem_status s;
   const int64_t n = (int64_t)(c->Nt - 1) * c->ne;
   if (!c->d_Vall) {
     if ((s = c->dalloc(&c->d_Vall, n * c->R))) return s;

@@ -142,13 +142,11 @@ struct FmmPlan {
   int64_t* d_hrow3 = nullptr;
   float* d_hval3 = nullptr;
   int32_t* d_hmeta3 = nullptr;
-  double* d_Rp = nullptr;          // [2][ne] V - (lags >= 3) of the step alpha in buffer alpha & 1
+  double* d_Rp = nullptr;          // [2][ne] -(lags >= 3) of the step alpha in buffer alpha & 1
   cudaStream_t nstream = nullptr;  // near stream (null: no pipelining)
   cudaEvent_t ev_solved = nullptr; // context stream: a solve has been enqueued
   cudaEvent_t ev_near[2] = {nullptr, nullptr};  // near stream: buffer b is written
   int32_t ahead[2] = {0, 0};       // step whose partial sum is in buffer b, launched ahead (0: none)
-  const double* ahead_V[2] = {nullptr, nullptr};  // incident row it was computed with
-  bool v_from_table = false;       // the last step took V from the incident table (not from the caller)
   int64_t nnz = 0, nval = 0, n_near_tri_pairs = 0;
   // far right-hand sides (targets ahead of the current step)
   int Lr = 0;
@@ -643,10 +641,12 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
 // Near field, flattened form: a warp streams its row's (coefficient,
 // column << 8 | lag) entries with coalesced loads; every lane does the same
 // work, and the lags of one column are neighbours in the history ring.
-// R_i = V_i + Rfar_i - sum over the row's entries of z J_col^{alpha-m}.
+// R_i = V_i + V2_i + Rfar_i - sum over the row's entries of z J_col^{alpha-m}
+// (V, V2 and Rfar may be null).
 __global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, const float* hval, const int32_t* hmeta,
                                                           int64_t ne, const double* ring, int L, int alpha,
-                                                          const double* V, double* Rfar_slot, double* R) {
+                                                          const double* V, const double* V2, double* Rfar_slot,
+                                                          double* R) {
   int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (i >= ne) return;
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, 
   for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
   if (lane == 0) {
     double far = Rfar_slot ? Rfar_slot[i] : 0.0;
-    R[i] = (V ? V[i] : 0.0) + far - d;
+    R[i] = (V ? V[i] : 0.0) + (V2 ? V2[i] : 0.0) + far - d;
     if (Rfar_slot) Rfar_slot[i] = 0.0;
   }
 }
@@ -1519,22 +1519,21 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
   if (F->lmax >= 2)
     slot = (eval ? F->d_Rfar_eval : F->d_Rfar) + (int64_t)((alpha - 1) & (F->Lr - 1)) * c->ne * c->R;
   if (!eval && F->nstream) {
-    // pipelined march: V - (lags >= 3) was summed ahead on the near stream
-    // when the incident row it used is still this step's; otherwise now
+    // pipelined march: -(lags >= 3) was summed ahead on the near stream
+    // (it depends on the history only); otherwise it is summed now
     const int b = alpha & 1;
     double* Rp = F->d_Rp + (int64_t)b * c->ne;
     const unsigned grid = (unsigned)((c->ne + 7) / 8);
     if (F->ahead[b]) TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, F->ev_near[b], 0));
-    const bool have = F->ahead[b] == alpha && F->ahead_V[b] == V && V != c->d_R;
+    const bool have = F->ahead[b] == alpha;
     F->ahead[b] = 0;
-    F->v_from_table = V != c->d_R;
     cudaEvent_t e = c->prof_begin(1);
     if (!have)
       k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring, c->L, alpha,
-                                                       V, nullptr, Rp);
-    // lag 2 (the currents of the step just solved) and the far field
+                                                       nullptr, nullptr, nullptr, Rp);
+    // V, lag 2 (the currents of the step just solved) and the far field
     k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow2, F->d_hval2, F->d_hmeta2, c->ne, ring, c->L, alpha,
-                                                     Rp, slot, c->d_R);
+                                                     V, Rp, slot, c->d_R);
     c->prof_end(1, e);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     return TDBEM_OK;
@@ -1542,7 +1541,8 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
   cudaEvent_t e = c->prof_begin(1);
   if (c->R == 1) {
     k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_hrow, F->d_hval, F->d_hmeta, c->ne,
-                                                                             ring, c->L, alpha, V, slot, c->d_R);
+                                                                             ring, c->L, alpha, V, nullptr, slot,
+                                                                             c->d_R);
   } else {
     int RL = 1;
     while (RL < c->R && RL < 32) RL <<= 1;
@@ -1556,27 +1556,26 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
 
 tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha) {
   FmmPlan* F = c->fmm;
-  if (F->nstream && F->v_from_table && alpha + 2 <= c->Nt - 1) {
-    // V - (lags >= 3) of step alpha + 2 needs the currents up to J^{alpha-1},
+  if (F->nstream && alpha + 2 <= c->Nt - 1) {
+    // -(lags >= 3) of step alpha + 2 needs the currents up to J^{alpha-1},
     // which this solve completes; its buffer was last read by the lag-2 pass
     // of step alpha, before the solve.  It runs on the near stream while the
     // far field of this step and the next step proceed.
     const int32_t a2 = alpha + 2;
     const int b = a2 & 1;
-    const double* V = tdbem_incident_row(c, a2);
     TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_solved, c->stream));
     TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(F->nstream, F->ev_solved, 0));
     cudaStream_t main = c->stream;
     c->stream = F->nstream;
     cudaEvent_t e = c->prof_begin(1);
     k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, F->nstream>>>(
-        F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, c->d_Jring, c->L, a2, V, nullptr, F->d_Rp + (int64_t)b * c->ne);
+        F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, c->d_Jring, c->L, a2, nullptr, nullptr, nullptr,
+        F->d_Rp + (int64_t)b * c->ne);
     c->prof_end(1, e);
     c->stream = main;
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_near[b], F->nstream));
     F->ahead[b] = a2;
-    F->ahead_V[b] = V;
   }
   return far_events(c, alpha, c->d_Jring, false);
 }
@@ -1640,8 +1639,8 @@ tdbem_status tdbem_fast_join(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
-// As tdbem_fast_join, and the sums launched ahead are discarded (the
-// incident field or the march state is about to change).
+// As tdbem_fast_join, and the sums launched ahead are discarded (the march
+// state is about to change).
 tdbem_status tdbem_fast_invalidate(tdbem_ctx* c) {
   FmmPlan* F = c->fmm;
   if (!F) return TDBEM_OK;

@@ -115,7 +115,8 @@ struct tdbem_ctx {
   int32_t alpha = 1;
   int64_t total_iters = 0;
   int64_t total_sweeps = 0;
-  int32_t cluster = 0;              // CTAs in the solver's thread-block cluster
+  int32_t cluster = 0;              // CTAs of the single-RHS solve (one cluster, or the cooperative grid)
+  double* d_gslots = nullptr;       // per-block partial sums of the grid-wide solve
   int32_t device = 0;               // CUDA device the context lives on
   double* d_Vtab = nullptr;         // [Nt-1][ne][R] incident field of every step (precomputed)
   cudaStream_t own_stream = nullptr;

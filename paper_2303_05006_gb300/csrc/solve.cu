@@ -12,7 +12,8 @@
 // memory (L2-resident), and every reduction is combined through distributed
 // shared memory after a hardware cluster barrier.  There is no host round trip
 // and no software spin-wait; all CTAs take identical branch decisions because
-// they read the same reduced values.
+// they read the same reduced values.  Large meshes (kGridSolveRows) run the
+// same loop over a cooperative grid of every SM, meeting at grid barriers.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -110,6 +111,7 @@ struct SolveArgs {
   int32_t* status;  // [0] inner iterations, [1] converged flag, [2] misses, [3] iteration total,
                     // [6] Jacobi sweeps of this solve, [7] Jacobi sweeps since the last reset
   double* resid;    // [0] final relative residual
+  double* gslots;   // grid-wide form: [2][gridDim][4] per-block partial sums
 };
 
 // Block sums of NV values; the totals end up in thread 0.
@@ -161,6 +163,57 @@ __device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = bc[k];
 }
+
+// Where the solve's CTAs meet.  ClusterSync: one thread-block cluster, the
+// sums combined through distributed shared memory.  GridSync: a cooperative
+// grid over the whole GPU (large meshes, where one cluster's 16 SMs are too
+// few), the per-block partials published in global memory and read back with
+// L2-only loads after the grid barrier, summed by every block in the same
+// fixed order.
+struct ClusterSync {
+  cg::cluster_group cl;
+  double (*slots)[4];
+  double* bc;
+  int phase = 0;
+  __device__ unsigned nblocks() const { return cl.num_blocks(); }
+  __device__ unsigned rank() const { return cl.block_rank(); }
+  __device__ void sync() { cl.sync(); }
+  template <int NV>
+  __device__ void sums(double (&v)[NV]) {
+    cluster_sums<NV>(cl, v, slots, bc, phase);
+  }
+};
+
+struct GridSync {
+  cg::grid_group g;
+  double* gslots;  // [2][gridDim.x][4]
+  double* bc;
+  int phase = 0;
+  __device__ unsigned nblocks() const { return gridDim.x; }
+  __device__ unsigned rank() const { return blockIdx.x; }
+  __device__ void sync() { g.sync(); }
+  template <int NV>
+  __device__ void sums(double (&v)[NV]) {
+    double* slot = gslots + (int64_t)(phase & 1) * gridDim.x * 4;
+    ++phase;
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) slot[(int64_t)blockIdx.x * 4 + k] = v[k];
+    g.sync();
+    if (threadIdx.x < 32) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(slot + (int64_t)b * 4 + k);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) bc[k] = s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = bc[k];
+  }
+};
 
 // Row i of Z0 times x (x[j*R + rl]: column rl of an [ne][R] block).  With the
 // column-major ELL layout consecutive rows (threads) read consecutive
@@ -218,14 +271,10 @@ __device__ __forceinline__ float precond_row(const SolveArgs& A, int64_t i, cons
 // correction, inner relative tolerance 1e-5 (kInner2).  Z0 is well conditioned (about 2
 // on the test spheres), so each refinement gains five to six digits and two to
 // three refinements reach 1e-13.
-__global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
-  cg::cluster_group cl = cg::this_cluster();
-  __shared__ double red[32 * 4];
-  __shared__ double slots[2][4];
-  __shared__ double bc[4];
-  int phase = 0;
+template <class Sync>
+__device__ __forceinline__ void bicgstab_body(const SolveArgs& A, Sync& cl, double* red) {
   const int64_t ne = A.ne;
-  const unsigned nb = cl.num_blocks(), rk = cl.block_rank();
+  const unsigned nb = cl.nblocks(), rk = cl.rank();
   const int64_t rows = (ne + nb - 1) / nb;
   const int64_t r0 = rk * rows, r1 = min(ne, r0 + rows);
   double* r64 = A.w;
@@ -263,7 +312,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       q2[1] += rc * rc;
     }
     block_sums<2>(q2, red);
-    cluster_sums<2>(cl, q2, slots, bc, phase);
+    cl.template sums<2>(q2);
     const bool keep = q2[0] < q2[1];
     if (!keep) {
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) A.x[i] = r64[i];
@@ -293,7 +342,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
         q2[1] += A.b[i] * A.b[i];
       }
       block_sums<2>(q2, red);
-      cluster_sums<2>(cl, q2, slots, bc, phase);  // its cluster barrier also publishes nxt
+      cl.template sums<2>(q2);  // its cluster barrier also publishes nxt
       if (bb < 0) bb = q2[1];
       rr = q2[0];
       if (rr <= A.tol * A.tol * bb) {  // cur is the solution
@@ -322,7 +371,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       q2[1] += A.b[i] * A.b[i];
     }
     block_sums<2>(q2, red);
-    cluster_sums<2>(cl, q2, slots, bc, phase);
+    cl.template sums<2>(q2);
     rr = q2[0];
     if (bb < 0) bb = q2[1];
     if (rr <= A.tol * A.tol * bb) {
@@ -342,7 +391,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
       q1[0] += (double)ri * ri;
     }
     block_sums<1>(*(double(*)[1])q1, red);
-    cluster_sums<1>(cl, *(double(*)[1])q1, slots, bc, phase);
+    cl.template sums<1>(*(double(*)[1])q1);
     double rho = q1[0], rho_old = 1.0, alp = 1.0, om = 1.0;
     const double tin2 = kInner2 * q1[0];
     for (int it = 0; it < kInnerMax && inner_total < A.maxit; ++it) {
@@ -367,7 +416,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
         e1[0] += (double)(rh[i] * vi);
       }
       block_sums<1>(e1, red);
-      cluster_sums<1>(cl, e1, slots, bc, phase);
+      cl.template sums<1>(e1);
       if (e1[0] == 0.0) break;
       alp = rho / e1[0];
       float alf = (float)alp;
@@ -379,7 +428,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
         e2[0] += (double)(si * si);
       }
       block_sums<1>(e2, red);
-      cluster_sums<1>(cl, e2, slots, bc, phase);  // also orders sh (or s) for what follows
+      cl.template sums<1>(e2);  // also orders sh (or s) for what follows
       if (e2[0] <= tin2) {
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] += alf * ph[i];
         break;
@@ -396,7 +445,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
         e3[1] += (double)(ti * ti);
       }
       block_sums<2>(e3, red);
-      cluster_sums<2>(cl, e3, slots, bc, phase);
+      cl.template sums<2>(e3);
       if (e3[1] == 0.0) break;
       om = e3[0] / e3[1];
       omf = (float)om;
@@ -409,7 +458,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
         e4[1] += (double)(rh[i] * ri);
       }
       block_sums<2>(e4, red);
-      cluster_sums<2>(cl, e4, slots, bc, phase);
+      cl.template sums<2>(e4);
       rho_old = rho;
       rho = e4[1];
       if (e4[0] <= tin2 || om == 0.0) break;
@@ -430,6 +479,23 @@ __global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
     A.resid[0] = bb > 0 ? sqrt(rr / bb) : 0.0;
   }
   cl.sync();  // keep every CTA's shared slots alive until all remote reads are done
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_bicgstab(SolveArgs A) {
+  __shared__ double red[32 * 4];
+  __shared__ double slots[2][4];
+  __shared__ double bc[4];
+  ClusterSync S{cg::this_cluster(), slots, bc};
+  bicgstab_body(A, S, red);
+}
+
+// The same solve over a cooperative grid (launched with
+// cudaLaunchCooperativeKernel, every block resident).
+__global__ void __launch_bounds__(kSolveThreads) k_bicgstab_grid(SolveArgs A) {
+  __shared__ double red[32 * 4];
+  __shared__ double bc[4];
+  GridSync S{cg::this_grid(), A.gslots, bc};
+  bicgstab_body(A, S, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -1041,6 +1107,26 @@ static tdbem_status pick_cluster(tdbem_ctx* c) {
   return TDBEM_ECUDA;
 }
 
+// Meshes with at least this many RWG functions solve over a cooperative grid
+// of every SM instead of one cluster: a 16-SM cluster spends about 1 ms per
+// BiCGStab iteration at 120000 unknowns.
+constexpr int64_t kGridSolveRows = 49152;
+static int g_grid = 0;
+static tdbem_status pick_grid(tdbem_ctx* c) {
+  if (g_grid) return TDBEM_OK;
+  int dev = 0, sms = 0, coop = 0, per = 0;
+  TDBEM_CUDA_TRY(c, cudaGetDevice(&dev));
+  TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicgstab_grid, kSolveThreads, 0));
+  if (!coop || per < 1) {
+    c->set_error("solve: cooperative launch not available for the grid-wide solve");
+    return TDBEM_ECUDA;
+  }
+  g_grid = sms * per;
+  return TDBEM_OK;
+}
+
 // Batched solver: the cluster size of the single-RHS solver and as many
 // co-resident clusters as there are right-hand sides, up to what fits.
 static int g_multi_ncl = 0;
@@ -1122,7 +1208,9 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t
   if (c->R > 1) {
     if ((s = solve_multi(c, alpha, warm))) return s;
   } else {
-    if ((s = pick_cluster(c))) return s;
+    const bool grid = c->p.solve_grid == 2 || (c->p.solve_grid == 0 && c->ne >= kGridSolveRows);
+    if ((s = grid ? pick_grid(c) : pick_cluster(c))) return s;
+    if (grid && !c->d_gslots && (s = c->dalloc(&c->d_gslots, (size_t)2 * g_grid * 4))) return s;
     SolveArgs A;
     A.len = c->d_ell_len;
     A.col = c->d_ell_col;
@@ -1144,19 +1232,27 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t
     A.jacobi = c->p.jacobi_sweeps;
     A.status = c->d_status;
     A.resid = c->d_dots;
-    c->cluster = g_cluster;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_cluster);
-    cfg.blockDim = dim3(kSolveThreads);
-    cfg.stream = c->stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = g_cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    TDBEM_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_bicgstab, A));
+    A.gslots = c->d_gslots;
+    if (grid) {
+      c->cluster = g_grid;
+      void* args[] = {&A};
+      TDBEM_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_bicgstab_grid, dim3(g_grid), dim3(kSolveThreads), args,
+                                                    0, c->stream));
+    } else {
+      c->cluster = g_cluster;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(g_cluster);
+      cfg.blockDim = dim3(kSolveThreads);
+      cfg.stream = c->stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = g_cluster;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      TDBEM_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, k_bicgstab, A));
+    }
   }
   if (iters) {
     int32_t h[2];

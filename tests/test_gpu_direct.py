@@ -127,3 +127,21 @@ def test_jacobi_preconditioner_march(sphere320_oracle, sphere320_march):
     J = s.march(w.Nt - 1)
     assert np.linalg.norm(J - sphere320_march) / np.linalg.norm(sphere320_march) < 1e-10
     assert s.info().total_solver_iters > 0
+
+
+def test_grid_wide_solve_matches_oracle_and_cluster(sphere320_oracle, sphere320_march):
+    """The cooperative-grid Z0 solve (solve_grid = 2; the default from 49152
+    RWG functions on) marches the 480-RWG sphere to the oracle's currents
+    within the 1e-10 bar, like the one-cluster solve, and uses more CTAs than
+    a cluster holds."""
+    w, o = sphere320_oracle
+    Jref = sphere320_march
+    n = Jref.shape[0]
+    sg = _solver(w, solve_grid=2)
+    Jg = sg.march(n)
+    sc = _solver(w, solve_grid=1)
+    Jc = sc.march(n)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert rel(Jg, Jref) < 1e-10, rel(Jg, Jref)
+    assert rel(Jg, Jc) < 1e-11
+    assert sg.info().solver_cluster > 16 >= sc.info().solver_cluster

@@ -190,7 +190,7 @@ def test_far_overlap_matches_program_order():
     s.reset()
     Jr = s.march(n)
     assert _rel(Jr, Jb) < max(4 * floor, 1e-6)
-    # caller-supplied right-hand sides (step_v) take no sums launched ahead
+    # caller-supplied right-hand sides (step_v) use the same sums launched ahead
     m = 180
     V = [s.history_eval(a, np.zeros((0, s.ne))) for a in range(1, m + 1)]
     s.reset()
