@@ -98,7 +98,7 @@ typedef struct {
                             lag q >= 2, whose local coefficients are first read one interval later, run on a
                             lowest-priority second stream of the context while the next steps proceed; with
                             one right-hand side, the near-field lags >= 3 of step alpha + 2 are summed on a
-                            highest-priority third stream while step alpha's solve runs.  0: every kernel on
+                            middle-priority third stream while step alpha's solve runs.  0: every kernel on
                             the context's stream in program 1's order.  The library's own stream has the
                             highest priority (a caller's stream keeps its own) */
   int32_t solve_grid;    /* single-RHS Z0 solve: 0 (default) one thread-block cluster below 49152 RWG functions

@@ -1027,9 +1027,12 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval3, v3.data(), v3.size() * sizeof(float), cudaMemcpyHostToDevice));
           TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta3, m3.data(), m3.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         }
+        // between the deferred M2L's lowest priority and the steps' highest:
+        // the next solve's cluster, which needs whole SMs, is dispatched ahead
+        // of this stream's remaining CTAs
         int prio_lo = 0, prio_hi = 0;
         TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-        TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->nstream, cudaStreamNonBlocking, prio_hi));
+        TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->nstream, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
         TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_solved, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b)
           TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_near[b], cudaEventDisableTiming));
