@@ -335,7 +335,9 @@ __global__ void k_p2m(const int32_t* leaf_cells, const int32_t* tri_b, const int
   __syncthreads();
   float* out = mom + (((int64_t)cell * 2 + (k & 1)) * 2 * R + rhs) * kNC * P;  // variant stride R kNC P
   const int64_t vstr = (int64_t)R * kNC * P;
-  for (int e = threadIdx.x; e < kNC * PS; e += blockDim.x) {
+  // the grid's z dimension splits a cell's (component, node) outputs over
+  // several blocks (each recomputes the cheap time moments above)
+  for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < kNC * PS; e += gridDim.z * blockDim.x) {
     int c = e / PS, b = e % PS;
     float a0[8], a1[8];
     for (int n = 0; n < pt; ++n) a0[n] = a1[n] = 0.f;
@@ -624,15 +626,38 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
   __syncthreads();
   int tb = tri_b[cell], te_ = tri_e[cell];
   int ntk = 3 * (te_ - tb);
-  for (int e = threadIdx.x; e < ntk * M; e += blockDim.x) {
-    int q = e / M, i = e % M;
-    int t = perm[tb + q / 3], kk = q % 3;
-    const float* Tt = T + ((int64_t)t * 3 + kk) * kNC * PS;
-    const float* le = Le + (int64_t)i * kNC * PS;
-    float s = 0.f;
-    for (int r = 0; r < kNC * PS; ++r) s += Tt[r] * le[r];
-    int rho = (k + 1) * M + i;
-    atomicAdd(Rfar + ((int64_t)(rho & (Lr - 1)) * ne + g.edge[3 * t + kk]) * R + rhs, -(double)s);
+  // one warp per (triangle, side): the lanes stride the row of T (coalesced,
+  // read once per 8 steps) and the rows of Le (consecutive words, no bank
+  // conflicts); the 8 partial dot products are then summed across the warp
+  constexpr int kSt = 8;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nr = kNC * PS;
+  for (int q = threadIdx.x >> 5; q < ntk; q += nw) {
+    const int t = perm[tb + q / 3], kk = q % 3;
+    const float* Tt = T + ((int64_t)t * 3 + kk) * nr;
+    const int64_t edge = g.edge[3 * t + kk];
+    for (int i0 = 0; i0 < M; i0 += kSt) {
+      float acc[kSt];
+#pragma unroll
+      for (int u = 0; u < kSt; ++u) acc[u] = 0.f;
+      for (int r = lane; r < nr; r += 32) {
+        const float tv = __ldg(Tt + r);
+#pragma unroll
+        for (int u = 0; u < kSt; ++u)
+          if (i0 + u < M) acc[u] += tv * Le[(int64_t)(i0 + u) * nr + r];
+      }
+#pragma unroll
+      for (int u = 0; u < kSt; ++u)
+        for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      if (lane < kSt && i0 + lane < M) {
+        float sv = acc[0];
+#pragma unroll
+        for (int u = 1; u < kSt; ++u)
+          if (lane == u) sv = acc[u];
+        const int rho = (k + 1) * M + i0 + lane;
+        atomicAdd(Rfar + ((int64_t)(rho & (Lr - 1)) * ne + edge) * R + rhs, -(double)sv);
+      }
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) L[e] = 0.f;
@@ -1417,7 +1442,7 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
         if (L.leaf[i]) maxtri = std::max(maxtri, L.tri_e[i] - L.tri_b[i]);
       size_t smem = (size_t)3 * maxtri * 2 * pt * sizeof(float);
       cudaEvent_t e = c->prof_begin(3);
-      k_p2m<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
+      k_p2m<<<dim3(L.nleaf, R, 2), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
                                                          F->d_W, L.d_tsrc, ring, c->L, p, pt, L.M, k, MOM(l), R);
       c->prof_end(3, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
