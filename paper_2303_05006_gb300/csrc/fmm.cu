@@ -417,11 +417,15 @@ __device__ __forceinline__ void contract_axis(const float* in, float* out, const
 
 // M2M, factorised: for each child and half-interval, the 14 channels (7
 // components x full/truncated) are interpolated one axis at a time and
-// accumulated into the parent moments of source interval k.
+// accumulated into the parent moments of source interval k.  The grid's z
+// dimension splits the channels over blocks (per = ceil(14 / gridDim.z)
+// channels each; shared memory 3 per P floats).
 __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
                            int k, const float* cmom, float* pmom, int R) {
   extern __shared__ float sm[];
-  const int PS = p * p * p, P = PS * pt, nch = 2 * kNC;
+  const int PS = p * p * p, P = PS * pt, nct = 2 * kNC;
+  const int per = (nct + gridDim.z - 1) / gridDim.z, c0 = blockIdx.z * per, nch = min(per, nct - c0);
+  if (nch <= 0) return;
   const int rhs = blockIdx.y;
   const int64_t vstr = (int64_t)R * kNC * P;  // stride of the full/truncated variant
   float* b0 = sm;
@@ -437,7 +441,8 @@ __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const flo
       const float* src = cmom + ((int64_t)ch * 2 + h) * 2 * vstr + (int64_t)rhs * kNC * P;
       __syncthreads();
       for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
-        int var = e / (kNC * P), r = e % (kNC * P);
+        const int gc = c0 + e / P;  // channel: variant * kNC + component
+        int var = gc / kNC, r = (gc % kNC) * P + e % P;
         int cvar = (var == 1 && h == 0) ? 1 : 0;  // truncated parent = truncated first half + full second half
         b0[e] = src[(int64_t)cvar * vstr + r];
       }
@@ -452,7 +457,8 @@ __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const flo
   __syncthreads();
   float* out = pmom + ((int64_t)cell * 2 + (k & 1)) * 2 * vstr + (int64_t)rhs * kNC * P;
   for (int e = threadIdx.x; e < nch * P; e += blockDim.x) {
-    int var = e / (kNC * P), r = e % (kNC * P);
+    const int gc = c0 + e / P;
+    int var = gc / kNC, r = (gc % kNC) * P + e % P;
     out[(int64_t)var * vstr + r] = acc[e];
   }
 }
@@ -463,13 +469,16 @@ __global__ void k_m2m_fact(const int32_t* cells, const int32_t* child, const flo
 __global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const float* Sx, const float* St, int p, int pt,
                            int k, float* ploc, int Qp, float* cloc, int Qc, int R) {
   extern __shared__ float sm[];
-  const int PS = p * p * p, P = PS * pt, nch = kNC;
+  const int PS = p * p * p, P = PS * pt;
+  // components c0 .. c0 + nch - 1 (the grid's z dimension splits the 7)
+  const int per = (kNC + gridDim.z - 1) / gridDim.z, c0 = blockIdx.z * per, nch = min(per, kNC - c0);
+  if (nch <= 0) return;
   const int rhs = blockIdx.y;
   float* b0 = sm;
   float* b1 = sm + nch * P;
   float* par = sm + 2 * nch * P;
   int cell = cells[blockIdx.x];
-  float* src = ploc + (((int64_t)cell * Qp + ((k + 1) % Qp)) * R + rhs) * kNC * P;
+  float* src = ploc + (((int64_t)cell * Qp + ((k + 1) % Qp)) * R + rhs) * kNC * P + (int64_t)c0 * P;
   for (int e = threadIdx.x; e < nch * P; e += blockDim.x) par[e] = src[e];
   for (int o = 0; o < 8; ++o) {
     int ch = child[cell * 8 + o];
@@ -482,7 +491,7 @@ __global__ void k_l2l_fact(const int32_t* cells, const int32_t* child, const flo
       contract_axis(b1, b0, Sx + sy * p * p, true, 1, p, pt, nch);
       contract_axis(b0, b1, Sx + sx * p * p, true, 0, p, pt, nch);
       int slot = (2 * (k + 1) + h) % Qc;
-      float* dst = cloc + (((int64_t)ch * Qc + slot) * R + rhs) * kNC * P;
+      float* dst = cloc + (((int64_t)ch * Qc + slot) * R + rhs) * kNC * P + (int64_t)c0 * P;
       for (int e = threadIdx.x; e < nch * P; e += blockDim.x) dst[e] += b1[e];
     }
   }
@@ -1449,9 +1458,10 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     }
     if (L.nnonleaf && l < lmax) {
       cudaEvent_t e = c->prof_begin(4);
-      size_t smem = (size_t)3 * 2 * kNC * P * sizeof(float);
+      constexpr int kZ = 7;  // blocks per cell, 2 of the 14 channels each
+      size_t smem = (size_t)3 * ((2 * kNC + kZ - 1) / kZ) * P * sizeof(float);
       if (smem <= 227 * 1024)
-        k_m2m_fact<<<dim3(L.nnonleaf, R), 512, smem, c->stream>>>(
+        k_m2m_fact<<<dim3(L.nnonleaf, R, kZ), 512, smem, c->stream>>>(
             L.d_nonleaf_cells, L.d_child, F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k, MOM(l + 1), MOM(l), R);
       else  // large p: direct tensor-product sums from global memory
         k_m2m<<<dim3(L.nnonleaf, R), 256, 0, c->stream>>>(L.d_nonleaf_cells, L.d_child,
@@ -1516,9 +1526,10 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
     }
     if (L.nnonleaf && l < lmax) {
       cudaEvent_t e = c->prof_begin(6);
-      size_t smem = (size_t)3 * kNC * P * sizeof(float);
+      constexpr int kZ = 7;  // blocks per cell, one component each
+      size_t smem = (size_t)3 * ((kNC + kZ - 1) / kZ) * P * sizeof(float);
       if (smem <= 227 * 1024)
-        k_l2l_fact<<<dim3(L.nnonleaf, R), 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child,
+        k_l2l_fact<<<dim3(L.nnonleaf, R, kZ), 512, smem, c->stream>>>(L.d_nonleaf_cells, L.d_child,
                                                                    F->d_Sx + (size_t)l * 2 * p * p, F->d_St, p, pt, k,
                                                                    LOC(l), L.Q, LOC(l + 1), F->lev[l + 1].Q, R);
       else
