@@ -7,8 +7,9 @@
 // edges (1.5 per triangle) and while its children's time intervals can still
 // hold d+1 = 3 steps (see below).  Cells at level l have size ds_l; the
 // interpolation box of a cell is its cube enlarged by delta = max distance
-// from a triangle centroid to its vertices, so that every quadrature point of
-// its triangles lies inside: half-width H_l = ds_l/2 + delta.
+// from a triangle centroid to its outer-rule points (the only points at which
+// the far field samples a triangle), so that all of them lie inside:
+// half-width H_l = ds_l/2 + delta.
 //
 // Time intervals (eq. Mt).  M_l steps per interval at level l, M_l = 2 M_{l+1}.
 // Causality of one interval requires M_l c dt <= (smallest distance between
@@ -871,7 +872,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
   for (int64_t t = 0; t < nt; ++t)
     for (int q = 0; q < 3; ++q)
       cen[3 * t + q] = (c->V[3 * c->T[3 * t] + q] + c->V[3 * c->T[3 * t + 1] + q] + c->V[3 * c->T[3 * t + 2] + q]) / 3.0;
-  F->delta = c->max_tri_rad;
+  F->delta = c->max_quad_rad;
   double D = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2])) * (1 + 1e-9);
   F->D = D;
   for (int q = 0; q < 3; ++q) F->root[q] = lo[q];

@@ -67,6 +67,7 @@ struct tdbem_ctx {
   tdbem::Phys phys;
   int64_t nv = 0, nt = 0, ne = 0;
   double max_tri_rad = 0;            // max over triangles of centroid-vertex distance
+  double max_quad_rad = 0;           // max over triangles of centroid-to-outer-rule-point distance
   // host mesh tables
   std::vector<double> V;
   std::vector<int32_t> T;

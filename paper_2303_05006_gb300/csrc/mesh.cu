@@ -115,6 +115,15 @@ tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, con
     }
     hr[t] = r;
     c->max_tri_rad = std::max(c->max_tri_rad, r);
+    // the far field samples a triangle only at its outer-rule points
+    for (int qq = 0; qq < tdbem::kNq; ++qq) {
+      double d2 = 0;
+      for (int q = 0; q < 3; ++q) {
+        const double x = c->phys.qb[qq][0] * P[0][q] + c->phys.qb[qq][1] * P[1][q] + c->phys.qb[qq][2] * P[2][q];
+        d2 += (x - hc[3 * t + q]) * (x - hc[3 * t + q]);
+      }
+      c->max_quad_rad = std::max(c->max_quad_rad, std::sqrt(d2));
+    }
     hl[t] = lm;
   }
   tdbem_status s;
