@@ -330,15 +330,16 @@ def run_sweep(args, rank, world, dist):
     nJd = np.linalg.norm(Jd)
     rows = []
     for item in args.sweep.split(","):
-        p, prec = item.split(":")
+        p, prec = item.split(":")  # "p" or "p_s x p_t", e.g. 4:tf32x3 or 5x4:tf32x3
+        ps, pt = (int(v) for v in p.split("x")) if "x" in p else (int(p), int(p))
         t0 = time.perf_counter()
-        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=1, p_s=int(p), p_t=int(p), m2l_prec=PREC[prec],
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=1, p_s=ps, p_t=pt, m2l_prec=PREC[prec],
                    precond=args.precond, solve_tol=args.solve_tol)
         setup = time.perf_counter() - t0
         J, sps = march(s)
         s.close()
         err = np.linalg.norm(J - Jd, axis=1) / np.maximum(np.linalg.norm(Jd, axis=1), 1e-300)
-        rows.append({"p_s": int(p), "p_t": int(p), "m2l": prec, "steps_per_s": sps, "setup_s": setup,
+        rows.append({"p_s": ps, "p_t": pt, "m2l": prec, "steps_per_s": sps, "setup_s": setup,
                      "rel_l2_vs_direct": float(np.linalg.norm(J - Jd) / nJd),
                      "rel_l2_last_100_steps": float(np.linalg.norm(J[-100:] - Jd[-100:]) / np.linalg.norm(Jd[-100:])),
                      "finite": bool(np.isfinite(J).all()), "max_step_rel_err": float(err.max())})
@@ -529,7 +530,8 @@ def main():
     ap.add_argument("--m2l-tile-rows", type=int, default=0, choices=(0, 128, 256),
                     help="tensor-core M2L CTA shape: 0 = autotuned at setup, 128 or 256 operator rows per CTA")
     ap.add_argument("--sweep", default="",
-                    help="comma-separated p:form settings (e.g. 3:fp32,4:tf32x3); prints error vs the FP64 march per setting")
+                    help="comma-separated p:form settings (e.g. 3:fp32,4:tf32x3,5x4:tf32x3 for p_s x p_t); prints error vs "
+                         "the FP64 march per setting")
     args = ap.parse_args()
     rank, world, dist = dist_setup(args.gpus)
     if args.impl == "reference":
