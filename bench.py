@@ -169,8 +169,9 @@ def batch_pulses(w, n: int, seed: int = 4):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per k_m2l_tc launch (TF32x3, p = 4, 7680 RWG, two
-# 128-row tiles per CTA, lag >= 2 products deferred): one gating period of six launches, 769.8 MB
-M2L_TRAFFIC_TF32X3 = 769.8e6 / 6
+# 128-row tiles per CTA, lag >= 2 products deferred): two leaf events of 289.5 MB and one level-2
+# event of 152.9 MB per gating period of six launches
+M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack"]
