@@ -20,7 +20,7 @@
 
 namespace tdbem {
 
-constexpr int kMaxWin = 32;   // max lags of one (observation point, source triangle) pair
+constexpr int kMaxWin = 64;   // max lags of one (observation point, source triangle) pair
 constexpr int kNq = 7;        // outer quadrature points per test triangle
 
 // Per-triangle geometry in device memory (structure of arrays).

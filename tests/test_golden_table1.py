@@ -10,8 +10,8 @@ stored in tests/golden/table1_test_problem.txt.
   1 / 2^lmax and c dt = 0.005, Mt^(lmax) = floor(ds / (c dt)) gives every
   entry of the table's last column, while the printed ceiling does not
   (12.5 -> 13 for cases 4 and 5).  The library takes the floor.
-* GPU: the library's octree over the meshes of cases 3 and 5 (N_leaf = 100,
-  dt = 0.005) has
+* GPU: the library's octree over those meshes (N_leaf = 100, dt = 0.005;
+  case 1's triangles span up to 17 c dt, a triangle pair up to 37 lags) has
   the table's lmax; its finest interval holds no more steps than the table's,
   since its boxes are enlarged by the triangles' extent (the paper ignores
   it), and at least floor((ds - 2 r_max) / (c dt)) with ds the finest cell of
@@ -76,11 +76,8 @@ def test_mt_column_is_the_floor_reading():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("ns", [5120, 20480])
+@pytest.mark.parametrize("ns", sorted(SUBDIV))
 def test_library_octree_matches_table(ns):
-    # Case 1 is left out: its triangles span up to 17 c dt, and a triangle
-    # pair's lag window (up to 37 lags there) exceeds the 32 lags the
-    # library's coefficient assembly handles per pair (it returns EINVAL)
     from paper_2303_05006_gb300 import Solver
 
     row = next(r for r in _table() if r["ns"] == ns)
