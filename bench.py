@@ -495,6 +495,24 @@ def run_ours(args, rank, world, dist):
         "m2l_tile_rows_per_level": list(info.m2l_tile_rows),
     }
     line.update(cmp)
+    if args.mode == "fast" and args.far_overlap and not args.no_compare:
+        # the same kernels in Program 1's serial order: each kernel's own
+        # rate, without the SMs and L2 it shares in the pipelined march
+        ss = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=mode, p_s=args.p, p_t=args.p,
+                    m2l_prec=PREC[args.prec], n_rhs=R, jacobi_sweeps=args.jacobi, precond=args.precond,
+                    solve_tol=args.solve_tol, m2l_tile_rows=args.m2l_tile_rows, far_overlap=0)
+        for r, pu in enumerate(pulses):
+            ss.set_incident_plane(pu, rhs=r)
+        ss.set_stream(stream.cuda_stream)
+        ss.march_dev(W)
+        ss.profile(True)
+        ss.march_dev(K)
+        l_s, ms_s = ss.profile_read()
+        ss.profile(False)
+        args_s = argparse.Namespace(**{**vars(args), "far_overlap": 0})
+        line["roofline_serial_order"] = roofline(args_s, ss.info(), l_s, ms_s, K, W)
+        line["kernel_ms_per_step_serial_order"] = {KERNELS[k]: ms_s[k] / K for k in range(len(ms_s)) if l_s[k]}
+        ss.close()
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         res = oracle_sample(w, 16, 16)
         line["cpu_baseline"] = {"value": res["steps_per_s"], "unit": "steps/s", "cores": res["cores"],
