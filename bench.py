@@ -248,7 +248,8 @@ def run_many(args, rank, world, dist):
     steps = [min(K, w.Nt - 1 - W) for w in ws]
     solvers = []
     for w in ws:
-        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+        s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+                   mode=1, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
                    precond=args.precond, solve_tol=args.solve_tol)
         for r, pu in enumerate([w.pulses[0]] + batch_pulses(w, R - 1)):
             s.set_incident_plane(pu, rhs=r)
@@ -323,7 +324,8 @@ def run_sweep(args, rank, world, dist):
         return out.cpu().numpy(), K / (e0.elapsed_time(e1) / 1000.0)
 
     t0 = time.perf_counter()
-    sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=0, precond=args.precond, solve_tol=args.solve_tol)
+    sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+                mode=0, precond=args.precond, solve_tol=args.solve_tol)
     setup_direct = time.perf_counter() - t0
     Jd, sps_d = march(sd)
     ne = sd.ne
@@ -371,7 +373,8 @@ def run_ours(args, rank, world, dist):
     R = args.rhs
     pulses = [w.pulses[0]] + batch_pulses(w, R - 1)
     t0 = time.perf_counter()
-    s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+               mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
                jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol,
                m2l_tile_rows=args.m2l_tile_rows, far_overlap=args.far_overlap)
     setup_s = time.perf_counter() - t0
@@ -435,7 +438,8 @@ def run_ours(args, rank, world, dist):
     # the plain GPU path on the same steps: speed and the fast path's error
     cmp = {}
     if args.mode == "fast" and not args.no_compare:
-        sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=0, precond=args.precond, solve_tol=args.solve_tol)
+        sd = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+                    mode=0, precond=args.precond, solve_tol=args.solve_tol)
         sd.set_incident_plane(w.pulses[0])
         sd.set_stream(stream.cuda_stream)
         outd = torch.empty((K, s.ne), dtype=torch.float64, device="cuda")
@@ -453,7 +457,8 @@ def run_ours(args, rank, world, dist):
         sd.close()
         if R > 1:
             # the same fast march one right-hand side at a time
-            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
+            s1 = Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+                        mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec],
                         jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol)
             s1.set_incident_plane(w.pulses[0])
             s1.set_stream(stream.cuda_stream)
