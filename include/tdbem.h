@@ -104,6 +104,9 @@ typedef struct {
   int32_t solve_grid;    /* single-RHS Z0 solve: 0 (default) one thread-block cluster below 49152 RWG functions
                             and a cooperative grid of every SM from there on; 1 always the cluster; 2 always
                             the grid */
+  double chi;            /* weight of the time-differentiated MFIE inside the coupling: the tested equation is
+                            dtEFIE + theta eta (chi dtMFIE + zeta MFIE).  1 (default): the paper's CFIE of
+                            eq. cfie (CFIE1); zeta = 0: CFIE2; chi = 0: CFIE3 (section 4.3) */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -114,7 +117,7 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0. */
+   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),

@@ -24,11 +24,13 @@
  *           (mu/4pi) f_i(x).f_j(y) Nddot(tau)/(dt^2 r)                (A-term)
  *         + (1/(4 pi eps)) div f_i div f_j N(tau)/r                    (phi-term)
  *         + theta eta (1/4pi) f_i(x).( n(x) x ( f_j(y) x grad_y g ) ) ] (P-term)
- *       with g(r) = (Ndot(tau)/dt + zeta N(tau)) / r,
+ *       with g(r) = (chi Ndot(tau)/dt + zeta N(tau)) / r, chi the weight of the
+ *       time-differentiated MFIE (1 in the paper's eq. cfie; 0 gives the
+ *       paper's CFIE3 of section 4.3),
  *     which is the paper's sum_k w^{k,d} Z^(m-k) (eq. layer_disc_tmp with
  *     U^d of eq. U), since sum_k w^k (tau-k)_+^d = N(tau).
  *   * The identity term of the MFIE (reading of the paper's eq. cfie, see the
- *     module notes): + s_J theta eta (1/2) G_ij (Ndot(m)/dt + zeta N(m)),
+ *     module notes): + s_J theta eta (1/2) G_ij (chi Ndot(m)/dt + zeta N(m)),
  *     G_ij = int f_i.f_j, which is non-zero only for m = 1, 2.
  *   * Incident right-hand side V_i^{alpha-1} (eq. v_i).
  *   * Time stepping (eqs. solve and R): Zt^(1) J^{alpha-1} =
@@ -171,7 +173,7 @@ typedef struct {
   double* elen;   /* ne */
   int32_t* te;    /* nt*3 edge of local edge k (v_k -> v_{k+1}) */
   int8_t* ts;     /* nt*3 +1 if the triangle is T+ of that edge, else -1 */
-  double dt, eps, mu, c, eta, a, theta, zeta, sJ;
+  double dt, eps, mu, c, eta, a, theta, zeta, sJ, chi;
   bspline bs;
   double qb[7][3], qw[7]; /* 7-point rule, barycentric */
 } orc_ctx;
@@ -209,7 +211,7 @@ void orc_destroy(orc_ctx* c) {
 /* Build the mesh tables.  Edges are numbered lexicographically by (min vertex,
    max vertex); T+ is the triangle whose winding traverses the edge min->max. */
 int orc_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double dt, double eps,
-               double mu, double theta, double zeta, double sJ, int d, orc_ctx** out) {
+               double mu, double theta, double zeta, double sJ, double chi, int d, orc_ctx** out) {
   *out = NULL;
   if (nv < 3 || nt < 2 || dt <= 0 || eps <= 0 || mu <= 0 || d < 2 || d > 5) return ORC_EINVAL;
   orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
@@ -224,7 +226,7 @@ int orc_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
   c->c = 1.0 / sqrt(eps * mu);
   c->eta = sqrt(mu / eps);
   c->a = c->c * dt;
-  c->theta = theta; c->zeta = zeta; c->sJ = sJ;
+  c->theta = theta; c->zeta = zeta; c->sJ = sJ; c->chi = chi;
   bs_init(&c->bs, d);
   /* 7-point degree-5 rule (Radon; Stroud T2:5-1), weights sum to 1 */
   {
@@ -330,7 +332,7 @@ typedef struct {
 /* radial antiderivatives (r dr = rho drho):
    scalar phi-term  F = N(tau)/r     -> Phi_phi(r) = -a C(tau)
    A-term           F = Nddot(tau)/r -> Phi_A(r)   = -a Ndot(tau)
-   P-term           g(r) = (Ndot(tau)/dt + zeta N(tau))/r, d/dr g = F_P r  */
+   P-term           g(r) = (chi Ndot(tau)/dt + zeta N(tau))/r, d/dr g = F_P r  */
 /* sphi/sA/sP receive the rounding scale of each value: the sum of the absolute
    truncated-power terms plus a tenth of the sensitivity to the rounding of
    tau = m - r/(c dt), whose operands are of size m + r/(c dt). */
@@ -348,8 +350,8 @@ static void radial_vals(const ig_ctx* g, double r, double* phi, double* A, doubl
     sA[i] = c->a * (s2 + 4.0 * stau);
     if (g->hasP) {
       double n0 = bs_eval2(&c->bs, tau, 0, &s3);
-      P[i] = (nd / c->dt + c->zeta * n0) / r;
-      sP[i] = (s2 / c->dt + c->zeta * s3 + (4.0 / c->dt + 4.0 * c->zeta) * stau) / r;
+      P[i] = (c->chi * nd / c->dt + c->zeta * n0) / r;
+      sP[i] = (c->chi * s2 / c->dt + c->zeta * s3 + (4.0 * c->chi / c->dt + 4.0 * c->zeta) * stau) / r;
     }
   }
 }
@@ -461,7 +463,7 @@ static void integrate_split(vfun f, ig_ctx* g, int nc, double lo, double hi, dou
      phi[m]    = int_T N(tau)/r dS
      A0[m]     = int_T Nddot(tau)/r dS
      A1[m][3]  = int_T Nddot(tau)/r (y - x) dS
-     P1[m][3]  = int_T (g'(r)/r) (y - x) dS,  g = (Ndot(tau)/dt + zeta N(tau))/r
+     P1[m][3]  = int_T (g'(r)/r) (y - x) dS,  g = (chi Ndot(tau)/dt + zeta N(tau))/r
    P1 is set to zero when x lies in the plane of t (then the tested P-term
    vanishes identically, see the notes on coplanar pairs). */
 int orc_inner(const orc_ctx* c, const double* x, int64_t t, int m0, int nm, double* phi, double* A0, double* A1,
@@ -706,7 +708,7 @@ int orc_assemble(const orc_ctx* c, const int64_t* rows, int64_t nrows, int W, in
             for (int u = 0; u < 3; ++u) fj[u] = fj_c * (x[u] - oj[u]);
             double G = wq * dot3(fi, fj);
             for (int m = 1; m <= c->bs.d + 1; ++m) {
-              double coef = bs_eval(&c->bs, (double)m, 1) / c->dt + c->zeta * bs_eval(&c->bs, (double)m, 0);
+              double coef = c->chi * bs_eval(&c->bs, (double)m, 1) / c->dt + c->zeta * bs_eval(&c->bs, (double)m, 0);
               if (coef == 0.0) continue;
               int w = m - mlo_row[j];
               if (w < 0 || w >= W) {
@@ -794,7 +796,7 @@ void orc_rhs(const orc_ctx* c, const double* pulse, int64_t alpha, const int64_t
         double Ed[3], Hm[3], nH[3];
         for (int u = 0; u < 3; ++u) {
           Ed[u] = pol[u] * gd;
-          Hm[u] = kxp[u] * (gd + c->zeta * g) / c->eta; /* Hdot + zeta H */
+          Hm[u] = kxp[u] * (c->chi * gd + c->zeta * g) / c->eta; /* chi Hdot + zeta H */
         }
         cross3(nin, Hm, nH);
         double val = 0;

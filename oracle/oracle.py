@@ -43,7 +43,7 @@ def lib():
         L = ctypes.CDLL(_SO)
         L.orc_create.argtypes = [c_double_p, ctypes.c_int64, c_int32_p, ctypes.c_int64, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                 ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.orc_create.restype = ctypes.c_int
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_num_edges.argtypes = [ctypes.c_void_p]
@@ -97,15 +97,15 @@ def gauss_legendre():
 class Oracle:
     """Conventional FP64 MOT TDBEM on one closed triangle mesh."""
 
-    def __init__(self, verts, tris, dt, theta=1.0, zeta=1.0, eps=1.0, mu=1.0, sJ=1.0, d=2):
+    def __init__(self, verts, tris, dt, theta=1.0, zeta=1.0, eps=1.0, mu=1.0, sJ=1.0, d=2, chi=1.0):
         L = lib()
         self.verts = np.ascontiguousarray(verts, dtype=np.float64)
         self.tris = np.ascontiguousarray(tris, dtype=np.int32)
         self.dt = float(dt)
-        self.params = dict(theta=theta, zeta=zeta, eps=eps, mu=mu, sJ=sJ, d=d)
+        self.params = dict(theta=theta, zeta=zeta, eps=eps, mu=mu, sJ=sJ, d=d, chi=chi)
         h = ctypes.c_void_p()
         rc = L.orc_create(_p(self.verts, c_double_p), len(self.verts), _p(self.tris, c_int32_p), len(self.tris),
-                          self.dt, eps, mu, theta, zeta, sJ, d, ctypes.byref(h))
+                          self.dt, eps, mu, theta, zeta, sJ, chi, d, ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle: invalid mesh or parameters (code {rc})")
         self._h = h

@@ -30,7 +30,7 @@ class Params(ctypes.Structure):
                 ("m2l_prec", ctypes.c_int32), ("solve_tol", ctypes.c_double), ("solve_maxit", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
                 ("m2l_tile_rows", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32)]
+                ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

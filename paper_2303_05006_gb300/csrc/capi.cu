@@ -59,6 +59,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->precond = 1;
   p->far_overlap = 1;
   p->solve_grid = 0;
+  p->chi = 1.0;
 }
 
 static void fill_phys(tdbem_ctx* c) {
@@ -71,6 +72,7 @@ static void fill_phys(tdbem_ctx* c) {
   ph.a = ph.c * c->dt;
   ph.theta = c->p.theta;
   ph.zeta = c->p.zeta;
+  ph.chi = c->p.chi;
   ph.s_jump = c->p.s_jump;
   // 7-point degree-5 rule on the triangle (Radon): centroid and two orbits of 3
   const double r15 = std::sqrt(15.0);
@@ -125,7 +127,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
     tdbem_default_params(&p);
   if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
-      !(p.mu > 0) || !(p.theta >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
+      !(p.mu > 0) || !(p.theta >= 0) || !(p.chi >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
       p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||

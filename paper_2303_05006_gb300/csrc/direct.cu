@@ -8,7 +8,7 @@
 //     sum_q w_q A_i^rho [ mu/(4 pi dt^2) f_i(x_q) . int f_j Nddot(tau)/r dS
 //                       + 1/(4 pi eps) div f_i div f_j int N(tau)/r dS
 //                       + theta eta/(4 pi) f_i(x_q) . (n x int f_j x grad_y g dS) ]
-// plus the MFIE identity term s_jump theta eta/2 (f_i, f_j) (Ndot(m)/dt + zeta N(m)).
+// plus the MFIE identity term s_jump theta eta/2 (f_i, f_j) (chi Ndot(m)/dt + zeta N(m)).
 // The outer integral uses the 7-point degree-5 rule; the inner integral is
 // exact (integrals.cuh).  One thread owns one (test triangle, source triangle)
 // pair, accumulates its 3x3 local edge pairs over the 7 points and adds them to
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) k_assemble(TriGeom g, Phys ph, int64_t nt
       atomicExch(err, 3);
       return;
     }
-    if (!inner_integrals(x, vs, ns, g.lmax[s], a, ph.dt, ph.zeta, m0, nm, io)) {
+    if (!inner_integrals(x, vs, ns, g.lmax[s], a, ph.chi / ph.dt, ph.zeta, m0, nm, io)) {
       atomicExch(err, 4);
       return;
     }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(128) k_assemble(TriGeom g, Phys ph, int64_t nt
     }
     // MFIE identity term on the test triangle itself (lags 1 and 2)
     if (s == t && ph.s_jump != 0.0) {
-      const double c1 = 1.0 / ph.dt + 0.5 * ph.zeta, c2 = -1.0 / ph.dt + 0.5 * ph.zeta;
+      const double c1 = ph.chi / ph.dt + 0.5 * ph.zeta, c2 = -ph.chi / ph.dt + 0.5 * ph.zeta;
       for (int kt = 0; kt < 3; ++kt)
         for (int ks = 0; ks < 3; ++ks) {
           double fj[3];
@@ -338,9 +338,9 @@ __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, c
       sincos(2 * PI * f0 * vv, &sw, &cw);
       double gg = cw * e;
       double gd = (-2 * PI * f0 * sw - vv / (sg * sg) * cw) * e;
-      // -Edot + theta eta n x (Hdot + zeta H), E = pol g, H = k x pol g / eta
+      // -Edot + theta eta n x (chi Hdot + zeta H), E = pol g, H = k x pol g / eta
       double Hm[3], nH[3];
-      for (int u = 0; u < 3; ++u) Hm[u] = kxp[u] * (gd + ph.zeta * gg) / ph.eta;
+      for (int u = 0; u < 3; ++u) Hm[u] = kxp[u] * (ph.chi * gd + ph.zeta * gg) / ph.eta;
       nH[0] = nin[1] * Hm[2] - nin[2] * Hm[1];
       nH[1] = nin[2] * Hm[0] - nin[0] * Hm[2];
       nH[2] = nin[0] * Hm[1] - nin[1] * Hm[0];

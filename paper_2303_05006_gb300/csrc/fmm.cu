@@ -106,7 +106,7 @@ struct FmmLevel {
   double flops_event = 0;         // M2L flops of one gating event
   // time tables: source/target factors for offsets i = 0..M-1
   float* d_tsrc = nullptr;        // [M][pt]  l_n(s_i)
-  float* d_ttgt = nullptr;        // [M][3][pt]  l_m, l_m'/h_t, l_m'/h_t + zeta l_m
+  float* d_ttgt = nullptr;        // [M][3][pt]  l_m, l_m'/h_t, chi l_m'/h_t + zeta l_m
 };
 
 struct FmmPlan {
@@ -628,7 +628,7 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
   for (int e = threadIdx.x; e < M * kNC * PS; e += blockDim.x) {
     int i = e / (kNC * PS), r = e % (kNC * PS);
     int c = r / PS, a = r % PS;
-    int kind = (c < 3) ? 1 : (c == 3 ? 0 : 2);  // A: l', phi: l, mag: l' + zeta l
+    int kind = (c < 3) ? 1 : (c == 3 ? 0 : 2);  // A: l', phi: l, mag: chi l' + zeta l
     float s = 0.f;
     for (int m = 0; m < pt; ++m) s += L[(int64_t)c * P + a * pt + m] * ttgt[(i * 3 + kind) * pt + m];
     Le[e] = s;
@@ -1125,7 +1125,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         ts[i * pt + n] = (float)lv[n];
         tt[(i * 3 + 0) * pt + n] = (float)lv[n];
         tt[(i * 3 + 1) * pt + n] = (float)(dv[n] / ht);
-        tt[(i * 3 + 2) * pt + n] = (float)(dv[n] / ht + c->p.zeta * lv[n]);
+        tt[(i * 3 + 2) * pt + n] = (float)(c->p.chi * dv[n] / ht + c->p.zeta * lv[n]);
       }
     }
     if ((s = c->dalloc(&L.d_tsrc, ts.size())) || (s = c->dalloc(&L.d_ttgt, tt.size()))) return s;

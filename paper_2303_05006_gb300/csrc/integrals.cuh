@@ -5,7 +5,8 @@
 // and the quadratic B-spline N (section 2.2), the library needs for each lag m
 //     phi  = int_T N(tau)/r dS,     A0 = int_T Nddot(tau)/r dS,
 //     A1   = int_T Nddot(tau)/r (y - x) dS,
-//     P1   = int_T g'(r)/r (y - x) dS,   g(r) = (Ndot(tau)/dt + zeta N(tau)) / r.
+//     P1   = int_T g'(r)/r (y - x) dS,   g(r) = (cdot Ndot(tau) + zeta N(tau)) / r,
+// cdot = chi / dt (chi: weight of the time-differentiated MFIE).
 // In polar coordinates about the projection p of x on the plane of T (height h,
 // r dr = rho drho) the radial integral of F is an antiderivative Q(r) with
 // Q' = F r; the in-plane part of the vector integrals is, by the divergence
@@ -126,7 +127,7 @@ __device__ __forceinline__ void lag_window(double rlo, double rhi, double a, int
 // (row-major), nT: unit normal of the winding, lmax: longest side.
 // Returns false if the number of light-cone pieces exceeds the local buffers.
 __device__ bool inner_integrals(const double* x, const double* v, const double* nT, double lmax, double a,
-                                double dt, double zeta, int m0, int nm, InnerOut& o) {
+                                double cdot, double zeta, int m0, int nm, InnerOut& o) {
   double h = (x[0] - v[0]) * nT[0] + (x[1] - v[1]) * nT[1] + (x[2] - v[2]) * nT[2];
   bool hasP = fabs(h) > 1e-10 * lmax;
   if (!hasP) h = 0.0;
@@ -145,7 +146,7 @@ __device__ bool inner_integrals(const double* x, const double* v, const double* 
     bspline_eval((m0 + i) - hh / a, &N, &Nd, &C);
     Qh_phi[i] = -a * C;
     Qh_A[i] = -a * Nd;
-    Qh_g[i] = hasP ? (Nd / dt + zeta * N) / hh : 0.0;
+    Qh_g[i] = hasP ? (Nd * cdot + zeta * N) / hh : 0.0;
   }
   // distance range of x to T, for the knot range
   double rmax = 0.0, cen[3];
@@ -237,9 +238,9 @@ __device__ bool inner_integrals(const double* x, const double* v, const double* 
           double Np[3], Ndp[3], Cp[4];
           bspline_piece_coeffs(kap, Np, Ndp, Cp);
           double u0 = (double)(m - kap), beta = -1.0 / a;
-          // Q_phi = -a C,  Q_A = -a Ndot,  G = Ndot/dt + zeta N  (g = G/r)
+          // Q_phi = -a C,  Q_A = -a Ndot,  G = cdot Ndot + zeta N  (g = G/r)
           double qC[4], qNd[2], qG[3], Gu[3];
-          for (int n = 0; n < 3; ++n) Gu[n] = Ndp[n] / dt + zeta * Np[n];
+          for (int n = 0; n < 3; ++n) Gu[n] = Ndp[n] * cdot + zeta * Np[n];
           poly_u_to_r<3>(Cp, u0, beta, qC);
           poly_u_to_r<1>(Ndp, u0, beta, qNd);
           poly_u_to_r<2>(Gu, u0, beta, qG);

@@ -42,6 +42,7 @@ struct Phys {
   double dt, a;                // time step, c*dt
   double c, eta, eps, mu;
   double theta, zeta, s_jump;
+  double chi;                  // weight of the time-differentiated MFIE (1: the paper's CFIE)
   double qb[kNq][3], qw[kNq];  // outer rule (barycentric points, weights summing to 1)
 };
 

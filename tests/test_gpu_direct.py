@@ -145,3 +145,21 @@ def test_grid_wide_solve_matches_oracle_and_cluster(sphere320_oracle, sphere320_
     assert rel(Jg, Jref) < 1e-10, rel(Jg, Jref)
     assert rel(Jg, Jc) < 1e-11
     assert sg.info().solver_cluster > 16 >= sc.info().solver_cluster
+
+
+@pytest.mark.parametrize("kw", [dict(chi=0.0), dict(zeta=0.0), dict(chi=0.5, zeta=2.0, theta=1.5)])
+def test_cfie_variants_match_oracle(kw):
+    """The paper's CFIE variants (section 4.3: CFIE3 drops the time-differentiated
+    MFIE, chi = 0; CFIE2 drops the MFIE, zeta = 0) and a general coupling: the
+    direct FP64 march equals the oracle's with the same weights to 1e-10."""
+    from oracle.oracle import Oracle
+    from workloads import workload
+
+    w = workload("sphere80")
+    n = 40
+    o = Oracle(w.verts, w.tris, w.dt, **kw)
+    Jref = o.march(w.pulses[0], n + 1)
+    s = _solver(w, **kw)
+    J = s.march(n)
+    rel = float(np.linalg.norm(J - Jref) / np.linalg.norm(Jref))
+    assert rel < 1e-10, (kw, rel)
