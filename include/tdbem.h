@@ -143,11 +143,16 @@ tdbem_status tdbem_edges(const tdbem_ctx* ctx, int32_t* edge_vert, int32_t* edge
    reads the profile makes this stream wait for them. */
 tdbem_status tdbem_set_stream(tdbem_ctx* ctx, void* stream);
 
-/* Incident modulated-Gaussian plane wave for right-hand side `rhs`
-   (0 <= rhs < n_rhs; a right-hand side never set has zero incident field):
+/* Incident plane wave for right-hand side `rhs` (0 <= rhs < n_rhs; a
+   right-hand side never set has zero incident field):
    pulse = {k[3], pol[3], f0, sigma, t0, z_min}; E = pol g(u), H = k x E / eta,
-   u = t - (k.x - z_min)/c, g(u) = cos(2 pi f0 (u - t0)) exp(-(u-t0)^2/(2 sigma^2)).
-   V^{alpha-1} (eq. v_i) is then evaluated on the device at every step. */
+   u = t - (k.x - z_min)/c, and
+     sigma > 0: the modulated Gaussian g(u) = cos(2 pi f0 (u - t0)) exp(-(u-t0)^2/(2 sigma^2));
+     sigma < 0: the Sin^2 pulse of the paper's test problem (section 4.1) with
+                length Lambda = f0 > 0 and amplitude A = -sigma:
+                g(u) = A sin^2(2 pi c (u - t0) / Lambda) while 0 <= 2 pi c (u - t0) / Lambda <= 2 pi, else 0.
+   V^{alpha-1} (eq. v_i) is then evaluated on the device at every step.
+   EINVAL for sigma = 0 or a Sin^2 length <= 0. */
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* ctx, int32_t rhs, const double* pulse);
 
 /* Use caller-supplied right-hand sides instead: V[(alpha-1)*ne + i] for

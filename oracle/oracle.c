@@ -757,13 +757,27 @@ void orc_history(const orc_ctx* c, const int32_t* m_lo, const double* Zw, int W,
    pulse = {k[3], pol[3], f0, sigma, t0, z_min}:
      E(x,t) = pol g(u), H = k x E / eta, u = t - (k.x - z_min)/c,
      g(u) = cos(2 pi f0 (u - t0)) exp(-(u - t0)^2/(2 sigma^2)).           */
-static void pulse_g(const double* P, double u, double* g, double* gd) {
+/* Pulse shape g and its time derivative at u.  sigma > 0: modulated Gaussian
+   cos(2 pi f0 (u - t0)) exp(-(u - t0)^2 / (2 sigma^2)); sigma < 0: the Sin^2
+   pulse of the paper's test problem (section 4.1), A sin^2(2 pi c (u - t0) /
+   Lambda) on one period 0 .. 2 pi of its argument, Lambda = f0, A = -sigma. */
+static void pulse_g(const double* P, double u, double c, double* g, double* gd) {
   double f0 = P[6], sg = P[7], t0 = P[8];
   double v = u - t0;
-  double e = exp(-v * v / (2 * sg * sg));
-  double cw = cos(2 * PI * f0 * v), sw = sin(2 * PI * f0 * v);
-  *g = cw * e;
-  *gd = (-2 * PI * f0 * sw - v / (sg * sg) * cw) * e;
+  if (sg > 0) {
+    double e = exp(-v * v / (2 * sg * sg));
+    double cw = cos(2 * PI * f0 * v), sw = sin(2 * PI * f0 * v);
+    *g = cw * e;
+    *gd = (-2 * PI * f0 * sw - v / (sg * sg) * cw) * e;
+    return;
+  }
+  double w = 2 * PI * c / f0, x = w * v;
+  *g = 0.0;
+  *gd = 0.0;
+  if (x >= 0.0 && x <= 2 * PI) {
+    *g = -sg * sin(x) * sin(x);
+    *gd = -sg * 2.0 * sin(x) * cos(x) * w;
+  }
 }
 
 void orc_rhs(const orc_ctx* c, const double* pulse, int64_t alpha, const int64_t* rows, int64_t nrows, double* V) {
@@ -792,7 +806,7 @@ void orc_rhs(const orc_ctx* c, const double* pulse, int64_t alpha, const int64_t
         for (int u = 0; u < 3; ++u) fi[u] = fi_c * (x[u] - oi[u]);
         double uu = t - (dot3(k, x) - pulse[9]) / c->c;
         double g, gd;
-        pulse_g(pulse, uu, &g, &gd);
+        pulse_g(pulse, uu, c->c, &g, &gd);
         double Ed[3], Hm[3], nH[3];
         for (int u = 0; u < 3; ++u) {
           Ed[u] = pol[u] * gd;

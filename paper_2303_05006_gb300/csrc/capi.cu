@@ -196,7 +196,7 @@ tdbem_status tdbem_set_stream(tdbem_ctx* c, void* stream) {
 
 tdbem_status tdbem_set_incident_plane(tdbem_ctx* c, int32_t rhs, const double* pulse) {
   if (!c || !pulse || rhs < 0 || rhs >= c->R) return TDBEM_EINVAL;
-  if (!(pulse[7] > 0)) return TDBEM_EINVAL;
+  if (!(pulse[7] > 0) && !(pulse[7] < 0 && pulse[6] > 0)) return TDBEM_EINVAL;
   double* hp = c->pulse.data() + 10 * (size_t)rhs;
   std::memcpy(hp, pulse, 10 * sizeof(double));
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_pulse + 10 * rhs, hp, 10 * sizeof(double), cudaMemcpyHostToDevice, c->stream));

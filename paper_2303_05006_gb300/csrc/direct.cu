@@ -302,8 +302,9 @@ __global__ void k_csr_windows(TriGeom g, const int32_t* et, const int64_t* row_p
 }
 
 // ---------------------------------------------------------------------------
-// Incident right-hand side V_i^{alpha-1} (eq. v_i) for a modulated Gaussian
-// plane wave; one thread per edge, 2 triangles x 7 points, FP64.
+// Incident right-hand side V_i^{alpha-1} (eq. v_i) for a plane wave (a
+// modulated Gaussian, or the Sin^2 pulse of section 4.1 when sigma < 0); one
+// thread per edge, 2 triangles x 7 points, FP64.
 // grid: (edge blocks, steps); right-hand side r of R:
 // V[((alpha-alpha0)*ne + i)*R + r] for alpha = alpha0 .. alpha0+gridDim.y-1
 __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, const double* pulse, int32_t alpha0,
@@ -333,11 +334,23 @@ __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, c
       for (int u = 0; u < 3; ++u) x[u] = ph.qb[q][0] * v[u] + ph.qb[q][1] * v[3 + u] + ph.qb[q][2] * v[6 + u];
       double u_ = t - (kv[0] * x[0] + kv[1] * x[1] + kv[2] * x[2] - zmin) / ph.c;
       double vv = u_ - t0;
-      double e = exp(-vv * vv / (2 * sg * sg));
-      double sw, cw;
-      sincos(2 * PI * f0 * vv, &sw, &cw);
-      double gg = cw * e;
-      double gd = (-2 * PI * f0 * sw - vv / (sg * sg) * cw) * e;
+      double gg, gd;
+      if (sg > 0) {
+        double e = exp(-vv * vv / (2 * sg * sg));
+        double sw, cw;
+        sincos(2 * PI * f0 * vv, &sw, &cw);
+        gg = cw * e;
+        gd = (-2 * PI * f0 * sw - vv / (sg * sg) * cw) * e;
+      } else {  // Sin^2 pulse: length f0, amplitude -sg
+        const double w = 2 * PI * ph.c / f0, ph_ = w * vv;
+        gg = gd = 0.0;
+        if (ph_ >= 0.0 && ph_ <= 2 * PI) {
+          double sw, cw;
+          sincos(ph_, &sw, &cw);
+          gg = -sg * sw * sw;
+          gd = -sg * 2.0 * sw * cw * w;
+        }
+      }
       // -Edot + theta eta n x (chi Hdot + zeta H), E = pol g, H = k x pol g / eta
       double Hm[3], nH[3];
       for (int u = 0; u < 3; ++u) Hm[u] = kxp[u] * (ph.chi * gd + ph.zeta * gg) / ph.eta;

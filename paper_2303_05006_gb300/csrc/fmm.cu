@@ -618,15 +618,18 @@ __global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* S
 // the local-coefficient slot is cleared afterwards.
 __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
                       const TriGeom g, const float* T, const float* ttgt, int p, int pt, int M, int k, float* loc,
-                      int Q, double* Rfar, int Lr, int64_t ne, int R) {
+                      int Q, double* Rfar, int Lr, int64_t ne, int R, int s0, int ns, int clear) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt;
   const int rhs = blockIdx.y;
   int cell = leaf_cells[blockIdx.x];
   float* L = loc + (((int64_t)cell * Q + ((k + 1) % Q)) * R + rhs) * kNC * P;
-  float* Le = sm;  // [M][kNC][PS]
-  for (int e = threadIdx.x; e < M * kNC * PS; e += blockDim.x) {
-    int i = e / (kNC * PS), r = e % (kNC * PS);
+  // steps s0 .. s0 + ns - 1 of the interval (several launches when the
+  // interval's evaluated coefficients exceed shared memory); the last clears
+  // the consumed local coefficients
+  float* Le = sm;  // [ns][kNC][PS]
+  for (int e = threadIdx.x; e < ns * kNC * PS; e += blockDim.x) {
+    int i = s0 + e / (kNC * PS), r = e % (kNC * PS);
     int c = r / PS, a = r % PS;
     int kind = (c < 3) ? 1 : (c == 3 ? 0 : 2);  // A: l', phi: l, mag: chi l' + zeta l
     float s = 0.f;
@@ -646,7 +649,7 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
     const int t = perm[tb + q / 3], kk = q % 3;
     const float* Tt = T + ((int64_t)t * 3 + kk) * nr;
     const int64_t edge = g.edge[3 * t + kk];
-    for (int i0 = 0; i0 < M; i0 += kSt) {
+    for (int i0 = 0; i0 < ns; i0 += kSt) {
       float acc[kSt];
 #pragma unroll
       for (int u = 0; u < kSt; ++u) acc[u] = 0.f;
@@ -654,21 +657,22 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
         const float tv = __ldg(Tt + r);
 #pragma unroll
         for (int u = 0; u < kSt; ++u)
-          if (i0 + u < M) acc[u] += tv * Le[(int64_t)(i0 + u) * nr + r];
+          if (i0 + u < ns) acc[u] += tv * Le[(int64_t)(i0 + u) * nr + r];
       }
 #pragma unroll
       for (int u = 0; u < kSt; ++u)
         for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-      if (lane < kSt && i0 + lane < M) {
+      if (lane < kSt && i0 + lane < ns) {
         float sv = acc[0];
 #pragma unroll
         for (int u = 1; u < kSt; ++u)
           if (lane == u) sv = acc[u];
-        const int rho = (k + 1) * M + i0 + lane;
+        const int rho = (k + 1) * M + s0 + i0 + lane;
         atomicAdd(Rfar + ((int64_t)(rho & (Lr - 1)) * ne + edge) * R + rhs, -(double)sv);
       }
     }
   }
+  if (!clear) return;
   __syncthreads();
   for (int e = threadIdx.x; e < kNC * P; e += blockDim.x) L[e] = 0.f;
 }
@@ -1541,11 +1545,18 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }
     if (L.nleaf) {
-      size_t smem = (size_t)L.M * kNC * PS * sizeof(float);
+      // steps per launch: as many of the interval's evaluated coefficients as
+      // fit the 200 KB of shared memory the kernel is set up for
+      const int per = std::max(1, (int)((200 * 1024) / (kNC * PS * sizeof(float))));
       cudaEvent_t e = c->prof_begin(7);
-      k_l2p<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
-                                                         F->d_T, L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr,
-                                                         c->ne, R);
+      for (int s0 = 0; s0 < L.M; s0 += per) {
+        const int ns = std::min(per, L.M - s0);
+        const size_t smem = (size_t)ns * kNC * PS * sizeof(float);
+        k_l2p<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
+                                                           F->d_T, L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr,
+                                                           c->ne, R, s0, ns, s0 + ns >= L.M ? 1 : 0);
+        TDBEM_CUDA_TRY(c, cudaGetLastError());
+      }
       c->prof_end(7, e);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
     }

@@ -155,3 +155,36 @@ class PECSphere:
         Hs = self.fields(p_o, "Hs")
         h_curl = np.abs(curl / (1j * k) - Hs).max() / np.abs(Hs).max()
         return {"incident_E": e_inc, "incident_H": h_inc, "boundary_E": e_bc, "curl_H": h_curl}
+
+
+def transient_current(a: float, points, times, g, delay: float, along_minus_z: bool, dt: float,
+                      f_cut: float, npad: int = 2):
+    """Physical surface current n_out x H of the PEC sphere at `points` (N x 3)
+    and `times` (multiples of dt) for an x-polarised plane wave along +z or -z
+    whose field at the origin is g(t - delay).  The transfer function is the
+    Mie series (exp(-i omega t) convention, conjugated for the exp(+i omega t)
+    transform of the real signal), applied to the pulse's discrete Fourier
+    transform on a grid of step dt, zero-padded to npad times the span, with
+    frequencies above f_cut dropped.  Incidence along -z is the +z series
+    rotated by 180 degrees about the x axis.  Returns [len(times)][N][3]."""
+    times = np.asarray(times, dtype=np.float64)
+    n_t = int(np.ceil(times.max() / dt)) + 1
+    N = 1 << int(np.ceil(np.log2(npad * n_t)))
+    t = np.arange(N) * dt
+    G = np.fft.rfft(g(t - delay))
+    f = np.fft.rfftfreq(N, dt)
+    P = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    if along_minus_z:
+        P = P * np.array([1.0, -1.0, -1.0])
+    out = np.zeros((len(f), len(P), 3), complex)
+    for kk in range(len(f)):
+        if f[kk] > f_cut:
+            break
+        om = max(2 * np.pi * f[kk], 1e-4)  # the static limit is finite
+        out[kk] = np.conj(PECSphere(a, om).surface_current(P)) * G[kk]
+    J = np.fft.irfft(out, n=N, axis=0)
+    idx = np.rint(times / dt).astype(int)
+    J = J[idx]
+    if along_minus_z:
+        J = J * np.array([1.0, -1.0, -1.0])
+    return J

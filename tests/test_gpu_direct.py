@@ -163,3 +163,30 @@ def test_cfie_variants_match_oracle(kw):
     J = s.march(n)
     rel = float(np.linalg.norm(J - Jref) / np.linalg.norm(Jref))
     assert rel < 1e-10, (kw, rel)
+
+
+def test_sin2_pulse_matches_oracle():
+    """The Sin^2 pulse of the paper's test problem (section 4.1), evaluated by
+    both sides from the same pulse record: the direct FP64 march equals the
+    oracle's to 1e-10, and the currents stay exactly zero before the pulse
+    reaches the mesh."""
+    from oracle.oracle import Oracle
+    from workloads import workload
+    from workloads.configs import sin2_pulse
+
+    w = workload("sphere80")
+    pu = sin2_pulse(w.verts, length=1.5, amplitude=0.5)
+    n = 40
+    o = Oracle(w.verts, w.tris, w.dt)
+    Jref = o.march(pu, n + 1)
+    s = _solver(w)
+    s.set_incident_plane(pu)
+    J = s.march(n)
+    assert np.abs(Jref).max() > 0
+    assert np.linalg.norm(J - Jref) <= 1e-10 * np.linalg.norm(Jref)
+    import dataclasses
+
+    delayed = dataclasses.replace(pu, t0=50 * w.dt)  # arrives after step 50
+    s2 = _solver(w)
+    s2.set_incident_plane(delayed)
+    assert np.abs(s2.march(n)).max() == 0.0

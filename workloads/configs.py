@@ -54,6 +54,19 @@ def pulse_star(verts: np.ndarray, k=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), f_scal
                  float(f0), float(sigma), float(6.0 * sigma), z_min)
 
 
+def sin2_pulse(verts: np.ndarray, k=(0.0, 0.0, -1.0), pol=(1.0, 0.0, 0.0), length: float = 0.5,
+               amplitude: float = 0.5) -> Pulse:
+    """The Sin^2 pulse of the paper's test problem (section 4.1): E = pol A
+    Sin^2(2 pi (c t - (k.x - z_min)) / Lambda), one period of sin^2 long; stored
+    in the pulse record as f0 = Lambda and sigma = -A (a negative sigma selects
+    this shape).  Defaults: along -x3, x-polarised, Lambda = A = 0.5."""
+    kk = np.asarray(k, dtype=np.float64)
+    kk = kk / np.linalg.norm(kk)
+    z_min = float(np.min(verts @ kk))
+    return Pulse(tuple(float(x) for x in kk), tuple(float(x) for x in np.asarray(pol, dtype=np.float64)),
+                 float(length), -float(amplitude), 0.0, z_min)
+
+
 def random_plane_waves(n: int, seed: int):
     """``n`` seeded (direction, polarisation) pairs: directions uniform on the
     sphere (normalised Gaussian 3-vectors), polarisation at a uniform angle in the
