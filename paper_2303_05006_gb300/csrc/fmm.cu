@@ -1029,12 +1029,18 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           }
       }
       hrow[ne] = (int64_t)hval.size();
-      if ((s = c->dalloc(&F->d_hrow, ne + 1)) || (s = c->dalloc(&F->d_hval, hval.size())) ||
-          (s = c->dalloc(&F->d_hmeta, hmeta.size())))
-        return s;
-      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow, hrow.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval, hval.data(), hval.size() * sizeof(float), cudaMemcpyHostToDevice));
-      TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta, hmeta.data(), hmeta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+      // one right-hand side with far_overlap keeps only the lag-split copy
+      // below (the history evaluation sums its two parts in turn); otherwise
+      // the flat entries go to the device as they are
+      if (!(c->R == 1 && c->p.far_overlap)) {
+        if ((s = c->dalloc(&F->d_hrow, ne + 1)) || (s = c->dalloc(&F->d_hval, hval.size())) ||
+            (s = c->dalloc(&F->d_hmeta, hmeta.size())))
+          return s;
+        TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hrow, hrow.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval, hval.data(), hval.size() * sizeof(float), cudaMemcpyHostToDevice));
+        TDBEM_CUDA_TRY(c,
+                       cudaMemcpy(F->d_hmeta, hmeta.data(), hmeta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+      }
       if (c->R == 1 && c->p.far_overlap) {
         // lag 2 / lags >= 3 (see FmmPlan), each row's entries in the same order
         std::vector<int64_t> r2(ne + 1, 0), r3(ne + 1, 0);
@@ -1590,7 +1596,15 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
     return TDBEM_OK;
   }
   cudaEvent_t e = c->prof_begin(1);
-  if (c->R == 1) {
+  if (c->R == 1 && F->d_hrow3) {
+    // history evaluation with only the lag-split entries: R = -(lags >= 3),
+    // then V + lag 2 + far field added in place (V is an incident row here)
+    const unsigned grid = (unsigned)((c->ne + 7) / 8);
+    k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring, c->L, alpha,
+                                                     nullptr, nullptr, nullptr, c->d_R);
+    k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow2, F->d_hval2, F->d_hmeta2, c->ne, ring, c->L, alpha,
+                                                     V, c->d_R, slot, c->d_R);
+  } else if (c->R == 1) {
     k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, c->stream>>>(F->d_hrow, F->d_hval, F->d_hmeta, c->ne,
                                                                              ring, c->L, alpha, V, nullptr, slot,
                                                                              c->d_R);
