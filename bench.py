@@ -174,7 +174,8 @@ def batch_pulses(w, n: int, seed: int = 4):
 M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
-KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack"]
+KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack",
+           "history_split"]
 
 
 def roofline(args, info, launches, ms, K, W):

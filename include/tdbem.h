@@ -20,7 +20,12 @@
  * B-spline of eq. J), Z0 = Zt^(1) and V is the tested incident field (eq. v_i).
  * Two modes evaluate the history sum R:
  *   TDBEM_DIRECT : every edge pair, FP64 (the conventional method, section
- *                  3.6.3);
+ *                  3.6.3).  Coefficients are assembled and Z0 solved in FP64;
+ *                  with one right-hand side the history products run in
+ *                  double-float arithmetic (each operand a pair of FP32
+ *                  numbers, 46 significant bits per term, compensated sums),
+ *                  which needs coefficients and currents inside FP32's normal
+ *                  range (about 1e-38 .. 3e38);
  *   TDBEM_FAST   : near pairs directly and far pairs by the space-time
  *                  interpolation-based FMM (section 3: P2M, M2M, M2L, L2L, L2P
  *                  over an octree with per-level time intervals).
@@ -273,8 +278,9 @@ tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
    device time in milliseconds since the last enable.  Classes (index):
    0 incident RHS, 1 history/near field, 2 Z0 solve, 3 P2M, 4 M2M, 5 M2L,
    6 L2L, 7 L2P, 8 M2L moment packing (the symmetry-permuted copy of the
-   moments that the tensor-core M2L reads).  n_classes receives the number of
-   classes (<= 16). */
+   moments that the tensor-core M2L reads), 9 history split (direct mode, one
+   right-hand side: the current history converted to FP32 hi/lo pairs before
+   the history sum).  n_classes receives the number of classes (<= 16). */
 tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
 tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
 

@@ -165,6 +165,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
     }
   }
   if (!s) s = finish_create(c);
+  if (!s && p.mode == TDBEM_DIRECT) s = tdbem_direct_split(c);
   if (s) {
     tdbem_destroy(c);
     return s;
@@ -277,10 +278,7 @@ static tdbem_status eval_R(tdbem_ctx* c, int32_t alpha, const double* d_ring, bo
                            bool eval = false) {
   const double* V = skip_rhs ? c->d_R : tdbem_incident_row(c, alpha);
   if (c->p.mode == TDBEM_FAST) return tdbem_fast_history(c, alpha, d_ring, V, eval);
-  cudaEvent_t e = c->prof_begin(1);
-  tdbem_status s = tdbem_direct_history(c, alpha, d_ring, V);
-  c->prof_end(1, e);
-  return s;
+  return tdbem_direct_history(c, alpha, d_ring, V);
 }
 
 // ring[(j*L + slot)*R + r] = x[r*ne + j] (x in the host layout [R][ne])

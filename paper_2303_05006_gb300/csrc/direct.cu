@@ -365,33 +365,142 @@ __global__ void k_rhs_plane(TriGeom g, Phys ph, const int32_t* et, int64_t ne, c
   Rv[i * R + r] = sum;
 }
 
-// R_i = V_i - sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m} (V may be
-// null: zero; V may alias R); one block per row.  ring[j*L + (beta mod L)] = J_j^beta.
-__global__ void __launch_bounds__(256) k_direct_history(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off,
-                                                       const double* val, int64_t ne, const double* ring, int32_t L,
-                                                       int32_t alpha, const double* V, double* R) {
-  int64_t i = blockIdx.x;
-  double s = 0.0;
-  for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
-    int64_t p = i * ne + j;
-    int lo = m_lo[p], n = nlag[p];
-    const double* z = val + off[p];
-    const double* Jr = ring + j * L;
-    for (int w = 0; w < n; ++w) {
-      int m = lo + w;
-      int b = alpha - m;
-      if (m < 2 || b < 0) continue;
-      s += __ldg(z + w) * Jr[b & (L - 1)];
-    }
+// The single-right-hand-side history sum runs on the FP32 pipes in
+// double-float arithmetic (each FP64 operand held as an unevaluated sum of two
+// FP32 numbers, hi + lo with |lo| <= ulp(hi)/2): GB300 issues FP64 FMAs at
+// 1/64 of its FP32 rate, which bounded the plain FP64 loop well below the HBM
+// roofline.  The product of two split numbers keeps hi*hi exactly (an FMA
+// recovers its rounding error) and the two cross terms; the dropped lo*lo and
+// the splits themselves are below 2^-47 of the product, so a term carries 46
+// significant bits against FP64's 53 while the sum stays compensated (TwoSum
+// into a hi/lo accumulator).  Operands must lie inside FP32's normal range.
+__device__ __forceinline__ float2 df_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float2 z, float2 x) {
+  const float p = __fmul_rn(z.x, x.x);
+  float e = __fmaf_rn(z.x, x.x, -p);
+  e = __fmaf_rn(z.x, x.y, e);
+  e = __fmaf_rn(z.y, x.x, e);
+  const float s = __fadd_rn(sh, p);  // TwoSum(sh, p)
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// Stored coefficients split in place, double -> (hi, lo) pair of the same 8 bytes.
+__global__ void k_split_values(double* val, int64_t n) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float2 s = df_split(val[t]);
+  reinterpret_cast<float2*>(val)[t] = s;
+}
+
+// ring2[slot*ne + j] = split(ring[j*L + slot]): the history of one right-hand
+// side transposed, so that the columns of a warp at one lag read contiguously.
+__global__ void k_ring_split(const double* ring, int64_t ne, int32_t L, float2* ring2) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne * L) return;
+  const int64_t j = t / L;
+  const int32_t slot = (int32_t)(t - j * L);
+  ring2[(int64_t)slot * ne + j] = df_split(ring[t]);
+}
+
+constexpr int kDhThreads = 256;  // column pairs per chunk (one per thread)
+constexpr int kDhCap = 3072;     // coefficients staged per chunk buffer (24 KB; four blocks per SM)
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct DhChunk {
+  int lo = 0, n = 0;
+  int64_t o = 0, start = 0, cnt = 0;
+};
+
+// Metadata of the chunk starting at column j0 (thread t takes column j0 + t).
+__device__ __forceinline__ DhChunk dh_meta(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, int64_t row0,
+                                           int64_t ne, int64_t j0) {
+  DhChunk m;
+  const int64_t j = j0 + threadIdx.x;
+  if (j < ne) {
+    m.lo = m_lo[row0 + j];
+    m.n = nlag[row0 + j];
+    m.o = off[row0 + j];
   }
-  __shared__ double red[32];
+  const int64_t last = min(j0 + kDhThreads, ne) - 1;
+  m.start = off[row0 + j0];
+  m.cnt = off[row0 + last] + nlag[row0 + last] - m.start;
+  return m;
+}
+
+// R_i = V_i - sum_j sum_{m >= 2, alpha-m >= 0} Zt^(m)_ij J_j^{alpha-m} (eq. R;
+// V may be null: zero; V may alias R); one block per row i, thread t taking
+// column j0 + t of each chunk of 256 columns.  The row's stored lags are
+// contiguous in column order, so a chunk owns one contiguous coefficient
+// range: it is copied into shared memory with asynchronous copies one chunk
+// ahead of the arithmetic (a chunk larger than a buffer is read from global
+// memory in place) while the metadata is loaded two chunks ahead.  val holds
+// split coefficients (k_split_values), ring2 the split, transposed history
+// (k_ring_split).
+__global__ void __launch_bounds__(kDhThreads) k_direct_history(const int16_t* m_lo, const uint8_t* nlag,
+                                                               const int64_t* off, const float2* val, int64_t ne,
+                                                               const float2* ring2, int32_t L, int32_t alpha,
+                                                               const double* V, double* R) {
+  extern __shared__ float2 zbuf[];  // [2][kDhCap]
+  __shared__ double red[kDhThreads / 32];
+  const int64_t row0 = (int64_t)blockIdx.x * ne;
+  const int64_t nchunk = (ne + kDhThreads - 1) / kDhThreads;
+  float sh = 0.f, sl = 0.f;
+  DhChunk cur = dh_meta(m_lo, nlag, off, row0, ne, 0);
+  if (cur.cnt <= kDhCap)
+    for (int64_t k = threadIdx.x; k < cur.cnt; k += kDhThreads) cp_async8(zbuf + k, val + cur.start + k);
+  cp_async_commit();
+  DhChunk nxt;
+  if (nchunk > 1) nxt = dh_meta(m_lo, nlag, off, row0, ne, kDhThreads);
+  for (int64_t c = 0; c < nchunk; ++c) {
+    float2* buf = zbuf + (c & 1) * kDhCap;
+    if (c + 1 < nchunk && nxt.cnt <= kDhCap) {
+      float2* nb = zbuf + ((c + 1) & 1) * kDhCap;
+      for (int64_t k = threadIdx.x; k < nxt.cnt; k += kDhThreads) cp_async8(nb + k, val + nxt.start + k);
+    }
+    cp_async_commit();
+    DhChunk nn;
+    if (c + 2 < nchunk) nn = dh_meta(m_lo, nlag, off, row0, ne, (c + 2) * kDhThreads);
+    cp_async_wait1();
+    __syncthreads();
+    {
+      // this column's lags m = lo + w with m >= 2 and alpha - m >= 0
+      const int64_t j = c * kDhThreads + threadIdx.x;
+      const float2* z = (cur.cnt <= kDhCap) ? buf + (cur.o - cur.start) : val + cur.o;
+      const int w0 = max(0, 2 - cur.lo), w1 = min(cur.n, alpha - cur.lo + 1);
+#pragma unroll 4
+      for (int w = w0; w < w1; ++w) {
+        const int slot = (alpha - cur.lo - w) & (L - 1);
+        df_fma_acc(sh, sl, z[w], __ldg(ring2 + (int64_t)slot * ne + j));
+      }
+    }
+    const float s = __fadd_rn(sh, sl);  // renormalise once per chunk
+    sl = __fsub_rn(sl, __fsub_rn(s, sh));
+    sh = s;
+    __syncthreads();
+    cur = nxt;
+    nxt = nn;
+  }
+  double s = (double)sh + (double)sl;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) R[i] = (V ? V[i] : 0.0) - s;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kDhThreads / 32; ++w) t += red[w];
+    R[blockIdx.x] = (V ? V[blockIdx.x] : 0.0) - t;
   }
 }
 
@@ -541,15 +650,39 @@ const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V) {
   const PairStore& st = c->direct;
   if (c->R == 1) {
-    k_direct_history<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring, c->L,
-                                                             alpha, V, c->d_R);
+    cudaEvent_t e = c->prof_begin(9);
+    const int64_t n = c->ne * (int64_t)c->L;
+    k_ring_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(d_ring, c->ne, c->L, c->d_ring2);
+    c->prof_end(9, e);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    e = c->prof_begin(1);
+    k_direct_history<<<(unsigned)c->ne, kDhThreads, 2 * kDhCap * sizeof(float2), c->stream>>>(
+        st.m_lo, st.nlag, st.off, reinterpret_cast<const float2*>(st.val), c->ne, c->d_ring2, c->L, alpha, V, c->d_R);
+    c->prof_end(1, e);
   } else {
     int RL = 1;
     while (RL < c->R && RL < 32) RL <<= 1;
+    cudaEvent_t e = c->prof_begin(1);
     k_direct_history_multi<<<(unsigned)c->ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, c->ne, d_ring,
                                                                    c->L, alpha, c->R, RL, V, c->d_R);
+    c->prof_end(1, e);
   }
   TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// Single right-hand side: split the stored coefficients in place (after Z0 has
+// been read from them) and make room for the split history.
+tdbem_status tdbem_direct_split(tdbem_ctx* c) {
+  if (c->R != 1) return TDBEM_OK;
+  PairStore& st = c->direct;
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * kDhCap * sizeof(float2))));
+  k_split_values<<<(unsigned)((st.nval + 255) / 256), 256, 0, c->stream>>>(st.val, st.nval);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  tdbem_status s = c->dalloc(&c->d_ring2, c->ne * (int64_t)c->L);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_ring2, 0, c->ne * (int64_t)c->L * sizeof(float2), c->stream));
   return TDBEM_OK;
 }
 

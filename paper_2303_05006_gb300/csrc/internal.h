@@ -54,7 +54,7 @@ struct PairStore {
   int16_t* m_lo = nullptr;
   uint8_t* nlag = nullptr;
   int64_t* off = nullptr;   // [npairs]
-  double* val = nullptr;    // [nval]
+  double* val = nullptr;    // [nval]; direct mode with one right-hand side: (hi, lo) FP32 pairs after setup
 };
 
 struct FmmPlan;
@@ -104,6 +104,7 @@ struct tdbem_ctx {
   int32_t R = 1;                    // right-hand sides (params.n_rhs)
   int32_t L = 0;                    // ring length (power of two)
   double* d_Jring = nullptr;        // [ne][L][R]
+  float2* d_ring2 = nullptr;        // direct mode, R = 1: split history [L][ne] (hi, lo)
   double* d_R = nullptr;            // [ne][R]
   double* d_J = nullptr;            // [ne][R] current solution
   double* d_Vall = nullptr;         // [Nt-1][ne][R] or null
@@ -126,7 +127,7 @@ struct tdbem_ctx {
   double setup_seconds = 0;
   int64_t device_bytes = 0;
   // kernel-class timing (tdbem_profile_*)
-  static constexpr int kClasses = 9;
+  static constexpr int kClasses = 10;
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
@@ -158,6 +159,7 @@ tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, con
 // direct.cu
 tdbem_status tdbem_build_direct(tdbem_ctx* c);
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V);
+tdbem_status tdbem_direct_split(tdbem_ctx* c);
 tdbem_status tdbem_incident_table(tdbem_ctx* c, int32_t r);
 const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha);
 tdbem_status tdbem_assemble_csr(tdbem_ctx* c, const int2* d_pairs, int64_t npairs, const int64_t* d_row_ptr,
