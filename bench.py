@@ -485,7 +485,8 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": steps_per_s, "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
         "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1000.0 * t / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.mode == "direct" else f"{args.prec}+f32+f64", "data": "synthetic",
+        "dtype": ("f64+df32" if R == 1 else "f64") if args.mode == "direct" else f"{args.prec}+f32+f64",
+        "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "mode": args.mode,
                    "p_s": args.p, "p_t": args.p, "m2l": args.prec if args.mode == "fast" else None, "n_rhs": R,
                    "jacobi_sweeps_max": args.jacobi, "precond": args.precond, "solve_tol": args.solve_tol,
