@@ -100,6 +100,38 @@ def test_sampled_rows_full_size_sphere7680():
         assert np.abs(R_gpu - R_ref).max() <= 1e-10 * scale
 
 
+def test_long_lag_windows_history_matches_oracle():
+    """A third of the workload's time step: the lag windows average more than
+    12 lags per edge pair, so a chunk of 256 columns holds more coefficients
+    than the history kernel stages in shared memory and is read in place from
+    global memory.  Same bar as the history test above, on sampled rows."""
+    from oracle.oracle import Oracle
+    from workloads import random_history, workload
+
+    w = workload("sphere320")
+    dt = w.dt / 3
+    s = _solver_dt(w, dt)
+    inf = s.info()
+    assert inf.near_coef_bytes / 8 / inf.n_near_pairs > 12
+    o = Oracle(w.verts, w.tris, dt)
+    rows = np.sort(np.random.default_rng(11).choice(o.ne, 24, replace=False))
+    mats = o.assemble(rows)
+    for alpha in (4, 70, 300):
+        J = random_history(o.ne, alpha - 1, seed=200 + alpha)
+        R_gpu = s.history_eval(alpha, J)[rows]
+        R_ref = o.rhs(w.pulses[0], alpha, rows) - o.history(alpha, J, rows, mats=mats)
+        scale = np.abs(R_ref).max() + np.abs(o.history(alpha, np.abs(J), rows, mats=mats)).max()
+        assert np.abs(R_gpu - R_ref).max() <= 1e-11 * scale, alpha
+
+
+def _solver_dt(w, dt):
+    from paper_2303_05006_gb300 import Solver
+
+    s = Solver(w.verts, w.tris, dt, 3 * w.Nt)
+    s.set_incident_plane(w.pulses[0])
+    return s
+
+
 def test_errors_are_returned():
     from paper_2303_05006_gb300 import Solver, TdbemError
     from workloads import icosphere
