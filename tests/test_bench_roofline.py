@@ -1,0 +1,84 @@
+"""Host logic of bench.py's roofline key (CPU only): the dominant kernel class
+is the one with the most device time, and `achieved` is its algorithmic work
+per launch over its mean launch time, against the peak of its own unit."""
+import types
+
+import numpy as np
+import pytest
+
+
+def _setup():
+    import bench
+
+    hbm, bf16, _ = bench._peaks()
+    info = types.SimpleNamespace(m2l_flops_per_step=2.0e10, m2l_tile_rows=[0, 0, 256, 256, 0, 0, 0, 0],
+                                 near_coef_bytes=4.0e9, n_near_pairs=5.0e7, z0_nnz=2.0e5,
+                                 total_solver_iters=400, ne=7680)
+    args = types.SimpleNamespace(prec="tf32x3", p=4, rhs=1, workload="sphere7680", far_overlap=1,
+                                 mode="fast", precond=1)
+    return bench, hbm, bf16, info, args
+
+
+def _times(bench, dominant, ms_dom, launches_dom):
+    n = len(bench.KERNELS)
+    launches = np.ones(n, dtype=np.int64)
+    ms = np.full(n, 1e-3)
+    k = bench.KERNELS.index(dominant)
+    launches[k], ms[k] = launches_dom, ms_dom
+    return launches, ms
+
+
+def test_profile_classes_match_the_header():
+    import os
+
+    import bench
+
+    hdr = open(os.path.join(bench.ROOT, "include", "tdbem.h")).read()
+    assert len(bench.KERNELS) == 10 and bench.KERNELS[9] == "history_split"
+    assert "9 history split" in hdr and "1 history/near field" in hdr
+
+
+def test_m2l_tensor_roofline():
+    bench, hbm, bf16, info, args = _setup()
+    K = 100
+    launches, ms = _times(bench, "m2l", 40.0, 300)
+    r = bench.roofline(args, info, launches, ms, K, 3)
+    tflops = info.m2l_flops_per_step * K / 0.040 / 1e12
+    assert r["kernel"] == "m2l" and r["bound"] == "tensor"
+    assert r["achieved"] == pytest.approx(tflops)
+    assert r["peak"] == pytest.approx(bf16 * 1.1 / 2.25)  # TF32 from the BF16 peak by the nominal ratio
+    assert r["frac"] == pytest.approx(tflops / r["peak"])
+    assert r["flops_per_launch"] == pytest.approx(info.m2l_flops_per_step * K / 300)
+    assert r["traffic"] == pytest.approx(bench.M2L_TRAFFIC_TF32X3)
+    # the committed DRAM traffic belongs to one configuration only
+    args.p = 5
+    assert bench.roofline(args, info, launches, ms, K, 3)["traffic"] is None
+    args.p, args.prec = 4, "bf16x3"
+    r = bench.roofline(args, info, launches, ms, K, 3)
+    assert r["peak"] == pytest.approx(bf16) and r["traffic"] is None
+
+
+def test_direct_history_hbm_roofline():
+    bench, hbm, _, info, args = _setup()
+    args.mode = "direct"
+    launches, ms = _times(bench, "near_history", 180.0, 100)
+    r = bench.roofline(args, info, launches, ms, 100, 5)
+    nbytes = info.near_coef_bytes + info.n_near_pairs * 11  # coefficients + m_lo, nlag, offset per pair
+    gbs = nbytes / 1.8e-3 / 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["bytes_per_launch"] == pytest.approx(nbytes)
+    assert r["achieved"] == pytest.approx(gbs) and r["frac"] == pytest.approx(gbs / hbm)
+
+
+def test_fast_near_field_counts_flattened_entries():
+    bench, hbm, _, info, args = _setup()
+    launches, ms = _times(bench, "near_history", 20.0, 100)
+    r = bench.roofline(args, info, launches, ms, 100, 5)
+    assert r["bytes_per_launch"] == pytest.approx(2 * info.near_coef_bytes)  # 8 B entry per 4 B coefficient
+
+
+def test_other_dominant_classes_are_latency_bound():
+    bench, _, _, info, args = _setup()
+    launches, ms = _times(bench, "l2p", 50.0, 100)
+    r = bench.roofline(args, info, launches, ms, 100, 5)
+    assert r["kernel"] == "l2p" and r["bound"] == "latency" and r["frac"] is None
