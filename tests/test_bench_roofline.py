@@ -82,3 +82,27 @@ def test_other_dominant_classes_are_latency_bound():
     launches, ms = _times(bench, "l2p", 50.0, 100)
     r = bench.roofline(args, info, launches, ms, 100, 5)
     assert r["kernel"] == "l2p" and r["bound"] == "latency" and r["frac"] is None
+
+
+def test_clock_sampler_parses_samples_and_reasons(tmp_path):
+    """The clocks key: median SM clock under load, the maximum, and every
+    throttle reason seen active in any sample (nvidia-smi csv, no header)."""
+    import bench
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.path = str(tmp_path / "clocks.csv")
+    s.p = _Done()
+    rows = ["0, 2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1200.5, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active"]
+    open(s.path, "w").write("\n".join(rows) + "\n")
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
