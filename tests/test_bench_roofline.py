@@ -106,3 +106,16 @@ def test_clock_sampler_parses_samples_and_reasons(tmp_path):
     open(s.path, "w").write("\n".join(rows) + "\n")
     c = s.stop()
     assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_z0_solve_counts_operand_bytes_per_solve():
+    bench, hbm, _, info, args = _setup()
+    K, W = 100, 4
+    launches, ms = _times(bench, "z0_solve", 25.0, K + W)
+    r = bench.roofline(args, info, launches, ms, K, W)
+    its = info.total_solver_iters / (K + W)
+    # per inner iteration two FP32 ELL SpMVs and 21 + 2 x 12 vector passes (triangle-block
+    # preconditioner); two FP64 residuals per solve
+    nbytes = its * (16 * info.z0_nnz + 4 * 45 * info.ne) + 2 * (12 * info.z0_nnz + 24 * info.ne)
+    assert r["bound"] == "hbm" and r["bytes_per_launch"] == pytest.approx(nbytes)
+    assert r["achieved"] == pytest.approx(nbytes / (25.0e-3 / (K + W)) / 1e9)
