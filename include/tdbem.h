@@ -233,8 +233,7 @@ tdbem_status tdbem_march_dev(tdbem_ctx* ctx, int32_t n_steps, double* J_all_dev)
    on its own stream (tdbem_set_stream, or the library's stream per context),
    so that the kernels of different scatterers overlap on the GPU where one
    scatterer alone leaves SMs idle (the Z0 solve of one context occupies one
-   16-SM cluster).  This is the batched form of the survey's configuration of
-   several scatterers; it is an interleave issued from the host, not a single
+   16-SM cluster).  It is an interleave issued from the host, not a single
    persistent launch.  J_all_dev (array of n device pointers, each
    [n_steps[i]][n_rhs][ne] or NULL; the array itself may be NULL) receives
    every current, as in tdbem_march_dev.  All contexts must live on the current
