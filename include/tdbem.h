@@ -99,19 +99,39 @@ typedef struct {
                             both at setup on each level and keeps the faster */
   int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
                             blocks of Z0 among the RWG functions of each triangle, summed) */
-  int32_t far_overlap;   /* fast mode, 1 (default): the steps overlap.  The M2L products of a gating event with
+  int32_t far_overlap;   /* 1 (default): the steps overlap.  Fast mode: the M2L products of a gating event with
                             lag q >= 2, whose local coefficients are first read one interval later, run on a
                             lowest-priority second stream of the context while the next steps proceed; with
                             one right-hand side, the near-field lags >= 3 of step alpha + 2 are summed on a
-                            middle-priority third stream while step alpha's solve runs.  0: every kernel on
-                            the context's stream in program 1's order.  The library's own stream has the
-                            highest priority (a caller's stream keeps its own) */
+                            middle-priority third stream while step alpha's solve runs.  Direct mode with one
+                            right-hand side: likewise the history lags >= 3 of step alpha + 2 (which need the
+                            currents up to J^{alpha-1} only) are summed on a middle-priority side stream during
+                            step alpha + 1; the step then adds the lag-2 coefficients and V.  Both orders do
+                            the same arithmetic there, so the currents are bitwise equal.  0: every kernel on the context's
+                            stream in program 1's order.  The library's own stream has the highest priority (a
+                            caller's stream keeps its own) */
   int32_t solve_grid;    /* single-RHS Z0 solve: 0 (default) one thread-block cluster below 49152 RWG functions
                             and a cooperative grid of every SM from there on; 1 always the cluster; 2 always
                             the grid */
   double chi;            /* weight of the time-differentiated MFIE inside the coupling: the tested equation is
                             dtEFIE + theta eta (chi dtMFIE + zeta MFIE).  1 (default): the paper's CFIE of
                             eq. cfie (CFIE1); zeta = 0: CFIE2; chi = 0: CFIE3 (section 4.3) */
+  int32_t far_kernel;    /* fast mode, kernel of the far field (for checks of the FMM's exactness):
+                              0 (default): the truncated-power kernels of the method, K_phi = (c tau - r)_+^2/(r (c dt)^2)
+                                 and K_A = dK_phi/dt (tau = t - s, r = |x - y|; eq. U and section 3.3);
+                              1: the polynomial K_phi = (1 + r^2) T3(tau/ts - 1), T3(x) = 4x^3 - 3x the
+                                 Chebyshev cubic, ts = 64 dt (lengths in the mesh's unit), with K_A = dK_phi/dt.
+                                 It has degree 2 in each coordinate and 3 in t and s, so the space-time
+                                 interpolation reproduces it exactly for p_s >= 3 and p_t >= 4: the far field
+                                 then equals its plain windowed sum up to rounding, whatever the tree;
+                              2: zero (no far field: the history sum is the near field alone).
+                            The window of source intervals, the truncated J-hat and the time gating are the
+                            same for every choice. */
+  int64_t max_device_bytes; /* device memory budget of the context's own allocations (0: none).  An allocation
+                               that would exceed it fails as if the device were full: tdbem_create returns
+                               TDBEM_ENOMEM with nothing left allocated.  Per-call temporaries of
+                               tdbem_history_eval and the learned warm start's buffers (tdbem_mlp_*) are
+                               outside it. */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -122,7 +142,8 @@ typedef struct {
 
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
-   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1. */
+   jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1, far_kernel=0,
+   max_device_bytes=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -197,7 +218,9 @@ tdbem_status tdbem_history_eval(tdbem_ctx* ctx, int32_t alpha, const double* J_h
      * The context's device must be the current device.
      * The first call on a device resolves the array's device address
        (cudaGetSymbolAddress) once; make that first call before any stream
-       capture.
+       capture.  The address is kept for the life of the process, so it does
+       not survive a cudaDeviceReset of that device (the array's storage does
+       not either).
      * Every call shares the one array and rewrites all of it that it reads, so
        no state carries over between calls; calls that overlap on the GPU (two
        streams, or two contexts on one device) race on it.
@@ -246,6 +269,26 @@ tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* 
 /* Restart the march at alpha = 1 (history and future right-hand sides cleared). */
 tdbem_status tdbem_reset(tdbem_ctx* ctx);
 
+/* Checkpoint and resume.  tdbem_save writes the march state to the file at
+   `path`: the step counter alpha, the history ring of the currents (every
+   J^beta a later step reads), the current solution and, in fast mode, the
+   far field in flight -- per octree level the moments of the recent source
+   intervals and the local coefficients of the target intervals not yet
+   reached, and the far right-hand sides ahead of the current step.  Deferred
+   work is waited for first.  tdbem_load reads such a file into a context
+   created with the same mesh, dt, Nt and parameters (checked against a header
+   and a hash of the mesh: EINVAL otherwise, with the state unchanged); the
+   march then continues from the saved step.  The incident fields or
+   caller-supplied right-hand sides, and the learned warm start's network, are
+   inputs and are not in the file: set them on the loading context as on the
+   saving one.  A direct march resumed this way is bit-identical to an
+   uninterrupted one; in fast mode the far field's FP32 atomic accumulation
+   already makes two uninterrupted marches differ in the last bits.  The
+   paper has no counterpart (its marches run in one go).  File errors give
+   EINVAL with tdbem_last_error naming the path. */
+tdbem_status tdbem_save(tdbem_ctx* ctx, const char* path);
+tdbem_status tdbem_load(tdbem_ctx* ctx, const char* path);
+
 /* Current step alpha (the next tdbem_step solves J^{alpha-1}). */
 tdbem_status tdbem_alpha(const tdbem_ctx* ctx, int32_t* alpha);
 
@@ -268,6 +311,9 @@ typedef struct {
   int32_t m2l_tile_rows[8];        /* per octree level: rows of the M2L product per tensor-core CTA (128 or
                                       256), chosen at setup by timing both shapes; 0 where no tensor-core M2L runs */
   int64_t z0_nnz;                  /* stored non-zeros of Z0 (the solver's sparse matrix) */
+  int32_t max_lag;                 /* largest time lag m with a stored coefficient: from step alpha = max_lag + 1 on,
+                                      every history step a coefficient can reach is inside the march (the steady
+                                      state of the history sum) */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 
@@ -278,8 +324,12 @@ tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
    0 incident RHS, 1 history/near field, 2 Z0 solve, 3 P2M, 4 M2M, 5 M2L,
    6 L2L, 7 L2P, 8 M2L moment packing (the symmetry-permuted copy of the
    moments that the tensor-core M2L reads), 9 history split (direct mode, one
-   right-hand side: the current history converted to FP32 hi/lo pairs before
-   the history sum).  n_classes receives the number of classes (<= 16). */
+   right-hand side, the untiled history sum: the current history converted to
+   FP32 hi/lo pairs before it), 10 history reduction (direct mode, one
+   right-hand side, the tiled history sum: the per-slice partial sums of a row
+   added in a fixed order with the lag-2 entries and V; class 1 is then the
+   tiled sum of the lags >= 3, launched ahead on the side stream when the steps
+   overlap).  n_classes receives the number of classes (<= 16). */
 tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
 tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
 

@@ -30,7 +30,8 @@ class Params(ctypes.Structure):
                 ("m2l_prec", ctypes.c_int32), ("solve_tol", ctypes.c_double), ("solve_maxit", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
                 ("m2l_tile_rows", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double)]
+                ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double),
+                ("far_kernel", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -40,7 +41,7 @@ class Info(ctypes.Structure):
                 ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
                 ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
                 ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64),
-                ("m2l_tile_rows", ctypes.c_int32 * 8), ("z0_nnz", ctypes.c_int64)]
+                ("m2l_tile_rows", ctypes.c_int32 * 8), ("z0_nnz", ctypes.c_int64), ("max_lag", ctypes.c_int32)]
 
 
 class TdbemError(RuntimeError):
@@ -100,12 +101,15 @@ def lib():
         L.tdbem_mlp_use.argtypes = [vp, ctypes.c_int32]
         L.tdbem_mlp_stats.argtypes = [vp, i64p, i64p]
         L.tdbem_march_many.argtypes = [ctypes.POINTER(vp), ctypes.c_int32, _i32p, ctypes.POINTER(vp), _i32p]
+        L.tdbem_save.argtypes = [vp, ctypes.c_char_p]
+        L.tdbem_load.argtypes = [vp, ctypes.c_char_p]
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
                      "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
                      "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_weights",
                      "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_samples", "tdbem_mlp_train",
-                     "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats", "tdbem_march_many"):
+                     "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats", "tdbem_march_many",
+                     "tdbem_save", "tdbem_load"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -306,6 +310,14 @@ class Solver:
         u, f = ctypes.c_int64(), ctypes.c_int64()
         self._check(lib().tdbem_mlp_stats(self._h, ctypes.byref(u), ctypes.byref(f)))
         return int(u.value), int(f.value)
+
+    def save(self, path: str) -> None:
+        """Write the march state to `path` (tdbem_save)."""
+        self._check(lib().tdbem_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        """Continue from the march state in `path` (tdbem_load)."""
+        self._check(lib().tdbem_load(self._h, os.fsencode(path)))
 
     def info(self) -> Info:
         inf = Info()

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -34,6 +35,61 @@ void tdbem_ctx::prof_end(int cls, cudaEvent_t b) {
   cudaEventRecord(e, stream);
   prof_marks.push_back({cls, {b, e}});
 }
+
+// Checkpoint file helpers (tdbem_save, tdbem_load).
+namespace {
+constexpr char kCkMagic[8] = {'T', 'D', 'B', 'E', 'M', 'C', 'K', '1'};
+
+struct CkHeader {
+  int32_t mode, n_rhs, L, Nt, alpha, p_s, p_t, n_leaf, far_kernel, m2l_prec, nbuf, pad;
+  int64_t ne, nt;
+  double dt, theta, zeta, chi;
+  uint64_t mesh_hash;  // FNV-1a of the vertex and triangle arrays
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+CkHeader ck_header(const tdbem_ctx* c, int32_t nbuf) {
+  CkHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.mode = c->p.mode;
+  h.n_rhs = c->R;
+  h.L = c->L;
+  h.Nt = c->Nt;
+  h.alpha = c->alpha;
+  h.p_s = c->p.p_s;
+  h.p_t = c->p.p_t;
+  h.n_leaf = c->p.n_leaf;
+  h.far_kernel = c->p.far_kernel;
+  h.m2l_prec = c->p.m2l_prec;
+  h.nbuf = nbuf;
+  h.ne = c->ne;
+  h.nt = c->nt;
+  h.dt = c->dt;
+  h.theta = c->p.theta;
+  h.zeta = c->p.zeta;
+  h.chi = c->p.chi;
+  uint64_t x = 1469598103934665603ull;
+  x = fnv1a(x, c->V.data(), c->V.size() * sizeof(double));
+  x = fnv1a(x, c->T.data(), c->T.size() * sizeof(int32_t));
+  h.mesh_hash = x;
+  return h;
+}
+
+// the march state's device buffers: history ring, current solution, and in
+// fast mode the far field's moments, local coefficients and far RHS ring
+std::vector<std::pair<void*, size_t>> ck_buffers(tdbem_ctx* c) {
+  const size_t NR = (size_t)c->ne * c->R;
+  std::vector<std::pair<void*, size_t>> b = {{c->d_Jring, NR * c->L * sizeof(double)},
+                                             {c->d_J, NR * sizeof(double)}};
+  if (c->p.mode == TDBEM_FAST) tdbem_fast_state(c, &b);
+  return b;
+}
+}  // namespace
 
 extern "C" {
 
@@ -89,7 +145,9 @@ static void fill_phys(tdbem_ctx* c) {
 void tdbem_destroy(tdbem_ctx* c) {
   if (!c) return;
   tdbem_fast_join(c);
+  tdbem_direct_join(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  tdbem_direct_free(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   tdbem_fast_free(c);
@@ -131,6 +189,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
       p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||
+      p.far_kernel < 0 || p.far_kernel > 2 || p.max_device_bytes < 0 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -461,6 +520,7 @@ static tdbem_status step_async(tdbem_ctx* c, bool have_V = false) {
   if (s) return s;
   if ((s = tdbem_mlp_after_solve(c, c->alpha))) return s;
   if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_after_solve(c, c->alpha))) return s;
+  if (c->p.mode == TDBEM_DIRECT && (s = tdbem_direct_after_solve(c, c->alpha))) return s;
   c->alpha++;
   return TDBEM_OK;
 }
@@ -512,6 +572,7 @@ tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t*
 tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
   if (!c) return TDBEM_EINVAL;
   tdbem_status s = tdbem_fast_join(c);
+  if (!s) s = tdbem_direct_join(c);
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->prof_on = on != 0;
@@ -523,6 +584,7 @@ tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
 tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int32_t* n_classes) {
   if (!c || !launches || !ms) return TDBEM_EINVAL;
   tdbem_status s = tdbem_fast_join(c);
+  if (!s) s = tdbem_direct_join(c);
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (int k = 0; k < tdbem_ctx::kClasses; ++k) {
@@ -542,6 +604,7 @@ tdbem_status tdbem_profile_read(tdbem_ctx* c, int64_t* launches, double* ms, int
 static tdbem_status check_misses(tdbem_ctx* c) {
   if (c->p.mode == TDBEM_FAST) {
     tdbem_status s = tdbem_fast_join(c);
+  if (!s) s = tdbem_direct_join(c);
     if (s) return s;
     s = tdbem_fast_check(c);
     if (s) return s;
@@ -625,6 +688,7 @@ tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* 
 tdbem_status tdbem_reset(tdbem_ctx* c) {
   if (!c) return TDBEM_EINVAL;
   tdbem_status s0 = tdbem_fast_invalidate(c);
+  if (!s0) s0 = tdbem_direct_invalidate(c);
   if (s0) return s0;
   const int64_t NR = c->ne * (int64_t)c->R;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_Jring, 0, NR * c->L * sizeof(double), c->stream));
@@ -638,6 +702,96 @@ tdbem_status tdbem_reset(tdbem_ctx* c) {
   c->alpha = 1;
   c->total_iters = 0;
   c->total_sweeps = 0;
+  return TDBEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the march state written to a file and read back (helpers above
+// the extern "C" block).
+
+
+tdbem_status tdbem_save(tdbem_ctx* c, const char* path) {
+  if (!c || !path) return TDBEM_EINVAL;
+  tdbem_status s = tdbem_fast_join(c);
+  if (!s) s = tdbem_direct_join(c);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const auto bufs = ck_buffers(c);
+  const CkHeader h = ck_header(c, (int32_t)bufs.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    c->set_error(std::string("save: cannot open ") + path + " for writing");
+    return TDBEM_EINVAL;
+  }
+  bool ok = std::fwrite(kCkMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof(h), 1, f) == 1;
+  std::vector<char> host;
+  for (size_t k = 0; ok && k < bufs.size(); ++k) {
+    const int64_t n = (int64_t)bufs[k].second;
+    host.resize(bufs[k].second);
+    cudaError_t e = cudaMemcpy(host.data(), bufs[k].first, bufs[k].second, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      c->set_error(std::string("save: ") + cudaGetErrorString(e));
+      return TDBEM_ECUDA;
+    }
+    ok = std::fwrite(&n, sizeof(n), 1, f) == 1 && std::fwrite(host.data(), 1, host.size(), f) == host.size();
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    c->set_error(std::string("save: write to ") + path + " failed");
+    return TDBEM_EINVAL;
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_load(tdbem_ctx* c, const char* path) {
+  if (!c || !path) return TDBEM_EINVAL;
+  tdbem_status s = tdbem_fast_invalidate(c);
+  if (!s) s = tdbem_direct_invalidate(c);
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    c->set_error(std::string("load: cannot open ") + path);
+    return TDBEM_EINVAL;
+  }
+  const auto bufs = ck_buffers(c);
+  const CkHeader want = ck_header(c, (int32_t)bufs.size());
+  char magic[8];
+  CkHeader h;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkMagic, 8) == 0 &&
+            std::fread(&h, sizeof(h), 1, f) == 1;
+  if (!ok) {
+    std::fclose(f);
+    c->set_error("load: not a checkpoint of this library");
+    return TDBEM_EINVAL;
+  }
+  CkHeader cmp = h;
+  cmp.alpha = want.alpha;  // the step is what the checkpoint brings
+  if (std::memcmp(&cmp, &want, sizeof(h)) != 0 || h.alpha < 1 || h.alpha > c->Nt) {
+    std::fclose(f);
+    c->set_error("load: the checkpoint was written by a context with another mesh, time axis or parameters");
+    return TDBEM_EINVAL;
+  }
+  std::vector<std::vector<char>> host(bufs.size());
+  for (size_t k = 0; ok && k < bufs.size(); ++k) {
+    int64_t n = 0;
+    ok = std::fread(&n, sizeof(n), 1, f) == 1 && n == (int64_t)bufs[k].second;
+    if (!ok) break;
+    host[k].resize(bufs[k].second);
+    ok = std::fread(host[k].data(), 1, host[k].size(), f) == host[k].size();
+  }
+  std::fclose(f);
+  if (!ok) {
+    c->set_error(std::string("load: ") + path + " is truncated or does not match this context");
+    return TDBEM_EINVAL;
+  }
+  // every size checked: now overwrite the state
+  for (size_t k = 0; k < bufs.size(); ++k)
+    TDBEM_CUDA_TRY(c, cudaMemcpy(bufs[k].first, host[k].data(), host[k].size(), cudaMemcpyHostToDevice));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, 16 * sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->alpha = h.alpha;
   return TDBEM_OK;
 }
 
@@ -660,6 +814,7 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->total_jacobi_sweeps = c->total_sweeps;
   info->z0_nnz = c->z0_nnz;
   info->solver_cluster = c->cluster;
+  info->max_lag = c->max_lag;
   if (c->p.mode == TDBEM_FAST) tdbem_fast_info(c, info);
   return TDBEM_OK;
 }

@@ -59,6 +59,15 @@ __global__ void k_direct_windows(TriGeom g, const int32_t* et, int64_t ne, doubl
   nlag[p] = (uint8_t)n;
 }
 
+// largest stored lag m_lo + nlag - 1 over all pairs (atomic maximum into *mx)
+__global__ void k_max_lag(const int16_t* m_lo, const uint8_t* nlag, int64_t n, int32_t* mx) {
+  int v = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    if (nlag[p]) v = max(v, (int)m_lo[p] + (int)nlag[p] - 1);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, v);
+}
+
 // per-row sums of nlag
 __global__ void k_row_totals(const uint8_t* nlag, int64_t ne, int64_t* tot) {
   int64_t i = blockIdx.x;
@@ -110,20 +119,40 @@ __global__ void k_row_offsets(const uint8_t* nlag, int64_t ne, const int64_t* ro
   }
 }
 
-// Sink of the direct store: every (i, j) of the mesh.
+// Sink of the direct store: every (i, j) of the mesh.  An edge pair receives
+// one contribution from each of the four triangle pairs of its two supports,
+// class k = 2 (test triangle is i's "-" triangle) + (source triangle is j's
+// "-" triangle).  With val4 set, contribution k goes to its own slot
+// val4[4 (off + w) + k] with a plain store, and k_sum4 adds the four in a
+// fixed order afterwards, so the stored coefficients do not depend on the
+// order in which threads finish; without it the contributions are added to
+// val with FP64 atomics.
 struct DirectSink {
   const int16_t* m_lo;
   const uint8_t* nlag;
   const int64_t* off;
   double* val;
   int64_t ne;
-  __device__ __forceinline__ double* slot(int i, int j, int m) const {
+  double* val4;
+  __device__ __forceinline__ bool add(int i, int j, int m, int k, double v) const {
     int64_t p = (int64_t)i * ne + j;
     int w = m - m_lo[p];
-    if (w < 0 || w >= nlag[p]) return nullptr;
-    return val + off[p] + w;
+    if (w < 0 || w >= nlag[p]) return false;
+    if (val4)
+      val4[4 * (off[p] + w) + k] = v;
+    else
+      atomicAdd(val + off[p] + w, v);
+    return true;
   }
 };
+
+// val[e] = ((v4[4e] + v4[4e+1]) + v4[4e+2]) + v4[4e+3]
+__global__ void k_sum4(const double* v4, int64_t n, double* val) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double* q = v4 + 4 * e;
+  val[e] = ((q[0] + q[1]) + q[2]) + q[3];
+}
 
 // One thread per (test triangle t, source triangle s) listed in `pairs` (or
 // all pairs when pairs == nullptr).
@@ -245,12 +274,8 @@ __global__ void __launch_bounds__(128) k_assemble(TriGeom g, Phys ph, int64_t nt
       for (int k = 0; k < NM; ++k) {
         double v = acc[kt][ks][k];
         if (v == 0.0) continue;
-        double* dst = sink.slot(i, j, M0 + k);
-        if (!dst) {
-          atomicExch(err, 5);
-          continue;
-        }
-        atomicAdd(dst, v);
+        const int cls = (g.sgn[3 * t + kt] < 0 ? 2 : 0) + (g.sgn[3 * s + ks] < 0 ? 1 : 0);
+        if (!sink.add(i, j, M0 + k, cls, v)) atomicExch(err, 5);
       }
     }
   }
@@ -266,19 +291,20 @@ struct CsrSink {
   const uint8_t* nlag;
   const int64_t* off;
   double* val;
-  __device__ __forceinline__ double* slot(int i, int j, int m) const {
+  __device__ __forceinline__ bool add(int i, int j, int m, int /*k*/, double v) const {
     int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
     while (lo <= hi) {
       int64_t mid = (lo + hi) >> 1;
       int c = col[mid];
       if (c == j) {
         int w = m - m_lo[mid];
-        if (w < 0 || w >= nlag[mid]) return nullptr;
-        return val + off[mid] + w;
+        if (w < 0 || w >= nlag[mid]) return false;
+        atomicAdd(val + off[mid] + w, v);
+        return true;
       }
       if (c < j) lo = mid + 1; else hi = mid - 1;
     }
-    return nullptr;
+    return false;
   }
 };
 
@@ -389,6 +415,16 @@ __device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float2 z, float
   const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   sh = s;
   sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// (sh, sl) += (bh, bl), both double-float: TwoSum of the high parts, the low
+// parts and the rounding error added to the low part.
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  const float s = __fadd_rn(sh, bh);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, bl));
 }
 
 // Stored coefficients split in place, double -> (hi, lo) pair of the same 8 bytes.
@@ -504,6 +540,154 @@ __global__ void __launch_bounds__(kDhThreads) k_direct_history(const int16_t* m_
   }
 }
 
+// Tiled form of the single-right-hand-side history sum.  Block (cb, rg) takes
+// the column block j0 = cb*CB .. j0+CB-1 (CB = 32 S columns, S slices of one
+// warp's width) and the row range of group rg.  The history of its columns is
+// split into (hi, lo) pairs and staged in shared memory once, slot-major
+// ([slot][column]: a lane always reads its own column, so its bank does not
+// depend on the lag it reads); the rows then stream past it, so no history
+// value is gathered from L2 per row.  A warp owns one 32-column slice, lane t its column js + t, and every
+// G-th row of the range (G = 16/S warps per slice).  Per row, the slice's
+// stored lags are one contiguous run of coefficients (each column's lags
+// consecutive, columns in order): the warp copies the run into its own
+// shared-memory buffer with cp.async (coalesced), the lanes find their
+// columns' offsets in it by a warp scan of the window lengths, and each lane
+// walks its column's lags against the staged history.  A row's lag windows
+// and run start are loaded one row ahead, while the previous row computes.
+// The lanes' double-float sums are added across the warp in double-float too
+// (FP64 runs at a small fraction of the FP32 rate on this part), and lane 0
+// writes the warp's sum for (row, slice) to partial[(cb*S + slice)*ne + row];
+// k_direct_reduce adds the partials of a row in a fixed order, so the result
+// does not depend on scheduling.  Lags m < m_min are left out (m_min = 2 for
+// the whole history); history slots of steps alpha - m_min + 1 .. alpha are
+// not read (another kernel may be writing them).
+constexpr int kDtWarps = 16;  // warps per block (two blocks per SM)
+constexpr int kDtCap = 384;   // coefficients a warp stages per row (3 KB); longer runs are read in place
+
+__host__ __device__ constexpr int dt_slices(int L) { return L <= 64 ? 2 : (L <= 128 ? 1 : 0); }
+
+__global__ void __launch_bounds__(kDtWarps * 32, 2)
+    k_direct_history_tile(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const float2* val,
+                          int64_t ne, const double* ring, int32_t L, int32_t alpha, int32_t m_min, int32_t S,
+                          int32_t rows_per_block, double* partial) {
+  extern __shared__ float2 dt_sm[];
+  const int CB = 32 * S;
+  float2* hist = dt_sm;          // [L][CB]
+  float2* zb = dt_sm + CB * L;   // [kDtWarps][kDtCap]
+  const int64_t j0 = (int64_t)blockIdx.x * CB;
+  for (int k = threadIdx.x; k < CB * L; k += blockDim.x) {
+    const int c = k / L, slot = k - c * L;  // consecutive threads read one column's slots (coalesced)
+    const int64_t j = j0 + c;
+    // steps alpha - m_min + 1 .. alpha are not needed (and may be in flux)
+    const bool used = ((alpha - slot) & (L - 1)) >= m_min;
+    hist[slot * CB + c] = (j < ne && used) ? df_split(ring[j * L + slot]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sl_ = w % S, g = w / S, G = kDtWarps / S;
+  const int64_t js = j0 + 32 * sl_;  // first column of this warp's slice
+  if (js >= ne) return;
+  const int64_t j = js + lane;
+  const bool valid = j < ne;
+  const int64_t i_begin = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t i_end = min(ne, i_begin + rows_per_block);
+  const float2* hcol = hist + 32 * sl_ + lane;  // this lane's column; slot k at hcol[k * CB]
+  float2* zw = zb + w * kDtCap;
+  double* out = partial + (int64_t)(blockIdx.x * S + sl_) * ne;
+  const unsigned full = 0xffffffffu;
+  int64_t i = i_begin + g;
+  if (i >= i_end) return;
+  int lo = valid ? m_lo[i * ne + j] : 0, n = valid ? nlag[i * ne + j] : 0;
+  int64_t base = off[i * ne + js];
+  for (; i < i_end; i += G) {
+    int x = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(full, x, d);
+      if (lane >= d) x += y;
+    }
+    const int o = x - n;                       // this column's offset in the run
+    const int cnt = __shfl_sync(full, x, 31);  // run length
+    const bool staged = cnt <= kDtCap;
+    if (staged)
+      for (int k = lane; k < cnt; k += 32) cp_async8(zw + k, val + base + k);
+    cp_async_commit();
+    // the next row's lag windows and run start load while this row's run copies
+    const int lo_c = lo, n_c = n;
+    const int64_t base_c = base;
+    if (i + G < i_end) {
+      const int64_t i2 = i + G;
+      lo = valid ? m_lo[i2 * ne + j] : 0;
+      n = valid ? nlag[i2 * ne + j] : 0;
+      base = off[i2 * ne + js];
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+    const float2* z = staged ? zw + o : val + base_c + o;
+    const int w0 = max(0, m_min - lo_c), w1 = min(n_c, alpha - lo_c + 1);
+    float sh = 0.f, sl = 0.f;
+    for (int u = w0; u < w1; ++u) df_fma_acc(sh, sl, z[u], hcol[((alpha - lo_c - u) & (L - 1)) * CB]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) df_add(sh, sl, __shfl_xor_sync(full, sh, d), __shfl_xor_sync(full, sl, d));
+    if (lane == 0) out[i] = (double)sh + (double)sl;
+    __syncwarp();  // every lane is done with the buffer before the next copy
+  }
+}
+
+// R_i = V_i - (sum_k partial[k*ne + i] over the nparts partials of row i, in
+// the order k = 0, 1, ..., then the row's lag-2 entries l2 against J^{alpha-2}
+// in FP64, in stored order).  V may be null (zero) and may alias R.
+__global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t ne, const int64_t* l2_ptr,
+                                const int32_t* l2_col, const double* l2_val, const double* ring, int32_t L,
+                                int32_t alpha, const double* V, double* R) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  double t = 0.0;
+  for (int k = 0; k < nparts; ++k) t += partial[(int64_t)k * ne + i];
+  if (alpha >= 2) {
+    const int slot = (alpha - 2) & (L - 1);
+    for (int64_t e = l2_ptr[i]; e < l2_ptr[i + 1]; ++e) t += l2_val[e] * ring[(int64_t)l2_col[e] * L + slot];
+  }
+  R[i] = (V ? V[i] : 0.0) - t;
+}
+
+// Lag-2 entries of the direct store, as a CSR over rows (before the split).
+__global__ void k_lag2_count(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int64_t* cnt) {
+  const int64_t i = blockIdx.x;
+  int64_t s = 0;
+  for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
+    const int lo = m_lo[i * ne + j], n = nlag[i * ne + j];
+    s += (lo <= 2 && 2 < lo + n) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ int64_t red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    cnt[i] = t;
+  }
+}
+
+// one thread per row: its lag-2 entries in column order
+__global__ void k_lag2_fill(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const double* val, int64_t ne,
+                            const int64_t* ptr, int32_t* col, double* v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  int64_t e = ptr[i];
+  const int64_t e1 = ptr[i + 1];
+  for (int64_t j = 0; j < ne && e < e1; ++j) {
+    const int64_t p = i * ne + j;
+    const int lo = m_lo[p], n = nlag[p];
+    if (lo <= 2 && 2 < lo + n) {
+      col[e] = (int32_t)j;
+      v[e] = val[off[p] + (2 - lo)];
+      ++e;
+    }
+  }
+}
+
 // Batched form of k_direct_history for R right-hand sides ([..][ne][R]
 // layouts): one block per row; the block's threads are split into groups of
 // RL lanes (RL = R rounded up to a power of two, at most 32), lane rr of a
@@ -589,11 +773,28 @@ tdbem_status tdbem_build_direct(tdbem_ctx* c) {
   k_row_offsets<<<(unsigned)ne, 1024, 0, c->stream>>>(st.nlag, ne, d_base, st.off);
   if ((s = c->dalloc(&st.val, st.nval))) return s;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(st.val, 0, st.nval * sizeof(double), c->stream));
-  DirectSink sink{st.m_lo, st.nlag, st.off, st.val, ne};
+  // four slots per stored coefficient for the order-independent sum, if the
+  // device (and the context's budget) has room; else FP64 atomics
+  double* val4 = nullptr;
+  const size_t b4 = (size_t)4 * st.nval * sizeof(double);
+  const bool fits = c->p.max_device_bytes <= 0 || c->device_bytes + (int64_t)b4 <= c->p.max_device_bytes;
+  if (fits && cudaMalloc(&val4, b4) != cudaSuccess) {
+    val4 = nullptr;
+    cudaGetLastError();  // clear the failed allocation
+  }
+  if (val4) TDBEM_CUDA_TRY(c, cudaMemsetAsync(val4, 0, b4, c->stream));
+  DirectSink sink{st.m_lo, st.nlag, st.off, st.val, ne, val4};
   const int64_t ntp = c->nt * c->nt;
   k_assemble<DirectSink><<<(unsigned)((ntp + 127) / 128), 128, 0, c->stream>>>(c->tg, c->phys, c->nt, nullptr, ntp,
                                                                                sink, d_err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if (val4) {
+    k_sum4<<<(unsigned)((st.nval + 255) / 256), 256, 0, c->stream>>>(val4, st.nval, st.val);
+    cudaError_t e4 = cudaGetLastError();
+    cudaStreamSynchronize(c->stream);
+    cudaFree(val4);
+    TDBEM_CUDA_TRY(c, e4);
+  }
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (herr) {
@@ -601,19 +802,16 @@ tdbem_status tdbem_build_direct(tdbem_ctx* c) {
                  std::to_string(herr));
     return TDBEM_EINVAL;
   }
-  // largest stored lag: every window ends below (bounding-box diagonal + two
-  // triangle radii)/(c dt) + 3
+  // largest stored lag (the history ring holds every step it reaches)
   int32_t mx = 0;
   {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, dmax = 0;
-    for (int64_t v = 0; v < c->nv; ++v)
-      for (int q = 0; q < 3; ++q) {
-        lo[q] = std::min(lo[q], c->V[3 * v + q]);
-        hi[q] = std::max(hi[q], c->V[3 * v + q]);
-      }
-    for (int q = 0; q < 3; ++q) dmax += (hi[q] - lo[q]) * (hi[q] - lo[q]);
-    dmax = std::sqrt(dmax) + 2.0 * c->max_tri_rad;
-    mx = (int32_t)std::ceil(dmax / c->phys.a + 3.0) + 1;
+    int32_t* d_mx = nullptr;
+    if ((s = c->dalloc(&d_mx, 1))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_mx, 0, sizeof(int32_t), c->stream));
+    k_max_lag<<<1024, 256, 0, c->stream>>>(st.m_lo, st.nlag, npair, d_mx);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&mx, d_mx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
   c->max_lag = mx;
   return TDBEM_OK;
@@ -647,9 +845,42 @@ const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
   return nullptr;
 }
 
+// The tiled history sum of the lags >= 3 of step alpha into partial buffer buf,
+// on the context's current stream.
+static tdbem_status direct_tile(tdbem_ctx* c, int32_t alpha, const double* d_ring, int buf) {
+  const PairStore& st = c->direct;
+  const size_t smem = ((size_t)32 * c->dt_S * c->L + (size_t)kDtWarps * kDtCap) * sizeof(float2);
+  const int64_t nparts = (int64_t)c->dt_ncb * c->dt_S;
+  k_direct_history_tile<<<dim3((unsigned)c->dt_ncb, (unsigned)c->dt_rg), kDtWarps * 32, smem, c->stream>>>(
+      st.m_lo, st.nlag, st.off, reinterpret_cast<const float2*>(st.val), c->ne, d_ring, c->L, alpha, 3, c->dt_S,
+      c->dt_rows, c->d_dpart + buf * nparts * c->ne);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V) {
   const PairStore& st = c->direct;
-  if (c->R == 1) {
+  if (c->R == 1 && c->dt_S > 0) {
+    // the march's own ring uses buffers alpha & 1 (possibly filled ahead, during
+    // the previous step), any other history buffer 2
+    const bool march = d_ring == c->d_Jring;
+    const int buf = march ? (alpha & 1) : 2;
+    const int64_t nparts = (int64_t)c->dt_ncb * c->dt_S;
+    if (march && c->dahead[buf] == alpha) {
+      TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_dahead[buf], 0));
+    } else {
+      cudaEvent_t e = c->prof_begin(1);
+      tdbem_status s = direct_tile(c, alpha, d_ring, buf);
+      if (s) return s;
+      c->prof_end(1, e);
+    }
+    if (march) c->dahead[buf] = 0;
+    cudaEvent_t e = c->prof_begin(10);
+    k_direct_reduce<<<(unsigned)((c->ne + 255) / 256), 256, 0, c->stream>>>(
+        c->d_dpart + buf * nparts * c->ne, (int32_t)nparts, c->ne, c->d_l2_ptr, c->d_l2_col, c->d_l2_val, d_ring,
+        c->L, alpha, V, c->d_R);
+    c->prof_end(10, e);
+  } else if (c->R == 1) {
     cudaEvent_t e = c->prof_begin(9);
     const int64_t n = c->ne * (int64_t)c->L;
     k_ring_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(d_ring, c->ne, c->L, c->d_ring2);
@@ -671,15 +902,130 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
   return TDBEM_OK;
 }
 
+// After step alpha's solve is enqueued: the lags >= 3 of step alpha + 2 need
+// the currents up to J^{alpha-1}, so they are summed on the side stream while
+// step alpha + 1 runs (its reduction, lag-2 entries and solve).  Buffer
+// (alpha + 2) & 1 was last read by step alpha's reduction, ordered before the
+// solve and so before this launch.
+tdbem_status tdbem_direct_after_solve(tdbem_ctx* c, int32_t alpha) {
+  if (!c->dstream || c->dt_S == 0 || c->R != 1) return TDBEM_OK;
+  const int32_t a2 = alpha + 2;
+  if (a2 > c->Nt - 1) return TDBEM_OK;
+  const int b = a2 & 1;
+  TDBEM_CUDA_TRY(c, cudaEventRecord(c->ev_dsolved, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->dstream, c->ev_dsolved, 0));
+  cudaStream_t main = c->stream;
+  c->stream = c->dstream;
+  cudaEvent_t e = c->prof_begin(1);
+  tdbem_status s = direct_tile(c, a2, c->d_Jring, b);
+  c->prof_end(1, e);
+  c->stream = main;
+  if (s) return s;
+  TDBEM_CUDA_TRY(c, cudaEventRecord(c->ev_dahead[b], c->dstream));
+  c->dahead[b] = a2;
+  return TDBEM_OK;
+}
+
+// The context's stream waits for the sums launched ahead (they stay usable).
+tdbem_status tdbem_direct_join(tdbem_ctx* c) {
+  for (int b = 0; b < 2; ++b)
+    if (c->dahead[b]) TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_dahead[b], 0));
+  return TDBEM_OK;
+}
+
+// As tdbem_direct_join, and the sums launched ahead are discarded.
+tdbem_status tdbem_direct_invalidate(tdbem_ctx* c) {
+  tdbem_status s = tdbem_direct_join(c);
+  c->dahead[0] = c->dahead[1] = 0;
+  return s;
+}
+
+void tdbem_direct_free(tdbem_ctx* c) {
+  if (c->dstream) cudaStreamSynchronize(c->dstream);
+  if (c->ev_dsolved) cudaEventDestroy(c->ev_dsolved);
+  for (int b = 0; b < 2; ++b)
+    if (c->ev_dahead[b]) cudaEventDestroy(c->ev_dahead[b]);
+  if (c->dstream) cudaStreamDestroy(c->dstream);
+  c->dstream = nullptr;
+}
+
 // Single right-hand side: split the stored coefficients in place (after Z0 has
-// been read from them) and make room for the split history.
+// been read from them) and lay out the history sum: the tiled kernel when two
+// blocks (one column block's history and the warps' buffers each) fit an SM's
+// shared memory (ring length L <= 128), else the untiled kernel and its split
+// ring.
 tdbem_status tdbem_direct_split(tdbem_ctx* c) {
   if (c->R != 1) return TDBEM_OK;
   PairStore& st = c->direct;
-  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * kDhCap * sizeof(float2))));
+  const int S = dt_slices(c->L);
+  if (S > 0) {
+    // lag-2 entries (read from the FP64 store before it is split)
+    const int64_t ne = c->ne;
+    int64_t* d_cnt = nullptr;
+    tdbem_status s0;
+    if ((s0 = c->dalloc(&c->d_l2_ptr, ne + 1)) || (s0 = c->dalloc(&d_cnt, ne))) return s0;
+    k_lag2_count<<<(unsigned)ne, 256, 0, c->stream>>>(st.m_lo, st.nlag, ne, d_cnt);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    std::vector<int64_t> cnt(ne), ptr(ne + 1, 0);
+    // the counts come from the context's stream: copy on it and wait
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(cnt.data(), d_cnt, ne * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < ne; ++i) ptr[i + 1] = ptr[i] + cnt[i];
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_l2_ptr, ptr.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                      c->stream));
+    if ((s0 = c->dalloc(&c->d_l2_col, std::max<int64_t>(1, ptr[ne]))) ||
+        (s0 = c->dalloc(&c->d_l2_val, std::max<int64_t>(1, ptr[ne]))))
+      return s0;
+    k_lag2_fill<<<(unsigned)((ne + 127) / 128), 128, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne,
+                                                                      c->d_l2_ptr, c->d_l2_col, c->d_l2_val);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // before ptr (host) goes out of scope
+  }
   k_split_values<<<(unsigned)((st.nval + 255) / 256), 256, 0, c->stream>>>(st.val, st.nval);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if (S > 0) {
+    const size_t smem = ((size_t)32 * S * c->L + (size_t)kDtWarps * kDtCap) * sizeof(float2);
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    int nsm = 0;
+    TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const int ncb = (int)((c->ne + 32 * S - 1) / (32 * S));
+    // row groups: the grid closest to whole waves of two blocks per SM
+    // (between just under one wave and four)
+    const int slots = 2 * nsm;
+    int rg_best = 1;
+    double waste_best = 1e30;
+    const int rg0 = std::max(1, slots / ncb), rg1 = 4 * std::max(1, (slots + ncb - 1) / ncb);
+    for (int rg = rg0; rg <= rg1; ++rg) {
+      const int64_t nb = (int64_t)ncb * rg;
+      const int64_t waves = (nb + slots - 1) / slots;
+      const double waste = (double)(waves * slots - nb) / (double)nb;
+      if (waste < waste_best - 1e-9) {
+        waste_best = waste;
+        rg_best = rg;
+      }
+    }
+    const int rows = (int)((c->ne + rg_best - 1) / rg_best);
+    tdbem_status s = c->dalloc(&c->d_dpart, (size_t)3 * ncb * S * c->ne);
+    if (s) return s;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_dpart, 0, (size_t)3 * ncb * S * c->ne * sizeof(double), c->stream));
+    if (c->p.far_overlap) {
+      // between the library stream's highest priority and the lowest: the
+      // next solve's cluster is dispatched ahead of this stream's blocks
+      int prio_lo = 0, prio_hi = 0;
+      TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+      TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->dstream, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+      TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_dsolved, cudaEventDisableTiming));
+      for (int b = 0; b < 2; ++b) TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_dahead[b], cudaEventDisableTiming));
+    }
+    c->dt_S = S;
+    c->dt_ncb = ncb;
+    c->dt_rg = (int)((c->ne + rows - 1) / rows);
+    c->dt_rows = rows;
+    return TDBEM_OK;
+  }
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * kDhCap * sizeof(float2))));
   tdbem_status s = c->dalloc(&c->d_ring2, c->ne * (int64_t)c->L);
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_ring2, 0, c->ne * (int64_t)c->L * sizeof(float2), c->stream));

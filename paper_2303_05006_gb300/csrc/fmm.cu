@@ -259,9 +259,12 @@ __global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* bo
 }
 
 // M2L operators of one level: for canonical offset cv[op] and lag qv[op],
-// ops[op][kind][(a,m)][(b,n)], kind 0 = K_A, 1 = K_phi.
+// ops[op][kind][(a,m)][(b,n)], kind 0 = K_A, 1 = K_phi.  kern selects the
+// kernel pair (tdbem_params.far_kernel): 0 the truncated powers of the method,
+// 1 the polynomial check kernel K_phi = (1 + r^2) T3(tau/(64 dt) - 1) with its
+// time derivative, 2 zero.
 __global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, double dt, double cc, double a,
-                          const int4* opdesc /* {c1,c2,c3,q} */, int nop, float* ops) {
+                          const int4* opdesc /* {c1,c2,c3,q} */, int nop, int kern, float* ops) {
   const int PS = p * p * p, P = PS * pt;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t total = (int64_t)nop * P * P;
@@ -282,7 +285,12 @@ __global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, 
   double tau = (d.w * M + 1) * dt + ht * (cheb_node(m, pt) - cheb_node(n, pt));
   double u = cc * tau - r;
   double kphi = 0.0, kA = 0.0;
-  if (u > 0.0) {
+  if (kern == 1) {
+    // (1 + r^2) T3(tau/ts - 1), T3(x) = 4x^3 - 3x, ts = 64 dt, and its time derivative
+    const double g = 1.0 + r2, ts = 64.0 * dt, x = tau / ts - 1.0;
+    kphi = g * (4.0 * x * x * x - 3.0 * x);
+    kA = g * (12.0 * x * x - 3.0) / ts;
+  } else if (kern == 0 && u > 0.0) {
     kphi = u * u / (r * a * a);
     kA = 2.0 * cc * u / (r * a * a);
   }
@@ -995,6 +1003,9 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     if ((s = c->dalloc(&F->d_val32, F->nval))) return s;
     k_f64_to_f32<<<(unsigned)((F->nval + 255) / 256), 256, 0, c->stream>>>(F->d_val64, F->d_val32, F->nval);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
+    // the blocking copies below run on the legacy stream, which does not wait
+    // for the context's (non-blocking) stream
+    TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     // largest near lag (ring length)
     std::vector<int16_t> ml(F->nnz);
     std::vector<uint8_t> nl(F->nnz);
@@ -1284,7 +1295,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles, tiles.data(), L.ntiles * sizeof(int4), cudaMemcpyHostToDevice));
       int64_t tot = (int64_t)L.nop * P * P;
       k_m2l_ops<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p, pt, L.ds, L.H, 0.5 * L.M * dt, L.M, dt, cc, a,
-                                                                      d_opdesc, L.nop, L.ops);
+                                                                      d_opdesc, L.nop, c->p.far_kernel, L.ops);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
       if (c->p.m2l_prec != TDBEM_P_FP32 && (s = tdbem_m2l_tc_images(c, L.ops, L.nop, P, c->p.m2l_prec, &L.ops_img)))
         return s;
@@ -1712,6 +1723,23 @@ tdbem_status tdbem_fast_invalidate(tdbem_ctx* c) {
   tdbem_status s = tdbem_fast_join(c);
   F->ahead[0] = F->ahead[1] = 0;
   return s;
+}
+
+// Device buffers of the fast mode's march state, in a fixed order: per far
+// level its moments and local coefficients, then the far right-hand-side
+// ring (the evaluation state of history_eval and the near-field sums launched
+// ahead are not part of it: the former is rebuilt per call, the latter are
+// recomputed by the same kernel when absent).
+void tdbem_fast_state(tdbem_ctx* c, std::vector<std::pair<void*, size_t>>* bufs) {
+  FmmPlan* F = c->fmm;
+  if (!F || F->lmax < 2) return;
+  const int64_t RP = (int64_t)c->R * kNC * F->P;
+  for (int l = 2; l <= F->lmax; ++l) {
+    FmmLevel& L = F->lev[l];
+    bufs->push_back({L.mom, (size_t)L.ncell * 4 * RP * sizeof(float)});
+    bufs->push_back({L.loc, (size_t)L.ncell * L.Q * RP * sizeof(float)});
+  }
+  bufs->push_back({F->d_Rfar, (size_t)F->Lr * c->ne * c->R * sizeof(double)});
 }
 
 void tdbem_fast_free(tdbem_ctx* c) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/tdbem.h"
@@ -104,7 +105,19 @@ struct tdbem_ctx {
   int32_t R = 1;                    // right-hand sides (params.n_rhs)
   int32_t L = 0;                    // ring length (power of two)
   double* d_Jring = nullptr;        // [ne][L][R]
-  float2* d_ring2 = nullptr;        // direct mode, R = 1: split history [L][ne] (hi, lo)
+  float2* d_ring2 = nullptr;        // direct mode, R = 1: split history [L][ne] (hi, lo) (untiled kernel)
+  // direct mode, R = 1, tiled history sum (lags >= 3) plus the lag-2 entries in the reduction
+  double* d_dpart = nullptr;        // partial sums [3][ncb*S][ne]: march steps alpha & 1, evaluations 2
+  int32_t dt_S = 0;                 // 32-column slices per block (0: untiled kernel)
+  int32_t dt_ncb = 0, dt_rg = 0;    // column blocks and row groups of its grid
+  int32_t dt_rows = 0;              // rows per block
+  int64_t* d_l2_ptr = nullptr;      // lag-2 coefficients, CSR over rows [ne + 1]
+  int32_t* d_l2_col = nullptr;
+  double* d_l2_val = nullptr;
+  cudaStream_t dstream = nullptr;   // far_overlap: the lags >= 3 of step alpha + 2 run here during step alpha + 1
+  cudaEvent_t ev_dsolved = nullptr;
+  cudaEvent_t ev_dahead[2] = {nullptr, nullptr};
+  int32_t dahead[2] = {0, 0};       // step whose lags >= 3 sit in partial buffer b (0: none)
   double* d_R = nullptr;            // [ne][R]
   double* d_J = nullptr;            // [ne][R] current solution
   double* d_Vall = nullptr;         // [Nt-1][ne][R] or null
@@ -127,7 +140,7 @@ struct tdbem_ctx {
   double setup_seconds = 0;
   int64_t device_bytes = 0;
   // kernel-class timing (tdbem_profile_*)
-  static constexpr int kClasses = 10;
+  static constexpr int kClasses = 11;
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_marks;
@@ -139,6 +152,11 @@ struct tdbem_ctx {
   template <class T>
   tdbem_status dalloc(T** ptr, size_t count) {
     if (count == 0) count = 1;
+    if (p.max_device_bytes > 0 && device_bytes + (int64_t)(count * sizeof(T)) > p.max_device_bytes) {
+      set_error("device memory budget (max_device_bytes) exceeded");
+      *ptr = nullptr;
+      return TDBEM_ENOMEM;
+    }
     cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
     if (e != cudaSuccess) {
       set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -160,6 +178,10 @@ tdbem_status tdbem_build_mesh(tdbem_ctx* c, const double* verts, int64_t nv, con
 tdbem_status tdbem_build_direct(tdbem_ctx* c);
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V);
 tdbem_status tdbem_direct_split(tdbem_ctx* c);
+tdbem_status tdbem_direct_after_solve(tdbem_ctx* c, int32_t alpha);
+tdbem_status tdbem_direct_join(tdbem_ctx* c);
+tdbem_status tdbem_direct_invalidate(tdbem_ctx* c);
+void tdbem_direct_free(tdbem_ctx* c);
 tdbem_status tdbem_incident_table(tdbem_ctx* c, int32_t r);
 const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha);
 tdbem_status tdbem_assemble_csr(tdbem_ctx* c, const int2* d_pairs, int64_t npairs, const int64_t* d_row_ptr,
@@ -188,6 +210,7 @@ tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym
                             const float* mom, int k, int R, int PS, int pt, float* pk);
 tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
+void tdbem_fast_state(tdbem_ctx* c, std::vector<std::pair<void*, size_t>>* bufs);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
                                   const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val);
 // mlp.cu

@@ -22,7 +22,8 @@ def declared_symbols():
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
-    for n in ("tdbem_create", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_destroy"):
+    for n in ("tdbem_create", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_save", "tdbem_load",
+              "tdbem_destroy"):
         assert n in names
 
 

@@ -222,3 +222,34 @@ def test_sin2_pulse_matches_oracle():
     s2 = _solver(w)
     s2.set_incident_plane(delayed)
     assert np.abs(s2.march(n)).max() == 0.0
+
+
+def test_pipelined_march_equals_program_order():
+    """far_overlap = 1 (default): the history lags >= 3 of step alpha + 2 are
+    summed on a side stream during step alpha + 1, and the step adds the lag-2
+    coefficients and V.  Program 1's serial order (far_overlap = 0) does the
+    same arithmetic, so the currents must be bitwise equal: through march,
+    step by step (each step returns while the side stream still works), across
+    a reset, with caller-supplied right-hand sides (step_v), and with history
+    evaluations interleaved between steps (they use a buffer of their own)."""
+    from workloads import random_history, workload
+
+    w = workload("sphere1280")
+    n = 120
+    Jb = _solver(w, far_overlap=0).march(n)
+    s = _solver(w, far_overlap=1)
+    assert np.array_equal(s.march(n), Jb)
+    s.reset()
+    Js = []
+    H = random_history(s.ne, 60, seed=8)
+    for a in range(n):
+        Js.append(s.step()[0])
+        if a in (30, 31, 77):
+            s.history_eval(61, H)
+    assert np.array_equal(np.stack(Js), Jb)
+    V = [s.history_eval(a, np.zeros((0, s.ne))) for a in range(1, n + 1)]
+    s.reset()
+    Jv = np.zeros((n, s.ne))
+    for a in range(n):
+        s.step_v(V[a], Jv[a])
+    assert np.array_equal(Jv, Jb)
