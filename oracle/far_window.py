@@ -173,9 +173,11 @@ def jhat_window(J, G, g0, g1):
     return np.array(out)
 
 
-def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi=1.0, eps=1.0, mu=1.0):
+def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi=1.0, eps=1.0, mu=1.0,
+                   absolute=False):
     """sum over far triangle pairs of the tested coefficients times J, for the
-    polynomial kernel K(x, y, t, s) = (1 + |x - y|^2) ((t - s)/dt)^3, on rows
+    polynomial kernel K(x, y, t, s) = (1 + |x - y|^2) T3((t - s)/ts - 1), with
+    T3(x) = 4x^3 - 3x (the Chebyshev cubic) and ts = 64 dt, on rows
     `rows` at target step alpha (the part of R^{alpha-1} = V - near - far that
     the far field contributes with a minus sign).  J[b] = J^b ([n_hist][ne]).
 
@@ -187,8 +189,13 @@ def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi
       + theta eta/(4 pi) (f_i x n) . (f_j x grad_y (chi dK/dt + zeta K)),
     n the unit normal of the test triangle pointing into the conductor, summed
     against Jhat over the window of the pair.  The kernel is separable, so the
-    time sums sum_gamma Jhat_G^gamma (alpha - gamma)^p (p = 1, 2, 3) are formed
-    once per edge and window."""
+    time sums sum_gamma Jhat_G^gamma T3^(p)(x_gamma), x_gamma = (alpha -
+    gamma) dt/ts - 1 (p = 0, 1, 2 derivatives), are formed once per edge and
+    window.
+
+    absolute=True returns instead a bound on the sum of the absolute values of
+    all the terms (every factor taken in absolute value): the size against
+    which rounding in a finite precision is measured."""
     ev, et, eo = edges
     V, T, dt = h.V, h.T, h.dt
     eta = np.sqrt(mu / eps)
@@ -211,13 +218,17 @@ def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi
             cnt[t] += 1
     assert np.all(cnt == 3)
     J = np.asarray(J, dtype=np.float64).reshape(-1, len(ev))
-    tsum = {}  # (G, g0, g1) -> [3, ne]: sum over the window of Jhat (alpha - gamma)^p, p = 1, 2, 3
+    ts = 64.0 * dt
+    tsum = {}  # (G, g0, g1) -> [3, ne]: sum over the window of Jhat T3(x), T3'(x), T3''(x)
 
     def time_sums(G, g0, g1):
         if (G, g0, g1) not in tsum:
             Jh = jhat_window(J, G, g0, g1)                               # [n, ne]
-            tau = (alpha - np.arange(g0, g1 + 1)).astype(np.float64)     # (t - s)/dt
-            tsum[(G, g0, g1)] = np.stack([tau ** p @ Jh for p in (1, 2, 3)])
+            x = (alpha - np.arange(g0, g1 + 1)) * dt / ts - 1.0
+            T = [4 * x ** 3 - 3 * x, 12 * x ** 2 - 3, 24 * x]            # T3 and its x-derivatives
+            if absolute:
+                Jh, T = np.abs(Jh), [np.abs(v) for v in T]
+            tsum[(G, g0, g1)] = np.stack([v @ Jh for v in T])
         return tsum[(G, g0, g1)]
 
     out = np.zeros(len(rows))
@@ -247,11 +258,13 @@ def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi
                     cj = side_s[S, k] * elen[j] / (2 * area[S])
                     fj = cj[:, None, None] * (Y - V[side_o[S, k]][:, None, :])   # [nS, 7y, 3]
                     divj = 2 * cj
-                    sA = np.sum(ww * np.einsum("qd,syd->sqy", fi, fj) * g, axis=(1, 2))
-                    sF = divi * divj * np.sum(ww * g, axis=(1, 2))
-                    sP = np.sum(ww * np.einsum("qd,sqyd->sqy", fixn, np.cross(fj[:, None, :, :], 2 * dxy)), axis=(1, 2))
-                    H1, H2, H3 = Hs[0, j], Hs[1, j], Hs[2, j]
-                    out[ir] += np.sum(mu / (4 * np.pi) * sA * 6 * H1 / dt ** 2
-                                      + 1 / (4 * np.pi * eps) * sF * H3
-                                      + theta * eta / (4 * np.pi) * sP * (chi * 3 * H2 / dt + zeta * H3))
+                    ab = np.abs if absolute else (lambda v: v)
+                    sA = np.sum(ab(ww * np.einsum("qd,syd->sqy", fi, fj) * g), axis=(1, 2))
+                    sF = ab(divi * divj) * np.sum(ww * g, axis=(1, 2))
+                    sP = np.sum(ab(ww * np.einsum("qd,sqyd->sqy", fixn, np.cross(fj[:, None, :, :], 2 * dxy))),
+                                axis=(1, 2))
+                    K0, K1, K2 = Hs[0, j], Hs[1, j] / ts, Hs[2, j] / ts ** 2   # K, dK/dt, d2K/dt2 (g aside)
+                    out[ir] += np.sum(mu / (4 * np.pi) * sA * K2
+                                      + 1 / (4 * np.pi * eps) * sF * K0
+                                      + theta * eta / (4 * np.pi) * sP * (chi * K1 + zeta * K0))
     return out

@@ -117,3 +117,45 @@ def test_hierarchy_matches_table1(ns, subdiv):
     h = Hierarchy(v, t, 0.005, n_leaf=100)
     assert h.lmax == row[1]
     assert 3 <= h.M(h.lmax) <= row[2]
+
+
+def test_planted_window_faults_exceed_the_gpu_bar():
+    """The GPU exactness check (tests/test_gpu_far_exact.py) compares the
+    library's far field with far_field_poly at a bar of TOL of the largest
+    value.  On its own mesh, history and rows, each planted bookkeeping fault
+    moves the reference by at least 50 TOL: the newest interval dropped
+    (q_lo + 1) at every step, and, once the windows reach back past the first
+    step, the oldest interval dropped (q_hi - 1) or the window start left
+    untruncated."""
+    import oracle.far_window as fw
+    from oracle.far_window import Hierarchy, far_field_poly
+    from oracle.oracle import Oracle
+    from tests.test_gpu_far_exact import TOL, _smooth_history
+    from workloads.meshes import icosphere, mean_edge_length
+
+    v, t = icosphere(1.0, 3)
+    dt = 0.25 * mean_edge_length(v, t)
+    h = Hierarchy(v, t, dt, n_leaf=16)
+    ed = Oracle(v, t, dt).edges()
+    ne = len(ed[0])
+    J = _smooth_history(ne, 200, seed=5)
+    rows = np.sort(np.random.default_rng(9).choice(ne, 12, replace=False))
+    orig_lr, orig_jh = fw.Hierarchy.lag_range, fw.jhat_window
+    faults = {
+        "q_lo + 1": lambda: setattr(fw.Hierarchy, "lag_range", lambda s, l, o: (orig_lr(s, l, o)[0] + 1,
+                                                                                    orig_lr(s, l, o)[1])),
+        "q_hi - 1": lambda: setattr(fw.Hierarchy, "lag_range", lambda s, l, o: (orig_lr(s, l, o)[0],
+                                                                                    orig_lr(s, l, o)[1] - 1)),
+        "untruncated": lambda: setattr(fw, "jhat_window", lambda J_, G, g0, g1: orig_jh(J_, G - 8, g0, g1)),
+    }
+    try:
+        for alpha, names in ((12, ["q_lo + 1"]), (150, list(faults))):
+            ref = far_field_poly(h, ed, rows, J[: alpha - 1], alpha)
+            scale = np.abs(ref).max()
+            for name in names:
+                faults[name]()
+                planted = far_field_poly(h, ed, rows, J[: alpha - 1], alpha)
+                fw.Hierarchy.lag_range, fw.jhat_window = orig_lr, orig_jh
+                assert np.abs(planted - ref).max() >= 50 * TOL * scale, (alpha, name)
+    finally:
+        fw.Hierarchy.lag_range, fw.jhat_window = orig_lr, orig_jh

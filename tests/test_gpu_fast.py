@@ -2,12 +2,20 @@
 
 The fast path evaluates the same discretisation as the direct path (near
 pairs with the identical coefficients, stored in FP32) and replaces the far
-pairs by interpolation of the kernel in space and time.  Its error is the
-interpolation error, which must fall with the number of interpolation points;
-the bookkeeping (time gating, interval lags, window truncation, symmetries of
-the M2L operators, M2M/L2L) is exact, so a bookkeeping mistake shows up as an
-error that does not fall with p.  Bars are set at about twice the measured
-errors and are stated per test.
+pairs by interpolation of the kernel in space and time.  Its bookkeeping --
+hierarchy, time gating, lag ranges, window truncation, the M2L symmetries,
+M2M and L2L -- is checked exact by tests/test_gpu_far_exact.py (a kernel the
+interpolation reproduces, against the oracle's plain windowed sum).  What is
+left here is the interpolation error of the method's own kernels:
+
+* it must fall with the interpolation orders (a property, not a tuned bar);
+* the absolute bounds below are regression guards at about twice the values
+  measured on a GB300 (stated per test), not accuracy claims;
+* the metric's 1e-4 on the 7680-RWG sphere is not reached, and the test that
+  asks for it is an expected failure (strict): the collocated second time
+  derivative of the quadratic B-spline makes the discrete vector-potential
+  response step with r at the scale c dt, which no polynomial interpolant of
+  the kernel follows (measured floor about 3e-4 at p = 8).
 """
 import numpy as np
 import pytest
@@ -121,6 +129,20 @@ def test_fast_full_size_sphere7680():
     e = _rel(Jf, Jd)
     assert e < 1.5e-2, e
     assert np.abs(Jf[-50:]).max() < 1e-2 * np.abs(Jd).max()
+
+
+@pytest.mark.xfail(strict=True, reason="interpolation floor of the vector-potential term: 6.0e-3 at p = 4, "
+                   "2.8e-4 at p = 8 (the collocated B-spline second derivative steps with r at the scale c dt)")
+def test_fast_meets_the_metric_bar_sphere7680():
+    """The metric's accuracy bar: fast currents within 1e-4 relative l2 of the
+    FP64 direct march (itself the oracle's to 1e-10) over all 999 steps of the
+    7680-RWG sphere at p_s = p_t = 4."""
+    from workloads import workload
+
+    w = workload("sphere7680")
+    Jd = _solver(w, mode=0).march(w.Nt - 1)
+    Jf = _solver(w, mode=1).march(w.Nt - 1)
+    assert _rel(Jf, Jd) <= 1e-4
 
 
 def test_tensor_core_m2l_precisions(sphere1280_direct):
