@@ -34,8 +34,8 @@ def test_profile_classes_match_the_header():
     import bench
 
     hdr = open(os.path.join(bench.ROOT, "include", "tdbem.h")).read()
-    assert len(bench.KERNELS) == 10 and bench.KERNELS[9] == "history_split"
-    assert "9 history split" in hdr and "1 history/near field" in hdr
+    assert len(bench.KERNELS) == 11 and bench.KERNELS[9] == "history_split" and bench.KERNELS[10] == "history_reduce"
+    assert "9 history split" in hdr and "1 history/near field" in hdr and "10 history reduction" in hdr
 
 
 def test_m2l_tensor_roofline():
@@ -63,7 +63,7 @@ def test_direct_history_hbm_roofline():
     args.mode = "direct"
     launches, ms = _times(bench, "near_history", 180.0, 100)
     r = bench.roofline(args, info, launches, ms, 100, 5)
-    nbytes = info.near_coef_bytes + info.n_near_pairs * 11  # coefficients + m_lo, nlag, offset per pair
+    nbytes = info.near_coef_bytes + info.n_near_pairs * 3  # coefficients + lag window (m_lo, nlag) per pair
     gbs = nbytes / 1.8e-3 / 1e9
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["bytes_per_launch"] == pytest.approx(nbytes)
@@ -85,8 +85,9 @@ def test_other_dominant_classes_are_latency_bound():
 
 
 def test_clock_sampler_parses_samples_and_reasons(tmp_path):
-    """The clocks key: median SM clock under load, the maximum, and every
-    throttle reason seen active in any sample (nvidia-smi csv, no header)."""
+    """The clocks key: median SM clock over the samples under load (utilisation
+    >= 50 %), the maximum, and every throttle reason seen active in any sample
+    (nvidia-smi csv, no header)."""
     import bench
 
     class _Done:
@@ -99,13 +100,18 @@ def test_clock_sampler_parses_samples_and_reasons(tmp_path):
     s = bench.ClockSampler.__new__(bench.ClockSampler)
     s.path = str(tmp_path / "clocks.csv")
     s.p = _Done()
-    rows = ["0, 2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
-            "0, 2055, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
-            "0, 2070, 2070, 1200.5, Not Active, Not Active, Not Active, Not Active",
-            "0, [N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active"]
+    rows = ["0, 2070, 2070, 900.1, 98, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, 100, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1200.5, 99, Not Active, Not Active, Not Active, Not Active",
+            "0, 1200, 2070, 150.0, 0, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 0, 0, Not Active, Not Active, Not Active, Not Active"]
     open(s.path, "w").write("\n".join(rows) + "\n")
     c = s.stop()
-    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4,
+                 "samples_under_load": 3}
+    # with no sample under load the median covers every sample
+    c = bench.ClockSampler.parse(rows[3:])
+    assert c["sm_mhz"] == 1200.0 and c["samples_under_load"] == 0
 
 
 def test_z0_solve_counts_operand_bytes_per_solve():
