@@ -60,6 +60,57 @@ def icosphere(radius: float = 1.0, subdivisions: int = 2):
     return V, _orient_outward(V, T, np.zeros(3))
 
 
+def geodesic_sphere(radius: float = 1.0, freq: int = 8):
+    """Icosahedral geodesic sphere of frequency ``freq`` with equal-arc
+    spacing (20 freq^2 triangles): on every face (A, B, C) of the icosahedron
+    inscribed in the unit sphere, the grid point with weights (n - i - j, i, j)
+    lies on the great circle between the points at arc fraction (i + j)/n from
+    A towards B and towards C, at fraction j/(i + j) of the arc between them.
+    These are the meshes of the paper's test problem (section 4.1, Table 1):
+    their edge lengths match the table's minimum, mean and maximum."""
+    g = (1.0 + 5.0 ** 0.5) / 2.0
+    base = np.array([(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0),
+                     (0, -1, g), (0, 1, g), (0, -1, -g), (0, 1, -g),
+                     (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)], dtype=np.float64)
+    base /= np.linalg.norm(base, axis=1)[:, None]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+             (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+             (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+             (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    n = freq
+
+    def slerp(p, q, t):
+        w = np.arccos(np.clip(p @ q, -1.0, 1.0))
+        if w < 1e-14:
+            return p
+        return (np.sin((1 - t) * w) * p + np.sin(t * w) * q) / np.sin(w)
+
+    index: dict[tuple, int] = {}
+    verts = []
+
+    def vid(a, b, c, i, j):
+        # points shared by two faces get one index through their integer weights
+        w = {a: n - i - j, b: i, c: j}
+        key = tuple(sorted((k, v) for k, v in w.items() if v))
+        if key not in index:
+            r = i + j
+            p = base[a] if r == 0 else slerp(slerp(base[a], base[b], r / n), slerp(base[a], base[c], r / n), j / r)
+            verts.append(p / np.linalg.norm(p))
+            index[key] = len(verts) - 1
+        return index[key]
+
+    tris = []
+    for a, b, c in faces:
+        for i in range(n):
+            for j in range(n - i):
+                tris.append((vid(a, b, c, i, j), vid(a, b, c, i + 1, j), vid(a, b, c, i, j + 1)))
+                if i + j < n - 1:
+                    tris.append((vid(a, b, c, i + 1, j), vid(a, b, c, i + 1, j + 1), vid(a, b, c, i, j + 1)))
+    V = np.array(verts) * radius
+    T = np.array(tris, dtype=np.int32)
+    return V, _orient_outward(V, T, np.zeros(3))
+
+
 def cube_jittered(side: float = 2.0, n: int = 16, jitter: float = 0.02, seed: int = 3,
                   centre=(0.0, 0.0, 0.0)):
     """Cube surface: each face is an ``n``x``n`` grid of squares, each square split
