@@ -452,6 +452,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
@@ -561,26 +565,26 @@ __global__ void __launch_bounds__(kDhThreads) k_direct_history(const int16_t* m_
 // does not depend on scheduling.  Lags m < m_min are left out (m_min = 2 for
 // the whole history); history slots of steps alpha - m_min + 1 .. alpha are
 // not read (another kernel may be writing them).
-constexpr int kDtWarps = 16;  // warps per block (two blocks per SM)
-constexpr int kDtCap = 384;   // coefficients a warp stages per row (3 KB); longer runs are read in place
+constexpr int kDtWarps = 16;  // warps per block (three blocks per SM)
+constexpr int kDtCap = 328;   // coefficients a warp stages per row (2.6 KB); longer runs are read in place
 
 __host__ __device__ constexpr int dt_slices(int L) { return L <= 64 ? 2 : (L <= 128 ? 1 : 0); }
 
-__global__ void __launch_bounds__(kDtWarps * 32, 2)
+__global__ void __launch_bounds__(kDtWarps * 32, 3)
     k_direct_history_tile(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const float2* val,
                           int64_t ne, const double* ring, int32_t L, int32_t alpha, int32_t m_min, int32_t S,
                           int32_t rows_per_block, double* partial) {
-  extern __shared__ float2 dt_sm[];
+  extern __shared__ __align__(16) float2 dt_sm[];
   const int CB = 32 * S;
-  float2* hist = dt_sm;          // [L][CB]
+  float2* hist = dt_sm;          // [L][CB]: row m holds J^{alpha-m} of the block's columns
   float2* zb = dt_sm + CB * L;   // [kDtWarps][kDtCap]
   const int64_t j0 = (int64_t)blockIdx.x * CB;
   for (int k = threadIdx.x; k < CB * L; k += blockDim.x) {
     const int c = k / L, slot = k - c * L;  // consecutive threads read one column's slots (coalesced)
     const int64_t j = j0 + c;
+    const int m = (alpha - slot) & (L - 1);  // the lag at which this slot's step is read at step alpha
     // steps alpha - m_min + 1 .. alpha are not needed (and may be in flux)
-    const bool used = ((alpha - slot) & (L - 1)) >= m_min;
-    hist[slot * CB + c] = (j < ne && used) ? df_split(ring[j * L + slot]) : make_float2(0.f, 0.f);
+    hist[m * CB + c] = (j < ne && m >= m_min) ? df_split(ring[j * L + slot]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(kDtWarps * 32, 2)
   const bool valid = j < ne;
   const int64_t i_begin = (int64_t)blockIdx.y * rows_per_block;
   const int64_t i_end = min(ne, i_begin + rows_per_block);
-  const float2* hcol = hist + 32 * sl_ + lane;  // this lane's column; slot k at hcol[k * CB]
+  const float2* hcol = hist + 32 * sl_ + lane;  // this lane's column; lag m at hcol[m * CB]
   float2* zw = zb + w * kDtCap;
   double* out = partial + (int64_t)(blockIdx.x * S + sl_) * ne;
   const unsigned full = 0xffffffffu;
@@ -608,13 +612,20 @@ __global__ void __launch_bounds__(kDtWarps * 32, 2)
     }
     const int o = x - n;                       // this column's offset in the run
     const int cnt = __shfl_sync(full, x, 31);  // run length
-    const bool staged = cnt <= kDtCap;
-    if (staged)
-      for (int k = lane; k < cnt; k += 32) cp_async8(zw + k, val + base + k);
+    // run element k goes to zw[par + k]: global and shared addresses then share
+    // their parity, and every aligned pair moves as one 16-byte copy
+    const int par = (int)(base & 1);
+    const bool staged = cnt + par <= kDtCap;
+    const float2* gz = val + base;
+    if (staged) {
+      const int npair = (cnt - par) >> 1;
+      for (int q = lane; q < npair; q += 32) cp_async16(zw + 2 * (par + q), gz + par + 2 * q);
+      if (lane == 0 && par && cnt > 0) cp_async8(zw + 1, gz);
+      if (lane == 31 && ((cnt - par) & 1)) cp_async8(zw + par + cnt - 1, gz + cnt - 1);
+    }
     cp_async_commit();
     // the next row's lag windows and run start load while this row's run copies
     const int lo_c = lo, n_c = n;
-    const int64_t base_c = base;
     if (i + G < i_end) {
       const int64_t i2 = i + G;
       lo = valid ? m_lo[i2 * ne + j] : 0;
@@ -623,10 +634,13 @@ __global__ void __launch_bounds__(kDtWarps * 32, 2)
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncwarp();
-    const float2* z = staged ? zw + o : val + base_c + o;
     const int w0 = max(0, m_min - lo_c), w1 = min(n_c, alpha - lo_c + 1);
+    // coefficient u of this column has lag lo + u: both operands advance by a fixed stride
+    const float2* z = (staged ? zw + par + o : gz + o) + w0;
+    const float2* h = hcol + (lo_c + w0) * CB;
     float sh = 0.f, sl = 0.f;
-    for (int u = w0; u < w1; ++u) df_fma_acc(sh, sl, z[u], hcol[((alpha - lo_c - u) & (L - 1)) * CB]);
+#pragma unroll 2
+    for (int u = w0; u < w1; ++u, ++z, h += CB) df_fma_acc(sh, sl, *z, *h);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) df_add(sh, sl, __shfl_xor_sync(full, sh, d), __shfl_xor_sync(full, sl, d));
     if (lane == 0) out[i] = (double)sh + (double)sl;
@@ -950,10 +964,10 @@ void tdbem_direct_free(tdbem_ctx* c) {
 }
 
 // Single right-hand side: split the stored coefficients in place (after Z0 has
-// been read from them) and lay out the history sum: the tiled kernel when two
-// blocks (one column block's history and the warps' buffers each) fit an SM's
-// shared memory (ring length L <= 128), else the untiled kernel and its split
-// ring.
+// been read from them) and lay out the history sum: the tiled kernel when one
+// column block's history and the warps' buffers fit shared memory (ring
+// length L <= 128; three blocks per SM at L = 64), else the untiled kernel and
+// its split ring.
 tdbem_status tdbem_direct_split(tdbem_ctx* c) {
   if (c->R != 1) return TDBEM_OK;
   PairStore& st = c->direct;
@@ -990,9 +1004,9 @@ tdbem_status tdbem_direct_split(tdbem_ctx* c) {
     int nsm = 0;
     TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     const int ncb = (int)((c->ne + 32 * S - 1) / (32 * S));
-    // row groups: the grid closest to whole waves of two blocks per SM
+    // row groups: the grid closest to whole waves of three blocks per SM
     // (between just under one wave and four)
-    const int slots = 2 * nsm;
+    const int slots = 3 * nsm;
     int rg_best = 1;
     double waste_best = 1e30;
     const int rg0 = std::max(1, slots / ncb), rg1 = 4 * std::max(1, (slots + ncb - 1) / ncb);
