@@ -610,6 +610,19 @@ int orc_window(const orc_ctx* c) {
   return W;
 }
 
+/* The same over the pairs of the given rows only (storage for assembling those rows). */
+int orc_window_rows(const orc_ctx* c, const int64_t* rows, int64_t nrows) {
+  int W = 0;
+#pragma omp parallel for reduction(max : W) schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrows; ++r)
+    for (int64_t j = 0; j < c->ne; ++j) {
+      int lo, hi;
+      pair_window(c, rows[r], j, &lo, &hi);
+      if (hi - lo + 1 > W) W = hi - lo + 1;
+    }
+  return W;
+}
+
 /* ------------------------------------------------------------------ */
 /* Assembly of the rows `rows` of every Zt^(m):
      m_lo[r*ne + j] = first lag of the window of (rows[r], j)

@@ -51,6 +51,8 @@ def lib():
         L.orc_edges.argtypes = [ctypes.c_void_p, c_int32_p, c_int32_p, c_int32_p]
         L.orc_window.argtypes = [ctypes.c_void_p]
         L.orc_window.restype = ctypes.c_int
+        L.orc_window_rows.argtypes = [ctypes.c_void_p, c_int64_p, ctypes.c_int64]
+        L.orc_window_rows.restype = ctypes.c_int
         L.orc_inner.argtypes = [ctypes.c_void_p, c_double_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                 c_double_p, c_double_p, c_double_p, c_double_p]
         L.orc_inner.restype = ctypes.c_int
@@ -152,7 +154,9 @@ class Oracle:
         if full and self._full is not None:
             return self._full
         rows = np.arange(self.ne, dtype=np.int64) if full else np.ascontiguousarray(rows, dtype=np.int64)
-        W = self.window()
+        # the storage window: over all pairs once for a full assembly, over the
+        # requested rows' pairs otherwise
+        W = self.window() if full else int(lib().orc_window_rows(self._h, _p(rows, c_int64_p), len(rows)))
         m_lo = np.zeros((len(rows), self.ne), np.int32)
         Zw = np.zeros((len(rows), self.ne, W), np.float64)
         rc = lib().orc_assemble(self._h, _p(rows, c_int64_p), len(rows), W, _p(m_lo, c_int32_p), _p(Zw, c_double_p))

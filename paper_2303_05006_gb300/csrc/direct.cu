@@ -648,21 +648,30 @@ __global__ void __launch_bounds__(kDtWarps * 32, 3)
   }
 }
 
-// R_i = V_i - (sum_k partial[k*ne + i] over the nparts partials of row i, in
-// the order k = 0, 1, ..., then the row's lag-2 entries l2 against J^{alpha-2}
-// in FP64, in stored order).  V may be null (zero) and may alias R.
+// R_i = V_i - (the nparts partials of row i plus the row's lag-2 entries l2
+// against J^{alpha-2}, in FP64).  Eight lanes share a row: lane s of the group
+// adds the partials k = s, s + 8, ... and the lag-2 entries e = s, s + 8, ...
+// in order, and the eight sums meet in a fixed shuffle tree, so the result
+// does not depend on scheduling.  V may be null (zero) and may alias R.
+constexpr int kRedLanes = 8;
+
 __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t ne, const int64_t* l2_ptr,
                                 const int32_t* l2_col, const double* l2_val, const double* ring, int32_t L,
                                 int32_t alpha, const double* V, double* R) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= ne) return;
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRedLanes;
+  const int sub = threadIdx.x % kRedLanes;
   double t = 0.0;
-  for (int k = 0; k < nparts; ++k) t += partial[(int64_t)k * ne + i];
-  if (alpha >= 2) {
-    const int slot = (alpha - 2) & (L - 1);
-    for (int64_t e = l2_ptr[i]; e < l2_ptr[i + 1]; ++e) t += l2_val[e] * ring[(int64_t)l2_col[e] * L + slot];
+  if (i < ne) {
+    for (int k = sub; k < nparts; k += kRedLanes) t += partial[(int64_t)k * ne + i];
+    if (alpha >= 2) {
+      const int slot = (alpha - 2) & (L - 1);
+      for (int64_t e = l2_ptr[i] + sub; e < l2_ptr[i + 1]; e += kRedLanes)
+        t += l2_val[e] * ring[(int64_t)l2_col[e] * L + slot];
+    }
   }
-  R[i] = (V ? V[i] : 0.0) - t;
+#pragma unroll
+  for (int d = kRedLanes / 2; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+  if (i < ne && sub == 0) R[i] = (V ? V[i] : 0.0) - t;
 }
 
 // Lag-2 entries of the direct store, as a CSR over rows (before the split).
@@ -890,7 +899,7 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
     }
     if (march) c->dahead[buf] = 0;
     cudaEvent_t e = c->prof_begin(10);
-    k_direct_reduce<<<(unsigned)((c->ne + 255) / 256), 256, 0, c->stream>>>(
+    k_direct_reduce<<<(unsigned)((c->ne * kRedLanes + 255) / 256), 256, 0, c->stream>>>(
         c->d_dpart + buf * nparts * c->ne, (int32_t)nparts, c->ne, c->d_l2_ptr, c->d_l2_col, c->d_l2_val, d_ring,
         c->L, alpha, V, c->d_R);
     c->prof_end(10, e);
