@@ -124,9 +124,23 @@ typedef struct {
                                  It has degree 2 in each coordinate and 3 in t and s, so the space-time
                                  interpolation reproduces it exactly for p_s >= 3 and p_t >= 4: the far field
                                  then equals its plain windowed sum up to rounding, whatever the tree;
-                              2: zero (no far field: the history sum is the near field alone).
+                              2: zero (no far field: the history sum is the near field alone);
+                              3: as 1 with the Chebyshev quadratic T2(x) = 2x^2 - 1 for T3: degree 2 in every
+                                 variable, reproduced exactly by both interpolants (s_interp, t_interp) for
+                                 p_s, p_t >= 3.
                             The window of source intervals, the truncated J-hat and the time gating are the
                             same for every choice. */
+  int32_t s_interp;      /* fast mode, interpolation in space: 0 (default) Lagrange on p_s Chebyshev nodes per
+                            direction of each cell; 1 the paper's CHI (section 3.2): piecewise cubic Hermite on
+                            p_s >= 2 uniformly spaced nodes per direction (the cell's faces included), the node
+                            derivatives finite differences of the node values (central inside, second-order
+                            one-sided at the faces, first-order when p_s = 2).  CHI reproduces quadratics */
+  int32_t t_interp;      /* fast mode, interpolation in time, the same two choices on the p_t nodes of each
+                            interval.  far_kernel = 1 (cubic in time) is reproduced exactly by t_interp = 0 only */
+  int32_t a_deriv;       /* fast mode, where the far field's vector potential takes its two time derivatives
+                            (section 4.3.2): 0 (default) the paper's split, one on the interpolated kernel
+                            (dU/dt) and one on the target's time factor; 1 both on the target factor (U
+                            interpolated); 2 both on the kernel (d^2U/dt^2, a step in time, interpolated) */
   int64_t max_device_bytes; /* device memory budget of the context's own allocations (0: none).  An allocation
                                that would exceed it fails as if the device were full: tdbem_create returns
                                TDBEM_ENOMEM with nothing left allocated.  Per-call temporaries of
@@ -143,7 +157,7 @@ typedef struct {
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
    jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1, far_kernel=0,
-   max_device_bytes=0. */
+   s_interp=0, t_interp=0, a_deriv=0, max_device_bytes=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),

@@ -174,10 +174,11 @@ def jhat_window(J, G, g0, g1):
 
 
 def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi=1.0, eps=1.0, mu=1.0,
-                   absolute=False):
+                   absolute=False, tdeg=3):
     """sum over far triangle pairs of the tested coefficients times J, for the
     polynomial kernel K(x, y, t, s) = (1 + |x - y|^2) T3((t - s)/ts - 1), with
-    T3(x) = 4x^3 - 3x (the Chebyshev cubic) and ts = 64 dt, on rows
+    T3(x) = 4x^3 - 3x (the Chebyshev cubic; with tdeg=2 the quadratic
+    T2(x) = 2x^2 - 1 instead) and ts = 64 dt, on rows
     `rows` at target step alpha (the part of R^{alpha-1} = V - near - far that
     the far field contributes with a minus sign).  J[b] = J^b ([n_hist][ne]).
 
@@ -225,7 +226,10 @@ def far_field_poly(h: Hierarchy, edges, rows, J, alpha, theta=1.0, zeta=1.0, chi
         if (G, g0, g1) not in tsum:
             Jh = jhat_window(J, G, g0, g1)                               # [n, ne]
             x = (alpha - np.arange(g0, g1 + 1)) * dt / ts - 1.0
-            T = [4 * x ** 3 - 3 * x, 12 * x ** 2 - 3, 24 * x]            # T3 and its x-derivatives
+            if tdeg == 3:
+                T = [4 * x ** 3 - 3 * x, 12 * x ** 2 - 3, 24 * x]        # T3 and its x-derivatives
+            else:
+                T = [2 * x ** 2 - 1, 4 * x, 4 + 0 * x]                   # T2 and its x-derivatives
             if absolute:
                 Jh, T = np.abs(Jh), [np.abs(v) for v in T]
             tsum[(G, g0, g1)] = np.stack([v @ Jh for v in T])

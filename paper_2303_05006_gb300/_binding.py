@@ -31,7 +31,9 @@ class Params(ctypes.Structure):
                 ("warm_start", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
                 ("m2l_tile_rows", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double),
-                ("far_kernel", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64)]
+                ("far_kernel", ctypes.c_int32), ("s_interp", ctypes.c_int32), ("t_interp", ctypes.c_int32),
+                ("a_deriv", ctypes.c_int32),
+                ("max_device_bytes", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):

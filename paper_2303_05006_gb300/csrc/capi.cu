@@ -41,7 +41,8 @@ namespace {
 constexpr char kCkMagic[8] = {'T', 'D', 'B', 'E', 'M', 'C', 'K', '1'};
 
 struct CkHeader {
-  int32_t mode, n_rhs, L, Nt, alpha, p_s, p_t, n_leaf, far_kernel, m2l_prec, nbuf, pad;
+  int32_t mode, n_rhs, L, Nt, alpha, p_s, p_t, n_leaf, far_kernel, m2l_prec, nbuf;
+  int32_t interp;  // s_interp | t_interp << 1 | a_deriv << 2 (0: the defaults)
   int64_t ne, nt;
   double dt, theta, zeta, chi;
   uint64_t mesh_hash;  // FNV-1a of the vertex and triangle arrays
@@ -65,6 +66,7 @@ CkHeader ck_header(const tdbem_ctx* c, int32_t nbuf) {
   h.p_t = c->p.p_t;
   h.n_leaf = c->p.n_leaf;
   h.far_kernel = c->p.far_kernel;
+  h.interp = c->p.s_interp | c->p.t_interp << 1 | c->p.a_deriv << 2;
   h.m2l_prec = c->p.m2l_prec;
   h.nbuf = nbuf;
   h.ne = c->ne;
@@ -189,7 +191,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
       p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||
-      p.far_kernel < 0 || p.far_kernel > 2 || p.max_device_bytes < 0 ||
+      p.far_kernel < 0 || p.far_kernel > 3 || p.max_device_bytes < 0 || p.s_interp < 0 || p.s_interp > 1 ||
+      p.t_interp < 0 || p.t_interp > 1 || p.a_deriv < 0 || p.a_deriv > 2 ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();

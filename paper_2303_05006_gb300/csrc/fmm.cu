@@ -183,13 +183,101 @@ __host__ __device__ inline void lagrange(int p, double x, double* l, double* dl)
   }
 }
 
+// The paper's CHI (section 3.2), read as piecewise cubic Hermite interpolation
+// on n >= 2 uniformly spaced nodes of [-1, 1] (the interval's ends included),
+// the node derivatives being finite differences of the node values: central
+// inside, second-order one-sided at the ends (first-order when n = 2).  It is
+// linear in the node values and reproduces polynomials of degree 2.  l[j] is
+// the interpolant of the node data e_j at x, dl and d2l its first two
+// derivatives (either may be null).
+__host__ __device__ inline double chi_node(int a, int n) { return -1.0 + 2.0 * a / (n - 1); }
+
+// h times the finite-difference derivative at node q of the node data e_j
+__host__ __device__ inline double chi_fd(int q, int j, int n) {
+  auto f = [j](int r) { return r == j ? 1.0 : 0.0; };
+  if (n == 2) return f(1) - f(0);
+  if (q == 0) return 0.5 * (-3.0 * f(0) + 4.0 * f(1) - f(2));
+  if (q == n - 1) return 0.5 * (3.0 * f(n - 1) - 4.0 * f(n - 2) + f(n - 3));
+  return 0.5 * (f(q + 1) - f(q - 1));
+}
+
+__host__ __device__ inline void chi_basis(int n, double x, double* l, double* dl, double* d2l) {
+  const double h = 2.0 / (n - 1);
+  int k = (int)floor((x + 1.0) / h);
+  k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+  const double t = (x + 1.0) / h - k;
+  // Hermite cubics on [0, 1]: values h00 h10 h01 h11, first (g) and second (s) derivatives in t
+  const double h00 = 2 * t * t * t - 3 * t * t + 1, h10 = t * t * t - 2 * t * t + t;
+  const double h01 = -2 * t * t * t + 3 * t * t, h11 = t * t * t - t * t;
+  const double g00 = 6 * t * t - 6 * t, g10 = 3 * t * t - 4 * t + 1, g01 = -6 * t * t + 6 * t, g11 = 3 * t * t - 2 * t;
+  const double s00 = 12 * t - 6, s10 = 6 * t - 4, s01 = -12 * t + 6, s11 = 6 * t - 2;
+  for (int j = 0; j < n; ++j) {
+    const double f0 = k == j ? 1.0 : 0.0, f1 = k + 1 == j ? 1.0 : 0.0;
+    const double m0 = chi_fd(k, j, n), m1 = chi_fd(k + 1, j, n);
+    l[j] = h00 * f0 + h10 * m0 + h01 * f1 + h11 * m1;
+    if (dl) dl[j] = (g00 * f0 + g10 * m0 + g01 * f1 + g11 * m1) / h;
+    if (d2l) d2l[j] = (s00 * f0 + s10 * m0 + s01 * f1 + s11 * m1) / (h * h);
+  }
+}
+
+// Interpolation in space (tdbem_params.s_interp) and in time (t_interp):
+// 0 Lagrange polynomials on the Chebyshev nodes above (degree n - 1), 1 CHI.
+__host__ __device__ inline double interp_node(int a, int n, int interp) {
+  return interp == 1 ? chi_node(a, n) : cheb_node(a, n);
+}
+
+__host__ __device__ inline void space_basis(int p, int interp, double x, double* l, double* dl) {
+  if (interp == 1)
+    chi_basis(p, x, l, dl, nullptr);
+  else
+    lagrange(p, x, l, dl);
+}
+
+// The vector potential's second time derivative (tdbem_params.a_deriv): how
+// many of the two the interpolated kernel K_A carries, and which time factor
+// of the L2P table the target takes (0 l, 1 l'/h_t, 3 l''/h_t^2).
+inline int a_kernel_derivs(int a_deriv) { return a_deriv == 0 ? 1 : (a_deriv == 1 ? 0 : 2); }
+inline int a_target_kind(int a_deriv) { return a_deriv == 0 ? 1 : (a_deriv == 1 ? 3 : 0); }
+
+// l[a], l'[a], l''[a] of the time basis at x (any of dl, d2l may be null).
+inline void time_basis(int pt, int interp, double x, double* l, double* dl, double* d2l) {
+  if (interp == 1) {
+    chi_basis(pt, x, l, dl, d2l);
+    return;
+  }
+  // Lagrange: monomial coefficients of each cardinal polynomial, then Horner
+  double w[8];
+  for (int a = 0; a < pt; ++a) w[a] = cheb_node(a, pt);
+  for (int a = 0; a < pt; ++a) {
+    double cf[9] = {1.0};  // cf[k]: coefficient of x^k, degree grows to pt - 1
+    int deg = 0;
+    double den = 1.0;
+    for (int b = 0; b < pt; ++b) {
+      if (b == a) continue;
+      for (int k = deg + 1; k >= 1; --k) cf[k] = cf[k - 1] - w[b] * cf[k];
+      cf[0] = -w[b] * cf[0];
+      ++deg;
+      den *= w[a] - w[b];
+    }
+    double v = 0, d1 = 0, d2 = 0;
+    for (int k = deg; k >= 0; --k) {
+      d2 = d2 * x + 2.0 * d1;
+      d1 = d1 * x + v;
+      v = v * x + cf[k];
+    }
+    l[a] = v / den;
+    if (dl) dl[a] = d1 / den;
+    if (d2l) d2l[a] = d2 / den;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Setup kernels
 
 // P2M table W[t][k][c][b] (exact collapsed-Gauss source rule, nq points) and
 // L2P table T[t][k][c][a] (the 7-point outer rule), relative to the leaf box
 // of each triangle.
-__global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* box /*[nt][4] centre, H*/,
+__global__ void k_far_tables(TriGeom g, Phys ph, int p, int sint, int nt, const double* box /*[nt][4] centre, H*/,
                              const double* qu, const double* qwt, int nq1, float* W, float* T) {
   int t = blockIdx.x;
   if (t >= nt) return;
@@ -215,9 +303,9 @@ __global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* bo
         double y[3];
         for (int q = 0; q < 3; ++q) y[q] = l0 * v[q] + l1 * v[3 + q] + l2 * v[6 + q];
         double L1[8], D1[8], L2[8], D2[8], L3[8], D3[8];
-        lagrange(p, (y[0] - cx) / H, L1, D1);
-        lagrange(p, (y[1] - cy) / H, L2, D2);
-        lagrange(p, (y[2] - cz) / H, L3, D3);
+        space_basis(p, sint, (y[0] - cx) / H, L1, D1);
+        space_basis(p, sint, (y[1] - cy) / H, L2, D2);
+        space_basis(p, sint, (y[2] - cz) / H, L3, D3);
         double lb = L1[b1] * L2[b2] * L3[b3];
         double gr[3] = {D1[b1] * L2[b2] * L3[b3] / H, L1[b1] * D2[b2] * L3[b3] / H, L1[b1] * L2[b2] * D3[b3] / H};
         double f[3] = {cf * (y[0] - o[0]), cf * (y[1] - o[1]), cf * (y[2] - o[2])};
@@ -237,9 +325,9 @@ __global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* bo
       for (int u = 0; u < 3; ++u) x[u] = ph.qb[q][0] * v[u] + ph.qb[q][1] * v[3 + u] + ph.qb[q][2] * v[6 + u];
       double wq = ph.qw[q] * A;
       double L1[8], L2[8], L3[8];
-      lagrange(p, (x[0] - cx) / H, L1, nullptr);
-      lagrange(p, (x[1] - cy) / H, L2, nullptr);
-      lagrange(p, (x[2] - cz) / H, L3, nullptr);
+      space_basis(p, sint, (x[0] - cx) / H, L1, nullptr);
+      space_basis(p, sint, (x[1] - cy) / H, L2, nullptr);
+      space_basis(p, sint, (x[2] - cz) / H, L3, nullptr);
       double la = L1[b1] * L2[b2] * L3[b3];
       double f[3] = {cf * (x[0] - o[0]), cf * (x[1] - o[1]), cf * (x[2] - o[2])};
       double fxn[3] = {f[1] * nin[2] - f[2] * nin[1], f[2] * nin[0] - f[0] * nin[2], f[0] * nin[1] - f[1] * nin[0]};
@@ -259,12 +347,16 @@ __global__ void k_far_tables(TriGeom g, Phys ph, int p, int nt, const double* bo
 }
 
 // M2L operators of one level: for canonical offset cv[op] and lag qv[op],
-// ops[op][kind][(a,m)][(b,n)], kind 0 = K_A, 1 = K_phi.  kern selects the
-// kernel pair (tdbem_params.far_kernel): 0 the truncated powers of the method,
-// 1 the polynomial check kernel K_phi = (1 + r^2) T3(tau/(64 dt) - 1) with its
-// time derivative, 2 zero.
+// ops[op][kind][(a,m)][(b,n)], kind 0 = the vector potential's kernel K_A,
+// 1 = K_phi.  kern selects the kernel pair (tdbem_params.far_kernel): 0 the
+// truncated powers of the method, 1 the polynomial check kernel K_phi =
+// (1 + r^2) T3(tau/(64 dt) - 1), 2 zero, 3 the check kernel with T2 for T3.  adeg is the number of time
+// derivatives K_A carries (tdbem_params.a_deriv): 1 (the paper's split, the
+// other on the target factor), 0 (both on the target factor) or 2 (both on the
+// kernel).  interp places the time nodes (tdbem_params.t_interp).
 __global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, double dt, double cc, double a,
-                          const int4* opdesc /* {c1,c2,c3,q} */, int nop, int kern, float* ops) {
+                          const int4* opdesc /* {c1,c2,c3,q} */, int nop, int kern, int adeg, int sint, int interp,
+                          float* ops) {
   const int PS = p * p * p, P = PS * pt;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t total = (int64_t)nop * P * P;
@@ -278,21 +370,26 @@ __global__ void k_m2l_ops(int p, int pt, double ds, double H, double ht, int M, 
   int cv[3] = {d.x, d.y, d.z};
   double r2 = 0.0;
   for (int k = 0; k < 3; ++k) {
-    double dx = cv[k] * ds + H * (cheb_node(ai[k], p) - cheb_node(bi[k], p));
+    double dx = cv[k] * ds + H * (interp_node(ai[k], p, sint) - interp_node(bi[k], p, sint));
     r2 += dx * dx;
   }
   double r = sqrt(r2);
-  double tau = (d.w * M + 1) * dt + ht * (cheb_node(m, pt) - cheb_node(n, pt));
+  double tau = (d.w * M + 1) * dt + ht * (interp_node(m, pt, interp) - interp_node(n, pt, interp));
   double u = cc * tau - r;
   double kphi = 0.0, kA = 0.0;
   if (kern == 1) {
-    // (1 + r^2) T3(tau/ts - 1), T3(x) = 4x^3 - 3x, ts = 64 dt, and its time derivative
+    // (1 + r^2) T3(tau/ts - 1), T3(x) = 4x^3 - 3x, ts = 64 dt, and its time derivatives
     const double g = 1.0 + r2, ts = 64.0 * dt, x = tau / ts - 1.0;
     kphi = g * (4.0 * x * x * x - 3.0 * x);
-    kA = g * (12.0 * x * x - 3.0) / ts;
+    kA = adeg == 0 ? kphi : (adeg == 1 ? g * (12.0 * x * x - 3.0) / ts : g * 24.0 * x / (ts * ts));
+  } else if (kern == 3) {
+    // (1 + r^2) T2(tau/ts - 1), T2(x) = 2x^2 - 1: degree 2 in every variable
+    const double g = 1.0 + r2, ts = 64.0 * dt, x = tau / ts - 1.0;
+    kphi = g * (2.0 * x * x - 1.0);
+    kA = adeg == 0 ? kphi : (adeg == 1 ? g * 4.0 * x / ts : g * 4.0 / (ts * ts));
   } else if (kern == 0 && u > 0.0) {
     kphi = u * u / (r * a * a);
-    kA = 2.0 * cc * u / (r * a * a);
+    kA = adeg == 0 ? kphi : (adeg == 1 ? 2.0 * cc * u / (r * a * a) : 2.0 * cc * cc / (r * a * a));
   }
   ops[((int64_t)op * 2 + 0) * P * P + rc] = (float)kA;
   ops[((int64_t)op * 2 + 1) * P * P + rc] = (float)kphi;
@@ -626,7 +723,7 @@ __global__ void k_l2l(const int32_t* cells, const int32_t* child, const float* S
 // the local-coefficient slot is cleared afterwards.
 __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int32_t* tri_e, const int32_t* perm,
                       const TriGeom g, const float* T, const float* ttgt, int p, int pt, int M, int k, float* loc,
-                      int Q, double* Rfar, int Lr, int64_t ne, int R, int s0, int ns, int clear) {
+                      int Q, double* Rfar, int Lr, int64_t ne, int R, int s0, int ns, int clear, int akind) {
   extern __shared__ float sm[];
   const int PS = p * p * p, P = PS * pt;
   const int rhs = blockIdx.y;
@@ -639,9 +736,10 @@ __global__ void k_l2p(const int32_t* leaf_cells, const int32_t* tri_b, const int
   for (int e = threadIdx.x; e < ns * kNC * PS; e += blockDim.x) {
     int i = s0 + e / (kNC * PS), r = e % (kNC * PS);
     int c = r / PS, a = r % PS;
-    int kind = (c < 3) ? 1 : (c == 3 ? 0 : 2);  // A: l', phi: l, mag: chi l' + zeta l
+    // A: l' (or l'' / l by the placement of its time derivatives), phi: l, mag: chi l' + zeta l
+    int kind = (c < 3) ? akind : (c == 3 ? 0 : 2);
     float s = 0.f;
-    for (int m = 0; m < pt; ++m) s += L[(int64_t)c * P + a * pt + m] * ttgt[(i * 3 + kind) * pt + m];
+    for (int m = 0; m < pt; ++m) s += L[(int64_t)c * P + a * pt + m] * ttgt[(i * 4 + kind) * pt + m];
     Le[e] = s;
   }
   __syncthreads();
@@ -1135,18 +1233,20 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     if (L.nnonleaf)
       TDBEM_CUDA_TRY(
           c, cudaMemcpy(L.d_nonleaf_cells, nlc.data(), L.nnonleaf * sizeof(int32_t), cudaMemcpyHostToDevice));
-    // time tables
-    std::vector<float> ts(L.M * pt), tt(L.M * 3 * pt);
+    // time tables: source factors, and per target step the factors of the
+    // four kinds l, l'/h_t, chi l'/h_t + zeta l, l''/h_t^2
+    std::vector<float> ts(L.M * pt), tt(L.M * 4 * pt);
     const double ht = 0.5 * L.M * dt;
     for (int i = 0; i < L.M; ++i) {
       double xi = (i - 0.5 * (L.M - 1)) / (0.5 * L.M);
-      double lv[8], dv[8];
-      lagrange(pt, xi, lv, dv);
+      double lv[8], dv[8], d2v[8];
+      time_basis(pt, c->p.t_interp, xi, lv, dv, d2v);
       for (int n = 0; n < pt; ++n) {
         ts[i * pt + n] = (float)lv[n];
-        tt[(i * 3 + 0) * pt + n] = (float)lv[n];
-        tt[(i * 3 + 1) * pt + n] = (float)(dv[n] / ht);
-        tt[(i * 3 + 2) * pt + n] = (float)(c->p.chi * dv[n] / ht + c->p.zeta * lv[n]);
+        tt[(i * 4 + 0) * pt + n] = (float)lv[n];
+        tt[(i * 4 + 1) * pt + n] = (float)(dv[n] / ht);
+        tt[(i * 4 + 2) * pt + n] = (float)(c->p.chi * dv[n] / ht + c->p.zeta * lv[n]);
+        tt[(i * 4 + 3) * pt + n] = (float)(d2v[n] / (ht * ht));
       }
     }
     if ((s = c->dalloc(&L.d_tsrc, ts.size())) || (s = c->dalloc(&L.d_ttgt, tt.size()))) return s;
@@ -1295,7 +1395,9 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_tiles, tiles.data(), L.ntiles * sizeof(int4), cudaMemcpyHostToDevice));
       int64_t tot = (int64_t)L.nop * P * P;
       k_m2l_ops<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(p, pt, L.ds, L.H, 0.5 * L.M * dt, L.M, dt, cc, a,
-                                                                      d_opdesc, L.nop, c->p.far_kernel, L.ops);
+                                                                      d_opdesc, L.nop, c->p.far_kernel,
+                                                                      a_kernel_derivs(c->p.a_deriv), c->p.s_interp,
+                                                                      c->p.t_interp, L.ops);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
       if (c->p.m2l_prec != TDBEM_P_FP32 && (s = tdbem_m2l_tc_images(c, L.ops, L.nop, P, c->p.m2l_prec, &L.ops_img)))
         return s;
@@ -1320,17 +1422,17 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       double Hp = F->lev[l].H, Hc = F->lev[l + 1].H, dsp = F->lev[l].ds;
       for (int sgn = 0; sgn < 2; ++sgn)
         for (int cb = 0; cb < p; ++cb) {
-          double xi = ((sgn ? 0.25 : -0.25) * dsp + Hc * cheb_node(cb, p)) / Hp;
+          double xi = ((sgn ? 0.25 : -0.25) * dsp + Hc * interp_node(cb, p, c->p.s_interp)) / Hp;
           double lv[8];
-          lagrange(p, xi, lv, nullptr);
+          space_basis(p, c->p.s_interp, xi, lv, nullptr);
           for (int b = 0; b < p; ++b) Sx[((l * 2 + sgn) * p + b) * p + cb] = (float)lv[b];
         }
     }
     for (int h = 0; h < 2; ++h)
       for (int cn = 0; cn < pt; ++cn) {
-        double xi = 0.5 * cheb_node(cn, pt) + (h ? 0.5 : -0.5);
+        double xi = 0.5 * interp_node(cn, pt, c->p.t_interp) + (h ? 0.5 : -0.5);
         double lv[8];
-        lagrange(pt, xi, lv, nullptr);
+        time_basis(pt, c->p.t_interp, xi, lv, nullptr, nullptr);
         for (int n = 0; n < pt; ++n) St[(h * pt + n) * pt + cn] = (float)lv[n];
       }
     if ((s = c->dalloc(&F->d_Sx, Sx.size())) || (s = c->dalloc(&F->d_St, St.size()))) return s;
@@ -1370,7 +1472,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     TDBEM_CUDA_TRY(c, cudaMemcpy(d_box, tbox.data(), 4 * nt * sizeof(double), cudaMemcpyHostToDevice));
     TDBEM_CUDA_TRY(c, cudaMemcpy(d_qx, qx.data(), nq1 * sizeof(double), cudaMemcpyHostToDevice));
     TDBEM_CUDA_TRY(c, cudaMemcpy(d_qw, qw.data(), nq1 * sizeof(double), cudaMemcpyHostToDevice));
-    k_far_tables<<<(unsigned)nt, 256, 0, c->stream>>>(c->tg, c->phys, p, (int)nt, d_box, d_qx, d_qw, nq1, F->d_W,
+    k_far_tables<<<(unsigned)nt, 256, 0, c->stream>>>(c->tg, c->phys, p, c->p.s_interp, (int)nt, d_box, d_qx, d_qw, nq1, F->d_W,
                                                        F->d_T);
     TDBEM_CUDA_TRY(c, cudaGetLastError());
   }
@@ -1571,7 +1673,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
         const size_t smem = (size_t)ns * kNC * PS * sizeof(float);
         k_l2p<<<dim3(L.nleaf, R), 256, smem, c->stream>>>(L.d_leaf_cells, L.d_tri_b, L.d_tri_e, F->d_perm, c->tg,
                                                            F->d_T, L.d_ttgt, p, pt, L.M, k, LOC(l), L.Q, Rfar, F->Lr,
-                                                           c->ne, R, s0, ns, s0 + ns >= L.M ? 1 : 0);
+                                                           c->ne, R, s0, ns, s0 + ns >= L.M ? 1 : 0,
+                                                           a_target_kind(c->p.a_deriv));
         TDBEM_CUDA_TRY(c, cudaGetLastError());
       }
       c->prof_end(7, e);

@@ -119,14 +119,20 @@ def test_hierarchy_matches_table1(ns, subdiv):
     assert 3 <= h.M(h.lmax) <= row[2]
 
 
-def test_planted_window_faults_exceed_the_gpu_bar():
+@pytest.mark.parametrize("tdeg", [3, 2])
+def test_planted_window_faults_exceed_the_gpu_bar(tdeg):
     """The GPU exactness check (tests/test_gpu_far_exact.py) compares the
     library's far field with far_field_poly at a bar of TOL of the largest
     value.  On its own mesh, history and rows, each planted bookkeeping fault
     moves the reference by at least 50 TOL: the newest interval dropped
     (q_lo + 1) at every step, and, once the windows reach back past the first
     step, the oldest interval dropped (q_hi - 1) or the window start left
-    untruncated."""
+    untruncated.  Both check kernels: T3 in time, and T2 (the one the CHI
+    interpolant reproduces).  With T2 the oldest interval is invisible: the
+    third difference J-hat summed against a quadratic in time telescopes to
+    terms at the window's ends, and the truncation at the start removes those
+    there, so the sum depends on the newest end alone (the T3 check covers
+    q_hi)."""
     import oracle.far_window as fw
     from oracle.far_window import Hierarchy, far_field_poly
     from oracle.oracle import Oracle
@@ -149,12 +155,13 @@ def test_planted_window_faults_exceed_the_gpu_bar():
         "untruncated": lambda: setattr(fw, "jhat_window", lambda J_, G, g0, g1: orig_jh(J_, G - 8, g0, g1)),
     }
     try:
-        for alpha, names in ((12, ["q_lo + 1"]), (150, list(faults))):
-            ref = far_field_poly(h, ed, rows, J[: alpha - 1], alpha)
+        late = list(faults) if tdeg == 3 else ["q_lo + 1", "untruncated"]
+        for alpha, names in ((12, ["q_lo + 1"]), (150, late)):
+            ref = far_field_poly(h, ed, rows, J[: alpha - 1], alpha, tdeg=tdeg)
             scale = np.abs(ref).max()
             for name in names:
                 faults[name]()
-                planted = far_field_poly(h, ed, rows, J[: alpha - 1], alpha)
+                planted = far_field_poly(h, ed, rows, J[: alpha - 1], alpha, tdeg=tdeg)
                 fw.Hierarchy.lag_range, fw.jhat_window = orig_lr, orig_jh
                 assert np.abs(planted - ref).max() >= 50 * TOL * scale, (alpha, name)
     finally:

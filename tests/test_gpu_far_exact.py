@@ -12,7 +12,11 @@ window truncated at its start, the full and truncated moment sets through
 M2M -- and FP32 rounding.  far_kernel = 2 zeroes the far field, so the
 difference of the two history evaluations is the library's far field alone.
 It must equal the oracle's plain windowed sum (oracle/far_window.py, pinned to
-Appendix A's identity and to Table 1 on the CPU) row by row.
+Appendix A's identity and to Table 1 on the CPU) row by row.  The same holds
+with the paper's CHI interpolant (section 3.2) in space, and in time for the
+check kernel with the Chebyshev quadratic T2 (CHI reproduces degree 2), and
+for each placement of the vector potential's two time derivatives (section
+4.3.2): every stage then reproduces the kernel.
 
 Bar: the far field runs in FP32 (moments, operators, local coefficients) with
 FP64 accumulation into the right-hand side.  In the J-hat form the windowed
@@ -52,15 +56,25 @@ def _smooth_history(ne, n, seed):
     return np.sin(2 * np.pi * np.arange(n)[:, None] / P[None, :] + ph[None, :])
 
 
-@pytest.mark.parametrize("prec", [0, 4])  # FP32 CUDA cores, TF32x3 tensor cores
-def test_far_field_equals_windowed_sum(setup, prec):
+# (M2L precision, check kernel, s_interp, t_interp, a_deriv): FP32 CUDA cores
+# and TF32x3 tensor cores; the T3 kernel under Lagrange interpolation, with
+# CHI in space, and with the two other placements of the vector potential's
+# time derivatives; the T2 kernel (degree 2 in time, which CHI reproduces)
+# under CHI in space and time, with every placement.
+CASES = [(0, 1, 0, 0, 0), (4, 1, 0, 0, 0), (4, 1, 1, 0, 0), (4, 1, 0, 0, 1), (4, 1, 0, 0, 2),
+         (4, 3, 1, 1, 0), (4, 3, 1, 1, 1), (4, 3, 1, 1, 2)]
+
+
+@pytest.mark.parametrize("prec,kern,s_interp,t_interp,a_deriv", CASES)
+def test_far_field_equals_windowed_sum(setup, prec, kern, s_interp, t_interp, a_deriv):
     from oracle.far_window import far_field_poly
     from paper_2303_05006_gb300 import Solver
 
     v, t, dt, h, edges = setup
     Nt = 200
-    kw = dict(mode=1, p_s=4, p_t=4, n_leaf=16, m2l_prec=prec)
-    s1 = Solver(v, t, dt, Nt, far_kernel=1, **kw)
+    kw = dict(mode=1, p_s=4, p_t=4, n_leaf=16, m2l_prec=prec, s_interp=s_interp, t_interp=t_interp,
+              a_deriv=a_deriv)
+    s1 = Solver(v, t, dt, Nt, far_kernel=kern, **kw)
     s2 = Solver(v, t, dt, Nt, far_kernel=2, **kw)
     inf = s1.info()
     # the library's hierarchy is the oracle's
@@ -75,11 +89,11 @@ def test_far_field_equals_windowed_sum(setup, prec):
     for alpha in (M2 + 1, 2 * M2, 3 * M2 + 2, 61, 150, Nt - 1):
         Jh = J[: alpha - 1]
         far = s2.history_eval(alpha, Jh) - s1.history_eval(alpha, Jh)
-        ref = far_field_poly(h, edges, rows, Jh, alpha)
+        ref = far_field_poly(h, edges, rows, Jh, alpha, tdeg=3 if kern == 1 else 2)
         scale = np.max(np.abs(ref))
         assert scale > 0
         err = np.max(np.abs(far[rows] - ref))
-        assert err <= TOL * scale, (prec, alpha, err / scale)
+        assert err <= TOL * scale, (alpha, err / scale)
     s1.close()
     s2.close()
 
