@@ -6,7 +6,7 @@ solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
 already resident in HBM.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3|tf32x3] [--p P]
+                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3|tf32x3|f16x3] [--p P]
                   [--rhs R] [--workload NAME] [--no-compare] [--no-cpu-baseline]
 
 --rhs R marches R incident plane waves on the same scatterer in one batch
@@ -185,7 +185,7 @@ def batch_pulses(w, n: int, seed: int = 4):
 # event of 152.9 MB per gating period of six launches
 M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
 
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4, "f16x3": 5}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack",
            "history_split", "history_reduce"]
 
@@ -204,7 +204,7 @@ def roofline(args, info, launches, ms, K, W):
             return {"kernel": name, "bound": "alu", "achieved": tflops, "peak": 80.5, "unit": "TFLOP/s",
                     "frac": tflops / 80.5, "traffic": None, "peak_source": "derived: FP32 lanes x clock",
                     "flops_per_launch": flops / max(launches[dom], 1)}
-        peak = bf16 if args.prec in ("bf16", "bf16x3") else bf16 * 1.1 / 2.25
+        peak = bf16 if args.prec in ("bf16", "bf16x3", "f16x3") else bf16 * 1.1 / 2.25
         how = f"{src} bf16_tflops" + ("" if not args.prec.startswith("tf32") else " x 1.1/2.25 (nominal TF32/BF16)")
         # DRAM bytes of one launch from the committed ncu capture of this kernel and configuration
         traffic = (M2L_TRAFFIC_TF32X3 if (M2L_TRAFFIC_TF32X3 and args.prec == "tf32x3" and args.p == 4

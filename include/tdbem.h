@@ -77,7 +77,11 @@ typedef enum {
   TDBEM_P_TF32 = 1,   /* TF32 tensor cores, FP32 accumulate */
   TDBEM_P_BF16 = 2,   /* BF16 tensor cores, FP32 accumulate */
   TDBEM_P_BF16X3 = 3, /* split-precision BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
-  TDBEM_P_TF32X3 = 4  /* split-precision TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  TDBEM_P_TF32X3 = 4, /* split-precision TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  TDBEM_P_F16X3 = 5   /* split-precision FP16 (hi*hi + hi*lo + lo*hi), FP32 accumulate, on the FP16 rate
+                         (twice TF32's): each operator and each moment column is scaled by a power of two
+                         (exact) that brings its largest magnitude into [2^14, 2^15), and the products are
+                         unscaled in FP32.  hi + lo carry 22 significand bits, as in TF32 x 3 */
 } tdbem_prec;
 
 typedef struct {

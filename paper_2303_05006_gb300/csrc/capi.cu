@@ -186,7 +186,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
   else
     tdbem_default_params(&p);
   if (p.d != 2 || p.p_s < 2 || p.p_s > 8 || p.p_t < 2 || p.p_t > 8 || p.n_leaf < 1 || !(p.eps > 0) ||
-      p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_TF32X3 ||
+      p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_F16X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.chi >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
       (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||

@@ -99,6 +99,8 @@ struct FmmLevel {
   int ntiles_urgent = 0;
   int ntiles_tc_urgent[2] = {0, 0};
   float* d_pack = nullptr;          // packed moments of this level's event (tensor-core M2L)
+  float* d_pkinv = nullptr;         // their inverse row scales (FP16 form)
+  float* d_opinv = nullptr;         // inverse operator scales (FP16 form)
   cudaEvent_t ev_defer = nullptr;   // recorded on the side stream after a deferred M2L
   bool defer_pending = false;       // host: a deferred M2L not yet waited for
   int tc_mt = 1;
@@ -1399,7 +1401,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
                                                                       a_kernel_derivs(c->p.a_deriv), c->p.s_interp,
                                                                       c->p.t_interp, L.ops);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
-      if (c->p.m2l_prec != TDBEM_P_FP32 && (s = tdbem_m2l_tc_images(c, L.ops, L.nop, P, c->p.m2l_prec, &L.ops_img)))
+      if (c->p.m2l_prec != TDBEM_P_FP32 && (s = tdbem_m2l_tc_images(c, L.ops, L.nop, P, c->p.m2l_prec, &L.ops_img, &L.d_opinv)))
         return s;
     }
     // moment and local-coefficient storage (march state and history_eval state)
@@ -1494,6 +1496,11 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       const int64_t npk = std::max<int64_t>(1, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC * P);
       if ((s = c->dalloc(&F->lev[l].d_pack, npk))) return s;
       TDBEM_CUDA_TRY(c, cudaMemset(F->lev[l].d_pack, 0, npk * sizeof(float)));
+      if (c->p.m2l_prec == TDBEM_P_F16X3) {
+        const int64_t nrow = std::max<int64_t>(1, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC);
+        if ((s = c->dalloc(&F->lev[l].d_pkinv, nrow))) return s;
+        TDBEM_CUDA_TRY(c, cudaMemset(F->lev[l].d_pkinv, 0, nrow * sizeof(float)));
+      }
     }
   }
   if (c->p.far_overlap) {
@@ -1525,7 +1532,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           if (it == 0) TDBEM_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
           if ((s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
                                 L.d_pC, L.d_psym, F->d_smap, L.d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec,
-                                F->d_err)))
+                                L.d_opinv, L.d_pkinv, F->d_err)))
             return s;
         }
         TDBEM_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
@@ -1605,7 +1612,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       const int v = L.tc_mt - 1;
       if (tc) {
         cudaEvent_t e = c->prof_begin(8);
-        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, L.d_pack);
+        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, L.d_pack,
+                                        L.d_pkinv);
         if (s) return s;
         c->prof_end(8, e);
       }
@@ -1620,7 +1628,7 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
         } else {
           tdbem_status s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v] + t0, n, L.ops_img, P, pt, PS, L.d_pO,
                                         L.d_pC, L.d_psym, F->d_smap, L.d_pack, k, LOC(l), L.Q, R, c->p.m2l_prec,
-                                        F->d_err);
+                                        L.d_opinv, L.d_pkinv, F->d_err);
           if (s) return s;
         }
         c->prof_end(5, e);

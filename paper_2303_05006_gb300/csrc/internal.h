@@ -205,10 +205,12 @@ tdbem_status tdbem_fast_check(tdbem_ctx* c);
 tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img, int P,
                           int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
                           const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
-                          int32_t* err);
+                          const float* opinv, const float* pkinv, int32_t* err);
+// pkinv: the FP16 form's per-row inverse scales (null for the other forms)
 tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo, const int16_t* smap,
-                            const float* mom, int k, int R, int PS, int pt, float* pk);
-tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img);
+                            const float* mom, int k, int R, int PS, int pt, float* pk, float* pkinv);
+tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img,
+                                 float** opinv);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 void tdbem_fast_state(tdbem_ctx* c, std::vector<std::pair<void*, size_t>>* bufs);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,

@@ -29,6 +29,7 @@
 // time nodes of one spatial node, contiguous in the local coefficients --
 // with one vector reduction red.global.add.v4.f32.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -128,10 +129,13 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
 __device__ __forceinline__ int unit_row(int u) { return ((u >> 6) << 3) | (u & 7); }
 __device__ __forceinline__ int unit_k16(int u) { return (u >> 3) & 7; }
 
+// operand formats of the tensor-core forms
+enum { kFmtTf32 = 0, kFmtBf16 = 1, kFmtF16 = 2 };
+
 // hi (and lo = residual) parts of E consecutive values in the tensor-core type
-template <bool kTf>
+template <int kFmt>
 __device__ __forceinline__ void split_unit(const float* x, uint4& hi, uint4& lo) {
-  if (kTf) {
+  if (kFmt == kFmtTf32) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -140,6 +144,15 @@ __device__ __forceinline__ void split_unit(const float* x, uint4& hi, uint4& lo)
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
+  } else if (kFmt == kFmtF16) {
+    __align__(16) __half h[8], l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      h[u] = __float2half_rn(x[u]);
+      l[u] = __float2half_rn(x[u] - __half2float(h[u]));
+    }
+    hi = *(uint4*)h;
+    lo = *(uint4*)l;
   } else {
     __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
@@ -152,13 +165,53 @@ __device__ __forceinline__ void split_unit(const float* x, uint4& hi, uint4& lo)
   }
 }
 
+__device__ __forceinline__ void split_any(int fmt, const float* x, uint4& hi, uint4& lo) {
+  if (fmt == kFmtTf32)
+    split_unit<kFmtTf32>(x, hi, lo);
+  else if (fmt == kFmtF16)
+    split_unit<kFmtF16>(x, hi, lo);
+  else
+    split_unit<kFmtBf16>(x, hi, lo);
+}
+
+// Power-of-two scale that brings the largest magnitude m of a block of
+// values into [2^14, 2^15) for the FP16 form (clamped so that the scale and
+// its inverse are normal FP32 numbers; 1 for an all-zero block).
+__device__ __forceinline__ int f16_scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  int e;
+  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return max(-126, min(126, 15 - e));
+}
+
 }  // namespace
+
+// Operator scales of the FP16 form: for every operator ops[opk] (P x P), the
+// power of two 2^s that brings its largest magnitude into [2^14, 2^15), and
+// 2^-s.  One block per operator.
+__global__ void k_m2l_opscale(const float* ops, int P, float* scale, float* inv) {
+  const int64_t opk = blockIdx.x;
+  const float* o = ops + opk * P * P;
+  float m = 0.f;
+  for (int64_t i = threadIdx.x; i < (int64_t)P * P; i += blockDim.x) m = fmaxf(m, fabsf(o[i]));
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  __shared__ float wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+    m = fmaxf(m, wm[0]);
+    const int sx = f16_scale_exp(m);
+    scale[opk] = ldexpf(1.f, sx);
+    inv[opk] = ldexpf(1.f, -sx);
+  }
+}
 
 // Operator images: img[((((op*2 + kind)*nrt + rt)*nch + ch)*nparts + part)*1024 + u]
 // is unit u of row tile rt, K chunk ch, part (0 hi, 1 lo) of operator
 // ops[op][kind] (P x P, row-major FP32).  One thread per unit.
-__global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, int nch, int nparts, int tf,
-                             uint4* img) {
+__global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, int nch, int nparts, int fmt,
+                             const float* scale, uint4* img) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nunits) return;
   const int u = (int)(t & 1023);
@@ -169,20 +222,19 @@ __global__ void k_m2l_images(const float* ops, int64_t nunits, int P, int nrt, i
   rest /= nch;
   const int rt = (int)(rest % nrt);
   const int64_t opk = rest / nrt;  // op * 2 + kind
+  const bool tf = fmt == kFmtTf32;
   const int E = tf ? 4 : 8, KC = tf ? 32 : 64;
   const int row = rt * kTileM + unit_row(u);
   const int k0 = ch * KC + unit_k16(u) * E;
+  const float sc = scale ? scale[opk] : 1.f;
   float x[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     int kk = k0 + e;
-    x[e] = (e < E && row < P && kk < P) ? ops[(opk * P + row) * P + kk] : 0.f;
+    x[e] = (e < E && row < P && kk < P) ? sc * ops[(opk * P + row) * P + kk] : 0.f;
   }
   uint4 hi, lo;
-  if (tf)
-    split_unit<true>(x, hi, lo);
-  else
-    split_unit<false>(x, hi, lo);
+  split_any(fmt, x, hi, lo);
   img[t] = part == 0 ? hi : lo;
 }
 
@@ -191,12 +243,14 @@ template <int kMT>
 __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int4* tiles, const uint4* img, int P,
                                                      int pt, int PS, const int32_t* pO, const int32_t* pC,
                                                      const int16_t* psym, const int16_t* smap, const float* pk,
-                                                     int k, float* loc, int Q, int R, int prec, int32_t* err) {
+                                                     int k, float* loc, int Q, int R, int prec, const float* opinv,
+                                                     const float* pkinv, int32_t* err) {
   constexpr uint32_t kTmemCols = 128 * kMT;
   extern __shared__ __align__(1024) uint8_t dsm[];
   __shared__ int64_t src_off[kTileN];
   __shared__ int64_t dst_off[kTileN];
   __shared__ int32_t map_off[kTileN];
+  __shared__ float col_inv[kTileN];  // the FP16 form's inverse column scales
   __shared__ __align__(8) uint64_t mbar;   // MMA completion
   __shared__ __align__(8) uint64_t abar;   // operator tiles landed
   __shared__ uint32_t tmem_base;
@@ -221,8 +275,9 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   const int row0 = rt0 * kTileM;
   const int ncol = gd.z * nk * R;  // columns (pair, right-hand side, component)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool split = prec == 3 || prec == 4;
-  const bool tf = prec == 1 || prec == 4;
+  const bool split = prec == 3 || prec == 4 || prec == 5;
+  const int fmt = (prec == 1 || prec == 4) ? kFmtTf32 : (prec == 5 ? kFmtF16 : kFmtBf16);
+  const bool tf = fmt == kFmtTf32;
   const int E = tf ? 4 : 8;    // K elements per 16-byte unit
   const int KC = 8 * E;        // K elements per chunk (128 bytes per row)
 
@@ -230,11 +285,14 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     int gcol = col0 + tid;
     if (gcol < ncol) {
       int pr = gd.y + gcol / (nk * R), rem = gcol % (nk * R), rhs = rem / nk, c = c0 + rem % nk;
-      src_off[tid] = ((((int64_t)pC[pr] * 2 + var) * R + rhs) * kNCmp + c) * P;  // packed row
+      const int64_t prow = (((int64_t)pC[pr] * 2 + var) * R + rhs) * kNCmp + c;  // packed row
+      src_off[tid] = prow * P;
+      col_inv[tid] = pkinv ? pkinv[prow] : 1.f;
       dst_off[tid] = ((((int64_t)pO[pr] * Q + ((k + q) % Q)) * R + rhs) * kNCmp + c) * P;
       map_off[tid] = (int32_t)psym[pr] * PS;
     } else {
       src_off[tid] = -1;
+      col_inv[tid] = 1.f;
     }
   }
   if (warp == 0) {
@@ -251,7 +309,8 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = make_idesc(tf ? 2u : 1u);
+  const uint32_t idesc = make_idesc(tf ? 2u : (fmt == kFmtF16 ? 0u : 1u));
+  const float op_inv = opinv ? opinv[gd.x * 2 + kind] : 1.f;
   const uint32_t mb = smem_u32(&mbar), ab = smem_u32(&abar);
   bool ok = true;
   bool a_pending = false;  // thread 0: an operator copy not yet seen complete
@@ -306,10 +365,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
         const int u = tid + j * kThreads;
         const float x[8] = {v[j][0].x, v[j][0].y, v[j][0].z, v[j][0].w, v[j][1].x, v[j][1].y, v[j][1].z, v[j][1].w};
         uint4 hi, lo;
-        if (tf)
-          split_unit<true>(x, hi, lo);
-        else
-          split_unit<false>(x, hi, lo);
+        split_any(fmt, x, hi, lo);
         ((uint4*)tB)[u] = hi;
         if (split) ((uint4*)tB2)[u] = lo;
       }
@@ -321,10 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
 #pragma unroll
         for (int e = 0; e < 8; ++e) x[e] = (so >= 0 && e < E && kk + e < P) ? pk[so + kk + e] : 0.f;
         uint4 hi, lo;
-        if (tf)
-          split_unit<true>(x, hi, lo);
-        else
-          split_unit<false>(x, hi, lo);
+        split_any(fmt, x, hi, lo);
         ((uint4*)tB)[u] = hi;
         if (split) ((uint4*)tB2)[u] = lo;
       }
@@ -391,7 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         const int n = cb + j0 + jj;
-        float val = __uint_as_float(v[jj]);
+        float val = __uint_as_float(v[jj]) * (op_inv * col_inv[n]);
         const bool col_ok = col0 + n < ncol;
         if (pt == 4) {
           float v1 = __shfl_down_sync(0xffffffffu, val, 1);
@@ -438,6 +491,41 @@ __global__ void k_m2l_pack(const int32_t* cS, const int16_t* csym, int64_t nrows
   }
 }
 
+// The same for the FP16 form, with each row scaled by the power of two that
+// brings its largest magnitude into [2^14, 2^15) (exact); pkinv[row] receives
+// the inverse.  One warp per row: the lanes find the row's largest magnitude,
+// then write the scaled row.
+__global__ void k_m2l_pack_scaled(const int32_t* cS, const int16_t* csym, int64_t nrows, const int16_t* smap,
+                                  const float* mom, int k, int R, int PS, int pt, float* pk, float* pkinv) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;  // whole warps: a warp's lanes share their row
+  const int64_t per = 2LL * R * kNCmp;
+  const int64_t combo = row / per, rem = row - combo * per;
+  const int P = PS * pt;
+  const float* base = mom + (((int64_t)cS[combo] * 2 + (k & 1)) * per + rem) * P;
+  const int16_t* sm = smap + csym[combo] * PS;
+  float m = 0.f;
+  for (int node = lane; node < PS; node += 32) {
+    const float* src = base + (int64_t)sm[node] * pt;
+    for (int t = 0; t < pt; ++t) m = fmaxf(m, fabsf(src[t]));
+  }
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  const int sx = f16_scale_exp(m);
+  const float sc = ldexpf(1.f, sx);
+  float* dst = pk + row * P;
+  for (int node = lane; node < PS; node += 32) {
+    const float* src = base + (int64_t)sm[node] * pt;
+    if (pt == 4) {
+      const float4 v = __ldg((const float4*)src);
+      *(float4*)(dst + node * 4) = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
+    } else {
+      for (int t = 0; t < pt; ++t) dst[node * pt + t] = sc * src[t];
+    }
+  }
+  if (lane == 0) pkinv[row] = ldexpf(1.f, -sx);
+}
+
 }  // namespace tdbem
 
 // Launch the tensor-core M2L of one level event with mt (1 or 2) 128-row
@@ -446,7 +534,7 @@ template <int kMT>
 static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
                                   int P, int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
                                   const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
-                                  int32_t* err) {
+                                  const float* opinv, const float* pkinv, int32_t* err) {
   using namespace tdbem;
   static bool attr = false;
   if (!attr) {
@@ -457,7 +545,7 @@ static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* ti
   if (ntiles == 0) return TDBEM_OK;
   const size_t smem = smem_tiles<kMT>() + (48 * PS * 2 <= kSmapSmem ? 48 * PS * 2 : 0) + 1024;
   k_m2l_tc<kMT><<<ntiles, kThreads, smem, c->stream>>>(gemm, tiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc,
-                                                        Q, R, prec, err);
+                                                        Q, R, prec, opinv, pkinv, err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
@@ -465,26 +553,39 @@ static tdbem_status launch_m2l_tc(tdbem_ctx* c, const int4* gemm, const int4* ti
 tdbem_status tdbem_m2l_tc(tdbem_ctx* c, int mt, const int4* gemm, const int4* tiles, int ntiles, const uint4* img,
                           int P, int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
                           const int16_t* smap, const float* pk, int k, float* loc, int Q, int R, int prec,
-                          int32_t* err) {
+                          const float* opinv, const float* pkinv, int32_t* err) {
   if (mt == 2)
-    return launch_m2l_tc<2>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, err);
-  return launch_m2l_tc<1>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, err);
+    return launch_m2l_tc<2>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, opinv,
+                            pkinv, err);
+  return launch_m2l_tc<1>(c, gemm, tiles, ntiles, img, P, pt, PS, pO, pC, psym, smap, pk, k, loc, Q, R, prec, opinv,
+                          pkinv, err);
 }
 
 // Convert the FP32 operators of one level into the tensor-core images read by
-// k_m2l_tc (allocated here, owned by the context).
-tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img) {
+// k_m2l_tc (allocated here, owned by the context).  The FP16 form scales each
+// operator by a power of two first; *opinv (allocated here, 2 nop floats)
+// then holds the inverse scales, and is null for the other forms.
+tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img,
+                                 float** opinv) {
   using namespace tdbem;
   *img = nullptr;
+  *opinv = nullptr;
   if (nop == 0) return TDBEM_OK;
-  const bool tf = prec == TDBEM_P_TF32 || prec == TDBEM_P_TF32X3;
-  const bool split = prec == TDBEM_P_TF32X3 || prec == TDBEM_P_BF16X3;
-  const int KC = tf ? 32 : 64;
+  const int fmt = (prec == TDBEM_P_TF32 || prec == TDBEM_P_TF32X3) ? kFmtTf32
+                                                                      : (prec == TDBEM_P_F16X3 ? kFmtF16 : kFmtBf16);
+  const bool split = prec == TDBEM_P_TF32X3 || prec == TDBEM_P_BF16X3 || prec == TDBEM_P_F16X3;
+  const int KC = fmt == kFmtTf32 ? 32 : 64;
   const int nrt = (P + kTileM - 1) / kTileM, nch = (P + KC - 1) / KC, nparts = split ? 2 : 1;
   const int64_t nunits = (int64_t)nop * 2 * nrt * nch * nparts * 1024;
   tdbem_status s = c->dalloc(img, nunits);
   if (s) return s;
-  k_m2l_images<<<(unsigned)((nunits + 255) / 256), 256, 0, c->stream>>>(ops, nunits, P, nrt, nch, nparts, tf ? 1 : 0,
+  float* scale = nullptr;
+  if (fmt == kFmtF16) {
+    if ((s = c->dalloc(&scale, 2 * (int64_t)nop)) || (s = c->dalloc(opinv, 2 * (int64_t)nop))) return s;
+    k_m2l_opscale<<<(unsigned)(2 * nop), 256, 0, c->stream>>>(ops, P, scale, *opinv);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
+  k_m2l_images<<<(unsigned)((nunits + 255) / 256), 256, 0, c->stream>>>(ops, nunits, P, nrt, nch, nparts, fmt, scale,
                                                                         *img);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
@@ -493,10 +594,16 @@ tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P,
 // Pack the moments of one level event for k_m2l_tc: ncombo (source cell,
 // symmetry) combinations, rows of P floats each (see k_m2l_pack).
 tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo, const int16_t* smap,
-                            const float* mom, int k, int R, int PS, int pt, float* pk) {
+                            const float* mom, int k, int R, int PS, int pt, float* pk, float* pkinv) {
   using namespace tdbem;
   const int64_t nrows = (int64_t)ncombo * 2 * R * kNCmp;
   if (nrows == 0) return TDBEM_OK;
+  if (pkinv) {
+    k_m2l_pack_scaled<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, c->stream>>>(cS, csym, nrows, smap, mom, k, R,
+                                                                                   PS, pt, pk, pkinv);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    return TDBEM_OK;
+  }
   const int64_t nth = nrows * PS;
   k_m2l_pack<<<(unsigned)((nth + 255) / 256), 256, 0, c->stream>>>(cS, csym, nrows, smap, mom, k, R, PS, pt, pk);
   TDBEM_CUDA_TRY(c, cudaGetLastError());

@@ -151,15 +151,20 @@ def test_tensor_core_m2l_precisions(sphere1280_direct):
     the lag and the far field of old sources is a telescoping cancellation
     across lags, so operand rounding is amplified: the split forms (about 16
     and 22 operand bits) track FP32, the single-pass TF32 and BF16 forms do
-    not (measured: BF16x3 6.8e-4, TF32 4.1e-2, BF16 3.6e-1)."""
+    not (measured: BF16x3 6.8e-4, TF32 4.1e-2, BF16 3.6e-1).  The FP16 split
+    (operators and moment columns scaled by powers of two into FP16's range)
+    carries as many bits as the TF32 split and is held to the same bar."""
     w, Jd = sphere1280_direct
-    J = {prec: _solver(w, mode=1, m2l_prec=prec).march(w.Nt - 1) for prec in (0, 1, 2, 3, 4)}
-    e = {prec: _rel(J[prec], J[0]) for prec in (1, 2, 3, 4)}
+    J = {prec: _solver(w, mode=1, m2l_prec=prec).march(w.Nt - 1) for prec in (0, 1, 2, 3, 4, 5)}
+    e = {prec: _rel(J[prec], J[0]) for prec in (1, 2, 3, 4, 5)}
+    print("\nM2L forms, rel l2 against the FP32 M2L:", {k: f"{v:.2e}" for k, v in e.items()})
     assert e[4] < 1e-4, e     # TF32 x 3
+    assert e[5] < 1e-4, e     # FP16 x 3
     assert e[3] < 3e-3, e     # BF16 x 3
     assert e[1] > 10 * e[4] and e[2] > 10 * e[3], e
-    # the accurate tensor-core form keeps the fast path's error at the FP32 level
+    # the accurate tensor-core forms keep the fast path's error at the FP32 level
     assert abs(_rel(J[4], Jd) - _rel(J[0], Jd)) < 1e-4
+    assert abs(_rel(J[5], Jd) - _rel(J[0], Jd)) < 1e-4
 
 
 def test_m2l_tile_shapes_and_autotuner(sphere1280_direct):
