@@ -598,7 +598,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["auto", "fast", "direct"], default="auto",
                     help="auto: both paths, the headline is the one meeting the 1e-4 accuracy bar")
-    ap.add_argument("--prec", choices=list(PREC), default="tf32x3")
+    ap.add_argument("--prec", choices=list(PREC), default="f16x3")
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")
     ap.add_argument("--jacobi", type=int, default=0, help="FP64 Jacobi sweeps before the Krylov solve (0: none)")
@@ -614,7 +614,7 @@ def main():
                     help="1: march on a highest-priority CUDA stream (the deferred far-field products run at the lowest)")
     ap.add_argument("--far-overlap", type=int, default=1, choices=(0, 1),
                     help="1: M2L products of lag >= 2 on a second stream, overlapping the next steps; 0: serial")
-    ap.add_argument("--m2l-tile-rows", type=int, default=0, choices=(0, 128, 256),
+    ap.add_argument("--m2l-tile-rows", type=int, default=0, choices=(0, 1, 128, 256),
                     help="tensor-core M2L CTA shape: 0 = autotuned at setup, 128 or 256 operator rows per CTA")
     ap.add_argument("--sweep", default="",
                     help="comma-separated p:form settings (e.g. 3:fp32,4:tf32x3,5x4:tf32x3 for p_s x p_t); prints error vs "

@@ -100,7 +100,9 @@ typedef struct {
   int32_t jacobi_sweeps; /* Z0 solve: at most this many FP64 Jacobi sweeps before the Krylov refinement
                             (0: Krylov only); a sweep that does not cut the residual by 0.7 ends them */
   int32_t m2l_tile_rows; /* tensor-core M2L: rows of the product per CTA, 128 or 256; 0 (default) times
-                            both at setup on each level and keeps the faster */
+                            both at setup on each level and keeps the faster, with the resident-operator
+                            kernel as a third candidate for the FP16 form (see tdbem_info.m2l_resident);
+                            1 forces the resident-operator kernel where it applies (128 elsewhere) */
   int32_t precond;       /* Z0 solve preconditioner: 0 Jacobi; 1 (default) triangle blocks (the inverses of the 3 x 3
                             blocks of Z0 among the RWG functions of each triangle, summed) */
   int32_t far_overlap;   /* 1 (default): the steps overlap.  Fast mode: the M2L products of a gating event with
@@ -332,6 +334,9 @@ typedef struct {
   int32_t max_lag;                 /* largest time lag m with a stored coefficient: from step alpha = max_lag + 1 on,
                                       every history step a coefficient can reach is inside the march (the steady
                                       state of the history sum) */
+  int32_t m2l_resident;            /* bit l set where level l's M2L runs the resident-operator kernel (FP16 form,
+                                      P <= 256: the operator's 128-row tiles stay in shared memory over runs of
+                                      column tiles), chosen at setup against the tiled shapes by timing */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 

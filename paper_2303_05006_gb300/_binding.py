@@ -43,7 +43,8 @@ class Info(ctypes.Structure):
                 ("setup_seconds", ctypes.c_double), ("total_solver_iters", ctypes.c_int64),
                 ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
                 ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64),
-                ("m2l_tile_rows", ctypes.c_int32 * 8), ("z0_nnz", ctypes.c_int64), ("max_lag", ctypes.c_int32)]
+                ("m2l_tile_rows", ctypes.c_int32 * 8), ("z0_nnz", ctypes.c_int64), ("max_lag", ctypes.c_int32),
+                ("m2l_resident", ctypes.c_int32)]
 
 
 class TdbemError(RuntimeError):

@@ -189,7 +189,7 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.m2l_prec < TDBEM_P_FP32 || p.m2l_prec > TDBEM_P_F16X3 ||
       !(p.mu > 0) || !(p.theta >= 0) || !(p.chi >= 0) || !(p.solve_tol > 0) || p.solve_maxit < 1 || p.n_rhs < 1 ||
       p.n_rhs > TDBEM_MAX_RHS || p.jacobi_sweeps < 0 ||
-      (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
+      (p.m2l_tile_rows != 0 && p.m2l_tile_rows != 1 && p.m2l_tile_rows != 128 && p.m2l_tile_rows != 256) || p.precond < 0 ||
       p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||
       p.far_kernel < 0 || p.far_kernel > 3 || p.max_device_bytes < 0 || p.s_interp < 0 || p.s_interp > 1 ||
       p.t_interp < 0 || p.t_interp > 1 || p.a_deriv < 0 || p.a_deriv > 2 ||

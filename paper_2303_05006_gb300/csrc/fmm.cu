@@ -101,6 +101,15 @@ struct FmmLevel {
   float* d_pack = nullptr;          // packed moments of this level's event (tensor-core M2L)
   float* d_pkinv = nullptr;         // their inverse row scales (FP16 form)
   float* d_opinv = nullptr;         // inverse operator scales (FP16 form)
+  // FP16 form with P <= 256: the resident-operator kernel k_m2l_res, its work
+  // units {gemm, 128-row tile, first 128-column tile, column tiles} (lag-1
+  // units first) and its packed FP16 hi/lo moments
+  bool res_ok = false;  // eligible (FP16 form, P <= 256)
+  bool res = false;     // chosen by the autotuner
+  float res_ms = 0.f;   // autotuner: mean time of one M2L event of the resident kernel
+  int4* d_units = nullptr;
+  int nunits = 0, nunits_urgent = 0;
+  __half* d_pk16 = nullptr;
   cudaEvent_t ev_defer = nullptr;   // recorded on the side stream after a deferred M2L
   bool defer_pending = false;       // host: a deferred M2L not yet waited for
   int tc_mt = 1;
@@ -1372,6 +1381,37 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     L.ntiles_urgent = lag1_first(tiles);
     L.ntiles_tc_urgent[0] = lag1_first(tiles_tc);
     L.ntiles_tc_urgent[1] = lag1_first(tiles_tc2);
+    // resident-operator units: runs of up to 8 column tiles per (GEMM, row
+    // tile), the run length chosen so that each list still has about four
+    // units per SM
+    L.res_ok = c->p.m2l_prec == TDBEM_P_F16X3 && P <= 256;
+    if (L.res_ok && !gemm.empty()) {
+      int nsm = 0;
+      TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+      const int nrt = (P + 127) / 128;
+      std::vector<int4> units;
+      for (int urgent = 1; urgent >= 0; --urgent) {
+        int64_t tot = 0;
+        for (size_t g = 0; g < gemm.size(); ++g)
+          if ((((gemm[g].w >> 8) & 0xff) == 1) == (urgent == 1)) {
+            const int nk = (gemm[g].w & 0xff) == 0 ? 3 : 4;
+            tot += (int64_t)nrt * ((gemm[g].z * nk * c->R + 127) / 128);
+          }
+        const int run = (int)std::max<int64_t>(1, std::min<int64_t>(8, (tot + 4 * nsm - 1) / (4 * nsm)));
+        for (size_t g = 0; g < gemm.size(); ++g) {
+          if ((((gemm[g].w >> 8) & 0xff) == 1) != (urgent == 1)) continue;
+          const int nk = (gemm[g].w & 0xff) == 0 ? 3 : 4;
+          const int nct = (gemm[g].z * nk * c->R + 127) / 128;
+          for (int rt = 0; rt < nrt; ++rt)
+            for (int c0 = 0; c0 < nct; c0 += run) units.push_back(make_int4((int)g, rt, c0, std::min(run, nct - c0)));
+        }
+        if (urgent) L.nunits_urgent = (int)units.size();
+      }
+      L.nunits = (int)units.size();
+      if ((s = c->dalloc(&L.d_units, std::max(1, L.nunits)))) return s;
+      if (L.nunits)
+        TDBEM_CUDA_TRY(c, cudaMemcpy(L.d_units, units.data(), L.nunits * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     if (qmax >= 255) {
       c->set_error("fast: too many time intervals per interaction");
       return TDBEM_EINVAL;
@@ -1500,6 +1540,11 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         const int64_t nrow = std::max<int64_t>(1, (int64_t)F->lev[l].ncombo * 2 * c->R * kNC);
         if ((s = c->dalloc(&F->lev[l].d_pkinv, nrow))) return s;
         TDBEM_CUDA_TRY(c, cudaMemset(F->lev[l].d_pkinv, 0, nrow * sizeof(float)));
+        if (F->lev[l].res_ok) {
+          const int64_t n16 = nrow * 2 * ((P + 63) / 64 * 64);
+          if ((s = c->dalloc(&F->lev[l].d_pk16, n16))) return s;
+          TDBEM_CUDA_TRY(c, cudaMemset(F->lev[l].d_pk16, 0, n16 * sizeof(__half)));
+        }
       }
     }
   }
@@ -1507,18 +1552,23 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     int prio_lo = 0, prio_hi = 0;
     TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
     TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->side, cudaStreamNonBlocking, prio_lo));
+
     TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_fork, cudaEventDisableTiming));
     for (int l = 2; l <= F->lmax; ++l)
       TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->lev[l].ev_defer, cudaEventDisableTiming));
   }
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  // M2L tile autotuner: time one gating event of each level in both CTA
-  // shapes (one or two 128-row operator tiles per CTA) on this context's own
-  // operators, pairs and right-hand sides, and keep the faster.  The packed
-  // moments are still zero, so the trial launches add nothing to the local
-  // coefficients.
+  // M2L autotuner: time one gating event of each level with every kernel
+  // shape that applies -- the tiled kernel with one or two 128-row operator
+  // tiles per CTA, and for the FP16 form with P <= 256 the resident-operator
+  // kernel -- on this context's own operators, pairs and right-hand sides,
+  // and keep the fastest.  The packed moments are still zero, so the trial
+  // launches add nothing to the local coefficients.
   if (c->p.m2l_prec != TDBEM_P_FP32 && c->p.m2l_tile_rows != 0) {
-    for (int l = 2; l <= F->lmax; ++l) F->lev[l].tc_mt = c->p.m2l_tile_rows / 128;
+    for (int l = 2; l <= F->lmax; ++l) {
+      F->lev[l].tc_mt = c->p.m2l_tile_rows == 256 ? 2 : 1;
+      F->lev[l].res = c->p.m2l_tile_rows == 1 && F->lev[l].res_ok;
+    }
   } else if (c->p.m2l_prec != TDBEM_P_FP32) {
     cudaEvent_t e0, e1;
     TDBEM_CUDA_TRY(c, cudaEventCreate(&e0));
@@ -1526,22 +1576,27 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
     for (int l = 2; l <= F->lmax; ++l) {
       FmmLevel& L = F->lev[l];
       if (!L.ntiles_tc[0]) continue;
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < (L.res_ok ? 3 : 2); ++v) {
         const int reps = 3;
         for (int it = -1; it < reps; ++it) {  // one untimed launch first
           if (it == 0) TDBEM_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
-          if ((s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
-                                L.d_pC, L.d_psym, F->d_smap, L.d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec,
-                                L.d_opinv, L.d_pkinv, F->d_err)))
-            return s;
+          if (v < 2)
+            s = tdbem_m2l_tc(c, v + 1, L.d_gemm, L.d_tiles_tc[v], L.ntiles_tc[v], L.ops_img, P, pt, PS, L.d_pO,
+                             L.d_pC, L.d_psym, F->d_smap, L.d_pack, 0, L.loc, L.Q, c->R, c->p.m2l_prec, L.d_opinv,
+                             L.d_pkinv, F->d_err);
+          else
+            s = tdbem_m2l_res(c, L.d_gemm, L.d_units, 0, L.nunits, L.ops_img, P, pt, PS, L.d_pO, L.d_pC, L.d_psym,
+                              F->d_smap, L.d_pk16, 0, L.loc, L.Q, c->R, L.d_opinv, L.d_pkinv, F->d_err, 0);
+          if (s) return s;
         }
         TDBEM_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
         TDBEM_CUDA_TRY(c, cudaEventSynchronize(e1));
         float ms = 0.f;
         TDBEM_CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
-        L.tc_ms[v] = ms / reps;
+        (v < 2 ? L.tc_ms[v] : L.res_ms) = ms / reps;
       }
       L.tc_mt = L.tc_ms[1] < L.tc_ms[0] ? 2 : 1;
+      L.res = L.res_ok && L.res_ms < std::min(L.tc_ms[0], L.tc_ms[1]);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1612,8 +1667,10 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
       const int v = L.tc_mt - 1;
       if (tc) {
         cudaEvent_t e = c->prof_begin(8);
-        tdbem_status s = tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt, L.d_pack,
-                                        L.d_pkinv);
+        tdbem_status s = L.res ? tdbem_m2l_pack_f16(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt,
+                                                    L.d_pk16, L.d_pkinv)
+                               : tdbem_m2l_pack(c, L.d_cS, L.d_csym, L.ncombo, F->d_smap, MOM(l), k, R, PS, pt,
+                                                L.d_pack, L.d_pkinv);
         if (s) return s;
         c->prof_end(8, e);
       }
@@ -1625,6 +1682,13 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
           k_m2l_fp32<<<n, 256, 0, c->stream>>>(L.d_gemm, L.d_tiles + t0, L.ops, P, pt, PS, L.d_pO, L.d_pS, L.d_psym,
                                                F->d_smap, MOM(l), k, LOC(l), L.Q, R);
           TDBEM_CUDA_TRY(c, cudaGetLastError());
+        } else if (L.res) {
+          // the deferred launch on the side stream runs one CTA per unit, so
+          // that the hardware interleaves it with the steps it overlaps
+          tdbem_status s = tdbem_m2l_res(c, L.d_gemm, L.d_units, t0, n, L.ops_img, P, pt, PS, L.d_pO, L.d_pC,
+                                         L.d_psym, F->d_smap, L.d_pk16, k, LOC(l), L.Q, R, L.d_opinv, L.d_pkinv,
+                                         F->d_err, (F->side && c->stream == F->side) ? -1 : 0);
+          if (s) return s;
         } else {
           tdbem_status s = tdbem_m2l_tc(c, L.tc_mt, L.d_gemm, L.d_tiles_tc[v] + t0, n, L.ops_img, P, pt, PS, L.d_pO,
                                         L.d_pC, L.d_psym, F->d_smap, L.d_pack, k, LOC(l), L.Q, R, c->p.m2l_prec,
@@ -1634,8 +1698,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
         c->prof_end(5, e);
         return TDBEM_OK;
       };
-      const int nall = tc ? L.ntiles_tc[v] : L.ntiles;
-      const int nu = tc ? L.ntiles_tc_urgent[v] : L.ntiles_urgent;
+      const int nall = L.res ? L.nunits : tc ? L.ntiles_tc[v] : L.ntiles;
+      const int nu = L.res ? L.nunits_urgent : tc ? L.ntiles_tc_urgent[v] : L.ntiles_urgent;
       tdbem_status s;
       if (!F->side || eval) {
         if ((s = m2l_range(0, nall))) return s;
@@ -1887,8 +1951,12 @@ void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info) {
   }
   info->n_far_pairs = il;
   info->m2l_flops_per_step = fl;
-  for (int l = 2; l <= F->lmax && l < 8; ++l)
-    info->m2l_tile_rows[l] = (c->p.m2l_prec != TDBEM_P_FP32 && F->lev[l].ntiles_tc[0]) ? 128 * F->lev[l].tc_mt : 0;
+  for (int l = 2; l <= F->lmax && l < 8; ++l) {
+    info->m2l_tile_rows[l] = (c->p.m2l_prec != TDBEM_P_FP32 && F->lev[l].ntiles_tc[0])
+                                 ? (F->lev[l].res ? 128 : 128 * F->lev[l].tc_mt)
+                                 : 0;
+    if (F->lev[l].res) info->m2l_resident |= 1 << l;
+  }
 }
 
 // CSR of Z0 from the near store

@@ -1,6 +1,7 @@
 // internal.h -- library-private declarations shared by the CUDA translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -211,6 +212,15 @@ tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym
                             const float* mom, int k, int R, int PS, int pt, float* pk, float* pkinv);
 tdbem_status tdbem_m2l_tc_images(tdbem_ctx* c, const float* ops, int nop, int P, int prec, uint4** img,
                                  float** opinv);
+// the FP16 form with the operator rows resident in shared memory (P <= 256):
+// units [u0, u0 + n) of the level's list, and the FP16 hi/lo moment pack it reads
+tdbem_status tdbem_m2l_res(tdbem_ctx* c, const int4* gemm, const int4* units, int u0, int n, const uint4* img, int P,
+                           int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
+                           const int16_t* smap, const __half* pk16, int k, float* loc, int Q, int R,
+                           const float* opinv, const float* pkinv, int32_t* err, int max_ctas);
+tdbem_status tdbem_m2l_pack_f16(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo,
+                                const int16_t* smap, const float* mom, int k, int R, int PS, int pt, __half* pk16,
+                                float* pkinv);
 void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 void tdbem_fast_state(tdbem_ctx* c, std::vector<std::pair<void*, size_t>>* bufs);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,

@@ -34,8 +34,11 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace tdbem {
+
+using namespace tc;
 
 namespace {
 
@@ -48,75 +51,11 @@ constexpr int smem_tiles() { return (2 * kMT + 2) * kTileBytes; }
 constexpr int kNCmp = 7;
 constexpr int kSmapSmem = 24 * 1024;  // largest symmetry-map table staged in shared memory
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
-  d |= (uint64_t)(128 >> 4) << 16;           // leading byte offset: next core matrix along K
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                    // descriptor version (sm_100 family)
-  return d;                                  // base offset 0, no swizzle
-}
-
 // instruction descriptor: D = F32, A/B format fmt (1 = BF16 in kind::f16,
 // 2 = TF32 in kind::tf32), both K-major, N = 128, M = 128
 __device__ __forceinline__ uint32_t make_idesc(uint32_t fmt) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 }
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 20); ++i)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
-}
-
-// arrive on mbar (one of its expected arrivals) and add bytes to the
-// transaction count the current phase waits for
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-// bulk copy (TMA, no tensor map) of bytes from global to this CTA's shared
-// memory, counted on mbar; both addresses 16-byte aligned, bytes a multiple of 16
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   uint32_t r;
@@ -124,10 +63,6 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
   return r;
 }
 
-// 16-byte unit u of a 128-row x 128-byte K-major tile: its row and its
-// 16-byte column along K (the unit's byte offset in the tile is 16 u)
-__device__ __forceinline__ int unit_row(int u) { return ((u >> 6) << 3) | (u & 7); }
-__device__ __forceinline__ int unit_k16(int u) { return (u >> 3) & 7; }
 
 // operand formats of the tensor-core forms
 enum { kFmtTf32 = 0, kFmtBf16 = 1, kFmtF16 = 2 };
@@ -526,6 +461,329 @@ __global__ void k_m2l_pack_scaled(const int32_t* cS, const int16_t* csym, int64_
   if (lane == 0) pkinv[row] = ldexpf(1.f, -sx);
 }
 
+// ---------------------------------------------------------------------------
+// The FP16 form with the operator resident in shared memory (P <= 256).
+//
+// A work unit is one 128-row tile of one operator (GEMM g, row tile rt) and a
+// run of up to kResRun consecutive 128-column tiles of its B.  The CTA brings
+// the unit's operator rows in once (hi and lo parts of every K chunk, by TMA
+// bulk copies) and streams the column tiles through a three-stage ring:
+//  - warps 0-3 copy each (column tile, K chunk) item of the packed moments,
+//    already scaled and split into FP16 hi and lo by k_m2l_pack_f16, into a
+//    ring stage with 16-byte cp.async copies, up to three items ahead of the
+//    tensor core; each thread's copies arrive on the stage's barrier when
+//    they land (cp.async.mbarrier.arrive), so the producers never wait on
+//    their own copies;
+//  - one thread of warp 4 issues the item's tcgen05 MMAs into one of two
+//    128-column TMEM accumulators, commits to the stage's barrier (which frees
+//    the stage), and after a tile's last chunk to the accumulator's barrier;
+//  - warps 5-8 drain each finished accumulator (tcgen05.ld), unscale, and add
+//    it to the local coefficients while the next tile accumulates in the other.
+// The CTA is persistent over units blockIdx.x, blockIdx.x + gridDim.x, ...
+// Every wait is bounded; a timeout sets *err, raises a shared abort flag
+// that ends every role's loop, and the CTA drains its copies and MMAs before
+// freeing TMEM.
+constexpr int kResThreads = 288;
+constexpr int kResMaxCh = 4;  // K chunks of 64 halves: P <= 256
+constexpr int kResStages = 3;
+constexpr int kResStage = 2 * kTileBytes;
+constexpr int kResSmem = kResMaxCh * 2 * kTileBytes + kResStages * kResStage;
+
+struct ResUnit {
+  int g, rt, ct0, nct;
+  int op, kind, q, nk, c0, var, ncol, pbase;
+};
+__device__ __forceinline__ ResUnit res_unit(const int4* gemm, const int4* units, int u, int R) {
+  ResUnit U;
+  const int4 un = units[u];
+  U.g = un.x;
+  U.rt = un.y;
+  U.ct0 = un.z;
+  U.nct = un.w;
+  const int4 gd = gemm[U.g];
+  U.op = gd.x;
+  U.pbase = gd.y;
+  U.kind = gd.w & 0xff;
+  U.q = (gd.w >> 8) & 0xff;
+  const int qhi = (gd.w >> 16) & 0xff;
+  U.nk = U.kind == 0 ? 3 : 4;
+  U.c0 = U.kind == 0 ? 0 : 3;
+  U.var = U.q == qhi ? 1 : 0;
+  U.ncol = gd.z * U.nk * R;
+  return U;
+}
+
+__global__ void __launch_bounds__(kResThreads, 1)
+    k_m2l_res(const int4* gemm, const int4* units, int nunits, const uint4* img, int P, int P16, int pt, int PS,
+              const int32_t* pO, const int32_t* pC, const int16_t* psym, const int16_t* smap, const __half* pk16,
+              int k, float* loc, int Q, int R, const float* opinv, const float* pkinv, int32_t* err) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  uint8_t* sA = dsm;                               // [chunk][hi, lo][16 KB]
+  uint8_t* sB = dsm + kResMaxCh * 2 * kTileBytes;  // [stage][hi, lo][16 KB]
+  __shared__ __align__(8) uint64_t a_full, b_full[kResStages], mma_done[kResStages], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = P16 / 64, nrt = (P + kTileM - 1) / kTileM;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_full)));
+    for (int i = 0; i < kResStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&b_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_done[i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&acc_empty[i])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(256u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  auto fail = [&]() {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicExch(err, 1);
+    }
+  };
+
+  if (warp < 4) {
+    // ---- producers: cp.async of the packed FP16 moments into the ring ----
+    const int tid = threadIdx.x;
+    const int k16 = (tid >> 3) & 7;  // this thread's 16-byte column along K (the same for its 8 units)
+    int64_t g_item = 0;
+    for (int u = blockIdx.x; u < nunits && !abort_flag; u += gridDim.x) {
+      const ResUnit U = res_unit(gemm, units, u, R);
+      for (int t = 0; t < U.nct && !abort_flag; ++t) {
+        const int col0 = (U.ct0 + t) * kTileN;
+        // units tid + 128 i (i < 8) of a part: row ((tid >> 6) + 2 i) * 8 + (tid & 7)
+        int64_t srow[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = (((tid >> 6) + 2 * i) << 3) | (tid & 7);
+          const int gcol = col0 + r;
+          srow[i] = -1;
+          if (gcol < U.ncol) {
+            const int pr = U.pbase + gcol / (U.nk * R), rem = gcol % (U.nk * R);
+            const int64_t prow = (((int64_t)pC[pr] * 2 + U.var) * R + rem / U.nk) * kNCmp + U.c0 + rem % U.nk;
+            srow[i] = prow * 2 * P16;
+          }
+        }
+        for (int ch = 0; ch < nch && !abort_flag; ++ch, ++g_item) {
+          const int st = (int)(g_item % kResStages);
+          const uint32_t ph = (uint32_t)((g_item / kResStages) & 1);  // this use's phase of the stage
+          // the stage was last read by the MMAs of item g_item - kResStages
+          if (g_item >= kResStages && !mbar_wait(smem_u32(&mma_done[st]), ph ^ 1u)) {
+            fail();
+            break;
+          }
+          const uint32_t base = smem_u32(sB + st * kResStage);
+#pragma unroll
+          for (int part = 0; part < 2; ++part)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int uu = tid + 128 * i;
+              const bool v = srow[i] >= 0;
+              const __half* src = v ? pk16 + srow[i] + part * P16 + ch * 64 + k16 * 8 : pk16;
+              cp_async16_zfill(base + part * kTileBytes + uu * 16, src, v ? 16u : 0u);
+            }
+          // arrive on the stage's barrier once this thread's copies have landed
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&b_full[st]))
+                       : "memory");
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 4) {
+    // ---- the MMA issuer: the whole warp runs the loop (its waits and their
+    // verdicts agreed by vote), lane 0 issues the copies, MMAs and commits ----
+    const uint32_t idesc = make_idesc(0u);  // FP16 operands in kind::f16
+    auto wait_all = [&](uint64_t* bar, uint32_t parity) {
+      return __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), parity));
+    };
+    int64_t g_item = 0, j = 0;
+    uint32_t a_par = 0;
+    bool issued = false;  // an MMA commit may be outstanding
+    for (int u = blockIdx.x; u < nunits && !__any_sync(0xffffffffu, abort_flag != 0); u += gridDim.x) {
+      const ResUnit U = res_unit(gemm, units, u, R);
+      // the operator rows are overwritten only after the previous unit's MMAs
+      if (g_item > 0 &&
+          !wait_all(&mma_done[(g_item - 1) % kResStages], (uint32_t)(((g_item - 1) / kResStages) & 1))) {
+        fail();
+        break;
+      }
+      if (lane == 0) {
+        const uint4* src = img + (((int64_t)U.op * 2 + U.kind) * nrt + U.rt) * nch * 2 * 1024;
+        mbar_expect_tx(smem_u32(&a_full), (uint32_t)(nch * 2 * kTileBytes));
+        for (int ch = 0; ch < nch; ++ch)
+          bulk_g2s(smem_u32(sA + ch * 2 * kTileBytes), src + (int64_t)ch * 2 * 1024, 2 * kTileBytes,
+                   smem_u32(&a_full));
+      }
+      __syncwarp();
+      if (!wait_all(&a_full, a_par)) {
+        fail();
+        // the copy engine may still write the operator tiles: give it a last bounded chance
+        wait_all(&a_full, a_par);
+        break;
+      }
+      a_par ^= 1;
+      bool stop = false;
+      for (int t = 0; t < U.nct && !stop; ++t, ++j) {
+        const int b = (int)(j & 1);
+        // the accumulator was last drained by the epilogue of tile j - 2
+        if (j >= 2 && !wait_all(&acc_empty[b], (uint32_t)(((j >> 1) - 1) & 1))) {
+          fail();
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * kTileN);
+        for (int ch = 0; ch < nch; ++ch, ++g_item) {
+          const int st = (int)(g_item % kResStages);
+          if (!wait_all(&b_full[st], (uint32_t)((g_item / kResStages) & 1))) {
+            fail();
+            stop = true;
+            break;
+          }
+          // the producers' copies (generic proxy) are read by the tensor core (async proxy)
+          fence_async_smem();
+          tc_fence_after();
+          if (lane == 0) {
+            // D[column][operator row] += moments . operator^T: the moment
+            // columns are the MMA's M side, the resident operator rows its N side
+            const uint32_t o0 = smem_u32(sA + ch * 2 * kTileBytes), o1 = o0 + kTileBytes;
+            const uint32_t m0 = smem_u32(sB + st * kResStage), m1 = m0 + kTileBytes;
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t off = 256u * ks;  // 32 bytes of K per instruction
+              mma_f16(d, make_desc(m0 + off), make_desc(o0 + off), idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+              mma_f16(d, make_desc(m1 + off), make_desc(o0 + off), idesc, 1u);
+              mma_f16(d, make_desc(m0 + off), make_desc(o1 + off), idesc, 1u);
+            }
+            mma_commit(smem_u32(&mma_done[st]));
+            if (ch == nch - 1) mma_commit(smem_u32(&acc_full[b]));
+          }
+          __syncwarp();
+          issued = true;
+        }
+      }
+      if (stop) break;
+    }
+    // drain: the last commit covers every MMA issued
+    if (issued) wait_all(&mma_done[(g_item - 1) % kResStages], (uint32_t)(((g_item - 1) / kResStages) & 1));
+  } else {
+    // ---- epilogue: TMEM -> unscale -> local coefficients.  TMEM lane =
+    // moment column of the tile, TMEM column = operator row, so each lane adds
+    // its own column's rows: pt consecutive rows (the time nodes of one
+    // spatial node) are contiguous in the local coefficients.  Control flow
+    // stays uniform across each warp (tcgen05.ld is .sync.aligned): the abort
+    // flag and every wait's verdict are agreed by vote ----
+    const int q4 = warp & 3;  // TMEM lane quarter this warp may read
+    int64_t j = 0;
+    for (int u = blockIdx.x; u < nunits && !__any_sync(0xffffffffu, abort_flag != 0); u += gridDim.x) {
+      const ResUnit U = res_unit(gemm, units, u, R);
+      const float op_inv = opinv[U.op * 2 + U.kind];
+      const int row0 = U.rt * kTileM;
+      for (int t = 0; t < U.nct && !__any_sync(0xffffffffu, abort_flag != 0); ++t, ++j) {
+        const int b = (int)(j & 1);
+        const int gcol = (U.ct0 + t) * kTileN + q4 * 32 + lane;  // this lane's column
+        int64_t dst_off = -1;
+        int32_t map_off = 0;
+        float ci = 0.f;
+        if (gcol < U.ncol) {
+          const int pr = U.pbase + gcol / (U.nk * R), rem = gcol % (U.nk * R), rhs = rem / U.nk, c = U.c0 + rem % U.nk;
+          const int64_t prow = (((int64_t)pC[pr] * 2 + U.var) * R + rhs) * kNCmp + c;
+          dst_off = ((((int64_t)pO[pr] * Q + ((k + U.q) % Q)) * R + rhs) * kNCmp + c) * P;
+          map_off = (int32_t)psym[pr] * PS;
+          ci = op_inv * pkinv[prow];
+        }
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((j >> 1) & 1)))) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        for (int j0 = 0; j0 < kTileN; j0 += 16) {
+          __syncwarp();  // the lanes leave the previous group's adds at different points
+          uint32_t v[16];
+          const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kTileN + j0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int rb = row0 + j0;  // operator row of v[0]
+          if (dst_off < 0) {
+          } else if (pt == 4) {
+#pragma unroll
+            for (int gi = 0; gi < 4; ++gi) {
+              const int r = rb + 4 * gi;
+              if (r < P) {
+                float* dst = loc + dst_off + (int64_t)smap[map_off + (r >> 2)] * 4;
+                atomicAdd((float4*)dst, make_float4(__uint_as_float(v[4 * gi]) * ci, __uint_as_float(v[4 * gi + 1]) * ci,
+                                                    __uint_as_float(v[4 * gi + 2]) * ci,
+                                                    __uint_as_float(v[4 * gi + 3]) * ci));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int r = rb + jj;
+              if (r < P) {
+                const int ap = r / pt, m = r - ap * pt;
+                atomicAdd(loc + dst_off + (int64_t)smap[map_off + ap] * pt + m, __uint_as_float(v[jj]) * ci);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&acc_empty[b]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
+}
+
+// Packed moments of the FP16 form for k_m2l_res: row (as in k_m2l_pack) scaled
+// by a power of two (k_m2l_pack_scaled) and split into FP16 hi and lo parts,
+// pk16[(row * 2 + part) * P16 + e], zero past P up to P16 (a multiple of 64).
+// One warp per row.
+__global__ void k_m2l_pack_f16(const int32_t* cS, const int16_t* csym, int64_t nrows, const int16_t* smap,
+                               const float* mom, int k, int R, int PS, int pt, int P16, __half* pk16,
+                               float* pkinv) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;  // whole warps: a warp's lanes share their row
+  const int64_t per = 2LL * R * kNCmp;
+  const int64_t combo = row / per, rem = row - combo * per;
+  const int P = PS * pt;
+  const float* base = mom + (((int64_t)cS[combo] * 2 + (k & 1)) * per + rem) * P;
+  const int16_t* sm = smap + csym[combo] * PS;
+  float m = 0.f;
+  for (int e = lane; e < P; e += 32) m = fmaxf(m, fabsf(base[(int64_t)sm[e / pt] * pt + e % pt]));
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  const int sx = f16_scale_exp(m);
+  const float sc = ldexpf(1.f, sx);
+  __half* hi = pk16 + row * 2 * P16;
+  __half* lo = hi + P16;
+  for (int e = lane; e < P16; e += 32) {
+    const float x = e < P ? sc * base[(int64_t)sm[e / pt] * pt + e % pt] : 0.f;
+    const __half h = __float2half_rn(x);
+    hi[e] = h;
+    lo[e] = __float2half_rn(x - __half2float(h));
+  }
+  if (lane == 0) pkinv[row] = ldexpf(1.f, -sx);
+}
+
 }  // namespace tdbem
 
 // Launch the tensor-core M2L of one level event with mt (1 or 2) 128-row
@@ -606,6 +864,48 @@ tdbem_status tdbem_m2l_pack(tdbem_ctx* c, const int32_t* cS, const int16_t* csym
   }
   const int64_t nth = nrows * PS;
   k_m2l_pack<<<(unsigned)((nth + 255) / 256), 256, 0, c->stream>>>(cS, csym, nrows, smap, mom, k, R, PS, pt, pk);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// The FP16 form with resident operator rows (k_m2l_res): units [u0, u0 + n) of
+// the level's unit list, on a persistent grid of at most one CTA per SM and at
+// most max_ctas CTAs (0: no further limit), or with max_ctas < 0 one CTA per
+// unit (the hardware then schedules the units among other streams' work).
+tdbem_status tdbem_m2l_res(tdbem_ctx* c, const int4* gemm, const int4* units, int u0, int n, const uint4* img, int P,
+                           int pt, int PS, const int32_t* pO, const int32_t* pC, const int16_t* psym,
+                           const int16_t* smap, const __half* pk16, int k, float* loc, int Q, int R,
+                           const float* opinv, const float* pkinv, int32_t* err, int max_ctas) {
+  using namespace tdbem;
+  static bool attr = false;
+  static int nsm = 0;
+  if (!attr) {
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_m2l_res, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmem));
+    TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    attr = true;
+  }
+  if (n <= 0) return TDBEM_OK;
+  const int P16 = (P + 63) / 64 * 64;
+  if (P16 > 64 * kResMaxCh) {
+    c->set_error("fast: resident-operator M2L needs P <= 256");
+    return TDBEM_EINVAL;
+  }
+  const int grid = max_ctas < 0 ? n : std::min(n, max_ctas > 0 ? std::min(max_ctas, nsm) : nsm);
+  k_m2l_res<<<grid, kResThreads, kResSmem, c->stream>>>(gemm, units + u0, n, img, P, P16, pt, PS, pO, pC, psym, smap,
+                                                         pk16, k, loc, Q, R, opinv, pkinv, err);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_m2l_pack_f16(tdbem_ctx* c, const int32_t* cS, const int16_t* csym, int ncombo,
+                                const int16_t* smap, const float* mom, int k, int R, int PS, int pt, __half* pk16,
+                                float* pkinv) {
+  using namespace tdbem;
+  const int64_t nrows = (int64_t)ncombo * 2 * R * kNCmp;
+  if (nrows == 0) return TDBEM_OK;
+  const int P16 = (PS * pt + 63) / 64 * 64;
+  k_m2l_pack_f16<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, c->stream>>>(cS, csym, nrows, smap, mom, k, R, PS,
+                                                                              pt, P16, pk16, pkinv);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }

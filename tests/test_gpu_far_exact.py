@@ -56,12 +56,13 @@ def _smooth_history(ne, n, seed):
     return np.sin(2 * np.pi * np.arange(n)[:, None] / P[None, :] + ph[None, :])
 
 
-# (M2L precision, check kernel, s_interp, t_interp, a_deriv): FP32 CUDA cores
-# and TF32x3 tensor cores; the T3 kernel under Lagrange interpolation, with
+# (M2L precision, check kernel, s_interp, t_interp, a_deriv): FP32 CUDA cores,
+# TF32x3 tensor cores, and FP16x3 with the operator resident in shared memory
+# (k_m2l_res); the T3 kernel under Lagrange interpolation, with
 # CHI in space, and with the two other placements of the vector potential's
 # time derivatives; the T2 kernel (degree 2 in time, which CHI reproduces)
 # under CHI in space and time, with every placement.
-CASES = [(0, 1, 0, 0, 0), (4, 1, 0, 0, 0), (4, 1, 1, 0, 0), (4, 1, 0, 0, 1), (4, 1, 0, 0, 2),
+CASES = [(0, 1, 0, 0, 0), (4, 1, 0, 0, 0), (5, 1, 0, 0, 0), (4, 1, 1, 0, 0), (4, 1, 0, 0, 1), (4, 1, 0, 0, 2),
          (4, 3, 1, 1, 0), (4, 3, 1, 1, 1), (4, 3, 1, 1, 2)]
 
 

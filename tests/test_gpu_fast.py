@@ -183,6 +183,25 @@ def test_m2l_tile_shapes_and_autotuner(sphere1280_direct):
     assert chosen and all(r in (128, 256) for r in chosen), chosen
 
 
+def test_fp16_resident_operator_kernel(sphere1280_direct):
+    """The FP16 form's two kernels -- the tiled one and the one that keeps the
+    operator's 128-row tiles resident in shared memory (m2l_tile_rows = 1
+    forces it) -- give the same march up to the order of the FP32 atomic
+    additions, and the autotuner reports which one each level runs."""
+    w, Jd = sphere1280_direct
+    Jt = _solver(w, mode=1, m2l_prec=5, m2l_tile_rows=128).march(w.Nt - 1)
+    sr = _solver(w, mode=1, m2l_prec=5, m2l_tile_rows=1)
+    inf = sr.info()
+    assert inf.m2l_resident == sum(1 << l for l in range(2, inf.lmax + 1)), inf.m2l_resident
+    Jr = sr.march(w.Nt - 1)
+    assert _rel(Jr, Jt) < 1e-4
+    assert abs(_rel(Jr, Jd) - _rel(Jt, Jd)) < 1e-4
+    sa = _solver(w, mode=1, m2l_prec=5)
+    ia = sa.info()
+    print("\nautotuned: resident levels mask", ia.m2l_resident, "tile rows", list(ia.m2l_tile_rows))
+    assert ia.m2l_resident & ~sum(1 << l for l in range(2, ia.lmax + 1)) == 0
+
+
 def test_far_overlap_matches_program_order():
     """The M2L products of lag q >= 2, whose local coefficients are first read
     one interval after the event that fires them, run on the context's second
