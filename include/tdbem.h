@@ -381,8 +381,16 @@ tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, i
 #define TDBEM_MLP_FEATURES 25
 #define TDBEM_MLP_WIDTH 64
 #define TDBEM_MLP_NPARAM (TDBEM_MLP_WIDTH * TDBEM_MLP_FEATURES + TDBEM_MLP_WIDTH * TDBEM_MLP_WIDTH + TDBEM_MLP_WIDTH)
+#define TDBEM_MLP_NPARAM_OF(H) ((H) * TDBEM_MLP_FEATURES + (H) * (H) + (H))
 
-/* Set (host array of TDBEM_MLP_NPARAM floats, copied) or read the network's
+/* Width of the network: TDBEM_MLP_WIDTH (64, the default; FP32 arithmetic on the CUDA cores) or 256.  At
+   width 256 the dense layers of inference and training and the weight gradients run as products on the
+   tensor cores (BF16 operands, FP32 accumulation; FP32 parameters and Adam), the parameter count being
+   TDBEM_MLP_NPARAM_OF(256).  Discards the weights, Adam's moments and the use flag (set the weights
+   again); recorded samples are kept. */
+tdbem_status tdbem_mlp_set_width(tdbem_ctx* ctx, int32_t width);
+
+/* Set (host array of TDBEM_MLP_NPARAM_OF(width) floats, copied) or read the network's
    parameters.  The first set allocates the network; Adam's moments are reset. */
 tdbem_status tdbem_mlp_set_weights(tdbem_ctx* ctx, const float* theta);
 tdbem_status tdbem_mlp_get_weights(tdbem_ctx* ctx, float* theta);
@@ -399,6 +407,9 @@ tdbem_status tdbem_mlp_get_weights(tdbem_ctx* ctx, float* theta);
    W [n], host; any may be NULL) and the number stored so far (count may be
    NULL). */
 tdbem_status tdbem_mlp_record(tdbem_ctx* ctx, int64_t capacity);
+/* Record only the steps alpha with alpha % every == 0 (default 1: every step), so that a buffer of a
+   given capacity spans more trajectories. */
+tdbem_status tdbem_mlp_record_every(tdbem_ctx* ctx, int32_t every);
 tdbem_status tdbem_mlp_samples(tdbem_ctx* ctx, int64_t first, int64_t n, float* X, float* T, float* W,
                                int64_t* count);
 

@@ -94,9 +94,11 @@ def lib():
         L.tdbem_destroy.argtypes = [vp]
         L.tdbem_destroy.restype = None
         i64, i64p = ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)
+        L.tdbem_mlp_set_width.argtypes = [vp, ctypes.c_int32]
         L.tdbem_mlp_set_weights.argtypes = [vp, _fp]
         L.tdbem_mlp_get_weights.argtypes = [vp, _fp]
         L.tdbem_mlp_record.argtypes = [vp, i64]
+        L.tdbem_mlp_record_every.argtypes = [vp, ctypes.c_int32]
         L.tdbem_mlp_samples.argtypes = [vp, i64, i64, _fp, _fp, _fp, i64p]
         L.tdbem_mlp_train.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _fp]
         L.tdbem_mlp_grad.argtypes = [vp, _fp, _fp, _fp, i64, ctypes.POINTER(ctypes.c_float), _fp]
@@ -109,8 +111,8 @@ def lib():
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
                      "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
-                     "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_weights",
-                     "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_samples", "tdbem_mlp_train",
+                     "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_width", "tdbem_mlp_set_weights",
+                     "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_record_every", "tdbem_mlp_samples", "tdbem_mlp_train",
                      "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats", "tdbem_march_many",
                      "tdbem_save", "tdbem_load"):
             getattr(L, name).restype = ctypes.c_int
@@ -251,7 +253,15 @@ class Solver:
 
     # ---- learned warm start (see include/tdbem.h)
     MLP_FEATURES, MLP_WIDTH = 25, 64
-    MLP_NPARAM = MLP_WIDTH * MLP_FEATURES + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH
+
+    @property
+    def MLP_NPARAM(self) -> int:
+        H = self.MLP_WIDTH
+        return H * self.MLP_FEATURES + H * H + H
+
+    def mlp_set_width(self, width: int):
+        self._check(lib().tdbem_mlp_set_width(self._h, int(width)))
+        self.MLP_WIDTH = int(width)
 
     def mlp_set_weights(self, theta):
         t = np.ascontiguousarray(theta, dtype=np.float32)
@@ -266,6 +276,9 @@ class Solver:
 
     def mlp_record(self, capacity: int):
         self._check(lib().tdbem_mlp_record(self._h, ctypes.c_int64(int(capacity))))
+
+    def mlp_record_every(self, every: int):
+        self._check(lib().tdbem_mlp_record_every(self._h, int(every)))
 
     def mlp_count(self) -> int:
         n = ctypes.c_int64()

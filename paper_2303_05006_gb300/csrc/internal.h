@@ -1,6 +1,7 @@
 // internal.h -- library-private declarations shared by the CUDA translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -225,6 +226,10 @@ void tdbem_fast_info(const tdbem_ctx* c, tdbem_info* info);
 void tdbem_fast_state(tdbem_ctx* c, std::vector<std::pair<void*, size_t>>* bufs);
 tdbem_status tdbem_fast_z0_source(const tdbem_ctx* c, const int64_t** row_ptr, const int32_t** col,
                                   const int16_t** m_lo, const uint8_t** nlag, const int64_t** off, const double** val);
+// gemm_tc.cu: C (M x N, FP32) = or += A (M x K) . B (N x K)^T, BF16 row-major operands on the tensor cores
+tdbem_status tdbem_gemm_bf16(tdbem_ctx* c, cudaStream_t st, const __nv_bfloat16* A, int64_t lda,
+                             const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc, int M, int N, int K, int add,
+                             int ksplit, int32_t* err);
 // mlp.cu
 tdbem_status tdbem_mlp_before_solve(tdbem_ctx* c, int32_t alpha, int32_t* warm);
 tdbem_status tdbem_mlp_after_solve(tdbem_ctx* c, int32_t alpha);

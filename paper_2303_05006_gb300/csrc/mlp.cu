@@ -21,12 +21,24 @@
 //                 weight gradients as block-level sums over the samples,
 //                 one atomic add per parameter per block;
 //   k_mlp_adam    Adam update, then the gradient is cleared.
+//
+// Width 256 (tdbem_mlp_set_width) runs the two dense layers and the weight
+// gradients as products on the tcgen05 tensor cores (gemm_tc.cu: BF16
+// operands, FP32 accumulation; FP32 master parameters, FP32 Adam).  A pass
+// over n rows is: features or gathered samples -> X (BF16, 25 features padded
+// to 32) -> Z1 = X W1^T -> H1 = tanh Z1 -> Z2 = H1 W2^T -> head (y, and for
+// training the loss, dy and D2 = dy w3 (1 - h2^2)); training then forms
+// dW2 = D2^T H1, dH1 = D2 W2, D1 = dH1 (1 - h1^2) and dW1 = D1^T X, the
+// products over the batch taking the transposed BF16 copies as K-major
+// operands (k_bf16_transpose).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <utility>
 #include <vector>
+
+#include <cuda_bf16.h>
 
 #include "internal.h"
 
@@ -262,6 +274,157 @@ __global__ void k_mlp_adam(float* W, float* G, float* M, float* V, int n, float 
   G[k] = 0.f;
 }
 
+// ---- width 256 on the tensor cores ----
+constexpr int kH2 = 256, kFP = 32;  // width; features padded to 32 (the products' K is a multiple of 8)
+constexpr int64_t kNP2 = (int64_t)kH2 * kF + (int64_t)kH2 * kH2 + kH2;
+
+// FP32 master parameters -> BF16 operands: W1 [H][F] -> wb1 [H][32]
+// (zero-padded), W2 [H][H] -> wb2 and its transpose wb2t
+__global__ void k_mlp_cast(const float* W, __nv_bfloat16* wb1, __nv_bfloat16* wb2, __nv_bfloat16* wb2t) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kH2 * kFP) {
+    const int j = t / kFP, f = t - j * kFP;
+    wb1[t] = __float2bfloat16_rn(f < kF ? W[j * kF + f] : 0.f);
+  }
+  if (t < kH2 * kH2) {
+    const int j = t / kH2, k = t - j * kH2;
+    const __nv_bfloat16 v = __float2bfloat16_rn(W[kH2 * kF + t]);
+    wb2[t] = v;
+    wb2t[k * kH2 + j] = v;
+  }
+}
+
+// inference features of every (edge, RHS) as BF16 rows of 32, with the
+// scale and the cubic extrapolation
+__global__ void __launch_bounds__(128) k_mlp_feat_tc(FeatArgs a, __nv_bfloat16* xb, double* sx, double* xcx) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.ne * a.R) return;
+  const int64_t i = t / a.R;
+  const int r = (int)(t - i * a.R);
+  float x[kF];
+  double s, xc;
+  features(a, i, r, x, s, xc);
+  for (int f = 0; f < kFP; ++f) xb[t * kFP + f] = __float2bfloat16_rn(f < kF ? x[f] : 0.f);
+  sx[t] = s;
+  xcx[t] = xc;
+}
+
+// rows [b0, b0 + nrows) of a batch: sample perm[b0 + k] (k when perm is null)
+// of X as a BF16 row of 32, its target and weight (1 when Wt is null); rows
+// k >= nb are zero with zero weight
+__global__ void k_mlp_gather_tc(const float* X, const float* T, const float* Wt, const int32_t* perm, int64_t b0,
+                                int nb, int nrows, __nv_bfloat16* xb, float* tb, float* wtb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nrows * kFP) return;
+  const int k = (int)(t / kFP), f = (int)(t - (int64_t)k * kFP);
+  const bool v = k < nb;
+  const int64_t idx = v ? (int64_t)(perm ? perm[b0 + k] : b0 + k) : 0;
+  xb[t] = __float2bfloat16_rn(v && f < kF ? X[idx * kF + f] : 0.f);
+  if (f == 0 && tb) {
+    tb[k] = v ? T[idx] : 0.f;
+    wtb[k] = v ? (Wt ? Wt[idx] : 1.f) : 0.f;
+  }
+}
+
+// out[c * ldo + r] = in[r * cols + c] (BF16), 32 x 32 tiles through shared memory
+__global__ void k_bf16_transpose(const __nv_bfloat16* in, int rows, int cols, __nv_bfloat16* out, int64_t ldo) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(int64_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(int64_t)c * ldo + r] = tile[threadIdx.x][k];
+  }
+}
+
+__global__ void k_tanh_bf16(const float* z, int64_t n, __nv_bfloat16* h) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) h[t] = __float2bfloat16_rn(tanhf(z[t]));
+}
+
+// d1 = dh1 (1 - h1^2) as BF16
+__global__ void k_mlp_dtanh(const float* dh1, const __nv_bfloat16* h1b, int64_t n, __nv_bfloat16* d1b) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float h = __bfloat162float(h1b[t]);
+  d1b[t] = __float2bfloat16_rn(dh1[t] * (1.f - h * h));
+}
+
+// inference head, one warp per row: y = w3 . tanh(z2); x0 = xc + s y (or y
+// itself into yout)
+__global__ void k_mlp_out_tc(const float* z2, const float* w3, int64_t n, const double* sx, const double* xcx,
+                             double* x0, float* yout) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float y = 0.f;
+  for (int j = lane; j < kH2; j += 32) y += w3[j] * tanhf(z2[row * kH2 + j]);
+  for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+  if (lane == 0) {
+    if (yout) yout[row] = y;
+    if (x0) x0[row] = sx[row] > 0.0 ? xcx[row] + sx[row] * (double)y : xcx[row];
+  }
+}
+
+// training head: warps stride over the rows; per row h2 = tanh(z2), y, the
+// weighted error, dy = 2 w e / nb, d2 = dy w3 (1 - h2^2) (BF16 into d2b) and
+// the loss; dL/dw3 = sum over rows of dy h2, per lane then per block, added
+// to g3 once per block
+__global__ void __launch_bounds__(256) k_mlp_head_tc(const float* z2, const float* w3, const float* tb,
+                                                     const float* wtb, int nrows, int nb, __nv_bfloat16* d2b,
+                                                     float* g3, double* loss) {
+  __shared__ float g3s[kH2];
+  __shared__ double ls[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x; j < kH2; j += blockDim.x) g3s[j] = 0.f;
+  __syncthreads();
+  float g[kH2 / 32];
+#pragma unroll
+  for (int q = 0; q < kH2 / 32; ++q) g[q] = 0.f;
+  double lw = 0.0;
+  for (int row = blockIdx.x * 8 + warp; row < nrows; row += gridDim.x * 8) {
+    float h2[kH2 / 32];
+    float y = 0.f;
+#pragma unroll
+    for (int q = 0; q < kH2 / 32; ++q) {
+      h2[q] = tanhf(z2[(int64_t)row * kH2 + lane + 32 * q]);
+      y += w3[lane + 32 * q] * h2[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    const float e = y - tb[row], w = wtb[row];
+    const float dy = 2.f * w * e / (float)nb;
+    lw += (double)w * (double)e * (double)e / (double)nb;
+#pragma unroll
+    for (int q = 0; q < kH2 / 32; ++q) {
+      const int j = lane + 32 * q;
+      d2b[(int64_t)row * kH2 + j] = __float2bfloat16_rn(dy * w3[j] * (1.f - h2[q] * h2[q]));
+      g[q] += dy * h2[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kH2 / 32; ++q) atomicAdd(&g3s[lane + 32 * q], g[q]);
+  if (lane == 0) ls[warp] = lw;  // lw is the same in every lane
+  __syncthreads();
+  for (int j = threadIdx.x; j < kH2; j += blockDim.x) atomicAdd(&g3[j], g3s[j]);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += ls[w];
+    atomicAdd(loss, t);
+  }
+}
+
+// G1 [H][F] += g1p[:, :F] (g1p [H][32])
+__global__ void k_mlp_fold_g1(const float* g1p, float* G) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kH2 * kF) return;
+  const int j = t / kF, f = t - j * kF;
+  G[t] += g1p[j * kFP + f];
+}
+
 constexpr size_t kTrainSmem =
     sizeof(float) * ((size_t)kNP + (size_t)kTB * kF + 4 * (size_t)kTB * kHS + (size_t)kTB);
 
@@ -270,7 +433,9 @@ constexpr size_t kTrainSmem =
 using namespace tdbem;
 
 struct Mlp {
-  float* w = nullptr;   // parameters [kNP]
+  int H = kH;           // width: 64 (FP32 CUDA cores) or 256 (tensor cores)
+  int64_t np = kNP;     // parameters of that width
+  float* w = nullptr;   // parameters [np]
   float* g = nullptr;   // gradient accumulator
   float* m = nullptr;   // Adam moments
   float* v = nullptr;
@@ -281,15 +446,45 @@ struct Mlp {
   float* T = nullptr;      // [cap]
   float* Wt = nullptr;     // [cap] sample weights
   int64_t cap = 0, count = 0;
+  int32_t every = 1;       // record the steps alpha with alpha % every == 0
   bool use = false;
   bool have_w = false;     // parameters set by the caller
   double* loss = nullptr;  // device accumulator
   int32_t* perm = nullptr; // [cap]
+  // width 256: BF16 operand copies of the parameters and the work rows
+  __nv_bfloat16 *wb1 = nullptr, *wb2 = nullptr, *wb2t = nullptr;
+  int64_t rows_cap = 0;
+  __nv_bfloat16 *xb = nullptr, *xbt = nullptr, *h1b = nullptr, *h1bt = nullptr, *d2b = nullptr, *d2bt = nullptr,
+                *d1b = nullptr, *d1bt = nullptr;
+  float *z = nullptr, *tb = nullptr, *wtb = nullptr, *g1p = nullptr;
+  double *sx = nullptr, *xcx = nullptr;
+  int32_t* err = nullptr;
 };
 
+static void mlp_free_rows(Mlp* M) {
+  for (void* p : {(void*)M->xb, (void*)M->xbt, (void*)M->h1b, (void*)M->h1bt, (void*)M->d2b, (void*)M->d2bt,
+                  (void*)M->d1b, (void*)M->d1bt, (void*)M->z, (void*)M->tb, (void*)M->wtb, (void*)M->sx,
+                  (void*)M->xcx})
+    if (p) cudaFree(p);
+  M->xb = M->xbt = M->h1b = M->h1bt = M->d2b = M->d2bt = M->d1b = M->d1bt = nullptr;
+  M->z = M->tb = M->wtb = nullptr;
+  M->sx = M->xcx = nullptr;
+  M->rows_cap = 0;
+}
+
+static void mlp_free_params(Mlp* M) {
+  for (void* p : {(void*)M->w, (void*)M->g, (void*)M->m, (void*)M->v, (void*)M->wb1, (void*)M->wb2, (void*)M->wb2t,
+                  (void*)M->g1p})
+    if (p) cudaFree(p);
+  M->w = M->g = M->m = M->v = M->g1p = nullptr;
+  M->wb1 = M->wb2 = M->wb2t = nullptr;
+}
+
 static void mlp_free_buffers(Mlp* M) {
-  for (void* p : {(void*)M->w, (void*)M->g, (void*)M->m, (void*)M->v, (void*)M->nb, (void*)M->nbs, (void*)M->X,
-                  (void*)M->T, (void*)M->Wt, (void*)M->loss, (void*)M->perm})
+  mlp_free_params(M);
+  mlp_free_rows(M);
+  for (void* p : {(void*)M->nb, (void*)M->nbs, (void*)M->X, (void*)M->T, (void*)M->Wt, (void*)M->loss,
+                  (void*)M->perm, (void*)M->err})
     if (p) cudaFree(p);
 }
 
@@ -316,11 +511,9 @@ static tdbem_status mlp_init(tdbem_ctx* c) {
   Mlp* M = new (std::nothrow) Mlp();
   if (!M) return TDBEM_ENOMEM;
   c->mlp = M;
-  MLP_TRY(cudaMalloc(&M->w, kNP * sizeof(float)));
-  MLP_TRY(cudaMalloc(&M->g, kNP * sizeof(float)));
-  MLP_TRY(cudaMalloc(&M->m, kNP * sizeof(float)));
-  MLP_TRY(cudaMalloc(&M->v, kNP * sizeof(float)));
   MLP_TRY(cudaMalloc(&M->loss, sizeof(double)));
+  MLP_TRY(cudaMalloc(&M->err, sizeof(int32_t)));
+  MLP_TRY(cudaMemset(M->err, 0, sizeof(int32_t)));
   MLP_TRY(cudaMalloc(&M->nb, 4 * c->ne * sizeof(int32_t)));
   MLP_TRY(cudaMalloc(&M->nbs, 4 * c->ne * sizeof(int8_t)));
   std::vector<int32_t> nb(4 * c->ne);
@@ -347,6 +540,114 @@ static tdbem_status mlp_init(tdbem_ctx* c) {
   return TDBEM_OK;
 }
 
+// Parameter buffers of the current width (and, for width 256, the BF16
+// operand copies and the padded first-layer gradient).
+static tdbem_status mlp_alloc_params(tdbem_ctx* c) {
+  Mlp* M = c->mlp;
+  if (M->w) return TDBEM_OK;
+  MLP_TRY(cudaMalloc(&M->w, M->np * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->g, M->np * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->m, M->np * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->v, M->np * sizeof(float)));
+  if (M->H == kH2) {
+    MLP_TRY(cudaMalloc(&M->wb1, (size_t)kH2 * kFP * sizeof(__nv_bfloat16)));
+    MLP_TRY(cudaMalloc(&M->wb2, (size_t)kH2 * kH2 * sizeof(__nv_bfloat16)));
+    MLP_TRY(cudaMalloc(&M->wb2t, (size_t)kH2 * kH2 * sizeof(__nv_bfloat16)));
+    MLP_TRY(cudaMalloc(&M->g1p, (size_t)kH2 * kFP * sizeof(float)));
+  }
+  return TDBEM_OK;
+}
+
+// Work rows of the width-256 passes, grown to hold n rows (a multiple of 128).
+static tdbem_status mlp_rows(tdbem_ctx* c, int64_t n) {
+  Mlp* M = c->mlp;
+  if (n <= M->rows_cap) return TDBEM_OK;
+  MLP_TRY(cudaStreamSynchronize(c->stream));
+  mlp_free_rows(M);
+  const size_t hb = (size_t)n * kH2 * sizeof(__nv_bfloat16), xbsz = (size_t)n * kFP * sizeof(__nv_bfloat16);
+  MLP_TRY(cudaMalloc(&M->xb, xbsz));
+  MLP_TRY(cudaMalloc(&M->xbt, xbsz));
+  for (__nv_bfloat16** p : {&M->h1b, &M->h1bt, &M->d2b, &M->d2bt, &M->d1b, &M->d1bt}) MLP_TRY(cudaMalloc(p, hb));
+  MLP_TRY(cudaMalloc(&M->z, (size_t)n * kH2 * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->tb, n * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->wtb, n * sizeof(float)));
+  MLP_TRY(cudaMalloc(&M->sx, n * sizeof(double)));
+  MLP_TRY(cudaMalloc(&M->xcx, n * sizeof(double)));
+  M->rows_cap = n;
+  return TDBEM_OK;
+}
+
+// BF16 operand copies of the current parameters (width 256)
+static tdbem_status mlp_cast(tdbem_ctx* c) {
+  Mlp* M = c->mlp;
+  k_mlp_cast<<<(kH2 * kH2 + 255) / 256, 256, 0, c->stream>>>(M->w, M->wb1, M->wb2, M->wb2t);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+static tdbem_status mlp_check_err(tdbem_ctx* c) {
+  int32_t e = 0;
+  MLP_TRY(cudaMemcpyAsync(&e, c->mlp->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  MLP_TRY(cudaStreamSynchronize(c->stream));
+  if (e) {
+    c->set_error("mlp: a tensor-core product timed out");
+    return TDBEM_ETIMEOUT;
+  }
+  return TDBEM_OK;
+}
+
+// Width 256: the two dense layers over rows xb [n] (n a multiple of 128) ->
+// z = Z2 and h1b = tanh(Z1)
+static tdbem_status mlp_forward_tc(tdbem_ctx* c, int64_t n) {
+  Mlp* M = c->mlp;
+  tdbem_status s;
+  if ((s = tdbem_gemm_bf16(c, c->stream, M->xb, kFP, M->wb1, kFP, M->z, kH2, (int)n, kH2, kFP, 0, 1, M->err)))
+    return s;
+  k_tanh_bf16<<<(unsigned)((n * kH2 + 255) / 256), 256, 0, c->stream>>>(M->z, n * kH2, M->h1b);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return tdbem_gemm_bf16(c, c->stream, M->h1b, kH2, M->wb2, kH2, M->z, kH2, (int)n, kH2, kH2, 0, 1, M->err);
+}
+
+// Width 256, one batch of nrows gathered rows (nb of them real): loss into
+// M->loss, gradient added to M->g
+static tdbem_status mlp_backward_tc(tdbem_ctx* c, int nrows, int nb) {
+  Mlp* M = c->mlp;
+  tdbem_status s;
+  if ((s = mlp_forward_tc(c, nrows))) return s;
+  float* G1 = M->g;
+  float* G2 = M->g + (int64_t)kH2 * kF;
+  float* G3 = G2 + (int64_t)kH2 * kH2;
+  k_mlp_head_tc<<<std::max(1, std::min(nrows / 8, 304)), 256, 0, c->stream>>>(M->z, M->w + kH2 * kF + kH2 * kH2,
+                                                                              M->tb, M->wtb, nrows, nb, M->d2b, G3,
+                                                                              M->loss);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  const dim3 tb(32, 8);
+  k_bf16_transpose<<<dim3(kH2 / 32, nrows / 32), tb, 0, c->stream>>>(M->d2b, nrows, kH2, M->d2bt, nrows);
+  k_bf16_transpose<<<dim3(kH2 / 32, nrows / 32), tb, 0, c->stream>>>(M->h1b, nrows, kH2, M->h1bt, nrows);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  const int ksplit = std::max(1, nrows / 256);  // two 128-row tiles of dW2: about nrows / 128 CTAs
+  // dW2 = D2^T H1
+  if ((s = tdbem_gemm_bf16(c, c->stream, M->d2bt, nrows, M->h1bt, nrows, G2, kH2, kH2, kH2, nrows, 1, ksplit,
+                           M->err)))
+    return s;
+  // dH1 = D2 W2 (into z), D1 = dH1 (1 - h1^2)
+  if ((s = tdbem_gemm_bf16(c, c->stream, M->d2b, kH2, M->wb2t, kH2, M->z, kH2, nrows, kH2, kH2, 0, 1, M->err)))
+    return s;
+  k_mlp_dtanh<<<(unsigned)(((int64_t)nrows * kH2 + 255) / 256), 256, 0, c->stream>>>(M->z, M->h1b,
+                                                                                     (int64_t)nrows * kH2, M->d1b);
+  k_bf16_transpose<<<dim3(kH2 / 32, nrows / 32), tb, 0, c->stream>>>(M->d1b, nrows, kH2, M->d1bt, nrows);
+  k_bf16_transpose<<<dim3(kFP / 32, nrows / 32), tb, 0, c->stream>>>(M->xb, nrows, kFP, M->xbt, nrows);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  // dW1 = D1^T X (padded to 32 columns, then folded into G1)
+  MLP_TRY(cudaMemsetAsync(M->g1p, 0, (size_t)kH2 * kFP * sizeof(float), c->stream));
+  if ((s = tdbem_gemm_bf16(c, c->stream, M->d1bt, nrows, M->xbt, nrows, M->g1p, kFP, kH2, kFP, nrows, 1,
+                           std::max(1, nrows / 128), M->err)))
+    return s;
+  k_mlp_fold_g1<<<(kH2 * kF + 255) / 256, 256, 0, c->stream>>>(M->g1p, G1);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
 static FeatArgs feat_args(tdbem_ctx* c, int32_t alpha) {
   FeatArgs a;
   a.ring = c->d_Jring;
@@ -364,9 +665,23 @@ static FeatArgs feat_args(tdbem_ctx* c, int32_t alpha) {
 // Before the solve of step alpha: the network's guess into d_J (warm = 2).
 tdbem_status tdbem_mlp_before_solve(tdbem_ctx* c, int32_t alpha, int32_t* warm) {
   if (!c->mlp || !c->mlp->use) return TDBEM_OK;
+  Mlp* M = c->mlp;
   const int64_t n = c->ne * (int64_t)c->R;
-  k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(feat_args(c, alpha), c->mlp->w, c->d_J);
-  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if (M->H == kH2) {
+    const int64_t nr = (n + 127) / 128 * 128;
+    tdbem_status s;
+    if ((s = mlp_rows(c, nr))) return s;
+    if (nr > n) MLP_TRY(cudaMemsetAsync(M->xb + n * kFP, 0, (nr - n) * kFP * sizeof(__nv_bfloat16), c->stream));
+    k_mlp_feat_tc<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(feat_args(c, alpha), M->xb, M->sx, M->xcx);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if ((s = mlp_forward_tc(c, nr))) return s;
+    k_mlp_out_tc<<<(unsigned)((n * 32 + 255) / 256), 256, 0, c->stream>>>(M->z, M->w + kH2 * kF + kH2 * kH2, n,
+                                                                          M->sx, M->xcx, c->d_J, nullptr);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  } else {
+    k_mlp_infer<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(feat_args(c, alpha), M->w, c->d_J);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
   *warm = 2;
   return TDBEM_OK;
 }
@@ -374,7 +689,7 @@ tdbem_status tdbem_mlp_before_solve(tdbem_ctx* c, int32_t alpha, int32_t* warm) 
 // After the solve of step alpha: record its samples while there is room.
 tdbem_status tdbem_mlp_after_solve(tdbem_ctx* c, int32_t alpha) {
   Mlp* M = c->mlp;
-  if (!M || !M->X) return TDBEM_OK;
+  if (!M || !M->X || alpha % M->every) return TDBEM_OK;
   const int64_t n = c->ne * (int64_t)c->R;
   if (M->count + n > M->cap) return TDBEM_OK;
   k_mlp_record<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(feat_args(c, alpha), c->d_J, M->count, M->X,
@@ -396,15 +711,31 @@ static uint64_t splitmix64(uint64_t& x) {
 
 extern "C" {
 
-tdbem_status tdbem_mlp_set_weights(tdbem_ctx* c, const float* theta) {
-  if (!c || !theta) return TDBEM_EINVAL;
+tdbem_status tdbem_mlp_set_width(tdbem_ctx* c, int32_t width) {
+  if (!c || (width != kH && width != kH2)) return TDBEM_EINVAL;
   tdbem_status s = mlp_init(c);
   if (s) return s;
   Mlp* M = c->mlp;
-  MLP_TRY(cudaMemcpyAsync(M->w, theta, kNP * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  MLP_TRY(cudaMemsetAsync(M->g, 0, kNP * sizeof(float), c->stream));
-  MLP_TRY(cudaMemsetAsync(M->m, 0, kNP * sizeof(float), c->stream));
-  MLP_TRY(cudaMemsetAsync(M->v, 0, kNP * sizeof(float), c->stream));
+  MLP_TRY(cudaStreamSynchronize(c->stream));
+  mlp_free_params(M);
+  mlp_free_rows(M);
+  M->H = width;
+  M->np = (int64_t)width * kF + (int64_t)width * width + width;
+  M->have_w = false;
+  M->use = false;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_mlp_set_weights(tdbem_ctx* c, const float* theta) {
+  if (!c || !theta) return TDBEM_EINVAL;
+  tdbem_status s = mlp_init(c);
+  if (s || (s = mlp_alloc_params(c))) return s;
+  Mlp* M = c->mlp;
+  MLP_TRY(cudaMemcpyAsync(M->w, theta, M->np * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  MLP_TRY(cudaMemsetAsync(M->g, 0, M->np * sizeof(float), c->stream));
+  MLP_TRY(cudaMemsetAsync(M->m, 0, M->np * sizeof(float), c->stream));
+  MLP_TRY(cudaMemsetAsync(M->v, 0, M->np * sizeof(float), c->stream));
+  if (M->H == kH2 && (s = mlp_cast(c))) return s;
   MLP_TRY(cudaStreamSynchronize(c->stream));
   M->adam_t = 0;
   M->have_w = true;
@@ -417,7 +748,7 @@ tdbem_status tdbem_mlp_get_weights(tdbem_ctx* c, float* theta) {
     c->set_error("mlp: no weights set");
     return TDBEM_ESTATE;
   }
-  MLP_TRY(cudaMemcpyAsync(theta, c->mlp->w, kNP * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  MLP_TRY(cudaMemcpyAsync(theta, c->mlp->w, c->mlp->np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   MLP_TRY(cudaStreamSynchronize(c->stream));
   return TDBEM_OK;
 }
@@ -441,6 +772,14 @@ tdbem_status tdbem_mlp_record(tdbem_ctx* c, int64_t capacity) {
   MLP_TRY(cudaMalloc(&M->Wt, capacity * sizeof(float)));
   MLP_TRY(cudaMalloc(&M->perm, capacity * sizeof(int32_t)));
   M->cap = capacity;
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_mlp_record_every(tdbem_ctx* c, int32_t every) {
+  if (!c || every < 1) return TDBEM_EINVAL;
+  tdbem_status s = mlp_init(c);
+  if (s) return s;
+  c->mlp->every = every;
   return TDBEM_OK;
 }
 
@@ -480,15 +819,33 @@ tdbem_status tdbem_mlp_train(tdbem_ctx* c, int32_t epochs, int32_t batch, float 
     int64_t nbatch = 0;
     for (int64_t b0 = 0; b0 < n; b0 += batch) {
       const int32_t nb = (int32_t)std::min<int64_t>(batch, n - b0);
-      k_mlp_train<<<(unsigned)((nb + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(M->X, M->T, M->Wt, M->perm, b0,
-                                                                                       nb, M->w, M->g, M->loss);
-      TDBEM_CUDA_TRY(c, cudaGetLastError());
+      if (M->H == kH2) {
+        const int nrows = (nb + kTB - 1) / kTB * kTB;
+        tdbem_status s;
+        if ((s = mlp_rows(c, nrows))) return s;
+        k_mlp_gather_tc<<<(unsigned)(((int64_t)nrows * kFP + 255) / 256), 256, 0, c->stream>>>(
+            M->X, M->T, M->Wt, M->perm, b0, nb, nrows, M->xb, M->tb, M->wtb);
+        TDBEM_CUDA_TRY(c, cudaGetLastError());
+        if ((s = mlp_backward_tc(c, nrows, nb))) return s;
+      } else {
+        k_mlp_train<<<(unsigned)((nb + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(M->X, M->T, M->Wt, M->perm,
+                                                                                         b0, nb, M->w, M->g, M->loss);
+        TDBEM_CUDA_TRY(c, cudaGetLastError());
+      }
       ++M->adam_t;
       const float c1 = 1.f - powf(0.9f, (float)M->adam_t), c2 = 1.f - powf(0.999f, (float)M->adam_t);
-      k_mlp_adam<<<(kNP + 255) / 256, 256, 0, c->stream>>>(M->w, M->g, M->m, M->v, kNP, lr, 0.9f, 0.999f, 1e-8f, c1,
-                                                           c2);
+      k_mlp_adam<<<(unsigned)((M->np + 255) / 256), 256, 0, c->stream>>>(M->w, M->g, M->m, M->v, (int)M->np, lr,
+                                                                          0.9f, 0.999f, 1e-8f, c1, c2);
       TDBEM_CUDA_TRY(c, cudaGetLastError());
+      if (M->H == kH2) {
+        tdbem_status s;
+        if ((s = mlp_cast(c))) return s;
+      }
       ++nbatch;
+    }
+    if (M->H == kH2) {
+      tdbem_status s;
+      if ((s = mlp_check_err(c))) return s;
     }
     double l = 0.0;
     MLP_TRY(cudaMemcpyAsync(&l, M->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -515,15 +872,25 @@ tdbem_status tdbem_mlp_grad(tdbem_ctx* c, const float* X, const float* T, const 
     MLP_TRY(cudaMallocAsync(&dW, n * sizeof(float), c->stream));
     MLP_TRY(cudaMemcpyAsync(dW, Wt, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   }
-  MLP_TRY(cudaMemsetAsync(M->g, 0, kNP * sizeof(float), c->stream));
+  MLP_TRY(cudaMemsetAsync(M->g, 0, M->np * sizeof(float), c->stream));
   MLP_TRY(cudaMemsetAsync(M->loss, 0, sizeof(double), c->stream));
-  k_mlp_train<<<(unsigned)((n + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(dX, dT, dW, nullptr, 0, (int32_t)n,
-                                                                                M->w, M->g, M->loss);
-  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if (M->H == kH2) {
+    const int nrows = (int)((n + kTB - 1) / kTB * kTB);
+    tdbem_status s;
+    if ((s = mlp_rows(c, nrows))) return s;
+    k_mlp_gather_tc<<<(unsigned)(((int64_t)nrows * kFP + 255) / 256), 256, 0, c->stream>>>(
+        dX, dT, dW, nullptr, 0, (int)n, nrows, M->xb, M->tb, M->wtb);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if ((s = mlp_backward_tc(c, nrows, (int)n)) || (s = mlp_check_err(c))) return s;
+  } else {
+    k_mlp_train<<<(unsigned)((n + kTB - 1) / kTB), kTB, kTrainSmem, c->stream>>>(dX, dT, dW, nullptr, 0, (int32_t)n,
+                                                                                  M->w, M->g, M->loss);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
   double l = 0.0;
-  MLP_TRY(cudaMemcpyAsync(grad, M->g, kNP * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  MLP_TRY(cudaMemcpyAsync(grad, M->g, M->np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   MLP_TRY(cudaMemcpyAsync(&l, M->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  MLP_TRY(cudaMemsetAsync(M->g, 0, kNP * sizeof(float), c->stream));
+  MLP_TRY(cudaMemsetAsync(M->g, 0, M->np * sizeof(float), c->stream));
   cudaFreeAsync(dX, c->stream);
   cudaFreeAsync(dT, c->stream);
   if (dW) cudaFreeAsync(dW, c->stream);
@@ -543,8 +910,23 @@ tdbem_status tdbem_mlp_forward(tdbem_ctx* c, const float* X, int64_t n, float* Y
   MLP_TRY(cudaMallocAsync(&dX, n * kF * sizeof(float), c->stream));
   MLP_TRY(cudaMallocAsync(&dY, n * sizeof(float), c->stream));
   MLP_TRY(cudaMemcpyAsync(dX, X, n * kF * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-  k_mlp_forward_rows<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(dX, n, M->w, dY);
-  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  if (M->H == kH2) {
+    const int64_t nrows = (n + kTB - 1) / kTB * kTB;
+    tdbem_status s;
+    if (nrows > INT32_MAX || (s = mlp_rows(c, nrows))) return nrows > INT32_MAX ? TDBEM_EINVAL : s;
+    k_mlp_gather_tc<<<(unsigned)((nrows * kFP + 255) / 256), 256, 0, c->stream>>>(dX, nullptr, nullptr, nullptr, 0,
+                                                                                 (int)n, (int)nrows, M->xb, nullptr,
+                                                                                 nullptr);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if ((s = mlp_forward_tc(c, nrows))) return s;
+    k_mlp_out_tc<<<(unsigned)((n * 32 + 255) / 256), 256, 0, c->stream>>>(M->z, M->w + kH2 * kF + kH2 * kH2, n,
+                                                                          nullptr, nullptr, nullptr, dY);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if ((s = mlp_check_err(c))) return s;
+  } else {
+    k_mlp_forward_rows<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(dX, n, M->w, dY);
+    TDBEM_CUDA_TRY(c, cudaGetLastError());
+  }
   MLP_TRY(cudaMemcpyAsync(Y, dY, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   cudaFreeAsync(dX, c->stream);
   cudaFreeAsync(dY, c->stream);

@@ -127,6 +127,8 @@ def workload(name: str) -> Workload:
                         (6144 triangles) centred at (3.5, 0, 0), Nt=1000
     * ``cylinder``    : cone-capped cylinder, 4096 triangles, Nt=1500
     * ``ellipsoid10k``: UV ellipsoid (2, 0.5, 0.25), 10240 triangles, Nt=1500
+    * ``ellipsoid5k`` : the 5120-triangle icosphere scaled to the ellipsoid (2, 0.5, 0.25), Nt=1000
+                        (the learned warm start's training shape)
     * ``ellipsoid80k``: octahedral geodesic ellipsoid, 80000 triangles, Nt=4000
     * ``*_small``     : the same shapes with fewer steps, for quick tests
     """
@@ -150,6 +152,10 @@ def workload(name: str) -> Workload:
     if name == "ellipsoid10k":
         v, t = ellipsoid_uv()
         return Workload(name, v, t, 0.5 * mean_edge_length(v, t), 1500, [pulse_star(v)], theta=3.0, zeta=3.0)
+    if name == "ellipsoid5k":
+        v, t = icosphere(1.0, 4)
+        v = v * np.array([2.0, 0.5, 0.25])
+        return Workload(name, v, t, 0.5 * mean_edge_length(v, t), 1000, [pulse_star(v)], theta=3.0, zeta=3.0)
     if name == "ellipsoid80k":
         v, t = octa_ellipsoid(freq=100)
         return Workload(name, v, t, 0.5 * mean_edge_length(v, t), 4000, [pulse_star(v)], theta=3.0, zeta=3.0)
@@ -157,7 +163,7 @@ def workload(name: str) -> Workload:
 
 
 WORKLOADS = ("sphere80", "sphere320", "sphere1280", "sphere7680", "sphere_cube", "cylinder",
-             "ellipsoid10k", "ellipsoid80k")
+             "ellipsoid10k", "ellipsoid5k", "ellipsoid80k")
 
 
 def random_history(n_edge: int, n_steps: int, seed: int) -> np.ndarray:
