@@ -261,6 +261,16 @@ tdbem_status tdbem_step(tdbem_ctx* ctx, double* J_out, int32_t* iters);
    incident field is produced on the host. */
 tdbem_status tdbem_step_v(tdbem_ctx* ctx, const double* V, double* J_out, int32_t* iters);
 
+/* The same, without waiting: the copy of V, the step and the copy of J^{alpha-1} into J_out are enqueued
+   on the context's stream and the call returns.  Up to 4 steps may be outstanding (a fifth call first
+   waits for the oldest).  With V and J_out in pinned host memory (cudaMallocHost) the copies overlap the
+   computation; V may be reused when the call returns, J_out is written once the step has been waited
+   for.  tdbem_step_wait waits for the oldest outstanding step and returns its status (ENOCONV when its
+   solve missed the tolerance; iters, may be NULL, its solver iterations; OK with iters 0 when none is
+   outstanding).  tdbem_reset and tdbem_save first wait for every outstanding step. */
+tdbem_status tdbem_step_v_async(tdbem_ctx* ctx, const double* V, double* J_out);
+tdbem_status tdbem_step_wait(tdbem_ctx* ctx, int32_t* iters);
+
 /* n_steps steps; J_all ([n_steps][n_rhs][ne], may be NULL) receives every J.
    Host arrays of every entry point keep the right-hand side index outside
    the edge index ([n_rhs][ne]); on the device the library stores it innermost

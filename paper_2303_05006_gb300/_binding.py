@@ -84,6 +84,8 @@ def lib():
         L.tdbem_march.argtypes = [vp, ctypes.c_int32, _dp]
         L.tdbem_march_dev.argtypes = [vp, ctypes.c_int32, vp]
         L.tdbem_step_v.argtypes = [vp, _dp, _dp, _i32p]
+        L.tdbem_step_v_async.argtypes = [vp, _dp, _dp]
+        L.tdbem_step_wait.argtypes = [vp, _i32p]
         L.tdbem_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.tdbem_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), _dp, _i32p]
         L.tdbem_reset.argtypes = [vp]
@@ -110,7 +112,8 @@ def lib():
         L.tdbem_load.argtypes = [vp, ctypes.c_char_p]
         for name in ("tdbem_create", "tdbem_num_edges", "tdbem_edges", "tdbem_set_stream", "tdbem_set_incident_plane",
                      "tdbem_set_rhs", "tdbem_history_eval", "tdbem_step", "tdbem_march", "tdbem_march_dev",
-                     "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_profile_enable",
+                     "tdbem_reset", "tdbem_alpha", "tdbem_get_info", "tdbem_step_v", "tdbem_step_v_async", "tdbem_step_wait",
+                     "tdbem_profile_enable",
                      "tdbem_profile_read", "tdbem_history_eval_noalloc", "tdbem_mlp_set_width", "tdbem_mlp_set_weights",
                      "tdbem_mlp_get_weights", "tdbem_mlp_record", "tdbem_mlp_record_every", "tdbem_mlp_samples", "tdbem_mlp_train",
                      "tdbem_mlp_grad", "tdbem_mlp_forward", "tdbem_mlp_use", "tdbem_mlp_stats", "tdbem_march_many",
@@ -220,6 +223,20 @@ class Solver:
             raise ValueError("V must hold n_rhs * ne values")
         it = ctypes.c_int32()
         self._check(lib().tdbem_step_v(self._h, _ptr(V), _ptr(J_out), ctypes.byref(it)))
+        return int(it.value)
+
+    def step_v_async(self, V, J_out=None):
+        """Enqueue one step with right-hand side V (tdbem_step_v_async).  V
+        and J_out should be pinned host arrays that stay alive until the step
+        is waited for; J_out is written then."""
+        if V.size != self.R * self.ne or V.dtype != np.float64 or not V.flags.c_contiguous:
+            raise ValueError("V must be a contiguous float64 array of n_rhs * ne values")
+        self._check(lib().tdbem_step_v_async(self._h, _ptr(V), _ptr(J_out)))
+
+    def step_wait(self) -> int:
+        """Wait for the oldest outstanding asynchronous step; its solver iterations."""
+        it = ctypes.c_int32()
+        self._check(lib().tdbem_step_wait(self._h, ctypes.byref(it)))
         return int(it.value)
 
     def profile(self, on: bool = True):

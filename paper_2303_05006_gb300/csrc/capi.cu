@@ -150,6 +150,9 @@ void tdbem_destroy(tdbem_ctx* c) {
   tdbem_direct_join(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   tdbem_direct_free(c);
+  if (c->h_async_status) cudaFreeHost(c->h_async_status);
+  for (cudaEvent_t e : c->ev_async)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   tdbem_fast_free(c);
@@ -572,6 +575,61 @@ tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t*
   return TDBEM_OK;
 }
 
+// Wait for the oldest outstanding asynchronous step and check its status.
+tdbem_status tdbem_step_wait(tdbem_ctx* c, int32_t* iters) {
+  if (!c) return TDBEM_EINVAL;
+  if (iters) *iters = 0;
+  if (c->async_waited == c->async_issued) return TDBEM_OK;
+  const int slot = (int)(c->async_waited % tdbem_ctx::kAsyncSlots);
+  TDBEM_CUDA_TRY(c, cudaEventSynchronize(c->ev_async[slot]));
+  ++c->async_waited;
+  const int32_t it = c->h_async_status[2 * slot], conv = c->h_async_status[2 * slot + 1];
+  if (iters) *iters = it;
+  c->total_iters += it;
+  tdbem_status s;
+  if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
+  if (!conv) {
+    c->set_error("step: Z0 solve missed the tolerance");
+    return TDBEM_ENOCONV;
+  }
+  return TDBEM_OK;
+}
+
+tdbem_status tdbem_step_v_async(tdbem_ctx* c, const double* V, double* J_out) {
+  if (!c || !V) return TDBEM_EINVAL;
+  tdbem_status s;
+  if (!c->h_async_status) {
+    TDBEM_CUDA_TRY(c, cudaMallocHost(&c->h_async_status, 2 * tdbem_ctx::kAsyncSlots * sizeof(int32_t)));
+    for (cudaEvent_t& e : c->ev_async) TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (c->async_issued - c->async_waited == tdbem_ctx::kAsyncSlots && (s = tdbem_step_wait(c, nullptr))) return s;
+  const int slot = (int)(c->async_issued % tdbem_ctx::kAsyncSlots);
+  const int64_t NR = c->ne * (int64_t)c->R;
+  if (c->R == 1) {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_R, V, NR * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, V, NR * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((s = from_host_layout(c, c->d_stage, c->d_R))) return s;
+  }
+  if ((s = step_async(c, true))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->h_async_status + 2 * slot, c->d_status, 2 * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  if (J_out) TDBEM_CUDA_TRY(c, copy_out(c, c->d_J, J_out));
+  TDBEM_CUDA_TRY(c, cudaEventRecord(c->ev_async[slot], c->stream));
+  ++c->async_issued;
+  return TDBEM_OK;
+}
+
+// Every outstanding asynchronous step waited for (their statuses checked).
+static tdbem_status drain_async(tdbem_ctx* c) {
+  tdbem_status first = TDBEM_OK;
+  while (c->async_waited < c->async_issued) {
+    tdbem_status s = tdbem_step_wait(c, nullptr);
+    if (s && !first) first = s;
+  }
+  return first;
+}
+
 tdbem_status tdbem_profile_enable(tdbem_ctx* c, int32_t on) {
   if (!c) return TDBEM_EINVAL;
   tdbem_status s = tdbem_fast_join(c);
@@ -690,6 +748,7 @@ tdbem_status tdbem_march_many(tdbem_ctx* const* ctxs, int32_t n, const int32_t* 
 
 tdbem_status tdbem_reset(tdbem_ctx* c) {
   if (!c) return TDBEM_EINVAL;
+  drain_async(c);  // the outstanding steps' statuses no longer matter
   tdbem_status s0 = tdbem_fast_invalidate(c);
   if (!s0) s0 = tdbem_direct_invalidate(c);
   if (s0) return s0;
@@ -715,7 +774,8 @@ tdbem_status tdbem_reset(tdbem_ctx* c) {
 
 tdbem_status tdbem_save(tdbem_ctx* c, const char* path) {
   if (!c || !path) return TDBEM_EINVAL;
-  tdbem_status s = tdbem_fast_join(c);
+  tdbem_status s = drain_async(c);
+  if (!s) s = tdbem_fast_join(c);
   if (!s) s = tdbem_direct_join(c);
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

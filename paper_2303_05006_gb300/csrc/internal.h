@@ -130,6 +130,13 @@ struct tdbem_ctx {
   double* d_work = nullptr;         // solver vectors [8][ne][R]
   double* d_dots = nullptr;         // solver reductions
   int32_t* d_status = nullptr;      // solver status / iterations [8]
+  // asynchronous steps (tdbem_step_v_async / tdbem_step_wait): per slot the
+  // step's solver status copied to pinned host memory and an event after its
+  // copies; issued and waited counts
+  static constexpr int kAsyncSlots = 4;
+  int32_t* h_async_status = nullptr;  // pinned [kAsyncSlots][2]
+  cudaEvent_t ev_async[kAsyncSlots] = {};
+  int64_t async_issued = 0, async_waited = 0;
   int32_t alpha = 1;
   int64_t total_iters = 0;
   int64_t total_sweeps = 0;
