@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
       map_off[tid] = (int32_t)psym[pr] * PS;
     } else {
       src_off[tid] = -1;
+      dst_off[tid] = -1;
+      map_off[tid] = 0;
       col_inv[tid] = 1.f;
     }
   }
@@ -363,7 +365,53 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
     }
   }
   tc_fence_after();
-  for (int mt = 0; ok && mt < nmt; ++mt) {
+  // With both 128-row tiles of a 256-row operator in this CTA every column's
+  // P outputs are here: they are placed, unscaled and un-permuted, into a
+  // staging row of P floats in the (now free) operand tiles, and each
+  // column's row is added to the local coefficients with one bulk reduction
+  // by the copy engine (cp.reduce.async.bulk ... add.f32), in place of P / 4
+  // 16-byte atomics.  64 columns are staged at a time.
+  const bool bulk = kMT == 2 && pt == 4 && nmt * kTileM >= P && (int64_t)P * 4 * 64 <= smem_tiles<kMT>();
+  if (ok && bulk) {
+    float* stage = (float*)dsm;  // [64][P]
+    const int q4 = warp & 3, mt = warp >> 2;
+    const int r = row0 + mt * kTileM + q4 * 32 + lane;
+    for (int h = 0; h < 2; ++h) {
+      if (mt < nmt) {
+        for (int j0 = 0; j0 < 64; j0 += 16) {
+          uint32_t v[16];
+          const uint32_t addr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mt * kTileN + 64 * h + j0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (r < P) {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int n = 64 * h + j0 + jj;
+              if (col0 + n < ncol)  // a column past the GEMM has no target (and is not added)
+                stage[(j0 + jj) * P + smp[map_off[n] + (r >> 2)] * 4 + (r & 3)] =
+                    __uint_as_float(v[jj]) * (op_inv * col_inv[n]);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid < 64) {
+        const int n = 64 * h + tid;
+        if (col0 + n < ncol) bulk_reduce_add_f32(loc + dst_off[n], smem_u32(stage + tid * P), (uint32_t)(P * 4));
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the stage may be overwritten
+      }
+      __syncthreads();
+    }
+    if (tid < 64) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  for (int mt = 0; ok && !bulk && mt < nmt; ++mt) {
     const int q4 = warp & 3, cb = (warp >> 2) * 64;
     const int r = row0 + mt * kTileM + q4 * 32 + lane;
     for (int j0 = 0; j0 < 64; j0 += 16) {

@@ -81,6 +81,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 
 
+// global[dst .. dst + bytes) += shared[src .. src + bytes) element-wise in
+// FP32, by the bulk copy engine (completion tracked by the bulk async-group);
+// both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_reduce_add_f32(float* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+
 // 16-byte unit u of a tile with 128 bytes of K per row: its row and its
 // 16-byte column along K (the unit's byte offset in the tile is 16 u)
 __device__ __forceinline__ int unit_row(int u) { return ((u >> 6) << 3) | (u & 7); }
