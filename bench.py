@@ -184,6 +184,12 @@ def batch_pulses(w, n: int, seed: int = 4):
 # 128-row tiles per CTA, lag >= 2 products deferred): two leaf events of 289.5 MB and one level-2
 # event of 152.9 MB per gating period of six launches
 M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
+# DRAM bytes over algorithmic bytes of the direct path's tiled history sum, from
+# one ncu capture of the same kernel on the 1920-RWG sphere (289.0 MB against
+# 269.6 MB; profiles/direct_history_sphere7680.md).  The stream of coefficients
+# and lag windows grows with the pairs stored, so the 7680-RWG launch is scaled
+# by its own algorithmic bytes.
+DIRECT_TILE_TRAFFIC_RATIO = 289.0 / 269.6
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4, "f16x3": 5}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack",
@@ -227,8 +233,13 @@ def roofline(args, info, launches, ms, K, W):
         else:  # flattened entries: FP32 coefficient + (column << 8 | lag), 8 B per stored lag
             nbytes = 2 * info.near_coef_bytes
         gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
+        traffic = DIRECT_TILE_TRAFFIC_RATIO * nbytes if (args.mode == "direct" and args.rhs == 1) else None
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": None, "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}
+                "traffic": traffic,
+                "traffic_source": "profiles/direct_history_sphere7680.md: ncu DRAM bytes of the same kernel on the "
+                                  "1920-RWG sphere, scaled to this launch by its algorithmic bytes" if traffic
+                else None,
+                "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}
     if name == "z0_solve" and info.z0_nnz > 0:
         # algorithmic operand bytes of one solve: per BiCGStab iteration two FP32
         # ELL SpMVs (value + column, 8 B per non-zero) and 4-byte vector passes
