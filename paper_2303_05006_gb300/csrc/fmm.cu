@@ -155,6 +155,22 @@ struct FmmPlan {
   float* d_hval3 = nullptr;
   int32_t* d_hmeta3 = nullptr;
   double* d_Rp = nullptr;          // [2][ne] -(lags >= 3) of the step alpha in buffer alpha & 1
+  // the lags >= 3 tiled by column blocks (k_near_tile): columns in Morton
+  // order of their edges' midpoints, blocks of kNB consecutive ones; a
+  // segment is one row's entries within one block (FP32 coefficient, and the
+  // column's place in the block << 8 | lag as 16 bits), the segments block
+  // by block; tasks (block, first and end segment) of at most kNTaskEntries
+  // entries; per row its segments (ascending) for the fixed-order reduce
+  int32_t* d_corder = nullptr;     // [ne] edge at sorted position k
+  int64_t* d_seg_ptr = nullptr;    // [nseg + 1]
+  float* d_cval = nullptr;         // [entries]
+  uint16_t* d_cmeta = nullptr;     // [entries]
+  int4* d_ntasks = nullptr;        // [ntask] {block, s0, s1, 0}
+  int64_t* d_rseg_ptr = nullptr;   // [ne + 1]
+  int32_t* d_rseg = nullptr;       // [nseg]
+  double* d_spart = nullptr;       // [nseg] segment sums
+  int64_t nseg = 0;
+  int32_t ntask = 0;
   cudaStream_t nstream = nullptr;  // near stream (null: no pipelining)
   cudaEvent_t ev_solved = nullptr; // context stream: a solve has been enqueued
   cudaEvent_t ev_near[2] = {nullptr, nullptr};  // near stream: buffer b is written
@@ -830,6 +846,65 @@ __global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Near field, lags >= 3, tiled by column blocks.  One CTA per task: it stages
+// the block's history, hist[m][c] = J^{alpha-m} of the block's column c (FP32:
+// the products are FP32, as in the flat kernel), zero for m < m_min or m >
+// alpha; then each warp takes one segment (one row's entries within the
+// block) at a time, its lanes striding the entries with the history read
+// from shared memory, and writes the segment's sum.  k_near_seg_reduce adds
+// each row's segment sums in a fixed order: R_i = -sum.
+constexpr int kNB = 128;              // columns per block
+constexpr int kNBS = kNB + 1;         // row stride of the staged block (no bank conflicts when staging)
+constexpr int kNTaskEntries = 16384;  // entries per task (about)
+
+__global__ void __launch_bounds__(256) k_near_tile(const int4* tasks, const int32_t* corder, const int64_t* seg_ptr,
+                                                   const float* cval, const uint16_t* cmeta, int64_t ne,
+                                                   const double* ring, int L, int alpha, int m_min, double* spart) {
+  extern __shared__ float nh[];  // [L][kNBS]
+  const int4 tk = tasks[blockIdx.x];
+  const int64_t p0 = (int64_t)tk.x * kNB;
+  for (int k = threadIdx.x; k < kNB * L; k += blockDim.x) {
+    const int cb = k / L, slot = k - cb * L;  // consecutive threads: one column's ring row
+    const int m = (alpha - slot) & (L - 1);
+    float v = 0.f;
+    if (p0 + cb < ne && m >= m_min && m <= alpha) v = (float)ring[(int64_t)corder[p0 + cb] * L + slot];
+    nh[m * kNBS + cb] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sg = tk.y + warp; sg < tk.z; sg += nw) {
+    const int64_t e1 = seg_ptr[sg + 1];
+    float a0 = 0.f, a1 = 0.f;
+    int64_t e = seg_ptr[sg] + lane;
+    for (; e + 32 < e1; e += 64) {
+      const uint32_t q0 = cmeta[e], q1 = cmeta[e + 32];
+      a0 += __ldg(cval + e) * nh[(q0 & 0xff) * kNBS + (q0 >> 8)];
+      a1 += __ldg(cval + e + 32) * nh[(q1 & 0xff) * kNBS + (q1 >> 8)];
+    }
+    if (e < e1) {
+      const uint32_t q0 = cmeta[e];
+      a0 += __ldg(cval + e) * nh[(q0 & 0xff) * kNBS + (q0 >> 8)];
+    }
+    double d = (double)a0 + (double)a1;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) spart[sg] = d;
+  }
+}
+
+// R_i = -(the sums of row i's segments), eight lanes per row, fixed order
+__global__ void k_near_seg_reduce(const int64_t* rseg_ptr, const int32_t* rseg, const double* spart, int64_t ne,
+                                  double* R) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 8;
+  const int sub = threadIdx.x % 8;
+  double t = 0.0;
+  if (i < ne)
+    for (int64_t k = rseg_ptr[i] + sub; k < rseg_ptr[i + 1]; k += 8) t += spart[rseg[k]];
+#pragma unroll
+  for (int d = 4; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+  if (i < ne && sub == 0) R[i] = -t;
+}
+
 // Batched near field on the flattened entries: one block per row; thread t
 // takes right-hand side r0 + t mod RL (RL = R rounded up to a power of two,
 // at most 32) and the row's entries sub, sub + nsub, ... (sub = t / RL), so
@@ -1152,7 +1227,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
       // one right-hand side with far_overlap keeps only the lag-split copy
       // below (the history evaluation sums its two parts in turn); otherwise
       // the flat entries go to the device as they are
-      if (!(c->R == 1 && c->p.far_overlap)) {
+      if (c->R != 1) {
         if ((s = c->dalloc(&F->d_hrow, ne + 1)) || (s = c->dalloc(&F->d_hval, hval.size())) ||
             (s = c->dalloc(&F->d_hmeta, hmeta.size())))
           return s;
@@ -1161,7 +1236,7 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         TDBEM_CUDA_TRY(c,
                        cudaMemcpy(F->d_hmeta, hmeta.data(), hmeta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
       }
-      if (c->R == 1 && c->p.far_overlap) {
+      if (c->R == 1) {
         // lag 2 / lags >= 3 (see FmmPlan), each row's entries in the same order
         std::vector<int64_t> r2(ne + 1, 0), r3(ne + 1, 0);
         std::vector<float> v2, v3;
@@ -1192,15 +1267,125 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hval3, v3.data(), v3.size() * sizeof(float), cudaMemcpyHostToDevice));
           TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_hmeta3, m3.data(), m3.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         }
-        // between the deferred M2L's lowest priority and the steps' highest:
-        // the next solve's cluster, which needs whole SMs, is dispatched ahead
-        // of this stream's remaining CTAs
-        int prio_lo = 0, prio_hi = 0;
-        TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-        TDBEM_CUDA_TRY(c, cudaStreamCreateWithPriority(&F->nstream, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
-        TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_solved, cudaEventDisableTiming));
-        for (int b = 0; b < 2; ++b)
-          TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_near[b], cudaEventDisableTiming));
+        // the lags >= 3 tiled by column blocks (k_near_tile) for the pipelined
+        // march, when the entry indices fit 32 bits.  Measured on the 7680-RWG
+        // sphere: the pipelined march gains 9% (the block's history comes from
+        // shared memory, not from L2 gathers that compete with the
+        // overlapped M2L), while alone the flat kernel is the faster one
+        if (c->p.far_overlap && !v3.empty() && (int64_t)v3.size() < ((int64_t)1 << 31)) {
+          // Morton order of the edges' midpoints (mean of the two triangles' centroids)
+          std::vector<double> mid(3 * ne);
+          double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+          for (int64_t e = 0; e < ne; ++e)
+            for (int d = 0; d < 3; ++d) {
+              double x = 0.0;
+              for (int side = 0; side < 2; ++side) {
+                const int32_t t = c->et[2 * e + side];
+                for (int q = 0; q < 3; ++q) x += c->V[3 * c->T[3 * t + q] + d];
+              }
+              mid[3 * e + d] = x / 6.0;
+              lo[d] = std::min(lo[d], x / 6.0);
+              hi[d] = std::max(hi[d], x / 6.0);
+            }
+          std::vector<uint64_t> key(ne);
+          for (int64_t e = 0; e < ne; ++e) {
+            uint64_t code = 0;
+            for (int d = 0; d < 3; ++d) {
+              const double u = (mid[3 * e + d] - lo[d]) / std::max(hi[d] - lo[d], 1e-300);
+              const uint64_t qd = (uint64_t)std::min(1023.0, std::max(0.0, std::floor(u * 1024.0)));
+              for (int bit = 0; bit < 10; ++bit) code |= ((qd >> bit) & 1ull) << (3 * bit + d);
+            }
+            key[e] = (code << 24) | (uint64_t)e;  // ties by edge index
+          }
+          std::sort(key.begin(), key.end());
+          std::vector<int32_t> corder(ne), cpos(ne);
+          for (int64_t k = 0; k < ne; ++k) {
+            corder[k] = (int32_t)(key[k] & 0xffffff);
+            cpos[corder[k]] = (int32_t)k;
+          }
+          // entries grouped by block (counting sort), rows in order within a block
+          const int64_t nblk = (ne + kNB - 1) / kNB, nent = (int64_t)v3.size();
+          std::vector<int64_t> bstart(nblk + 1, 0);
+          for (int64_t e = 0; e < nent; ++e) ++bstart[cpos[m3[e] >> 8] / kNB + 1];
+          for (int64_t b = 0; b < nblk; ++b) bstart[b + 1] += bstart[b];
+          std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+          std::vector<float> cval(nent);
+          std::vector<uint16_t> cmeta(nent);
+          std::vector<int32_t> erow(nent);
+          for (int64_t i = 0; i < ne; ++i)
+            for (int64_t e = r3[i]; e < r3[i + 1]; ++e) {
+              const int32_t pos = cpos[m3[e] >> 8];
+              const int64_t k = fill[pos / kNB]++;
+              cval[k] = v3[e];
+              cmeta[k] = (uint16_t)(((pos % kNB) << 8) | (m3[e] & 0xff));
+              erow[k] = (int32_t)i;
+            }
+          // segments, tasks and each row's segment list
+          std::vector<int64_t> seg_ptr;
+          std::vector<int32_t> seg_row;
+          std::vector<int4> tasks;
+          for (int64_t b = 0; b < nblk; ++b) {
+            int64_t t0 = (int64_t)seg_row.size(), tent = 0;
+            for (int64_t k = bstart[b]; k < bstart[b + 1];) {
+              int64_t k1 = k;
+              while (k1 < bstart[b + 1] && erow[k1] == erow[k]) ++k1;
+              if (tent > 0 && tent + (k1 - k) > kNTaskEntries) {
+                tasks.push_back(make_int4((int)b, (int)t0, (int)seg_row.size(), 0));
+                t0 = (int64_t)seg_row.size();
+                tent = 0;
+              }
+              seg_ptr.push_back(k);
+              seg_row.push_back(erow[k]);
+              tent += k1 - k;
+              k = k1;
+            }
+            if ((int64_t)seg_row.size() > t0) tasks.push_back(make_int4((int)b, (int)t0, (int)seg_row.size(), 0));
+          }
+          seg_ptr.push_back(nent);
+          const int64_t nseg = (int64_t)seg_row.size();
+          std::vector<int64_t> rptr(ne + 1, 0);
+          for (int64_t g = 0; g < nseg; ++g) ++rptr[seg_row[g] + 1];
+          for (int64_t i = 0; i < ne; ++i) rptr[i + 1] += rptr[i];
+          std::vector<int32_t> rseg(std::max<int64_t>(1, nseg));
+          {
+            std::vector<int64_t> rf(rptr.begin(), rptr.end() - 1);
+            for (int64_t g = 0; g < nseg; ++g) rseg[rf[seg_row[g]]++] = (int32_t)g;  // ascending per row
+          }
+          if (nseg >= INT32_MAX) {
+            c->set_error("fast: too many near-field segments");
+            return TDBEM_EINVAL;
+          }
+          F->nseg = nseg;
+          F->ntask = (int32_t)tasks.size();
+          if ((s = c->dalloc(&F->d_corder, ne)) || (s = c->dalloc(&F->d_seg_ptr, nseg + 1)) ||
+              (s = c->dalloc(&F->d_cval, nent)) || (s = c->dalloc(&F->d_cmeta, nent)) ||
+              (s = c->dalloc(&F->d_ntasks, std::max<int64_t>(1, F->ntask))) || (s = c->dalloc(&F->d_rseg_ptr, ne + 1)) ||
+              (s = c->dalloc(&F->d_rseg, std::max<int64_t>(1, nseg))) ||
+              (s = c->dalloc(&F->d_spart, std::max<int64_t>(1, nseg))))
+            return s;
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_corder, corder.data(), ne * sizeof(int32_t), cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_seg_ptr, seg_ptr.data(), (nseg + 1) * sizeof(int64_t),
+                                       cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_cval, cval.data(), nent * sizeof(float), cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_cmeta, cmeta.data(), nent * sizeof(uint16_t), cudaMemcpyHostToDevice));
+          if (F->ntask)
+            TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_ntasks, tasks.data(), F->ntask * sizeof(int4), cudaMemcpyHostToDevice));
+          TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_rseg_ptr, rptr.data(), (ne + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+          if (nseg)
+            TDBEM_CUDA_TRY(c, cudaMemcpy(F->d_rseg, rseg.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        if (c->p.far_overlap) {
+          // between the deferred M2L's lowest priority and the steps' highest:
+          // the next solve's cluster, which needs whole SMs, is dispatched ahead
+          // of this stream's remaining CTAs
+          int prio_lo = 0, prio_hi = 0;
+          TDBEM_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+          TDBEM_CUDA_TRY(c,
+                         cudaStreamCreateWithPriority(&F->nstream, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+          TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_solved, cudaEventDisableTiming));
+          for (int b = 0; b < 2; ++b)
+            TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&F->ev_near[b], cudaEventDisableTiming));
+        }
       }
     }
   }
@@ -1756,6 +1941,8 @@ static tdbem_status far_events(tdbem_ctx* c, int32_t alpha, const double* ring, 
   return TDBEM_OK;
 }
 
+static tdbem_status near_lags3(tdbem_ctx* c, const double* ring, int32_t alpha, double* out, cudaStream_t st);
+
 tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring, const double* V, bool eval) {
   FmmPlan* F = c->fmm;
   double* slot = nullptr;
@@ -1771,9 +1958,10 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
     const bool have = F->ahead[b] == alpha;
     F->ahead[b] = 0;
     cudaEvent_t e = c->prof_begin(1);
-    if (!have)
-      k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring, c->L, alpha,
-                                                       nullptr, nullptr, nullptr, Rp);
+    if (!have) {
+      tdbem_status s = near_lags3(c, ring, alpha, Rp, c->stream);
+      if (s) return s;
+    }
     // V, lag 2 (the currents of the step just solved) and the far field
     k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow2, F->d_hval2, F->d_hmeta2, c->ne, ring, c->L, alpha,
                                                      V, Rp, slot, c->d_R);
@@ -1786,8 +1974,8 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
     // history evaluation with only the lag-split entries: R = -(lags >= 3),
     // then V + lag 2 + far field added in place (V is an incident row here)
     const unsigned grid = (unsigned)((c->ne + 7) / 8);
-    k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring, c->L, alpha,
-                                                     nullptr, nullptr, nullptr, c->d_R);
+    tdbem_status s = near_lags3(c, ring, alpha, c->d_R, c->stream);
+    if (s) return s;
     k_near_history_flat<<<grid, 256, 0, c->stream>>>(F->d_hrow2, F->d_hval2, F->d_hmeta2, c->ne, ring, c->L, alpha,
                                                      V, c->d_R, slot, c->d_R);
   } else if (c->R == 1) {
@@ -1801,6 +1989,31 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
                                                                         c->L, alpha, c->R, RL, V, slot, c->d_R);
   }
   c->prof_end(1, e);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  return TDBEM_OK;
+}
+
+// -(lags >= 3) of step alpha into out[ne] on stream st: the tiled kernel
+// where it was built, else the flat one
+static tdbem_status near_lags3(tdbem_ctx* c, const double* ring, int32_t alpha, double* out, cudaStream_t st) {
+  FmmPlan* F = c->fmm;
+  if (F->d_seg_ptr) {
+    // the staged block holds the ring's L lags of kNB columns
+    static int smem_set = 0;
+    const int smem = (int)(kNBS * c->L * sizeof(float));
+    if (smem > smem_set) {
+      TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_near_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      smem_set = smem;
+    }
+    if (F->ntask)
+      k_near_tile<<<(unsigned)F->ntask, 256, smem, st>>>(
+          F->d_ntasks, F->d_corder, F->d_seg_ptr, F->d_cval, F->d_cmeta, c->ne, ring, c->L, alpha, 3, F->d_spart);
+    k_near_seg_reduce<<<(unsigned)((c->ne * 8 + 255) / 256), 256, 0, st>>>(F->d_rseg_ptr, F->d_rseg, F->d_spart,
+                                                                          c->ne, out);
+  } else {
+    k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, st>>>(F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, ring,
+                                                                     c->L, alpha, nullptr, nullptr, nullptr, out);
+  }
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
@@ -1819,12 +2032,10 @@ tdbem_status tdbem_fast_after_solve(tdbem_ctx* c, int32_t alpha) {
     cudaStream_t main = c->stream;
     c->stream = F->nstream;
     cudaEvent_t e = c->prof_begin(1);
-    k_near_history_flat<<<(unsigned)((c->ne + 7) / 8), 256, 0, F->nstream>>>(
-        F->d_hrow3, F->d_hval3, F->d_hmeta3, c->ne, c->d_Jring, c->L, a2, nullptr, nullptr, nullptr,
-        F->d_Rp + (int64_t)b * c->ne);
+    tdbem_status s = near_lags3(c, c->d_Jring, a2, F->d_Rp + (int64_t)b * c->ne, F->nstream);
     c->prof_end(1, e);
     c->stream = main;
-    TDBEM_CUDA_TRY(c, cudaGetLastError());
+    if (s) return s;
     TDBEM_CUDA_TRY(c, cudaEventRecord(F->ev_near[b], F->nstream));
     F->ahead[b] = a2;
   }
