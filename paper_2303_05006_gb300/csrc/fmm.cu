@@ -848,7 +848,8 @@ __global__ void __launch_bounds__(256) k_near_history_flat(const int64_t* hrow, 
 
 // ---------------------------------------------------------------------------
 // Near field, lags >= 3, tiled by column blocks.  One CTA per task: it stages
-// the block's history, hist[m][c] = J^{alpha-m} of the block's column c (FP32:
+// the block's history for the lags the entries use (up to the largest stored
+// near-field lag), hist[m][c] = J^{alpha-m} of the block's column c (FP32:
 // the products are FP32, as in the flat kernel), zero for m < m_min or m >
 // alpha; then each warp takes one segment (one row's entries within the
 // block) at a time, its lanes striding the entries with the history read
@@ -860,15 +861,16 @@ constexpr int kNTaskEntries = 16384;  // entries per task (about)
 
 __global__ void __launch_bounds__(256) k_near_tile(const int4* tasks, const int32_t* corder, const int64_t* seg_ptr,
                                                    const float* cval, const uint16_t* cmeta, int64_t ne,
-                                                   const double* ring, int L, int alpha, int m_min, double* spart) {
-  extern __shared__ float nh[];  // [L][kNBS]
+                                                   const double* ring, int L, int nlag, int alpha, int m_min,
+                                                   double* spart) {
+  extern __shared__ float nh[];  // [nlag][kNBS]: the lags 0 .. nlag - 1 the entries use
   const int4 tk = tasks[blockIdx.x];
   const int64_t p0 = (int64_t)tk.x * kNB;
-  for (int k = threadIdx.x; k < kNB * L; k += blockDim.x) {
-    const int cb = k / L, slot = k - cb * L;  // consecutive threads: one column's ring row
-    const int m = (alpha - slot) & (L - 1);
+  for (int k = threadIdx.x; k < kNB * nlag; k += blockDim.x) {
+    const int cb = k / nlag, m = k - cb * nlag;  // consecutive threads: one column's ring row
     float v = 0.f;
-    if (p0 + cb < ne && m >= m_min && m <= alpha) v = (float)ring[(int64_t)corder[p0 + cb] * L + slot];
+    if (p0 + cb < ne && m >= m_min && m <= alpha)
+      v = (float)ring[(int64_t)corder[p0 + cb] * L + ((alpha - m) & (L - 1))];
     nh[m * kNBS + cb] = v;
   }
   __syncthreads();
@@ -1272,7 +1274,18 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
         // sphere: the pipelined march gains 9% (the block's history comes from
         // shared memory, not from L2 gathers that compete with the
         // overlapped M2L), while alone the flat kernel is the faster one
-        if (c->p.far_overlap && !v3.empty() && (int64_t)v3.size() < ((int64_t)1 << 31)) {
+        // A task stages L x kNB history values before its entries: the tiling
+        // pays only where a block holds many entries per staged value (long
+        // lag windows over few columns, as with a small step, do not)
+        // Measured in the pipelined march: on the 7680-RWG sphere (4.0 k
+        // entries per row) the tiled form gains 9%; on the paper's case 2
+        // (4320 RWG, dt = h/7, 32 k entries per row) the flat kernel's long
+        // rows stream well and the tiled form loses 30%.  Rows of at most 16 k
+        // entries are tiled.
+        const int64_t nlag = F->max_near_lag + 1;  // lags staged per block
+        const int64_t nblk_est = (ne + kNB - 1) / kNB;
+        const bool tile_pays = (int64_t)v3.size() >= 8 * nblk_est * kNB * nlag && (int64_t)v3.size() <= 16384 * ne;
+        if (c->p.far_overlap && tile_pays && !v3.empty() && (int64_t)v3.size() < ((int64_t)1 << 31)) {
           // Morton order of the edges' midpoints (mean of the two triangles' centroids)
           std::vector<double> mid(3 * ne);
           double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -1324,12 +1337,14 @@ tdbem_status tdbem_build_fast(tdbem_ctx* c) {
           std::vector<int64_t> seg_ptr;
           std::vector<int32_t> seg_row;
           std::vector<int4> tasks;
+          // at least four entries per staged value in a task
+          const int64_t task_entries = std::max<int64_t>(kNTaskEntries, 4 * kNB * nlag);
           for (int64_t b = 0; b < nblk; ++b) {
             int64_t t0 = (int64_t)seg_row.size(), tent = 0;
             for (int64_t k = bstart[b]; k < bstart[b + 1];) {
               int64_t k1 = k;
               while (k1 < bstart[b + 1] && erow[k1] == erow[k]) ++k1;
-              if (tent > 0 && tent + (k1 - k) > kNTaskEntries) {
+              if (tent > 0 && tent + (k1 - k) > task_entries) {
                 tasks.push_back(make_int4((int)b, (int)t0, (int)seg_row.size(), 0));
                 t0 = (int64_t)seg_row.size();
                 tent = 0;
@@ -1997,17 +2012,19 @@ tdbem_status tdbem_fast_history(tdbem_ctx* c, int32_t alpha, const double* ring,
 // where it was built, else the flat one
 static tdbem_status near_lags3(tdbem_ctx* c, const double* ring, int32_t alpha, double* out, cudaStream_t st) {
   FmmPlan* F = c->fmm;
-  if (F->d_seg_ptr) {
-    // the staged block holds the ring's L lags of kNB columns
+  // the staged block holds the lags 0 .. max_near_lag of kNB columns
+  const int nlag = F->max_near_lag + 1;
+  const int smem = (int)(kNBS * nlag * sizeof(float));
+  if (F->d_seg_ptr && smem <= 160 * 1024) {
     static int smem_set = 0;
-    const int smem = (int)(kNBS * c->L * sizeof(float));
     if (smem > smem_set) {
       TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_near_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       smem_set = smem;
     }
     if (F->ntask)
       k_near_tile<<<(unsigned)F->ntask, 256, smem, st>>>(
-          F->d_ntasks, F->d_corder, F->d_seg_ptr, F->d_cval, F->d_cmeta, c->ne, ring, c->L, alpha, 3, F->d_spart);
+          F->d_ntasks, F->d_corder, F->d_seg_ptr, F->d_cval, F->d_cmeta, c->ne, ring, c->L, nlag, alpha, 3,
+          F->d_spart);
     k_near_seg_reduce<<<(unsigned)((c->ne * 8 + 255) / 256), 256, 0, st>>>(F->d_rseg_ptr, F->d_rseg, F->d_spart,
                                                                           c->ne, out);
   } else {

@@ -371,7 +371,10 @@ __global__ void __launch_bounds__(kThreads) k_m2l_tc(const int4* gemm, const int
   // column's row is added to the local coefficients with one bulk reduction
   // by the copy engine (cp.reduce.async.bulk ... add.f32), in place of P / 4
   // 16-byte atomics.  64 columns are staged at a time.
-  const bool bulk = kMT == 2 && pt == 4 && nmt * kTileM >= P && (int64_t)P * 4 * 64 <= smem_tiles<kMT>();
+  // (a tile with few valid columns, the last of a small GEMM, keeps the
+  // per-column atomics: the staging's cost does not shrink with the columns)
+  const bool bulk = kMT == 2 && pt == 4 && nmt * kTileM >= P && (int64_t)P * 4 * 64 <= smem_tiles<kMT>() &&
+                    ncol - col0 >= 32;
   if (ok && bulk) {
     float* stage = (float*)dsm;  // [64][P]
     const int q4 = warp & 3, mt = warp >> 2;

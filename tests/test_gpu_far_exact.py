@@ -110,3 +110,30 @@ def test_zero_far_kernel_leaves_the_near_field(setup):
     J = _smooth_history(120, 40, seed=2)
     R = [Solver(w.verts, w.tris, w.dt, w.Nt, mode=1, far_kernel=k).history_eval(30, J[:29]) for k in (0, 1, 2)]
     assert np.array_equal(R[0], R[1]) and np.array_equal(R[0], R[2])
+
+
+@pytest.mark.parametrize("prec", [4, 5])
+def test_batched_far_field_equals_windowed_sum(setup, prec):
+    """The batched form (three right-hand sides, each with its own history):
+    the far field of every right-hand side equals the oracle's windowed sum,
+    through the batched P2M, M2M, M2L columns (pair, right-hand side,
+    component), L2L and L2P."""
+    from oracle.far_window import far_field_poly
+    from paper_2303_05006_gb300 import Solver
+
+    v, t, dt, h, edges = setup
+    Nt, R = 200, 3
+    kw = dict(mode=1, p_s=4, p_t=4, n_leaf=16, m2l_prec=prec, n_rhs=R)
+    s1 = Solver(v, t, dt, Nt, far_kernel=1, **kw)
+    s2 = Solver(v, t, dt, Nt, far_kernel=2, **kw)
+    alpha = 150
+    H = np.stack([_smooth_history(s1.ne, alpha - 1, seed=20 + r) for r in range(R)], axis=1)  # (a-1, R, ne)
+    far = s2.history_eval(alpha, H) - s1.history_eval(alpha, H)
+    rows = np.sort(np.random.default_rng(13).choice(s1.ne, 8, replace=False))
+    for r in range(R):
+        ref = far_field_poly(h, edges, rows, H[:, r], alpha)
+        scale = np.max(np.abs(ref))
+        err = np.max(np.abs(far[r][rows] - ref))
+        assert err <= TOL * scale, (prec, r, err / scale)
+    s1.close()
+    s2.close()
