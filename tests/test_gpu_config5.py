@@ -1,5 +1,5 @@
-"""Accuracy of the fast path at the survey's largest configuration: the 8:2:1
-ellipsoid with 80000 triangles (120000 RWG functions), dt = h/2, p_s = p_t = 4,
+"""Accuracy of the fast path at the largest workload: the 8:2:1 ellipsoid with
+80000 triangles (120000 RWG functions), dt = h/2, p_s = p_t = 4,
 theta = zeta = 3.  The conventional method cannot run there (about 1 TB of
 coefficients), so the check is per step on sampled rows: the fast history
 evaluation R^{alpha-1} = V - near - far against the FP64 oracle's rows,

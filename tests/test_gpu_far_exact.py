@@ -1,4 +1,4 @@
-"""Exactness of the fast path's far-field machinery (the survey's exact-kernel
+"""Exactness of the fast path's far-field machinery (the exact-kernel
 check), on the GPU.
 
 With far_kernel = 1 the library's M2L operators hold the polynomial kernel
