@@ -393,7 +393,7 @@ def _solver(args, w, mode, R=1, far_overlap=None):
     return Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
                   mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
                   jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol,
-                  m2l_tile_rows=args.m2l_tile_rows,
+                  m2l_tile_rows=args.m2l_tile_rows, solve_cluster=args.solve_cluster,
                   far_overlap=args.far_overlap if far_overlap is None else far_overlap)
 
 
@@ -629,6 +629,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--high-priority", type=int, default=1, choices=(0, 1),
                     help="1: march on a highest-priority CUDA stream (the deferred far-field products run at the lowest)")
+    ap.add_argument("--solve-cluster", type=int, default=0, choices=(0, 1, 2, 4, 8, 16),
+                    help="CTAs of the single-RHS cluster solve (0: the largest the device schedules)")
     ap.add_argument("--far-overlap", type=int, default=1, choices=(0, 1),
                     help="1: M2L products of lag >= 2 on a second stream, overlapping the next steps; 0: serial")
     ap.add_argument("--m2l-tile-rows", type=int, default=0, choices=(0, 1, 128, 256),

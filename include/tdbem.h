@@ -147,6 +147,10 @@ typedef struct {
                             (section 4.3.2): 0 (default) the paper's split, one on the interpolated kernel
                             (dU/dt) and one on the target's time factor; 1 both on the target factor (U
                             interpolated); 2 both on the kernel (d^2U/dt^2, a step in time, interpolated) */
+  int32_t solve_cluster;  /* CTAs of the single-RHS cluster solve: 1, 2, 4, 8 or 16 caps it; 0 (default) the
+                             largest cluster the device schedules (16 on GB300), except in the pipelined direct
+                             march with at least 2 GB of stored coefficients, where it is 4: the solve overlaps
+                             the history sum there, and a smaller cluster leaves SMs to that sum */
   int64_t max_device_bytes; /* device memory budget of the context's own allocations (0: none).  An allocation
                                that would exceed it fails as if the device were full: tdbem_create returns
                                TDBEM_ENOMEM with nothing left allocated.  Per-call temporaries of
@@ -163,7 +167,7 @@ typedef struct {
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
    jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1, far_kernel=0,
-   s_interp=0, t_interp=0, a_deriv=0, max_device_bytes=0. */
+   s_interp=0, t_interp=0, a_deriv=0, solve_cluster=0, max_device_bytes=0. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),

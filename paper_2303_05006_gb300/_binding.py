@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
                 ("m2l_tile_rows", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double),
                 ("far_kernel", ctypes.c_int32), ("s_interp", ctypes.c_int32), ("t_interp", ctypes.c_int32),
-                ("a_deriv", ctypes.c_int32),
+                ("a_deriv", ctypes.c_int32), ("solve_cluster", ctypes.c_int32),
                 ("max_device_bytes", ctypes.c_int64)]
 
 

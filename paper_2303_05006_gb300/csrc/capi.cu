@@ -196,6 +196,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.precond > 1 || (p.far_overlap != 0 && p.far_overlap != 1) || p.solve_grid < 0 || p.solve_grid > 2 ||
       p.far_kernel < 0 || p.far_kernel > 3 || p.max_device_bytes < 0 || p.s_interp < 0 || p.s_interp > 1 ||
       p.t_interp < 0 || p.t_interp > 1 || p.a_deriv < 0 || p.a_deriv > 2 ||
+      (p.solve_cluster != 0 && p.solve_cluster != 1 && p.solve_cluster != 2 && p.solve_cluster != 4 &&
+       p.solve_cluster != 8 && p.solve_cluster != 16) ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();

@@ -1242,14 +1242,25 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t
       TDBEM_CUDA_TRY(c, cudaLaunchCooperativeKernel((void*)k_bicgstab_grid, dim3(g_grid), dim3(kSolveThreads), args,
                                                     0, c->stream));
     } else {
-      c->cluster = g_cluster;
+      // Default: the largest cluster, except in the pipelined direct march with
+      // a history sum of at least 2 GB per step (about 0.4 ms).  There the
+      // solve overlaps that sum on its own SMs, and a cluster of 4 leaves 12
+      // more SMs to it while the solve still hides behind it (7680-RWG sphere:
+      // 1088 steps/s against 1055 with 16, the solve taking 0.76 ms of a
+      // 0.93 ms step).
+      int cs = g_cluster;
+      if (c->p.solve_cluster > 0)
+        cs = std::min(c->p.solve_cluster, g_cluster);
+      else if (c->p.mode == TDBEM_DIRECT && c->p.far_overlap && c->direct.nval * (int64_t)sizeof(double) >= (2LL << 30))
+        cs = std::min(4, g_cluster);
+      c->cluster = cs;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(g_cluster);
+      cfg.gridDim = dim3(cs);
       cfg.blockDim = dim3(kSolveThreads);
       cfg.stream = c->stream;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = g_cluster;
+      at[0].val.clusterDim.x = cs;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;

@@ -179,6 +179,18 @@ def test_grid_wide_solve_matches_oracle_and_cluster(sphere320_oracle, sphere320_
     assert sg.info().solver_cluster > 16 >= sc.info().solver_cluster
 
 
+@pytest.mark.parametrize("cs", [4, 8])
+def test_capped_solve_cluster_matches_oracle(sphere320_oracle, sphere320_march, cs):
+    """A solve cluster capped below the device's largest (solve_cluster) marches
+    the 480-RWG sphere to the oracle's currents within the 1e-10 bar."""
+    w, o = sphere320_oracle
+    Jref = sphere320_march
+    s = _solver(w, solve_grid=1, solve_cluster=cs)
+    J = s.march(Jref.shape[0])
+    assert s.info().solver_cluster == cs
+    assert float(np.linalg.norm(J - Jref) / np.linalg.norm(Jref)) < 1e-10
+
+
 @pytest.mark.parametrize("kw", [dict(chi=0.0), dict(zeta=0.0), dict(chi=0.5, zeta=2.0, theta=1.5)])
 def test_cfie_variants_match_oracle(kw):
     """The paper's CFIE variants (section 4.3: CFIE3 drops the time-differentiated
