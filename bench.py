@@ -450,14 +450,14 @@ def kernel_profile(s, pre, K):
 def e2e_rate(s, pre, K, R, dist, world):
     """The same steps through the C ABI with host buffers: every step copies
     V^{alpha-1} in from pinned memory and J^{alpha-1} out to pinned memory
-    (tdbem_step_v_async), and the host takes each step's result one step
+    (tdbem_step_v_async), and the host takes each step's result two steps
     later (tdbem_step_wait, which also checks the solve's status), so that the
-    copies and the next step's launches overlap the step in flight."""
+    copies and the next steps' launches overlap the steps in flight."""
     import torch
 
     s.reset()
     Vh = torch.empty((pre + K, R, s.ne), dtype=torch.float64).pin_memory()
-    Jh = torch.empty((2, R, s.ne), dtype=torch.float64).pin_memory()
+    Jh = torch.empty((3, R, s.ne), dtype=torch.float64).pin_memory()
     for a in range(1, pre + K + 1):
         Vh[a - 1].copy_(torch.from_numpy(s.history_eval(a, np.zeros((0, R * s.ne))).reshape(R, s.ne)))
     s.reset()
@@ -468,9 +468,10 @@ def e2e_rate(s, pre, K, R, dist, world):
         dist.barrier()
     t0 = time.perf_counter()
     for a in range(pre, pre + K):
-        s.step_v_async(Vh[a].numpy(), Jh[a & 1].numpy())
-        if a > pre:
+        s.step_v_async(Vh[a].numpy(), Jh[a % 3].numpy())
+        if a > pre + 1:
             s.step_wait()
+    s.step_wait()
     s.step_wait()
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - t0, dist)
