@@ -6,8 +6,16 @@ solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
 already resident in HBM.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode fast|direct] [--prec fp32|tf32|bf16|bf16x3|tf32x3|f16x3] [--p P]
+                  [--mode auto|fast|direct|direct32] [--prec fp32|tf32|bf16|bf16x3|tf32x3|f16x3] [--p P]
                   [--rhs R] [--workload NAME] [--no-compare] [--no-cpu-baseline]
+
+Paths: `direct` is the conventional method with FP64-equivalent stored
+coefficients (equal to the oracle to 1e-10, the accuracy reference);
+`direct32` the same march with the coefficients of the lags >= 3 stored in
+FP32 (half the bytes streamed per step, every sum still double-float); `fast`
+the near field plus the space-time interpolation FMM.  `auto` marches all
+three and reports the fastest one whose currents stay within 1e-4 relative l2
+of the `direct` path's over the whole march.
 
 --rhs R marches R incident plane waves on the same scatterer in one batch
 (the reference pulse plus R-1 seeded directions); `value` is then the steps/s
@@ -184,12 +192,12 @@ def batch_pulses(w, n: int, seed: int = 4):
 # 128-row tiles per CTA, lag >= 2 products deferred): two leaf events of 289.5 MB and one level-2
 # event of 152.9 MB per gating period of six launches
 M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
-# DRAM bytes over algorithmic bytes of the direct path's tiled history sum, from
-# one ncu capture of the same kernel on the 1920-RWG sphere (289.0 MB against
-# 269.6 MB; profiles/direct_history_sphere7680.md).  The stream of coefficients
-# and lag windows grows with the pairs stored, so the 7680-RWG launch is scaled
-# by its own algorithmic bytes.
-DIRECT_TILE_TRAFFIC_RATIO = 289.0 / 269.6
+# DRAM bytes over algorithmic bytes of the direct paths' row-tile history sum,
+# per store precision, from one ncu capture of the same kernel on the 1920-RWG
+# sphere (the stream grows with the pairs stored, so the 7680-RWG launch is
+# scaled by its own algorithmic bytes); None until captured
+RT_TRAFFIC_RATIO = {"direct": None, "direct32": None}
+RT_TRAFFIC_SOURCE = ""
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4, "f16x3": 5}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack",
@@ -201,6 +209,8 @@ def roofline(args, info, launches, ms, K, W):
     times on the library's stream: achieved = algorithmic work / device time."""
     hbm, bf16, src = _peaks()
     dom = int(np.argmax(ms))
+    if args.mode in ("direct", "direct32") and launches[1]:
+        dom = 1  # the history sum: the solve beside it can take longer in the pipelined order, on 4 to 16 SMs
     name = KERNELS[dom]
     if name == "m2l" and info.m2l_flops_per_step > 0:
         flops = info.m2l_flops_per_step * K
@@ -225,20 +235,20 @@ def roofline(args, info, launches, ms, K, W):
                 "note": "algorithmic flops (a split form executes three products per flop counted)"
                 if args.prec.endswith("x3") else ""}
     if name in ("near_history",):
-        if args.mode == "direct":
-            # every stored coefficient (an FP32 hi/lo pair, 8 B) and each edge pair's lag window
-            # (first lag int16 + count uint8); the tiled kernel rebuilds the per-pair offsets by a
-            # warp scan and reads one int64 offset per 32 pairs, left out here
+        if args.mode in ("direct", "direct32") and info.history_bytes > 0:
+            # the row-tile store streamed once per launch: the groups of 32 coefficients (8 B pairs
+            # or 4 B FP32, zero-padded to the tile's longest window per column), one first-lag byte
+            # per (row, column) and one 4-byte group offset per (row tile, column)
+            nbytes = info.history_bytes
+        elif args.mode in ("direct", "direct32"):  # batched kernel: FP64 coefficients and lag windows
             nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1)
         else:  # flattened entries: FP32 coefficient + (column << 8 | lag), 8 B per stored lag
             nbytes = 2 * info.near_coef_bytes
         gbs = nbytes / (ms[dom] / launches[dom] / 1e3) / 1e9
-        traffic = DIRECT_TILE_TRAFFIC_RATIO * nbytes if (args.mode == "direct" and args.rhs == 1) else None
+        ratio = RT_TRAFFIC_RATIO.get(args.mode) if (info.history_bytes > 0 and args.rhs == 1) else None
+        traffic = ratio * nbytes if ratio else None
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": traffic,
-                "traffic_source": "profiles/direct_history_sphere7680.md: ncu DRAM bytes of the same kernel on the "
-                                  "1920-RWG sphere, scaled to this launch by its algorithmic bytes" if traffic
-                else None,
+                "traffic": traffic, "traffic_source": RT_TRAFFIC_SOURCE if traffic else None,
                 "peak_source": f"{src} hbm_gbs", "bytes_per_launch": nbytes}
     if name == "z0_solve" and info.z0_nnz > 0:
         # algorithmic operand bytes of one solve: per BiCGStab iteration two FP32
@@ -387,10 +397,14 @@ def run_sweep(args, rank, world, dist):
 ACC_BAR = 1e-4  # the metric's accuracy bar: relative l2 of the marched currents against the FP64 path
 
 
-def _solver(args, w, mode, R=1, far_overlap=None):
+PATHS = {"direct": (0, 6), "direct32": (0, 0), "fast": (1, 6)}  # (mode, p2p_prec)
+
+
+def _solver(args, w, path, R=1, far_overlap=None):
     from paper_2303_05006_gb300 import Solver
 
-    return Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta,
+    mode, p2p = PATHS[path]
+    return Solver(w.verts, w.tris, w.dt, w.Nt, theta=w.theta, zeta=w.zeta, p2p_prec=p2p,
                   mode=mode, p_s=args.p, p_t=args.p, m2l_prec=PREC[args.prec], n_rhs=R,
                   jacobi_sweeps=args.jacobi, precond=args.precond, solve_tol=args.solve_tol,
                   m2l_tile_rows=args.m2l_tile_rows, solve_cluster=args.solve_cluster,
@@ -479,15 +493,16 @@ def e2e_rate(s, pre, K, R, dist, world):
 
 
 def run_ours(args, rank, world, dist):
-    """The metric's line: MOT steps/s of the path that meets the accuracy bar.
+    """The metric's line: MOT steps/s of the fastest path that meets the accuracy bar.
 
-    Both GPU paths march the whole workload once, untimed: the FP64 direct
-    path (the conventional method, equal to the oracle to 1e-10) and the fast
-    path (near field + space-time interpolation FMM).  The fast path is the
-    headline when its currents are within ACC_BAR relative l2 of the direct
-    ones over the full march, else the direct path is.  The headline path is
-    then timed over K steps of the steady state, profiled per kernel, and run
-    end to end through the C ABI with host buffers."""
+    Every GPU path marches the whole workload once, untimed: the FP64 direct
+    path (the conventional method, equal to the oracle to 1e-10, the
+    reference), the direct path with FP32 coefficient storage, and the fast
+    path (near field + space-time interpolation FMM).  A path meets the bar
+    when its currents are within ACC_BAR relative l2 of the FP64 direct ones
+    over the full march.  Every path is timed over K steps of the steady
+    state; the fastest one meeting the bar is the headline, profiled per
+    kernel and run end to end through the C ABI with host buffers."""
     import torch
 
     from workloads import workload
@@ -502,29 +517,33 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream(priority=-100) if args.high_priority else torch.cuda.current_stream()
     clocks = ClockSampler(dev)
     paths = {}
-    modes = {"auto": ["direct", "fast"], "direct": ["direct"], "fast": ["fast"]}[args.mode]
+    modes = {"auto": ["direct", "direct32", "fast"], "direct": ["direct"], "direct32": ["direct32"],
+             "fast": ["fast"]}[args.mode]
+    if R > 1:  # the FP32 store serves one right-hand side
+        modes = [m for m in modes if m != "direct32"] or ["direct"]
     for name in modes:
         t0 = time.perf_counter()
-        s = _solver(args, w, {"direct": 0, "fast": 1}[name], R)
+        s = _solver(args, w, name, R)
         setup = time.perf_counter() - t0
         for r, pu in enumerate(pulses):
             s.set_incident_plane(pu, rhs=r)
         s.set_stream(stream.cuda_stream)
         paths[name] = {"solver": s, "setup_s": setup}
-    # accuracy over the whole march (untimed): the fast currents against the FP64 direct ones
+    # accuracy over the whole march (untimed): every path's currents against the FP64 direct ones
     acc = {}
-    if "direct" in paths and "fast" in paths and not args.no_compare:
+    if "direct" in paths and len(paths) > 1 and not args.no_compare:
         n = w.Nt - 1
         Jd = full_march(paths["direct"]["solver"], stream, n)
-        Jf = full_march(paths["fast"]["solver"], stream, n)
-        rel = float(np.linalg.norm(Jf - Jd) / np.linalg.norm(Jd))
-        acc = {"rel_l2_fast_vs_direct_full_march": rel, "steps_compared": f"alpha 1..{n} (every step of the march)",
-               "fast_meets": bool(rel <= ACC_BAR)}
-        del Jd, Jf
-    if args.mode == "auto":
-        head = "fast" if acc.get("fast_meets") else "direct"
-    else:
-        head = args.mode
+        acc = {"steps_compared": f"alpha 1..{n} (every step of the march)"}
+        for name in paths:
+            if name == "direct":
+                continue
+            J = full_march(paths[name]["solver"], stream, n)
+            rel = float(np.linalg.norm(J - Jd) / np.linalg.norm(Jd))
+            acc[f"rel_l2_{name}_vs_direct_full_march"] = rel
+            acc[f"{name}_meets"] = bool(rel <= ACC_BAR)
+            del J
+        del Jd
     # time every path over the same steady-state window
     for name, P in paths.items():
         s = P["solver"]
@@ -533,6 +552,11 @@ def run_ours(args, rank, world, dist):
         t = max_over_ranks(timed_march(s, stream, pre, K, dist, out), dist)
         P.update({"pre": pre, "t": t, "steps_per_s": job_rate(K * R, world, t), "out": out})
     ck = clocks.stop()
+    if args.mode == "auto":
+        ok = [n for n in paths if n == "direct" or acc.get(f"{n}_meets")]
+        head = max(ok, key=lambda n: paths[n]["steps_per_s"])
+    else:
+        head = args.mode
     H = paths[head]
     s = H["solver"]
     if args.timed_only:  # for profiler launch lists: nothing after the timed marches
@@ -551,11 +575,14 @@ def run_ours(args, rank, world, dist):
         "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
         "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1000.0 * H["t"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f64+df32" if R == 1 else "f64") if head == "direct" else f"{args.prec}+f32+f64",
+        "dtype": {"direct": "f64+df32" if R == 1 else "f64", "direct32": "f32+df32+f64"}.get(
+            head, f"{args.prec}+f32+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "path": head,
-                   "path_rule": f"fast if its full-march rel l2 vs the FP64 direct path <= {ACC_BAR:g}, else direct"
-                   if args.mode == "auto" else "forced by --mode",
+                   "path_rule": f"the fastest of direct, direct32 and fast whose full-march rel l2 vs the FP64 "
+                                f"direct path is <= {ACC_BAR:g}" if args.mode == "auto" else "forced by --mode",
+                   "stored_coefficients": {"direct": "FP64 as (hi, lo) FP32 pairs", "direct32": "FP32",
+                                           "fast": "FP32 near field"}[head],
                    "n_rhs": R, "precond": args.precond, "solve_tol": args.solve_tol,
                    "theta": w.theta, "zeta": w.zeta,
                    "steps_timed": f"alpha {H['pre'] + 1}..{H['pre'] + K}",
@@ -575,7 +602,7 @@ def run_ours(args, rank, world, dist):
     }
     if acc:
         line["accuracy"] = {**acc, "rel_l2_bar": ACC_BAR,
-                            "path_meeting_it": "fast" if acc["fast_meets"] else "direct FP64",
+                            "paths_meeting_it": [n for n in paths if n == "direct" or acc.get(f"{n}_meets")],
                             "direct_equals_oracle": "to 1e-10 relative l2 (tests/test_gpu_direct.py)"}
     for name, P in paths.items():
         if name == head:
@@ -589,10 +616,11 @@ def run_ours(args, rank, world, dist):
                      "kernel_ms_per_step": {KERNELS[k]: ms_o[k] / K for k in range(len(ms_o)) if l_o[k]},
                      "roofline": roofline(argparse.Namespace(**{**vars(args), "mode": name}), oi, l_o, ms_o, K,
                                           P["pre"])}
+        if name != "direct":
+            line[key].update({"meets_bar": acc.get(f"{name}_meets"),
+                              "rel_l2_full_march_vs_direct": acc.get(f"rel_l2_{name}_vs_direct_full_march")})
         if name == "fast":
             line[key].update({"p_s": args.p, "p_t": args.p, "m2l": args.prec,
-                              "meets_bar": acc.get("fast_meets"),
-                              "rel_l2_full_march_vs_direct": acc.get("rel_l2_fast_vs_direct_full_march"),
                               "m2l_tile_rows_per_level": list(oi.m2l_tile_rows)})
         line[f"{head}_over_{name}"] = H["steps_per_s"] / P["steps_per_s"]
     for P in paths.values():
@@ -614,8 +642,8 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["auto", "fast", "direct"], default="auto",
-                    help="auto: both paths, the headline is the one meeting the 1e-4 accuracy bar")
+    ap.add_argument("--mode", choices=["auto", "fast", "direct", "direct32"], default="auto",
+                    help="auto: every path, the headline is the fastest one meeting the 1e-4 accuracy bar")
     ap.add_argument("--prec", choices=list(PREC), default="f16x3")
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides marched together (1..64)")

@@ -71,17 +71,19 @@ typedef enum {
 
 typedef enum { TDBEM_DIRECT = 0, TDBEM_FAST = 1 } tdbem_mode;
 
-/* arithmetic of the M2L contraction (fast mode) */
+/* arithmetic of the M2L contraction (fast mode, m2l_prec) and of the direct
+   history sum (p2p_prec) */
 typedef enum {
   TDBEM_P_FP32 = 0,   /* FP32 CUDA cores */
   TDBEM_P_TF32 = 1,   /* TF32 tensor cores, FP32 accumulate */
   TDBEM_P_BF16 = 2,   /* BF16 tensor cores, FP32 accumulate */
   TDBEM_P_BF16X3 = 3, /* split-precision BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
   TDBEM_P_TF32X3 = 4, /* split-precision TF32 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
-  TDBEM_P_F16X3 = 5   /* split-precision FP16 (hi*hi + hi*lo + lo*hi), FP32 accumulate, on the FP16 rate
+  TDBEM_P_F16X3 = 5,  /* split-precision FP16 (hi*hi + hi*lo + lo*hi), FP32 accumulate, on the FP16 rate
                          (twice TF32's): each operator and each moment column is scaled by a power of two
                          (exact) that brings its largest magnitude into [2^14, 2^15), and the products are
                          unscaled in FP32.  hi + lo carry 22 significand bits, as in TF32 x 3 */
+  TDBEM_P_FP64 = 6    /* FP64: for p2p_prec, the default (see there) */
 } tdbem_prec;
 
 typedef struct {
@@ -149,13 +151,29 @@ typedef struct {
                             interpolated); 2 both on the kernel (d^2U/dt^2, a step in time, interpolated) */
   int32_t solve_cluster;  /* CTAs of the single-RHS cluster solve: 1, 2, 4, 8 or 16 caps it; 0 (default) the
                              largest cluster the device schedules (16 on GB300), except in the pipelined direct
-                             march with at least 2 GB of stored coefficients, where it is 4: the solve overlaps
-                             the history sum there, and a smaller cluster leaves SMs to that sum */
+                             march with a history sum streaming at least 3 GB per step, where it is 4: the
+                             solve overlaps that sum there, and a smaller cluster leaves SMs to it */
   int64_t max_device_bytes; /* device memory budget of the context's own allocations (0: none).  An allocation
                                that would exceed it fails as if the device were full: tdbem_create returns
                                TDBEM_ENOMEM with nothing left allocated.  Per-call temporaries of
                                tdbem_history_eval and the learned warm start's buffers (tdbem_mlp_*) are
                                outside it. */
+  int32_t p2p_prec;      /* direct mode, precision of the stored coefficients Zt^(m) of the lags m >= 3 in the
+                            history sum of eq. R (the instantaneous Z0 of the solve, the lag-2 coefficients,
+                            the currents and every sum stay in FP64 or double-float):
+                              TDBEM_P_FP64 (default): each coefficient held as an unevaluated sum of two FP32
+                                 numbers (hi + lo, 8 bytes, 48 significand bits), products and sums in
+                                 double-float; the currents equal the FP64 oracle's to about 1e-10;
+                              TDBEM_P_FP32: the P2P arithmetic of the paper's FP32 form: each coefficient
+                                 rounded to FP32 (4 bytes, half the memory traffic of the history sum),
+                                 multiplied by the FP32-rounded history and summed over the lags of one
+                                 edge pair with FP32 FMAs; the per-pair sums are added in double-float and
+                                 the currents stay FP64.  With u = 2^-24 and n the longest lag window, the
+                                 history sum of row i moves by at most about (2 + n) u sum |Zt^(m)_ij|
+                                 |J_j|.  Needs n_rhs = 1 and a history ring of at most 128 steps (EINVAL
+                                 otherwise).
+                            Fast mode stores its near field in FP32 whatever the value (FP32 and FP64 are
+                            accepted). */
 } tdbem_params;
 
 /* Largest n_rhs.  The R right-hand sides of a context (incident waves on one
@@ -167,7 +185,7 @@ typedef struct {
 /* Fills defaults: d=2, p_s=p_t=4, n_leaf=64, theta=zeta=1, eps=mu=1, s_jump=1,
    DIRECT, FP32, solve_tol=1e-13, solve_maxit=1000, warm_start=1, n_rhs=1,
    jacobi_sweeps=0, m2l_tile_rows=0, precond=1, far_overlap=1, solve_grid=0, chi=1, far_kernel=0,
-   s_interp=0, t_interp=0, a_deriv=0, solve_cluster=0, max_device_bytes=0. */
+   s_interp=0, t_interp=0, a_deriv=0, solve_cluster=0, max_device_bytes=0, p2p_prec=FP64. */
 void tdbem_default_params(tdbem_params* p);
 
 /* Builds the context for a closed triangle mesh: verts [nv][3] (float64),
@@ -351,6 +369,10 @@ typedef struct {
   int32_t m2l_resident;            /* bit l set where level l's M2L runs the resident-operator kernel (FP16 form,
                                       P <= 256: the operator's 128-row tiles stay in shared memory over runs of
                                       column tiles), chosen at setup against the tiled shapes by timing */
+  int64_t device_bytes_peak;       /* the most device memory the context held at once, setup included (a
+                                      max_device_bytes at least this large lets tdbem_create succeed) */
+  int64_t history_bytes;           /* direct mode: bytes the history sum of the lags >= 3 streams per step (its
+                                      coefficient store and lag windows); 0 where it runs untiled */
 } tdbem_info;
 tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
 

@@ -15,6 +15,7 @@ _LIB = os.path.join(_HERE, "libtdbem.so")
 
 TDBEM_DIRECT, TDBEM_FAST = 0, 1
 TDBEM_P_FP32, TDBEM_P_TF32, TDBEM_P_BF16, TDBEM_P_BF16X3, TDBEM_P_TF32X3 = 0, 1, 2, 3, 4
+TDBEM_P_F16X3, TDBEM_P_FP64 = 5, 6
 _STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "EBREAKDOWN", 4: "ENOMEM", 5: "ENOCONV", 6: "ETIMEOUT",
            7: "ESTATE", 8: "ECUDA"}
 
@@ -33,7 +34,7 @@ class Params(ctypes.Structure):
                 ("far_overlap", ctypes.c_int32), ("solve_grid", ctypes.c_int32), ("chi", ctypes.c_double),
                 ("far_kernel", ctypes.c_int32), ("s_interp", ctypes.c_int32), ("t_interp", ctypes.c_int32),
                 ("a_deriv", ctypes.c_int32), ("solve_cluster", ctypes.c_int32),
-                ("max_device_bytes", ctypes.c_int64)]
+                ("max_device_bytes", ctypes.c_int64), ("p2p_prec", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -44,7 +45,8 @@ class Info(ctypes.Structure):
                 ("solver_cluster", ctypes.c_int32), ("n_far_pairs", ctypes.c_int64),
                 ("m2l_flops_per_step", ctypes.c_double), ("total_jacobi_sweeps", ctypes.c_int64),
                 ("m2l_tile_rows", ctypes.c_int32 * 8), ("z0_nnz", ctypes.c_int64), ("max_lag", ctypes.c_int32),
-                ("m2l_resident", ctypes.c_int32)]
+                ("m2l_resident", ctypes.c_int32), ("device_bytes_peak", ctypes.c_int64),
+                ("history_bytes", ctypes.c_int64)]
 
 
 class TdbemError(RuntimeError):

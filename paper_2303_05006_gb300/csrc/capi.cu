@@ -108,6 +108,7 @@ void tdbem_default_params(tdbem_params* p) {
   p->mu = 1.0;
   p->s_jump = 1.0;
   p->mode = TDBEM_DIRECT;
+  p->p2p_prec = TDBEM_P_FP64;
   p->m2l_prec = TDBEM_P_FP32;
   p->solve_tol = 1e-13;
   p->solve_maxit = 1000;
@@ -198,6 +199,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.t_interp < 0 || p.t_interp > 1 || p.a_deriv < 0 || p.a_deriv > 2 ||
       (p.solve_cluster != 0 && p.solve_cluster != 1 && p.solve_cluster != 2 && p.solve_cluster != 4 &&
        p.solve_cluster != 8 && p.solve_cluster != 16) ||
+      (p.p2p_prec != TDBEM_P_FP64 && p.p2p_prec != TDBEM_P_FP32) ||
+      (p.mode == TDBEM_DIRECT && p.p2p_prec == TDBEM_P_FP32 && p.n_rhs != 1) ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -545,6 +548,7 @@ tdbem_status tdbem_step(tdbem_ctx* c, double* J_out, int32_t* iters) {
   c->total_iters += h[0];
   if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
   if (!h[1]) {
+    if (c->p.mode == TDBEM_DIRECT && (s = tdbem_direct_check(c))) return s;
     c->set_error("step: Z0 solve missed the tolerance");
     return TDBEM_ENOCONV;
   }
@@ -571,6 +575,7 @@ tdbem_status tdbem_step_v(tdbem_ctx* c, const double* V, double* J_out, int32_t*
   c->total_iters += h[0];
   if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
   if (!h[1]) {
+    if (c->p.mode == TDBEM_DIRECT && (s = tdbem_direct_check(c))) return s;
     c->set_error("step: Z0 solve missed the tolerance");
     return TDBEM_ENOCONV;
   }
@@ -591,6 +596,7 @@ tdbem_status tdbem_step_wait(tdbem_ctx* c, int32_t* iters) {
   tdbem_status s;
   if (c->p.mode == TDBEM_FAST && (s = tdbem_fast_check(c))) return s;
   if (!conv) {
+    if (c->p.mode == TDBEM_DIRECT && (s = tdbem_direct_check(c))) return s;
     c->set_error("step: Z0 solve missed the tolerance");
     return TDBEM_ENOCONV;
   }
@@ -670,6 +676,9 @@ static tdbem_status check_misses(tdbem_ctx* c) {
   if (!s) s = tdbem_direct_join(c);
     if (s) return s;
     s = tdbem_fast_check(c);
+    if (s) return s;
+  } else {
+    tdbem_status s = tdbem_direct_check(c);
     if (s) return s;
   }
   int32_t h[8];
@@ -873,6 +882,9 @@ tdbem_status tdbem_get_info(const tdbem_ctx* c, tdbem_info* info) {
   info->n_tri = c->nt;
   info->n_near_pairs = c->direct.npairs;
   info->near_coef_bytes = c->direct.nval * (int64_t)sizeof(double);
+  info->device_bytes_peak = c->peak_bytes;
+  if (c->p.mode == TDBEM_DIRECT && c->R == 1)
+    info->history_bytes = c->rt_bytes;
   info->device_bytes = c->device_bytes;
   info->setup_seconds = c->setup_seconds;
   info->total_solver_iters = c->total_iters;

@@ -16,10 +16,12 @@
 // triangle pairs of its two supports).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "integrals.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace tdbem {
 
@@ -544,110 +546,6 @@ __global__ void __launch_bounds__(kDhThreads) k_direct_history(const int16_t* m_
   }
 }
 
-// Tiled form of the single-right-hand-side history sum.  Block (cb, rg) takes
-// the column block j0 = cb*CB .. j0+CB-1 (CB = 32 S columns, S slices of one
-// warp's width) and the row range of group rg.  The history of its columns is
-// split into (hi, lo) pairs and staged in shared memory once, slot-major
-// ([slot][column]: a lane always reads its own column, so its bank does not
-// depend on the lag it reads); the rows then stream past it, so no history
-// value is gathered from L2 per row.  A warp owns one 32-column slice, lane t its column js + t, and every
-// G-th row of the range (G = 16/S warps per slice).  Per row, the slice's
-// stored lags are one contiguous run of coefficients (each column's lags
-// consecutive, columns in order): the warp copies the run into its own
-// shared-memory buffer with cp.async (coalesced), the lanes find their
-// columns' offsets in it by a warp scan of the window lengths, and each lane
-// walks its column's lags against the staged history.  A row's lag windows
-// and run start are loaded one row ahead, while the previous row computes.
-// The lanes' double-float sums are added across the warp in double-float too
-// (FP64 runs at a small fraction of the FP32 rate on this part), and lane 0
-// writes the warp's sum for (row, slice) to partial[(cb*S + slice)*ne + row];
-// k_direct_reduce adds the partials of a row in a fixed order, so the result
-// does not depend on scheduling.  Lags m < m_min are left out (m_min = 2 for
-// the whole history); history slots of steps alpha - m_min + 1 .. alpha are
-// not read (another kernel may be writing them).
-constexpr int kDtWarps = 16;  // warps per block (three blocks per SM)
-constexpr int kDtCap = 328;   // coefficients a warp stages per row (2.6 KB); longer runs are read in place
-
-__host__ __device__ constexpr int dt_slices(int L) { return L <= 64 ? 2 : (L <= 128 ? 1 : 0); }
-
-__global__ void __launch_bounds__(kDtWarps * 32, 3)
-    k_direct_history_tile(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const float2* val,
-                          int64_t ne, const double* ring, int32_t L, int32_t alpha, int32_t m_min, int32_t S,
-                          int32_t rows_per_block, double* partial) {
-  extern __shared__ __align__(16) float2 dt_sm[];
-  const int CB = 32 * S;
-  float2* hist = dt_sm;          // [L][CB]: row m holds J^{alpha-m} of the block's columns
-  float2* zb = dt_sm + CB * L;   // [kDtWarps][kDtCap]
-  const int64_t j0 = (int64_t)blockIdx.x * CB;
-  for (int k = threadIdx.x; k < CB * L; k += blockDim.x) {
-    const int c = k / L, slot = k - c * L;  // consecutive threads read one column's slots (coalesced)
-    const int64_t j = j0 + c;
-    const int m = (alpha - slot) & (L - 1);  // the lag at which this slot's step is read at step alpha
-    // steps alpha - m_min + 1 .. alpha are not needed (and may be in flux)
-    hist[m * CB + c] = (j < ne && m >= m_min) ? df_split(ring[j * L + slot]) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sl_ = w % S, g = w / S, G = kDtWarps / S;
-  const int64_t js = j0 + 32 * sl_;  // first column of this warp's slice
-  if (js >= ne) return;
-  const int64_t j = js + lane;
-  const bool valid = j < ne;
-  const int64_t i_begin = (int64_t)blockIdx.y * rows_per_block;
-  const int64_t i_end = min(ne, i_begin + rows_per_block);
-  const float2* hcol = hist + 32 * sl_ + lane;  // this lane's column; lag m at hcol[m * CB]
-  float2* zw = zb + w * kDtCap;
-  double* out = partial + (int64_t)(blockIdx.x * S + sl_) * ne;
-  const unsigned full = 0xffffffffu;
-  int64_t i = i_begin + g;
-  if (i >= i_end) return;
-  int lo = valid ? m_lo[i * ne + j] : 0, n = valid ? nlag[i * ne + j] : 0;
-  int64_t base = off[i * ne + js];
-  for (; i < i_end; i += G) {
-    int x = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(full, x, d);
-      if (lane >= d) x += y;
-    }
-    const int o = x - n;                       // this column's offset in the run
-    const int cnt = __shfl_sync(full, x, 31);  // run length
-    // run element k goes to zw[par + k]: global and shared addresses then share
-    // their parity, and every aligned pair moves as one 16-byte copy
-    const int par = (int)(base & 1);
-    const bool staged = cnt + par <= kDtCap;
-    const float2* gz = val + base;
-    if (staged) {
-      const int npair = (cnt - par) >> 1;
-      for (int q = lane; q < npair; q += 32) cp_async16(zw + 2 * (par + q), gz + par + 2 * q);
-      if (lane == 0 && par && cnt > 0) cp_async8(zw + 1, gz);
-      if (lane == 31 && ((cnt - par) & 1)) cp_async8(zw + par + cnt - 1, gz + cnt - 1);
-    }
-    cp_async_commit();
-    // the next row's lag windows and run start load while this row's run copies
-    const int lo_c = lo, n_c = n;
-    if (i + G < i_end) {
-      const int64_t i2 = i + G;
-      lo = valid ? m_lo[i2 * ne + j] : 0;
-      n = valid ? nlag[i2 * ne + j] : 0;
-      base = off[i2 * ne + js];
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncwarp();
-    const int w0 = max(0, m_min - lo_c), w1 = min(n_c, alpha - lo_c + 1);
-    // coefficient u of this column has lag lo + u: both operands advance by a fixed stride
-    const float2* z = (staged ? zw + par + o : gz + o) + w0;
-    const float2* h = hcol + (lo_c + w0) * CB;
-    float sh = 0.f, sl = 0.f;
-#pragma unroll 2
-    for (int u = w0; u < w1; ++u, ++z, h += CB) df_fma_acc(sh, sl, *z, *h);
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) df_add(sh, sl, __shfl_xor_sync(full, sh, d), __shfl_xor_sync(full, sl, d));
-    if (lane == 0) out[i] = (double)sh + (double)sl;
-    __syncwarp();  // every lane is done with the buffer before the next copy
-  }
-}
-
 // R_i = V_i - (the nparts partials of row i plus the row's lag-2 entries l2
 // against J^{alpha-2}, in FP64).  Eight lanes share a row: lane s of the group
 // adds the partials k = s, s + 8, ... and the lag-2 entries e = s, s + 8, ...
@@ -672,6 +570,284 @@ __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t n
 #pragma unroll
   for (int d = kRedLanes / 2; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
   if (i < ne && sub == 0) R[i] = (V ? V[i] : 0.0) - t;
+}
+
+// Row-tile form of the single-right-hand-side history sum of the lags >= 3.
+//
+// Store.  Rows are taken in tiles of 32 (tile rt: rows 32 rt .. 32 rt + 31,
+// lane t of a warp is row 32 rt + t).  For each (tile, column j) let nmax be
+// the largest number of stored lags >= 3 over the tile's rows; the pair
+// (tile, j) owns nmax groups of 32 values, group u holding for lane t the
+// coefficient of lag lo3 + u of (32 rt + t, j), where lo3 = max(first stored
+// lag, 3), and zero past that row's own window.  Groups run tile by tile and,
+// inside a tile, column by column, so the groups of one tile and one block of
+// columns are one contiguous stretch of memory.  A group is 32 values in a
+// row: 128 bytes in FP32, 256 in (hi, lo) pairs.  goff[rt * ne + j] is the
+// first group of (rt, j) (the next entry its end), lo3 one byte per
+// (row, column).
+//
+// Kernel.  Block (cb, rg) takes the column block j0 = 64 cb .. j0 + 63 and the
+// row tiles of group rg; its history J^{alpha - m}_j (m = 0 .. Lh - 1) is
+// staged column-major in shared memory once, zero for the lags not summed
+// (m < m_min, m > alpha, m >= L), so that zero padding and early steps need
+// no test.  Each warp owns a row tile at a time and streams the tile's
+// stretch for the block's columns through a private ring of 2 KB stages
+// filled by bulk copies (cp.async.bulk, one lane issues, an mbarrier per
+// stage counts the bytes); every lane sums its own row over the block's
+// columns and lags, so no cross-lane reduction is needed, and writes
+// partial[cb * ne + row].  Per (tile, column) a lane's first lag and the
+// column's end group are loaded five columns ahead.  The lanes of a warp read
+// one column at lags that differ by their rows' distances, so the history
+// reads are broadcasts or distinct banks.  Every wait is bounded: on expiry
+// the warp writes NaN partials (the solve then misses its tolerance), sets
+// *err, waits (bounded) for its copies in flight and stops.
+//
+// Arithmetic.  (hi, lo) pairs: the history is split into (hi, lo) pairs too
+// and every product and sum is double-float (df_fma_acc).  FP32 store: the
+// history is rounded to FP32, each column's lags are summed with FP32 FMAs
+// (at most nmax terms) and the column sums are added in double-float.  With
+// u = 2^-24 the FP32 form's error on row i is then at most about
+// (2 + nmax) u sum |Zt^(m)_ij| |J_j^{alpha-m}| (two roundings per product,
+// the recursive-sum bound over a column), one FMA per stored value.
+constexpr int kRtWarps = 8;  // warps per block
+constexpr int kRtCB = 64;    // columns per block
+
+template <typename Coef>
+struct RtPrec;
+template <>
+struct RtPrec<float> {  // FP32 store: FP32 history, FP32 column sums
+  using Hist = float;
+};
+template <>
+struct RtPrec<float2> {  // (hi, lo) store: double-float throughout
+  using Hist = float2;
+};
+
+// shared memory of a block: NS stages of SB bytes and an mbarrier per stage
+// and warp, and the history of kRtCB columns x Lh lags
+template <typename Coef>
+size_t rt_smem_bytes(int ns, int sb, int Lh) {
+  return (size_t)kRtWarps * ns * (sb + 8) + (size_t)kRtCB * Lh * sizeof(typename RtPrec<Coef>::Hist);
+}
+
+// coefficient z (FP32) times history x (double-float) added to (sh, sl)
+__device__ __forceinline__ void df_fma_acc(float& sh, float& sl, float z, float2 x) {
+  const float p = __fmul_rn(z, x.x);
+  float e = __fmaf_rn(z, x.x, -p);
+  e = __fmaf_rn(z, x.y, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void rt_hist(float* o, double v) { *o = __double2float_rn(v); }
+__device__ __forceinline__ void rt_hist(float2* o, double v) { *o = df_split(v); }
+
+// NS stages of SB bytes per warp; MINB blocks per SM
+template <typename Coef, int NS, int SB, int MINB>
+__global__ void __launch_bounds__(kRtWarps * 32, MINB)
+    k_direct_history_rt(const Coef* __restrict__ val, const uint32_t* __restrict__ goff,
+                        const uint8_t* __restrict__ lo3, int64_t ne, int32_t nrt, const double* __restrict__ ring,
+                        int32_t L, int32_t Lh, int32_t alpha, int32_t m_min, int32_t tiles,
+                        double* __restrict__ partial, int32_t* err) {
+  using Hist = typename RtPrec<Coef>::Hist;
+  constexpr int CG = SB / (32 * (int)sizeof(Coef));  // groups per stage
+  constexpr bool kF32 = sizeof(Coef) == 4;
+  extern __shared__ __align__(128) unsigned char rt_sm[];
+  Coef* stages = reinterpret_cast<Coef*>(rt_sm);  // [kRtWarps][NS][CG][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(rt_sm + (size_t)kRtWarps * NS * SB);
+  Hist* hist = reinterpret_cast<Hist*>(bars + kRtWarps * NS);  // [kRtCB][Lh]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j0 = (int64_t)blockIdx.x * kRtCB;
+  const int ncol = (int)min((int64_t)kRtCB, ne - j0);
+  const int rt_begin = blockIdx.y * tiles, rt_end = min(nrt, rt_begin + tiles);
+  const uint32_t bar0 = tc::smem_u32(bars + w * NS);
+  Coef* wst = stages + (size_t)w * NS * CG * 32;
+  if (lane == 0) {
+    for (int s = 0; s < NS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * s));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  // producer cursor of this warp's stretches (every lane keeps it; lane 0 copies)
+  int p_rt = rt_begin + w;
+  uint32_t p_g = 0, p_ge = 0, issued = 0;
+  if (p_rt < rt_end) {
+    p_g = goff[(int64_t)p_rt * ne + j0];
+    p_ge = goff[(int64_t)p_rt * ne + j0 + ncol];
+  }
+  auto issue = [&](int s) {  // the cursor's next chunk into stage s (none once the warp's tiles are done)
+    while (p_rt < rt_end && p_g == p_ge) {
+      p_rt += kRtWarps;
+      if (p_rt < rt_end) {
+        p_g = goff[(int64_t)p_rt * ne + j0];
+        p_ge = goff[(int64_t)p_rt * ne + j0 + ncol];
+      }
+    }
+    if (p_rt >= rt_end) return;
+    const uint32_t n = min((uint32_t)CG, p_ge - p_g);
+    if (lane == 0) {  // every lane's reads of the stage have returned (their values were used)
+      const uint32_t bytes = n * 32u * (uint32_t)sizeof(Coef);
+      tc::mbar_expect_tx(bar0 + 8 * s, bytes);
+      tc::bulk_g2s(tc::smem_u32(wst + (size_t)s * CG * 32), val + (size_t)p_g * 32, bytes, bar0 + 8 * s);
+    }
+    p_g += n;
+    ++issued;
+  };
+  for (int s = 0; s < NS; ++s) issue(s);
+  // the block's history, while the first copies are in flight
+  for (int k = threadIdx.x; k < kRtCB * Lh; k += blockDim.x) {
+    const int c = k / Lh, m = k - c * Lh;
+    const bool on = c < ncol && m >= m_min && m <= alpha && m < L;
+    rt_hist(hist + k, on ? ring[(j0 + c) * L + ((alpha - m) & (L - 1))] : 0.0);
+  }
+  __syncthreads();
+  double* out = partial + (int64_t)blockIdx.x * ne;
+  uint32_t q = 0;  // chunks taken
+  bool failed = false;
+  const Coef* zp = wst;
+  // per column its first lag (this lane's row) and its end group, loaded five
+  // columns ahead over the warp's sequence of (tile, column)
+  int pf_rt = rt_begin + w, pf_c = 0;
+  auto meta = [&](int& l, uint32_t& e) {
+    l = 0;
+    e = 0;
+    if (pf_rt < rt_end) {
+      const int64_t m = (int64_t)pf_rt * ne + j0 + pf_c;
+      l = lo3[m * 32 + lane];
+      e = goff[m + 1];
+      if (++pf_c == ncol) {
+        pf_c = 0;
+        pf_rt += kRtWarps;
+      }
+    }
+  };
+  int l0, l1, l2, l3, l4;
+  uint32_t e0, e1, e2, e3, e4;
+  meta(l0, e0);
+  meta(l1, e1);
+  meta(l2, e2);
+  meta(l3, e3);
+  meta(l4, e4);
+  // the range of the warp's next tile, loaded a tile ahead
+  uint32_t nx_g = 0, nx_end = 0;
+  if (rt_begin + w < rt_end) {
+    nx_g = goff[(int64_t)(rt_begin + w) * ne + j0];
+    nx_end = goff[(int64_t)(rt_begin + w) * ne + j0 + ncol];
+  }
+  for (int rt = rt_begin + w; rt < rt_end; rt += kRtWarps) {
+    uint32_t g = nx_g;
+    const uint32_t gend = nx_end;
+    if (rt + kRtWarps < rt_end) {
+      nx_g = goff[(int64_t)(rt + kRtWarps) * ne + j0];
+      nx_end = goff[(int64_t)(rt + kRtWarps) * ne + j0 + ncol];
+    }
+    uint32_t cend = g;  // end of the chunk held (none yet in this tile)
+    float sh = 0.f, sl = 0.f;
+    for (int c = 0; c < ncol && !failed; ++c) {
+      const int lo = l0;
+      const uint32_t ge = e0;
+      l0 = l1;
+      e0 = e1;
+      l1 = l2;
+      e1 = e2;
+      l2 = l3;
+      e2 = e3;
+      l3 = l4;
+      e3 = e4;
+      meta(l4, e4);
+      const Hist* h = hist + c * Lh + lo;
+      float a = 0.f;  // FP32 store: the column's sum
+      while (g < ge) {
+        if (g == cend) {
+          if (q > 0) {
+            __syncwarp();
+            issue((int)((q - 1) % NS));  // chunk q - 1 is consumed: its stage takes the next
+          }
+          const bool ok = tc::mbar_wait(bar0 + 8 * (q % NS), (q / NS) & 1);
+          if (__any_sync(0xffffffffu, !ok)) {
+            failed = true;
+            break;
+          }
+          zp = wst + (size_t)(q % NS) * CG * 32 + lane;
+          cend = min(g + (uint32_t)CG, gend);
+          ++q;
+        }
+        const uint32_t gs = min(ge, cend);
+        if constexpr (kF32) {
+#pragma unroll 4
+          for (; g < gs; ++g, ++h, zp += 32) a = __fmaf_rn(*zp, *h, a);
+        } else {
+#pragma unroll 4
+          for (; g < gs; ++g, ++h, zp += 32) df_fma_acc(sh, sl, *zp, *h);
+        }
+      }
+      if constexpr (kF32) df_add(sh, sl, a, 0.f);
+    }
+    const int64_t i = (int64_t)rt * 32 + lane;
+    if (i < ne) out[i] = failed ? __longlong_as_double(0x7ff8000000000000LL) : (double)sh + (double)sl;
+  }
+  if (failed) {
+    if (lane == 0) atomicExch(err, 1);
+    for (uint32_t k = q; k < issued; ++k) tc::mbar_wait(bar0 + 8 * (k % NS), (k / NS) & 1);
+  }
+}
+
+// Row-tile store, step 1: one warp per (tile, column), lane t row 32 rt + t.
+// nmax[rt * ne + j] = the tile's largest count of stored lags >= 3 of column j;
+// lo3[(rt * ne + j) * 32 + t] = the row's first lag >= 3 (3 where it has none);
+// *lh = max over everything of lo3 + nmax (history rows the kernel reads).
+__global__ void k_rt_meta(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, int32_t nrt, uint8_t* nmax,
+                          uint8_t* lo3, int32_t* lh) {
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)nrt * ne) return;  // whole warps
+  const int64_t rt = wid / ne, j = wid - rt * ne, i = rt * 32 + lane;
+  int n3 = 0, l3 = 3;
+  if (i < ne) {
+    const int lo = m_lo[i * ne + j], hi = lo + nlag[i * ne + j];  // lags lo .. hi - 1
+    l3 = max(lo, 3);
+    n3 = max(0, hi - l3);
+    if (n3 == 0) l3 = 3;
+  }
+  int mx = n3;
+  for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  int need = l3 + mx;
+  for (int d = 16; d > 0; d >>= 1) need = max(need, __shfl_xor_sync(0xffffffffu, need, d));
+  lo3[wid * 32 + lane] = (uint8_t)l3;
+  if (lane == 0) {
+    nmax[wid] = (uint8_t)mx;
+    atomicMax(lh, need);
+  }
+}
+
+__device__ __forceinline__ void rt_put(float* o, double v) { *o = __double2float_rn(v); }
+__device__ __forceinline__ void rt_put(float2* o, double v) { *o = df_split(v); }
+
+// Row-tile store, step 2: the groups of (tile, column), zero past each row's window.
+template <typename Coef>
+__global__ void k_rt_fill(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const double* val,
+                          int64_t ne, int32_t nrt, const uint32_t* goff, const uint8_t* lo3, Coef* out) {
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (int64_t)nrt * ne) return;
+  const int64_t rt = wid / ne, j = wid - rt * ne, i = rt * 32 + lane;
+  const uint32_t g0 = goff[wid], nm = goff[wid + 1] - g0;
+  int n3 = 0;
+  int64_t src = 0;
+  if (i < ne) {
+    const int lo = m_lo[i * ne + j], l3 = lo3[wid * 32 + lane];
+    n3 = max(0, lo + (int)nlag[i * ne + j] - max(lo, 3));
+    src = off[i * ne + j] + (l3 - lo);
+  }
+  for (uint32_t u = 0; u < nm; ++u) {
+    Coef* o = out + ((size_t)g0 + u) * 32 + lane;
+    if ((int)u < n3)
+      rt_put(o, val[src + u]);
+    else
+      rt_put(o, 0.0);
+  }
 }
 
 // Lag-2 entries of the direct store, as a CSR over rows (before the split).
@@ -868,27 +1044,58 @@ const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
   return nullptr;
 }
 
+// Row-tile kernel shapes (stages x stage bytes, blocks per SM).  The (hi, lo)
+// store needs twice the history in shared memory and twice the stage time
+// per byte: four 2 KB stages at two blocks per SM.  The FP32 store is bound
+// by how many warps keep copies in flight: three 2 KB stages at three blocks
+// per SM (on the 7680-RWG sphere 0.41 ms per launch alone, against 0.47 with
+// five stages at two blocks and 0.49 to 0.51 with 1 KB stages).
+struct RtShape {
+  int ns, sb;
+};
+constexpr RtShape kRtShape2 = {4, 2048}, kRtShape1 = {3, 2048};
+template <typename Coef>
+using RtFn = void (*)(const Coef*, const uint32_t*, const uint8_t*, int64_t, int32_t, const double*, int32_t, int32_t,
+                      int32_t, int32_t, int32_t, double*, int32_t*);
+static RtFn<float2> rt_fn2() { return k_direct_history_rt<float2, kRtShape2.ns, kRtShape2.sb, 2>; }
+static RtFn<float> rt_fn1() { return k_direct_history_rt<float, kRtShape1.ns, kRtShape1.sb, 3>; }
+static size_t rt_smem(const tdbem_ctx* c) {
+  return c->rt_prec == 1 ? rt_smem_bytes<float>(kRtShape1.ns, kRtShape1.sb, c->rt_Lh)
+                         : rt_smem_bytes<float2>(kRtShape2.ns, kRtShape2.sb, c->rt_Lh);
+}
+
+// partial sums per row of the tiled history sum
+static int64_t direct_nparts(const tdbem_ctx* c) {
+  return c->rt_ncb;
+}
+
 // The tiled history sum of the lags >= 3 of step alpha into partial buffer buf,
 // on the context's current stream.
 static tdbem_status direct_tile(tdbem_ctx* c, int32_t alpha, const double* d_ring, int buf) {
-  const PairStore& st = c->direct;
-  const size_t smem = ((size_t)32 * c->dt_S * c->L + (size_t)kDtWarps * kDtCap) * sizeof(float2);
-  const int64_t nparts = (int64_t)c->dt_ncb * c->dt_S;
-  k_direct_history_tile<<<dim3((unsigned)c->dt_ncb, (unsigned)c->dt_rg), kDtWarps * 32, smem, c->stream>>>(
-      st.m_lo, st.nlag, st.off, reinterpret_cast<const float2*>(st.val), c->ne, d_ring, c->L, alpha, 3, c->dt_S,
-      c->dt_rows, c->d_dpart + buf * nparts * c->ne);
+  const int64_t nrt = (c->ne + 31) / 32;
+  const dim3 grid((unsigned)c->rt_ncb, (unsigned)c->rt_nrg);
+  const size_t smem = rt_smem(c);
+  double* part = c->d_dpart + buf * direct_nparts(c) * c->ne;
+  if (c->rt_prec == 1)
+    rt_fn1()<<<grid, kRtWarps * 32, smem, c->stream>>>(static_cast<const float*>(c->d_rt_val), c->d_rt_goff,
+                                                       c->d_rt_lo, c->ne, (int32_t)nrt, d_ring, c->L, c->rt_Lh,
+                                                       alpha, 3, c->rt_tiles, part, c->d_dt_err);
+  else
+    rt_fn2()<<<grid, kRtWarps * 32, smem, c->stream>>>(static_cast<const float2*>(c->d_rt_val), c->d_rt_goff,
+                                                       c->d_rt_lo, c->ne, (int32_t)nrt, d_ring, c->L, c->rt_Lh,
+                                                       alpha, 3, c->rt_tiles, part, c->d_dt_err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
 
 tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_ring, const double* V) {
   const PairStore& st = c->direct;
-  if (c->R == 1 && c->dt_S > 0) {
+  if (c->R == 1 && c->rt_prec) {
     // the march's own ring uses buffers alpha & 1 (possibly filled ahead, during
     // the previous step), any other history buffer 2
     const bool march = d_ring == c->d_Jring;
     const int buf = march ? (alpha & 1) : 2;
-    const int64_t nparts = (int64_t)c->dt_ncb * c->dt_S;
+    const int64_t nparts = direct_nparts(c);
     if (march && c->dahead[buf] == alpha) {
       TDBEM_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_dahead[buf], 0));
     } else {
@@ -904,6 +1111,10 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
         c->L, alpha, V, c->d_R);
     c->prof_end(10, e);
   } else if (c->R == 1) {
+    if (!c->d_ring2 || !st.val) {
+      c->set_error("direct: untiled history sum without its split ring");
+      return TDBEM_ESTATE;
+    }
     cudaEvent_t e = c->prof_begin(9);
     const int64_t n = c->ne * (int64_t)c->L;
     k_ring_split<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(d_ring, c->ne, c->L, c->d_ring2);
@@ -931,7 +1142,7 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
 // (alpha + 2) & 1 was last read by step alpha's reduction, ordered before the
 // solve and so before this launch.
 tdbem_status tdbem_direct_after_solve(tdbem_ctx* c, int32_t alpha) {
-  if (!c->dstream || c->dt_S == 0 || c->R != 1) return TDBEM_OK;
+  if (!c->dstream || !c->rt_prec || c->R != 1) return TDBEM_OK;
   const int32_t a2 = alpha + 2;
   if (a2 > c->Nt - 1) return TDBEM_OK;
   const int b = a2 & 1;
@@ -946,6 +1157,22 @@ tdbem_status tdbem_direct_after_solve(tdbem_ctx* c, int32_t alpha) {
   if (s) return s;
   TDBEM_CUDA_TRY(c, cudaEventRecord(c->ev_dahead[b], c->dstream));
   c->dahead[b] = a2;
+  return TDBEM_OK;
+}
+
+// ETIMEOUT if a bounded wait of the row-tile history sum expired (its partial
+// sums are NaN then, so the step's solve also misses its tolerance).
+tdbem_status tdbem_direct_check(tdbem_ctx* c) {
+  if (!c->d_dt_err) return TDBEM_OK;
+  tdbem_status s = tdbem_direct_join(c);
+  if (s) return s;
+  int32_t h = 0;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_dt_err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    c->set_error("direct: a bounded wait of the history sum expired");
+    return TDBEM_ETIMEOUT;
+  }
   return TDBEM_OK;
 }
 
@@ -972,17 +1199,107 @@ void tdbem_direct_free(tdbem_ctx* c) {
   c->dstream = nullptr;
 }
 
-// Single right-hand side: split the stored coefficients in place (after Z0 has
-// been read from them) and lay out the history sum: the tiled kernel when one
-// column block's history and the warps' buffers fit shared memory (ring
-// length L <= 128; three blocks per SM at L = 64), else the untiled kernel and
+// Builds the row-tile store of the lags >= 3 from the FP64 store (prec 1: FP32
+// values, 2: (hi, lo) pairs), frees the FP64 values and sets the grid.
+static tdbem_status build_row_tiles(tdbem_ctx* c, int prec) {
+  PairStore& st = c->direct;
+  const int64_t ne = c->ne, nrt = (ne + 31) / 32, ntc = nrt * ne;
+  tdbem_status s;
+  uint8_t* d_nmax = nullptr;
+  int32_t* d_lh = nullptr;
+  if ((s = c->dalloc(&d_nmax, ntc)) || (s = c->dalloc(&c->d_rt_lo, ntc * 32)) || (s = c->dalloc(&d_lh, 1)) ||
+      (s = c->dalloc(&c->d_dt_err, 1)))
+    return s;
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(d_lh, 0, sizeof(int32_t), c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_dt_err, 0, sizeof(int32_t), c->stream));
+  const unsigned nb = (unsigned)((ntc * 32 + 255) / 256);
+  k_rt_meta<<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, ne, (int32_t)nrt, d_nmax, c->d_rt_lo, d_lh);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  std::vector<uint8_t> nmax(ntc);
+  int32_t lh = 0;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(nmax.data(), d_nmax, ntc, cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(&lh, d_lh, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->dfree(d_nmax);
+  c->dfree(d_lh);
+  std::vector<uint32_t> goff(ntc + 1);
+  uint64_t acc = 0;
+  for (int64_t k = 0; k < ntc; ++k) {
+    goff[k] = (uint32_t)acc;
+    acc += nmax[k];
+  }
+  if (acc >= (1ull << 32) || lh > 255) {
+    c->set_error("direct: row-tile store too large (group offsets are 32-bit)");
+    return TDBEM_EINVAL;
+  }
+  goff[ntc] = (uint32_t)acc;
+  if ((s = c->dalloc(&c->d_rt_goff, ntc + 1))) return s;
+  TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_rt_goff, goff.data(), (ntc + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                    c->stream));
+  const size_t nv = (size_t)acc * 32;
+  if (prec == 1) {
+    float* v = nullptr;
+    if ((s = c->dalloc(&v, nv))) return s;
+    k_rt_fill<float><<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, (int32_t)nrt, c->d_rt_goff,
+                                                c->d_rt_lo, v);
+    c->d_rt_val = v;
+  } else {
+    float2* v = nullptr;
+    if ((s = c->dalloc(&v, nv))) return s;
+    k_rt_fill<float2><<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, (int32_t)nrt, c->d_rt_goff,
+                                                 c->d_rt_lo, v);
+    c->d_rt_val = v;
+  }
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
+  // the goff vector (host) and the FP64 values are read by the fill: wait before both go
+  TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->dfree(st.val);
+  st.val = nullptr;
+  c->rt_Lh = std::max(lh, 4);
+  c->rt_prec = prec;
+  c->rt_bytes = (int64_t)nv * (prec == 1 ? 4 : 8) + ntc * 32 + (ntc + 1) * 4;
+  const size_t smem = rt_smem(c);
+  int nsm = 0, per_sm = 0;
+  TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+  if (prec == 1) {
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(rt_fn1(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_fn1(), kRtWarps * 32, smem));
+  } else {
+    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(rt_fn2(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_fn2(), kRtWarps * 32, smem));
+  }
+  const int64_t slots = (int64_t)std::max(1, per_sm) * nsm;
+  const int ncb = (int)((ne + kRtCB - 1) / kRtCB);
+  // row-tile groups: the fewest waves of blocks times the tiles a warp takes
+  // per block (a small charge per block for its history staging)
+  double best = 1e300;
+  int tiles_best = (int)nrt;
+  for (int64_t nrg = 1; nrg <= nrt; ++nrg) {
+    const int64_t tiles = (nrt + nrg - 1) / nrg, groups = (nrt + tiles - 1) / tiles;
+    const int64_t waves = (ncb * groups + slots - 1) / slots;
+    const double cost = (double)waves * ((double)((tiles + kRtWarps - 1) / kRtWarps) + 0.25);
+    if (cost < best - 1e-9) {
+      best = cost;
+      tiles_best = (int)tiles;
+    }
+  }
+  c->rt_ncb = ncb;
+  c->rt_tiles = tiles_best;
+  c->rt_nrg = (int)((nrt + tiles_best - 1) / tiles_best);
+  return TDBEM_OK;
+}
+
+// Single right-hand side, after Z0 and the lag-2 entries have been read from
+// the FP64 store: the row-tile store of the lags >= 3 in the precision of
+// p2p_prec (ring length L <= 128), which replaces the FP64 values; else the
+// FP64 values split in place into (hi, lo) pairs for the untiled kernel and
 // its split ring.
 tdbem_status tdbem_direct_split(tdbem_ctx* c) {
   if (c->R != 1) return TDBEM_OK;
   PairStore& st = c->direct;
-  const int S = dt_slices(c->L);
-  if (S > 0) {
-    // lag-2 entries (read from the FP64 store before it is split)
+  const bool tiled = c->L <= 128;  // the row-tile store's first lags are bytes, its history fits shared memory
+  if (tiled) {
+    // lag-2 entries (read from the FP64 store before the row tiles replace it)
     const int64_t ne = c->ne;
     int64_t* d_cnt = nullptr;
     tdbem_status s0;
@@ -1004,34 +1321,15 @@ tdbem_status tdbem_direct_split(tdbem_ctx* c) {
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // before ptr (host) goes out of scope
   }
-  k_split_values<<<(unsigned)((st.nval + 255) / 256), 256, 0, c->stream>>>(st.val, st.nval);
-  TDBEM_CUDA_TRY(c, cudaGetLastError());
-  if (S > 0) {
-    const size_t smem = ((size_t)32 * S * c->L + (size_t)kDtWarps * kDtCap) * sizeof(float2);
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-    int nsm = 0;
-    TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    const int ncb = (int)((c->ne + 32 * S - 1) / (32 * S));
-    // row groups: the grid closest to whole waves of three blocks per SM
-    // (between just under one wave and four)
-    const int slots = 3 * nsm;
-    int rg_best = 1;
-    double waste_best = 1e30;
-    const int rg0 = std::max(1, slots / ncb), rg1 = 4 * std::max(1, (slots + ncb - 1) / ncb);
-    for (int rg = rg0; rg <= rg1; ++rg) {
-      const int64_t nb = (int64_t)ncb * rg;
-      const int64_t waves = (nb + slots - 1) / slots;
-      const double waste = (double)(waves * slots - nb) / (double)nb;
-      if (waste < waste_best - 1e-9) {
-        waste_best = waste;
-        rg_best = rg;
-      }
-    }
-    const int rows = (int)((c->ne + rg_best - 1) / rg_best);
-    tdbem_status s = c->dalloc(&c->d_dpart, (size_t)3 * ncb * S * c->ne);
+  if (!tiled && c->p.p2p_prec == TDBEM_P_FP32) {
+    c->set_error("p2p_prec FP32 needs one right-hand side and a history ring of at most 128 steps");
+    return TDBEM_EINVAL;
+  }
+  if (tiled) {
+    tdbem_status s = build_row_tiles(c, c->p.p2p_prec == TDBEM_P_FP32 ? 1 : 2);
     if (s) return s;
-    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_dpart, 0, (size_t)3 * ncb * S * c->ne * sizeof(double), c->stream));
+    if ((s = c->dalloc(&c->d_dpart, (size_t)3 * c->rt_ncb * c->ne))) return s;
+    TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_dpart, 0, (size_t)3 * c->rt_ncb * c->ne * sizeof(double), c->stream));
     if (c->p.far_overlap) {
       // between the library stream's highest priority and the lowest: the
       // next solve's cluster is dispatched ahead of this stream's blocks
@@ -1041,12 +1339,10 @@ tdbem_status tdbem_direct_split(tdbem_ctx* c) {
       TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_dsolved, cudaEventDisableTiming));
       for (int b = 0; b < 2; ++b) TDBEM_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_dahead[b], cudaEventDisableTiming));
     }
-    c->dt_S = S;
-    c->dt_ncb = ncb;
-    c->dt_rg = (int)((c->ne + rows - 1) / rows);
-    c->dt_rows = rows;
     return TDBEM_OK;
   }
+  k_split_values<<<(unsigned)((st.nval + 255) / 256), 256, 0, c->stream>>>(st.val, st.nval);
+  TDBEM_CUDA_TRY(c, cudaGetLastError());
   TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(k_direct_history, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(2 * kDhCap * sizeof(float2))));
   tdbem_status s = c->dalloc(&c->d_ring2, c->ne * (int64_t)c->L);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -109,10 +110,18 @@ struct tdbem_ctx {
   double* d_Jring = nullptr;        // [ne][L][R]
   float2* d_ring2 = nullptr;        // direct mode, R = 1: split history [L][ne] (hi, lo) (untiled kernel)
   // direct mode, R = 1, tiled history sum (lags >= 3) plus the lag-2 entries in the reduction
-  double* d_dpart = nullptr;        // partial sums [3][ncb*S][ne]: march steps alpha & 1, evaluations 2
-  int32_t dt_S = 0;                 // 32-column slices per block (0: untiled kernel)
-  int32_t dt_ncb = 0, dt_rg = 0;    // column blocks and row groups of its grid
-  int32_t dt_rows = 0;              // rows per block
+  double* d_dpart = nullptr;        // partial sums [3][ncb][ne]: march steps alpha & 1, evaluations 2
+  // direct mode, R = 1, row-tile store of the lags >= 3 (rows in tiles of 32,
+  // one lane per row; see k_direct_history_rt)
+  int32_t rt_prec = 0;              // 0: untiled (ring > 128 steps), 1: FP32 values, 2: (hi, lo) pairs
+  void* d_rt_val = nullptr;         // [groups][32] float or float2
+  uint32_t* d_rt_goff = nullptr;    // [nrt * ne + 1] first group of (tile, column)
+  uint8_t* d_rt_lo = nullptr;       // [nrt * ne][32] first stored lag (>= 3) of (row, column)
+  int32_t rt_Lh = 0;                // history rows staged per column (every lag a group reaches)
+  int32_t rt_ncb = 0, rt_nrg = 0;   // column blocks and row-tile groups of its grid
+  int32_t rt_tiles = 0;             // row tiles per block
+  int64_t rt_bytes = 0;             // bytes streamed per launch (values, lag bytes, group offsets)
+  int32_t* d_dt_err = nullptr;      // set by a bounded wait of the history sum that expired
   int64_t* d_l2_ptr = nullptr;      // lag-2 coefficients, CSR over rows [ne + 1]
   int32_t* d_l2_col = nullptr;
   double* d_l2_val = nullptr;
@@ -148,6 +157,7 @@ struct tdbem_ctx {
   cudaStream_t stream = nullptr;
   double setup_seconds = 0;
   int64_t device_bytes = 0;
+  int64_t peak_bytes = 0;           // the most device_bytes has been
   // kernel-class timing (tdbem_profile_*)
   static constexpr int kClasses = 11;
   bool prof_on = false;
@@ -173,10 +183,24 @@ struct tdbem_ctx {
       return TDBEM_ENOMEM;
     }
     device_bytes += (int64_t)(count * sizeof(T));
+    peak_bytes = std::max(peak_bytes, device_bytes);
     allocs.push_back((void*)*ptr);
+    alloc_bytes.push_back(count * sizeof(T));
     return TDBEM_OK;
   }
+  // returns an allocation of dalloc early (no-op for a pointer it did not make)
+  void dfree(void* ptr) {
+    for (size_t k = 0; k < allocs.size(); ++k)
+      if (allocs[k] == ptr) {
+        cudaFree(ptr);
+        device_bytes -= (int64_t)alloc_bytes[k];
+        allocs.erase(allocs.begin() + k);
+        alloc_bytes.erase(alloc_bytes.begin() + k);
+        return;
+      }
+  }
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
   // learned warm start (mlp.cu)
   struct Mlp* mlp = nullptr;
 };
@@ -189,6 +213,7 @@ tdbem_status tdbem_direct_history(tdbem_ctx* c, int32_t alpha, const double* d_r
 tdbem_status tdbem_direct_split(tdbem_ctx* c);
 tdbem_status tdbem_direct_after_solve(tdbem_ctx* c, int32_t alpha);
 tdbem_status tdbem_direct_join(tdbem_ctx* c);
+tdbem_status tdbem_direct_check(tdbem_ctx* c);
 tdbem_status tdbem_direct_invalidate(tdbem_ctx* c);
 void tdbem_direct_free(tdbem_ctx* c);
 tdbem_status tdbem_incident_table(tdbem_ctx* c, int32_t r);

@@ -1243,15 +1243,16 @@ tdbem_status tdbem_solve_z0(tdbem_ctx* c, int32_t alpha, int32_t* iters, int32_t
                                                     0, c->stream));
     } else {
       // Default: the largest cluster, except in the pipelined direct march with
-      // a history sum of at least 2 GB per step (about 0.4 ms).  There the
-      // solve overlaps that sum on its own SMs, and a cluster of 4 leaves 12
-      // more SMs to it while the solve still hides behind it (7680-RWG sphere:
-      // 1088 steps/s against 1055 with 16, the solve taking 0.76 ms of a
-      // 0.93 ms step).
+      // a history sum streaming at least 3 GB per step (about 0.5 ms).  There
+      // the solve overlaps that sum on its own SMs, and a cluster of 4 leaves
+      // 12 more SMs to it while the solve still hides behind it (7680-RWG
+      // sphere, (hi, lo) store of 4.6 GB: 1145 steps/s against 1106 with 16).
+      // A shorter sum (the FP32 store's 2.3 GB) leaves the solve on the
+      // critical path, where 16 CTAs win (2160 steps/s against 1855 with 4).
       int cs = g_cluster;
       if (c->p.solve_cluster > 0)
         cs = std::min(c->p.solve_cluster, g_cluster);
-      else if (c->p.mode == TDBEM_DIRECT && c->p.far_overlap && c->direct.nval * (int64_t)sizeof(double) >= (2LL << 30))
+      else if (c->p.mode == TDBEM_DIRECT && c->p.far_overlap && c->rt_bytes >= (3LL << 30))
         cs = std::min(4, g_cluster);
       c->cluster = cs;
       cudaLaunchConfig_t cfg = {};

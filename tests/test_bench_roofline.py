@@ -13,7 +13,7 @@ def _setup():
     hbm, bf16, _ = bench._peaks()
     info = types.SimpleNamespace(m2l_flops_per_step=2.0e10, m2l_tile_rows=[0, 0, 256, 256, 0, 0, 0, 0],
                                  near_coef_bytes=4.0e9, n_near_pairs=5.0e7, z0_nnz=2.0e5,
-                                 total_solver_iters=400, ne=7680)
+                                 total_solver_iters=400, ne=7680, history_bytes=0)
     args = types.SimpleNamespace(prec="tf32x3", p=4, rhs=1, workload="sphere7680", far_overlap=1,
                                  mode="fast", precond=1)
     return bench, hbm, bf16, info, args
@@ -68,6 +68,22 @@ def test_direct_history_hbm_roofline():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["bytes_per_launch"] == pytest.approx(nbytes)
     assert r["achieved"] == pytest.approx(gbs) and r["frac"] == pytest.approx(gbs / hbm)
+
+
+@pytest.mark.parametrize("mode", ["direct", "direct32"])
+def test_row_tile_history_counts_its_store(mode):
+    """The row-tile history sum streams its store once per launch: the bytes
+    the library reports (values, first-lag bytes, group offsets); the solve
+    beside it does not take the roofline even where it runs longer."""
+    bench, hbm, _, info, args = _setup()
+    args.mode = mode
+    info.history_bytes = 2.3e9
+    launches, ms = _times(bench, "near_history", 50.0, 100)
+    k = bench.KERNELS.index("z0_solve")
+    ms[k] = 60.0
+    r = bench.roofline(args, info, launches, ms, 100, 5)
+    assert r["kernel"] == "near_history" and r["bytes_per_launch"] == pytest.approx(2.3e9)
+    assert r["achieved"] == pytest.approx(2.3e9 / 0.5e-3 / 1e9)
 
 
 def test_fast_near_field_counts_flattened_entries():

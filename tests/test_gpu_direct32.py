@@ -1,0 +1,122 @@
+"""Direct march with the P2P arithmetic of the FP32 form (p2p_prec = FP32)
+against the FP64 oracle.
+
+The coefficients of the lags >= 3 are rounded to FP32 once and multiplied by
+the FP32-rounded history; the lags of one edge pair are summed with FP32
+FMAs (at most n = the longest lag window of terms) and the pair sums in
+double-float; the lag-2 coefficients, Z0 and the currents stay FP64.  With
+u = 2^-24, each product carries two roundings and a recursive sum of n terms
+at most (n - 1) u of their absolute sum, so the history evaluation
+R^{alpha-1} (eq. R) of row i differs from the oracle's by at most
+(2 + n) u sum_{m,j} |Zt^(m)_ij| |J_j^{alpha-m}| (to first order in u),
+element by element; the marched currents stay within the metric's 1e-4 of
+the oracle's by a wide margin.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 6
+
+
+def _solver(w, **kw):
+    from paper_2303_05006_gb300 import Solver
+
+    s = Solver(w.verts, w.tris, w.dt, w.Nt, **kw)
+    s.set_incident_plane(w.pulses[0])
+    return s
+
+
+def _bound(o, alpha, J, rows=None, mats=None):
+    """(2 + n) 2^-24 sum |Z| |J| per row, n the oracle's lag window (lags >= 2;
+    the lag-2 terms are FP64 on the GPU, so this bounds from above)."""
+    m_lo, Zw = mats if mats is not None else o.assemble(rows)
+    n = Zw.shape[2]
+    return (2 + n) * 2.0 ** -24 * o.history(alpha, np.abs(J), rows, mats=(m_lo, np.abs(Zw)))
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 5, 17, 64, 127])
+def test_fp32_store_history_eval_within_rounding_bound(sphere320_oracle, alpha):
+    from workloads import random_history
+
+    w, o = sphere320_oracle
+    s = _solver(w, p2p_prec=FP32)
+    J = random_history(o.ne, alpha - 1, seed=alpha)
+    R_gpu = s.history_eval(alpha, J)
+    R_ref = o.rhs(w.pulses[0], alpha) - o.history(alpha, J)
+    scale = np.abs(R_ref).max() + np.abs(o.history(alpha, np.abs(J))).max()
+    err = np.abs(R_gpu - R_ref)
+    assert np.all(err <= _bound(o, alpha, J) + 1e-11 * scale)
+    if alpha > 3:  # the FP32 store is the one summed: its rounding shows
+        assert err.max() > 1e-12 * scale
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_ragged_row_tiles_and_column_blocks_sphere80(prec):
+    """120 RWG functions: the last row tile holds 24 rows and the second
+    column block 56 columns; every history evaluation matches the oracle."""
+    from oracle.oracle import Oracle
+    from workloads import random_history, workload
+
+    w = workload("sphere80")
+    s = _solver(w, p2p_prec=prec)
+    assert s.info().history_bytes > 0
+    o = Oracle(w.verts, w.tris, w.dt)
+    o.assemble()
+    for alpha in (3, 9, 40, 63):
+        J = random_history(o.ne, alpha - 1, seed=300 + alpha)
+        R_gpu = s.history_eval(alpha, J)
+        R_ref = o.rhs(w.pulses[0], alpha) - o.history(alpha, J)
+        scale = np.abs(R_ref).max() + np.abs(o.history(alpha, np.abs(J))).max()
+        tol = (_bound(o, alpha, J) if prec == FP32 else 0.0) + 1e-11 * scale
+        assert np.all(np.abs(R_gpu - R_ref) <= tol), alpha
+
+
+def test_fp32_store_march_matches_oracle(sphere320_oracle, sphere320_march):
+    """Whole 127-step march: the FP32 roundings (a few 2^-24 relative per
+    term) amplified by the march stay below 1e-5, a tenth of the metric's
+    bar."""
+    w, o = sphere320_oracle
+    s = _solver(w, p2p_prec=FP32)
+    J = s.march(w.Nt - 1)
+    rel = np.linalg.norm(J - sphere320_march) / np.linalg.norm(sphere320_march)
+    print(f"\nFP32 store, 480 RWG, 127 steps: rel l2 vs oracle {rel:.2e}")
+    assert 1e-12 < rel <= 1e-5, rel
+
+
+def test_fp32_store_pipelined_equals_serial(sphere320_oracle):
+    """The lags >= 3 summed one step ahead on the side stream give the same
+    bits as Program 1's serial order."""
+    w, _ = sphere320_oracle
+    a = _solver(w, p2p_prec=FP32, far_overlap=1).march(w.Nt - 1)
+    b = _solver(w, p2p_prec=FP32, far_overlap=0).march(w.Nt - 1)
+    assert np.array_equal(a, b)
+
+
+def test_fp32_store_sampled_rows_sphere7680():
+    """7680-RWG sphere (the benchmark workload), FP32 store: sampled rows of
+    the history evaluation within the element-wise rounding bound."""
+    from oracle.oracle import Oracle
+    from workloads import random_history, workload
+
+    w = workload("sphere7680")
+    s = _solver(w, p2p_prec=FP32)
+    o = Oracle(w.verts, w.tris, w.dt)
+    rows = np.sort(np.random.default_rng(17).choice(o.ne, 16, replace=False))
+    mats = o.assemble(rows)
+    for alpha in (3, 150, 600):
+        J = random_history(o.ne, alpha - 1, seed=500 + alpha)
+        R_gpu = s.history_eval(alpha, J)[rows]
+        R_ref = o.rhs(w.pulses[0], alpha, rows) - o.history(alpha, J, rows, mats=mats)
+        scale = np.abs(R_ref).max() + np.abs(o.history(alpha, np.abs(J), rows, mats=mats)).max()
+        assert np.all(np.abs(R_gpu - R_ref) <= _bound(o, alpha, J, rows, mats) + 1e-10 * scale), alpha
+
+
+def test_fp32_store_needs_one_rhs():
+    from paper_2303_05006_gb300 import TdbemError
+    from workloads import workload
+
+    w = workload("sphere80")
+    with pytest.raises(TdbemError, match="EINVAL"):
+        _solver(w, p2p_prec=FP32, n_rhs=2)
