@@ -193,11 +193,13 @@ def batch_pulses(w, n: int, seed: int = 4):
 # event of 152.9 MB per gating period of six launches
 M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
 # DRAM bytes over algorithmic bytes of the direct paths' row-tile history sum,
-# per store precision, from one ncu capture of the same kernel on the 1920-RWG
-# sphere (the stream grows with the pairs stored, so the 7680-RWG launch is
-# scaled by its own algorithmic bytes); None until captured
-RT_TRAFFIC_RATIO = {"direct": None, "direct32": None}
-RT_TRAFFIC_SOURCE = ""
+# per store precision: FP32 from the ncu launch list of the 7680-RWG march
+# itself (2363.4 MB per launch against 2328.3 MB), the (hi, lo) store from a
+# capture on the 1920-RWG sphere (294.0 MB against 289.4 MB), scaled to the
+# 7680-RWG launch by its own algorithmic bytes (the stream grows with the
+# pairs stored)
+RT_TRAFFIC_RATIO = {"direct": 294.02 / 289.45, "direct32": 2363.4 / 2328.3}
+RT_TRAFFIC_SOURCE = "profiles/direct_history_rt_sphere7680.md: ncu DRAM bytes of the same kernel over its algorithmic bytes"
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4, "f16x3": 5}
 KERNELS = ["incident_rhs", "near_history", "z0_solve", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack",
