@@ -6,16 +6,17 @@ solve) on the 7680-RWG sphere (5120 triangles, Nt = 1000), with every input
 already resident in HBM.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--mode auto|fast|direct|direct32] [--prec fp32|tf32|bf16|bf16x3|tf32x3|f16x3] [--p P]
+                  [--mode auto|fast|direct|direct32|direct24] [--prec fp32|tf32|bf16|bf16x3|tf32x3|f16x3] [--p P]
                   [--rhs R] [--workload NAME] [--no-compare] [--no-cpu-baseline]
 
 Paths: `direct` is the conventional method with FP64-equivalent stored
 coefficients (equal to the oracle to 1e-10, the accuracy reference);
-`direct32` the same march with the coefficients of the lags >= 3 stored in
-FP32 (half the bytes streamed per step, every sum still double-float); `fast`
-the near field plus the space-time interpolation FMM.  `auto` marches all
-three and reports the fastest one whose currents stay within 1e-4 relative l2
-of the `direct` path's over the whole march.
+`direct32` the same march with the P2P arithmetic of the FP32 form (the
+coefficients of the lags >= 3 stored in FP32, half the bytes streamed per
+step); `direct24` the same with each stored coefficient's significand rounded
+to 16 bits (3 bytes); `fast` the near field plus the space-time interpolation
+FMM.  `auto` marches all four and reports the fastest one whose currents stay
+within 1e-4 relative l2 of the `direct` path's over the whole march.
 
 --rhs R marches R incident plane waves on the same scatterer in one batch
 (the reference pulse plus R-1 seeded directions); `value` is then the steps/s
@@ -198,7 +199,7 @@ M2L_TRAFFIC_TF32X3 = (2 * 289.5e6 + 152.9e6) / 6
 # capture on the 1920-RWG sphere (294.0 MB against 289.4 MB), scaled to the
 # 7680-RWG launch by its own algorithmic bytes (the stream grows with the
 # pairs stored)
-RT_TRAFFIC_RATIO = {"direct": 294.02 / 289.45, "direct32": 2363.4 / 2328.3}
+RT_TRAFFIC_RATIO = {"direct": 294.02 / 289.45, "direct32": 2363.4 / 2328.3, "direct24": None}
 RT_TRAFFIC_SOURCE = "profiles/direct_history_rt_sphere7680.md: ncu DRAM bytes of the same kernel over its algorithmic bytes"
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4, "f16x3": 5}
@@ -211,7 +212,7 @@ def roofline(args, info, launches, ms, K, W):
     times on the library's stream: achieved = algorithmic work / device time."""
     hbm, bf16, src = _peaks()
     dom = int(np.argmax(ms))
-    if args.mode in ("direct", "direct32") and launches[1]:
+    if args.mode in ("direct", "direct32", "direct24") and launches[1]:
         dom = 1  # the history sum: the solve beside it can take longer in the pipelined order, on 4 to 16 SMs
     name = KERNELS[dom]
     if name == "m2l" and info.m2l_flops_per_step > 0:
@@ -237,12 +238,12 @@ def roofline(args, info, launches, ms, K, W):
                 "note": "algorithmic flops (a split form executes three products per flop counted)"
                 if args.prec.endswith("x3") else ""}
     if name in ("near_history",):
-        if args.mode in ("direct", "direct32") and info.history_bytes > 0:
+        if args.mode in ("direct", "direct32", "direct24") and info.history_bytes > 0:
             # the row-tile store streamed once per launch: the groups of 32 coefficients (8 B pairs
             # or 4 B FP32, zero-padded to the tile's longest window per column), one first-lag byte
             # per (row, column) and one 4-byte group offset per (row tile, column)
             nbytes = info.history_bytes
-        elif args.mode in ("direct", "direct32"):  # batched kernel: FP64 coefficients and lag windows
+        elif args.mode in ("direct", "direct32", "direct24"):  # batched kernel: FP64 coefficients and lag windows
             nbytes = info.near_coef_bytes + info.n_near_pairs * (2 + 1)
         else:  # flattened entries: FP32 coefficient + (column << 8 | lag), 8 B per stored lag
             nbytes = 2 * info.near_coef_bytes
@@ -399,7 +400,7 @@ def run_sweep(args, rank, world, dist):
 ACC_BAR = 1e-4  # the metric's accuracy bar: relative l2 of the marched currents against the FP64 path
 
 
-PATHS = {"direct": (0, 6), "direct32": (0, 0), "fast": (1, 6)}  # (mode, p2p_prec)
+PATHS = {"direct": (0, 6), "direct32": (0, 0), "direct24": (0, 7), "fast": (1, 6)}  # (mode, p2p_prec)
 
 
 def _solver(args, w, path, R=1, far_overlap=None):
@@ -519,10 +520,10 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.Stream(priority=-100) if args.high_priority else torch.cuda.current_stream()
     clocks = ClockSampler(dev)
     paths = {}
-    modes = {"auto": ["direct", "direct32", "fast"], "direct": ["direct"], "direct32": ["direct32"],
-             "fast": ["fast"]}[args.mode]
-    if R > 1:  # the FP32 store serves one right-hand side
-        modes = [m for m in modes if m != "direct32"] or ["direct"]
+    modes = {"auto": ["direct", "direct32", "direct24", "fast"], "direct": ["direct"], "direct32": ["direct32"],
+             "direct24": ["direct24"], "fast": ["fast"]}[args.mode]
+    if R > 1:  # the FP32 and 24-bit stores serve one right-hand side
+        modes = [m for m in modes if m not in ("direct32", "direct24")] or ["direct"]
     for name in modes:
         t0 = time.perf_counter()
         s = _solver(args, w, name, R)
@@ -577,13 +578,14 @@ def run_ours(args, rank, world, dist):
         "unit": "steps/s" if R == 1 else "steps/s (sum over right-hand sides)",
         "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1000.0 * H["t"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"direct": "f64+df32" if R == 1 else "f64", "direct32": "f32+df32+f64"}.get(
-            head, f"{args.prec}+f32+f64"),
+        "dtype": {"direct": "f64+df32" if R == 1 else "f64", "direct32": "f32+df32+f64",
+                  "direct24": "f24+f32+df32+f64"}.get(head, f"{args.prec}+f32+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "path": head,
-                   "path_rule": f"the fastest of direct, direct32 and fast whose full-march rel l2 vs the FP64 "
-                                f"direct path is <= {ACC_BAR:g}" if args.mode == "auto" else "forced by --mode",
+                   "path_rule": f"the fastest of direct, direct32, direct24 and fast whose full-march rel l2 vs "
+                                f"the FP64 direct path is <= {ACC_BAR:g}" if args.mode == "auto" else "forced by --mode",
                    "stored_coefficients": {"direct": "FP64 as (hi, lo) FP32 pairs", "direct32": "FP32",
+                                           "direct24": "FP32 rounded to a 16-bit significand (3 bytes)",
                                            "fast": "FP32 near field"}[head],
                    "n_rhs": R, "precond": args.precond, "solve_tol": args.solve_tol,
                    "theta": w.theta, "zeta": w.zeta,
@@ -644,7 +646,7 @@ def main():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=12)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["auto", "fast", "direct", "direct32"], default="auto",
+    ap.add_argument("--mode", choices=["auto", "fast", "direct", "direct32", "direct24"], default="auto",
                     help="auto: every path, the headline is the fastest one meeting the 1e-4 accuracy bar")
     ap.add_argument("--prec", choices=list(PREC), default="f16x3")
     ap.add_argument("--p", type=int, default=4)

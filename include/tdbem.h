@@ -83,7 +83,8 @@ typedef enum {
                          (twice TF32's): each operator and each moment column is scaled by a power of two
                          (exact) that brings its largest magnitude into [2^14, 2^15), and the products are
                          unscaled in FP32.  hi + lo carry 22 significand bits, as in TF32 x 3 */
-  TDBEM_P_FP64 = 6    /* FP64: for p2p_prec, the default (see there) */
+  TDBEM_P_FP64 = 6,   /* FP64: for p2p_prec, the default (see there) */
+  TDBEM_P_FP24 = 7    /* p2p_prec only: FP32 with the significand rounded to 16 bits, 3 bytes (see there) */
 } tdbem_prec;
 
 typedef struct {
@@ -171,8 +172,11 @@ typedef struct {
                                  the currents stay FP64.  With u = 2^-24 and n the longest lag window, the
                                  history sum of row i moves by at most about (2 + n) u sum |Zt^(m)_ij|
                                  |J_j|.  Needs n_rhs = 1 and a history ring of at most 128 steps (EINVAL
-                                 otherwise).
-                            Fast mode stores its near field in FP32 whatever the value (FP32 and FP64 are
+                                 otherwise);
+                              TDBEM_P_FP24: as FP32, with each stored coefficient's significand further
+                                 rounded to 16 bits (relative 2^-16, 3 bytes: a quarter less traffic than
+                                 FP32); the bound gains 2^-16 sum |Zt^(m)_ij| |J_j|.  Same conditions.
+                            Fast mode stores its near field in FP32 whatever the value (every value is
                             accepted). */
 } tdbem_params;
 

@@ -15,7 +15,7 @@ _LIB = os.path.join(_HERE, "libtdbem.so")
 
 TDBEM_DIRECT, TDBEM_FAST = 0, 1
 TDBEM_P_FP32, TDBEM_P_TF32, TDBEM_P_BF16, TDBEM_P_BF16X3, TDBEM_P_TF32X3 = 0, 1, 2, 3, 4
-TDBEM_P_F16X3, TDBEM_P_FP64 = 5, 6
+TDBEM_P_F16X3, TDBEM_P_FP64, TDBEM_P_FP24 = 5, 6, 7
 _STATUS = {0: "OK", 1: "EINVAL", 2: "EMESH", 3: "EBREAKDOWN", 4: "ENOMEM", 5: "ENOCONV", 6: "ETIMEOUT",
            7: "ESTATE", 8: "ECUDA"}
 

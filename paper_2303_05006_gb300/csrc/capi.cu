@@ -199,8 +199,8 @@ tdbem_status tdbem_create(const double* verts, int64_t nv, const int32_t* tris, 
       p.t_interp < 0 || p.t_interp > 1 || p.a_deriv < 0 || p.a_deriv > 2 ||
       (p.solve_cluster != 0 && p.solve_cluster != 1 && p.solve_cluster != 2 && p.solve_cluster != 4 &&
        p.solve_cluster != 8 && p.solve_cluster != 16) ||
-      (p.p2p_prec != TDBEM_P_FP64 && p.p2p_prec != TDBEM_P_FP32) ||
-      (p.mode == TDBEM_DIRECT && p.p2p_prec == TDBEM_P_FP32 && p.n_rhs != 1) ||
+      (p.p2p_prec != TDBEM_P_FP64 && p.p2p_prec != TDBEM_P_FP32 && p.p2p_prec != TDBEM_P_FP24) ||
+      (p.mode == TDBEM_DIRECT && p.p2p_prec != TDBEM_P_FP64 && p.n_rhs != 1) ||
       (p.mode != TDBEM_DIRECT && p.mode != TDBEM_FAST))
     return TDBEM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();

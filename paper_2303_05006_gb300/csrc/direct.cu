@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "integrals.cuh"
@@ -612,15 +614,63 @@ __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t n
 constexpr int kRtWarps = 8;  // warps per block
 constexpr int kRtCB = 64;    // columns per block
 
+// A value of the 24-bit store: an FP32 number with its significand rounded
+// to 16 bits (round half away from zero on the dropped byte), kept as its top
+// two bytes and its third byte.  A group of 32 is 96 bytes: the 32 top halves
+// (64 B), then the 32 third bytes (32 B).
+struct F24 {};
+
+__host__ __device__ inline uint32_t f24_bits(float f) {  // the 24 kept bits, right-aligned
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  return (b + 0x80u) >> 8;
+}
+
+// Per store: the history's type, the bytes of a group of 32 values, and a
+// lane's read position in a staged group (at: the group's first byte; get:
+// this lane's value; next: the following group).
 template <typename Coef>
 struct RtPrec;
 template <>
 struct RtPrec<float> {  // FP32 store: FP32 history, FP32 column sums
   using Hist = float;
+  static constexpr int kGroupBytes = 128;
+  struct Cur {
+    const float* p;
+    __device__ void at(const unsigned char* g, int lane) { p = reinterpret_cast<const float*>(g) + lane; }
+    __device__ float get() const { return *p; }
+    __device__ void next() { p += 32; }
+  };
+};
+template <>
+struct RtPrec<F24> {  // 24-bit store: as FP32 after the load
+  using Hist = float;
+  static constexpr int kGroupBytes = 96;
+  struct Cur {
+    const uint16_t* h;
+    const uint8_t* l;
+    __device__ void at(const unsigned char* g, int lane) {
+      h = reinterpret_cast<const uint16_t*>(g) + lane;
+      l = g + 64 + lane;
+    }
+    // bytes (top half, third byte, 0): x = third byte (bytes 1..3 zero), y = top half
+    __device__ float get() const { return __uint_as_float(__byte_perm((uint32_t)*l, (uint32_t)*h, 0x5401)); }
+    __device__ void next() {
+      h += 48;
+      l += 96;
+    }
+  };
 };
 template <>
 struct RtPrec<float2> {  // (hi, lo) store: double-float throughout
   using Hist = float2;
+  static constexpr int kGroupBytes = 256;
+  struct Cur {
+    const float2* p;
+    __device__ void at(const unsigned char* g, int lane) { p = reinterpret_cast<const float2*>(g) + lane; }
+    __device__ float2 get() const { return *p; }
+    __device__ void next() { p += 32; }
+  };
 };
 
 // shared memory of a block: NS stages of SB bytes and an mbarrier per stage
@@ -648,15 +698,17 @@ __device__ __forceinline__ void rt_hist(float2* o, double v) { *o = df_split(v);
 // NS stages of SB bytes per warp; MINB blocks per SM
 template <typename Coef, int NS, int SB, int MINB>
 __global__ void __launch_bounds__(kRtWarps * 32, MINB)
-    k_direct_history_rt(const Coef* __restrict__ val, const uint32_t* __restrict__ goff,
+    k_direct_history_rt(const unsigned char* __restrict__ val, const uint32_t* __restrict__ goff,
                         const uint8_t* __restrict__ lo3, int64_t ne, int32_t nrt, const double* __restrict__ ring,
                         int32_t L, int32_t Lh, int32_t alpha, int32_t m_min, int32_t tiles,
                         double* __restrict__ partial, int32_t* err) {
   using Hist = typename RtPrec<Coef>::Hist;
-  constexpr int CG = SB / (32 * (int)sizeof(Coef));  // groups per stage
-  constexpr bool kF32 = sizeof(Coef) == 4;
+  constexpr int GB = RtPrec<Coef>::kGroupBytes;
+  constexpr int CG = SB / GB;  // groups per stage
+  static_assert(CG * GB == SB && SB % 16 == 0, "a stage holds whole groups and 16-byte copies");
+  constexpr bool kF32 = !std::is_same<Coef, float2>::value;  // FP32 arithmetic (FP32 and 24-bit stores)
   extern __shared__ __align__(128) unsigned char rt_sm[];
-  Coef* stages = reinterpret_cast<Coef*>(rt_sm);  // [kRtWarps][NS][CG][32]
+  unsigned char* stages = rt_sm;  // [kRtWarps][NS][SB]
   uint64_t* bars = reinterpret_cast<uint64_t*>(rt_sm + (size_t)kRtWarps * NS * SB);
   Hist* hist = reinterpret_cast<Hist*>(bars + kRtWarps * NS);  // [kRtCB][Lh]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -664,7 +716,7 @@ __global__ void __launch_bounds__(kRtWarps * 32, MINB)
   const int ncol = (int)min((int64_t)kRtCB, ne - j0);
   const int rt_begin = blockIdx.y * tiles, rt_end = min(nrt, rt_begin + tiles);
   const uint32_t bar0 = tc::smem_u32(bars + w * NS);
-  Coef* wst = stages + (size_t)w * NS * CG * 32;
+  unsigned char* wst = stages + (size_t)w * NS * SB;
   if (lane == 0) {
     for (int s = 0; s < NS; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * s));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -688,9 +740,9 @@ __global__ void __launch_bounds__(kRtWarps * 32, MINB)
     if (p_rt >= rt_end) return;
     const uint32_t n = min((uint32_t)CG, p_ge - p_g);
     if (lane == 0) {  // every lane's reads of the stage have returned (their values were used)
-      const uint32_t bytes = n * 32u * (uint32_t)sizeof(Coef);
+      const uint32_t bytes = n * (uint32_t)GB;
       tc::mbar_expect_tx(bar0 + 8 * s, bytes);
-      tc::bulk_g2s(tc::smem_u32(wst + (size_t)s * CG * 32), val + (size_t)p_g * 32, bytes, bar0 + 8 * s);
+      tc::bulk_g2s(tc::smem_u32(wst + (size_t)s * SB), val + (size_t)p_g * GB, bytes, bar0 + 8 * s);
     }
     p_g += n;
     ++issued;
@@ -706,7 +758,8 @@ __global__ void __launch_bounds__(kRtWarps * 32, MINB)
   double* out = partial + (int64_t)blockIdx.x * ne;
   uint32_t q = 0;  // chunks taken
   bool failed = false;
-  const Coef* zp = wst;
+  typename RtPrec<Coef>::Cur zc;
+  zc.at(wst, lane);
   // per column its first lag (this lane's row) and its end group, loaded five
   // columns ahead over the warp's sequence of (tile, column)
   int pf_rt = rt_begin + w, pf_c = 0;
@@ -758,7 +811,7 @@ __global__ void __launch_bounds__(kRtWarps * 32, MINB)
       e3 = e4;
       meta(l4, e4);
       const Hist* h = hist + c * Lh + lo;
-      float a = 0.f;  // FP32 store: the column's sum
+      float a = 0.f;  // FP32 arithmetic: the column's sum
       while (g < ge) {
         if (g == cend) {
           if (q > 0) {
@@ -770,17 +823,17 @@ __global__ void __launch_bounds__(kRtWarps * 32, MINB)
             failed = true;
             break;
           }
-          zp = wst + (size_t)(q % NS) * CG * 32 + lane;
+          zc.at(wst + (size_t)(q % NS) * SB, lane);
           cend = min(g + (uint32_t)CG, gend);
           ++q;
         }
         const uint32_t gs = min(ge, cend);
         if constexpr (kF32) {
 #pragma unroll 4
-          for (; g < gs; ++g, ++h, zp += 32) a = __fmaf_rn(*zp, *h, a);
+          for (; g < gs; ++g, ++h, zc.next()) a = __fmaf_rn(zc.get(), *h, a);
         } else {
 #pragma unroll 4
-          for (; g < gs; ++g, ++h, zp += 32) df_fma_acc(sh, sl, *zp, *h);
+          for (; g < gs; ++g, ++h, zc.next()) df_fma_acc(sh, sl, zc.get(), *h);
         }
       }
       if constexpr (kF32) df_add(sh, sl, a, 0.f);
@@ -822,13 +875,23 @@ __global__ void k_rt_meta(const int16_t* m_lo, const uint8_t* nlag, int64_t ne, 
   }
 }
 
-__device__ __forceinline__ void rt_put(float* o, double v) { *o = __double2float_rn(v); }
-__device__ __forceinline__ void rt_put(float2* o, double v) { *o = df_split(v); }
+// value v at lane t of the group starting at byte g
+__device__ __forceinline__ void rt_put(float, unsigned char* g, int t, double v) {
+  reinterpret_cast<float*>(g)[t] = __double2float_rn(v);
+}
+__device__ __forceinline__ void rt_put(float2, unsigned char* g, int t, double v) {
+  reinterpret_cast<float2*>(g)[t] = df_split(v);
+}
+__device__ __forceinline__ void rt_put(F24, unsigned char* g, int t, double v) {
+  const uint32_t b = f24_bits(__double2float_rn(v));
+  reinterpret_cast<uint16_t*>(g)[t] = (uint16_t)(b >> 8);
+  g[64 + t] = (uint8_t)(b & 0xffu);
+}
 
 // Row-tile store, step 2: the groups of (tile, column), zero past each row's window.
 template <typename Coef>
 __global__ void k_rt_fill(const int16_t* m_lo, const uint8_t* nlag, const int64_t* off, const double* val,
-                          int64_t ne, int32_t nrt, const uint32_t* goff, const uint8_t* lo3, Coef* out) {
+                          int64_t ne, int32_t nrt, const uint32_t* goff, const uint8_t* lo3, unsigned char* out) {
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= (int64_t)nrt * ne) return;
@@ -841,13 +904,8 @@ __global__ void k_rt_fill(const int16_t* m_lo, const uint8_t* nlag, const int64_
     n3 = max(0, lo + (int)nlag[i * ne + j] - max(lo, 3));
     src = off[i * ne + j] + (l3 - lo);
   }
-  for (uint32_t u = 0; u < nm; ++u) {
-    Coef* o = out + ((size_t)g0 + u) * 32 + lane;
-    if ((int)u < n3)
-      rt_put(o, val[src + u]);
-    else
-      rt_put(o, 0.0);
-  }
+  for (uint32_t u = 0; u < nm; ++u)
+    rt_put(Coef{}, out + ((size_t)g0 + u) * RtPrec<Coef>::kGroupBytes, lane, (int)u < n3 ? val[src + u] : 0.0);
 }
 
 // Lag-2 entries of the direct store, as a CSR over rows (before the split).
@@ -1053,15 +1111,22 @@ const double* tdbem_incident_row(const tdbem_ctx* c, int32_t alpha) {
 struct RtShape {
   int ns, sb;
 };
-constexpr RtShape kRtShape2 = {4, 2048}, kRtShape1 = {3, 2048};
-template <typename Coef>
-using RtFn = void (*)(const Coef*, const uint32_t*, const uint8_t*, int64_t, int32_t, const double*, int32_t, int32_t,
-                      int32_t, int32_t, int32_t, double*, int32_t*);
-static RtFn<float2> rt_fn2() { return k_direct_history_rt<float2, kRtShape2.ns, kRtShape2.sb, 2>; }
-static RtFn<float> rt_fn1() { return k_direct_history_rt<float, kRtShape1.ns, kRtShape1.sb, 3>; }
+constexpr RtShape kRtShape2 = {4, 2048}, kRtShape1 = {3, 2048}, kRtShape3 = {3, 2304};
+using RtFn = void (*)(const unsigned char*, const uint32_t*, const uint8_t*, int64_t, int32_t, const double*,
+                      int32_t, int32_t, int32_t, int32_t, int32_t, double*, int32_t*);
+// rt_prec 1: FP32 store, 2: (hi, lo) pairs, 3: 24-bit store
+static RtFn rt_fn(int prec) {
+  if (prec == 1) return k_direct_history_rt<float, kRtShape1.ns, kRtShape1.sb, 3>;
+  if (prec == 3) return k_direct_history_rt<F24, kRtShape3.ns, kRtShape3.sb, 3>;
+  return k_direct_history_rt<float2, kRtShape2.ns, kRtShape2.sb, 2>;
+}
+static int rt_group_bytes(int prec) {
+  return prec == 1 ? RtPrec<float>::kGroupBytes : prec == 3 ? RtPrec<F24>::kGroupBytes : RtPrec<float2>::kGroupBytes;
+}
 static size_t rt_smem(const tdbem_ctx* c) {
-  return c->rt_prec == 1 ? rt_smem_bytes<float>(kRtShape1.ns, kRtShape1.sb, c->rt_Lh)
-                         : rt_smem_bytes<float2>(kRtShape2.ns, kRtShape2.sb, c->rt_Lh);
+  if (c->rt_prec == 1) return rt_smem_bytes<float>(kRtShape1.ns, kRtShape1.sb, c->rt_Lh);
+  if (c->rt_prec == 3) return rt_smem_bytes<F24>(kRtShape3.ns, kRtShape3.sb, c->rt_Lh);
+  return rt_smem_bytes<float2>(kRtShape2.ns, kRtShape2.sb, c->rt_Lh);
 }
 
 // partial sums per row of the tiled history sum
@@ -1076,14 +1141,9 @@ static tdbem_status direct_tile(tdbem_ctx* c, int32_t alpha, const double* d_rin
   const dim3 grid((unsigned)c->rt_ncb, (unsigned)c->rt_nrg);
   const size_t smem = rt_smem(c);
   double* part = c->d_dpart + buf * direct_nparts(c) * c->ne;
-  if (c->rt_prec == 1)
-    rt_fn1()<<<grid, kRtWarps * 32, smem, c->stream>>>(static_cast<const float*>(c->d_rt_val), c->d_rt_goff,
-                                                       c->d_rt_lo, c->ne, (int32_t)nrt, d_ring, c->L, c->rt_Lh,
-                                                       alpha, 3, c->rt_tiles, part, c->d_dt_err);
-  else
-    rt_fn2()<<<grid, kRtWarps * 32, smem, c->stream>>>(static_cast<const float2*>(c->d_rt_val), c->d_rt_goff,
-                                                       c->d_rt_lo, c->ne, (int32_t)nrt, d_ring, c->L, c->rt_Lh,
-                                                       alpha, 3, c->rt_tiles, part, c->d_dt_err);
+  rt_fn(c->rt_prec)<<<grid, kRtWarps * 32, smem, c->stream>>>(c->d_rt_val, c->d_rt_goff, c->d_rt_lo, c->ne,
+                                                                (int32_t)nrt, d_ring, c->L, c->rt_Lh, alpha, 3,
+                                                                c->rt_tiles, part, c->d_dt_err);
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   return TDBEM_OK;
 }
@@ -1236,20 +1296,19 @@ static tdbem_status build_row_tiles(tdbem_ctx* c, int prec) {
   if ((s = c->dalloc(&c->d_rt_goff, ntc + 1))) return s;
   TDBEM_CUDA_TRY(c, cudaMemcpyAsync(c->d_rt_goff, goff.data(), (ntc + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                     c->stream));
-  const size_t nv = (size_t)acc * 32;
-  if (prec == 1) {
-    float* v = nullptr;
-    if ((s = c->dalloc(&v, nv))) return s;
+  const size_t nbytes = (size_t)acc * rt_group_bytes(prec);
+  unsigned char* v = nullptr;
+  if ((s = c->dalloc(&v, nbytes))) return s;
+  if (prec == 1)
     k_rt_fill<float><<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, (int32_t)nrt, c->d_rt_goff,
                                                 c->d_rt_lo, v);
-    c->d_rt_val = v;
-  } else {
-    float2* v = nullptr;
-    if ((s = c->dalloc(&v, nv))) return s;
+  else if (prec == 3)
+    k_rt_fill<F24><<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, (int32_t)nrt, c->d_rt_goff,
+                                              c->d_rt_lo, v);
+  else
     k_rt_fill<float2><<<nb, 256, 0, c->stream>>>(st.m_lo, st.nlag, st.off, st.val, ne, (int32_t)nrt, c->d_rt_goff,
                                                  c->d_rt_lo, v);
-    c->d_rt_val = v;
-  }
+  c->d_rt_val = v;
   TDBEM_CUDA_TRY(c, cudaGetLastError());
   // the goff vector (host) and the FP64 values are read by the fill: wait before both go
   TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1257,17 +1316,12 @@ static tdbem_status build_row_tiles(tdbem_ctx* c, int prec) {
   st.val = nullptr;
   c->rt_Lh = std::max(lh, 4);
   c->rt_prec = prec;
-  c->rt_bytes = (int64_t)nv * (prec == 1 ? 4 : 8) + ntc * 32 + (ntc + 1) * 4;
+  c->rt_bytes = (int64_t)nbytes + ntc * 32 + (ntc + 1) * 4;
   const size_t smem = rt_smem(c);
   int nsm = 0, per_sm = 0;
   TDBEM_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-  if (prec == 1) {
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(rt_fn1(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_fn1(), kRtWarps * 32, smem));
-  } else {
-    TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(rt_fn2(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_fn2(), kRtWarps * 32, smem));
-  }
+  TDBEM_CUDA_TRY(c, cudaFuncSetAttribute(rt_fn(prec), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TDBEM_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_fn(prec), kRtWarps * 32, smem));
   const int64_t slots = (int64_t)std::max(1, per_sm) * nsm;
   const int ncb = (int)((ne + kRtCB - 1) / kRtCB);
   // row-tile groups: the fewest waves of blocks times the tiles a warp takes
@@ -1321,12 +1375,13 @@ tdbem_status tdbem_direct_split(tdbem_ctx* c) {
     TDBEM_CUDA_TRY(c, cudaGetLastError());
     TDBEM_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // before ptr (host) goes out of scope
   }
-  if (!tiled && c->p.p2p_prec == TDBEM_P_FP32) {
-    c->set_error("p2p_prec FP32 needs one right-hand side and a history ring of at most 128 steps");
+  if (!tiled && c->p.p2p_prec != TDBEM_P_FP64) {
+    c->set_error("p2p_prec FP32 and FP24 need one right-hand side and a history ring of at most 128 steps");
     return TDBEM_EINVAL;
   }
   if (tiled) {
-    tdbem_status s = build_row_tiles(c, c->p.p2p_prec == TDBEM_P_FP32 ? 1 : 2);
+    tdbem_status s =
+        build_row_tiles(c, c->p.p2p_prec == TDBEM_P_FP32 ? 1 : c->p.p2p_prec == TDBEM_P_FP24 ? 3 : 2);
     if (s) return s;
     if ((s = c->dalloc(&c->d_dpart, (size_t)3 * c->rt_ncb * c->ne))) return s;
     TDBEM_CUDA_TRY(c, cudaMemsetAsync(c->d_dpart, 0, (size_t)3 * c->rt_ncb * c->ne * sizeof(double), c->stream));

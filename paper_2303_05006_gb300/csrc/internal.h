@@ -113,8 +113,8 @@ struct tdbem_ctx {
   double* d_dpart = nullptr;        // partial sums [3][ncb][ne]: march steps alpha & 1, evaluations 2
   // direct mode, R = 1, row-tile store of the lags >= 3 (rows in tiles of 32,
   // one lane per row; see k_direct_history_rt)
-  int32_t rt_prec = 0;              // 0: untiled (ring > 128 steps), 1: FP32 values, 2: (hi, lo) pairs
-  void* d_rt_val = nullptr;         // [groups][32] float or float2
+  int32_t rt_prec = 0;              // 0: untiled (ring > 128 steps), 1: FP32 values, 2: (hi, lo) pairs, 3: 24-bit
+  unsigned char* d_rt_val = nullptr;  // [groups] of 32 values (128, 256 or 96 bytes)
   uint32_t* d_rt_goff = nullptr;    // [nrt * ne + 1] first group of (tile, column)
   uint8_t* d_rt_lo = nullptr;       // [nrt * ne][32] first stored lag (>= 3) of (row, column)
   int32_t rt_Lh = 0;                // history rows staged per column (every lag a group reaches)
