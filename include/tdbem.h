@@ -389,10 +389,10 @@ tdbem_status tdbem_get_info(const tdbem_ctx* ctx, tdbem_info* info);
    moments that the tensor-core M2L reads), 9 history split (direct mode, one
    right-hand side, the untiled history sum: the current history converted to
    FP32 hi/lo pairs before it), 10 history reduction (direct mode, one
-   right-hand side, the tiled history sum: the per-slice partial sums of a row
-   added in a fixed order with the lag-2 entries and V; class 1 is then the
-   tiled sum of the lags >= 3, launched ahead on the side stream when the steps
-   overlap).  n_classes receives the number of classes (<= 16). */
+   right-hand side, the tiled history sum: the per-column-block partial sums of
+   a row added in a fixed order with the lag-2 entries and V; class 1 is then
+   the row-tile sum of the lags >= 3, launched ahead on the side stream when
+   the steps overlap).  n_classes receives the number of classes (<= 16). */
 tdbem_status tdbem_profile_enable(tdbem_ctx* ctx, int32_t on);
 tdbem_status tdbem_profile_read(tdbem_ctx* ctx, int64_t* launches, double* ms, int32_t* n_classes);
 
