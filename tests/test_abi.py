@@ -45,3 +45,50 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(b, "_lib", None)
     with pytest.raises(ImportError):
         b.lib()
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of the header's struct, from a C program built with gcc."""
+    import tempfile
+
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "tdbem.h"', "int main(void) {",
+           f'  printf("%zu\\n", sizeof({struct}));']
+    src += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c, "w").write("\n".join(src))
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["Params", "Info"])
+def test_binding_structs_match_the_header(name):
+    """Every field of the ctypes mirror sits at the header's offset, and the
+    sizes agree (a field added to the header but not to the binding, or in
+    another order, fails here)."""
+    import paper_2303_05006_gb300._binding as b
+
+    if not __import__("shutil").which("gcc"):
+        pytest.skip("gcc not available")
+    cls = getattr(b, name)
+    struct = {"Params": "tdbem_params", "Info": "tdbem_info"}[name]
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(struct, fields)
+    assert __import__("ctypes").sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
+
+
+def test_default_params_match_the_header():
+    """tdbem_default_params (host only) fills the documented defaults."""
+    import ctypes
+
+    import paper_2303_05006_gb300._binding as b
+
+    p = b.Params()
+    b.lib().tdbem_default_params(ctypes.byref(p))
+    assert (p.d, p.p_s, p.p_t, p.n_leaf, p.mode, p.m2l_prec, p.n_rhs, p.warm_start) == (2, 4, 4, 64, 0, 0, 1, 1)
+    assert (p.theta, p.zeta, p.eps, p.mu, p.s_jump, p.chi) == (1.0, 1.0, 1.0, 1.0, 1.0, 1.0)
+    assert (p.solve_tol, p.solve_maxit, p.precond, p.far_overlap) == (1e-13, 1000, 1, 1)
+    assert p.p2p_prec == b.TDBEM_P_FP64 and p.max_device_bytes == 0 and p.solve_cluster == 0
