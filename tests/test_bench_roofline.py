@@ -141,3 +141,13 @@ def test_z0_solve_counts_operand_bytes_per_solve():
     nbytes = its * (16 * info.z0_nnz + 4 * 45 * info.ne) + 2 * (12 * info.z0_nnz + 24 * info.ne)
     assert r["bound"] == "hbm" and r["bytes_per_launch"] == pytest.approx(nbytes)
     assert r["achieved"] == pytest.approx(nbytes / (25.0e-3 / (K + W)) / 1e9)
+
+
+def test_headline_is_the_fastest_path_meeting_the_bar():
+    import bench
+
+    rates = {"direct": 1180.0, "direct32": 2170.0, "direct24": 2140.0, "fast": 2700.0}
+    assert bench.headline_path(rates, {"direct32": True, "direct24": True, "fast": False}) == "direct32"
+    assert bench.headline_path(rates, {"direct32": True, "direct24": True, "fast": True}) == "fast"
+    assert bench.headline_path(rates, {}) == "direct"  # the reference always qualifies
+    assert bench.headline_path({"direct": 1.0, "fast": 2.0}, {"fast": False}) == "direct"
