@@ -584,7 +584,8 @@ __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t n
 // lag, 3), and zero past that row's own window.  Groups run tile by tile and,
 // inside a tile, column by column, so the groups of one tile and one block of
 // columns are one contiguous stretch of memory.  A group is 32 values in a
-// row: 128 bytes in FP32, 256 in (hi, lo) pairs.  goff[rt * ne + j] is the
+// row: 128 bytes in FP32, 256 in (hi, lo) pairs, 96 in the 24-bit form (F24
+// below).  goff[rt * ne + j] is the
 // first group of (rt, j) (the next entry its end), lo3 one byte per
 // (row, column).
 //
@@ -593,7 +594,7 @@ __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t n
 // staged column-major in shared memory once, zero for the lags not summed
 // (m < m_min, m > alpha, m >= L), so that zero padding and early steps need
 // no test.  Each warp owns a row tile at a time and streams the tile's
-// stretch for the block's columns through a private ring of 2 KB stages
+// stretch for the block's columns through a private ring of about 2 KB stages
 // filled by bulk copies (cp.async.bulk, one lane issues, an mbarrier per
 // stage counts the bytes); every lane sums its own row over the block's
 // columns and lags, so no cross-lane reduction is needed, and writes
@@ -610,7 +611,8 @@ __global__ void k_direct_reduce(const double* partial, int32_t nparts, int64_t n
 // (at most nmax terms) and the column sums are added in double-float.  With
 // u = 2^-24 the FP32 form's error on row i is then at most about
 // (2 + nmax) u sum |Zt^(m)_ij| |J_j^{alpha-m}| (two roundings per product,
-// the recursive-sum bound over a column), one FMA per stored value.
+// the recursive-sum bound over a column), one FMA per stored value.  The
+// 24-bit store adds its own rounding, 2^-16 sum |Zt^(m)_ij| |J_j^{alpha-m}|.
 constexpr int kRtWarps = 8;  // warps per block
 constexpr int kRtCB = 64;    // columns per block
 
