@@ -15,8 +15,10 @@ coefficients (equal to the oracle to 1e-10, the accuracy reference);
 coefficients of the lags >= 3 stored in FP32, half the bytes streamed per
 step); `direct24` the same with each stored coefficient's significand rounded
 to 16 bits (3 bytes); `fast` the near field plus the space-time interpolation
-FMM.  `auto` marches all four and reports the fastest one whose currents stay
-within 1e-4 relative l2 of the `direct` path's over the whole march.
+FMM.  `auto` marches all four and reports the fastest of `direct`, `direct32`
+and `fast` whose currents stay within 1e-4 relative l2 of the `direct` path's
+over the whole march (`direct24` stores less than the FP32 the workload
+states for P2P, so it is measured and reported beside them only).
 
 --rhs R marches R incident plane waves on the same scatterer in one batch
 (the reference pulse plus R-1 seeded directions); `value` is then the steps/s
@@ -400,10 +402,15 @@ def run_sweep(args, rank, world, dist):
 ACC_BAR = 1e-4  # the metric's accuracy bar: relative l2 of the marched currents against the FP64 path
 
 
+# paths at or above the precision the workload states for P2P (FP32); the
+# 24-bit store is measured and reported beside them but is not a candidate
+HEADLINE_CANDIDATES = ("direct", "direct32", "fast")
+
+
 def headline_path(rates: dict, meets: dict) -> str:
-    """The fastest path that meets the accuracy bar; the FP64 direct path is
-    the reference and always does (it equals the oracle to 1e-10)."""
-    ok = [n for n in rates if n == "direct" or meets.get(n)]
+    """The fastest candidate path that meets the accuracy bar; the FP64 direct
+    path is the reference and always does (it equals the oracle to 1e-10)."""
+    ok = [n for n in rates if n in HEADLINE_CANDIDATES and (n == "direct" or meets.get(n))]
     return max(ok, key=lambda n: rates[n])
 
 
@@ -589,8 +596,9 @@ def run_ours(args, rank, world, dist):
                   "direct24": "f24+f32+df32+f64"}.get(head, f"{args.prec}+f32+f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "n_rwg": s.ne, "n_tri": w.n_tri, "Nt": w.Nt, "path": head,
-                   "path_rule": f"the fastest of direct, direct32, direct24 and fast whose full-march rel l2 vs "
-                                f"the FP64 direct path is <= {ACC_BAR:g}" if args.mode == "auto" else "forced by --mode",
+                   "path_rule": f"the fastest of direct, direct32 and fast whose full-march rel l2 vs the FP64 "
+                                f"direct path is <= {ACC_BAR:g} (direct24, below the stated FP32 P2P, is reported "
+                                "only)" if args.mode == "auto" else "forced by --mode",
                    "stored_coefficients": {"direct": "FP64 as (hi, lo) FP32 pairs", "direct32": "FP32",
                                            "direct24": "FP32 rounded to a 16-bit significand (3 bytes)",
                                            "fast": "FP32 near field"}[head],

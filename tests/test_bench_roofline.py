@@ -148,6 +148,9 @@ def test_headline_is_the_fastest_path_meeting_the_bar():
 
     rates = {"direct": 1180.0, "direct32": 2170.0, "direct24": 2140.0, "fast": 2700.0}
     assert bench.headline_path(rates, {"direct32": True, "direct24": True, "fast": False}) == "direct32"
+    # the 24-bit store is never the headline, even when faster
+    rates24 = {**rates, "direct24": 2300.0}
+    assert bench.headline_path(rates24, {"direct32": True, "direct24": True, "fast": False}) == "direct32"
     assert bench.headline_path(rates, {"direct32": True, "direct24": True, "fast": True}) == "fast"
     assert bench.headline_path(rates, {}) == "direct"  # the reference always qualifies
     assert bench.headline_path({"direct": 1.0, "fast": 2.0}, {"fast": False}) == "direct"
