@@ -1262,7 +1262,8 @@ void tdbem_direct_free(tdbem_ctx* c) {
 }
 
 // Builds the row-tile store of the lags >= 3 from the FP64 store (prec 1: FP32
-// values, 2: (hi, lo) pairs), frees the FP64 values and sets the grid.
+// values, 2: (hi, lo) pairs, 3: 24-bit values), frees the FP64 values and sets
+// the grid.
 static tdbem_status build_row_tiles(tdbem_ctx* c, int prec) {
   PairStore& st = c->direct;
   const int64_t ne = c->ne, nrt = (ne + 31) / 32, ntc = nrt * ne;
@@ -1291,7 +1292,7 @@ static tdbem_status build_row_tiles(tdbem_ctx* c, int prec) {
     acc += nmax[k];
   }
   if (acc >= (1ull << 32) || lh > 255) {
-    c->set_error("direct: row-tile store too large (group offsets are 32-bit)");
+    c->set_error("direct: row-tile store too large (32-bit group offsets, 8-bit first lags)");
     return TDBEM_EINVAL;
   }
   goff[ntc] = (uint32_t)acc;
