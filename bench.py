@@ -607,8 +607,8 @@ def run_ours(args, rank, world, dist):
                    "steps_timed": f"alpha {H['pre'] + 1}..{H['pre'] + K}",
                    "untimed_before": f"{H['pre']} steps (warm-up, and the history window filled: max lag "
                                      f"{info.max_lag})",
-                   "l2": f"inputs larger than L2 ({info.near_coef_bytes / 1e9:.2f} GB of stored coefficients read "
-                         "every step)",
+                   "l2": f"inputs larger than L2 ({(info.history_bytes or info.near_coef_bytes) / 1e9:.2f} GB of "
+                         "stored coefficients read every step)",
                    "setup_s": H["setup_s"]},
         "ns_nt_per_s": H["steps_per_s"] * w.n_tri,
         "roofline": roofline(rf_args, info, launches, ms, K, H["pre"]),
