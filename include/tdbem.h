@@ -354,7 +354,9 @@ typedef struct {
   int32_t lmax, n_levels;          /* octree depth (fast mode) */
   int32_t mt_leaf;                 /* steps per time interval at the finest level */
   int64_t n_near_pairs;            /* edge pairs handled directly */
-  int64_t near_coef_bytes;         /* bytes of stored near-field coefficients */
+  int64_t near_coef_bytes;         /* bytes of the near-field coefficients as assembled in FP64 (direct mode: every
+                                      pair; with one right-hand side the history sum then streams its own store,
+                                      history_bytes) */
   int64_t device_bytes;            /* device memory held by the context */
   double setup_seconds;            /* wall time of tdbem_create */
   int64_t total_solver_iters;
