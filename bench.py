@@ -407,6 +407,21 @@ ACC_BAR = 1e-4  # the metric's accuracy bar: relative l2 of the marched currents
 HEADLINE_CANDIDATES = ("direct", "direct32", "fast")
 
 
+def per_step_history_error(ref_eval, path_eval, J, steps) -> dict:
+    """Relative l2 of R^{alpha-1} (eq. R) of a path against the reference's at
+    the given steps, both evaluated on the reference march's own history
+    J^0 .. J^{alpha-2} (the per-step error, beside the accumulated one)."""
+    out = {}
+    for a in steps:
+        if a < 2 or a - 1 > len(J):
+            continue
+        h = J[: a - 1]
+        r0 = np.asarray(ref_eval(a, h))
+        r1 = np.asarray(path_eval(a, h))
+        out[str(a)] = float(np.linalg.norm(r1 - r0) / np.linalg.norm(r0))
+    return out
+
+
 def headline_path(rates: dict, meets: dict) -> str:
     """The fastest candidate path that meets the accuracy bar; the FP64 direct
     path is the reference and always does (it equals the oracle to 1e-10)."""
@@ -560,6 +575,15 @@ def run_ours(args, rank, world, dist):
             acc[f"rel_l2_{name}_vs_direct_full_march"] = rel
             acc[f"{name}_meets"] = bool(rel <= ACC_BAR)
             del J
+        # the per-step error of the history evaluation, on the direct march's own history
+        try:
+            ref = paths["direct"]["solver"]
+            acc["history_eval_rel_l2_vs_direct"] = {
+                name: per_step_history_error(lambda a, h: ref.history_eval(a, h),
+                                             lambda a, h, s_=P["solver"]: s_.history_eval(a, h), Jd, (100, 300, 600))
+                for name, P in paths.items() if name != "direct"}
+        except Exception as ex:  # a report only: the full-march errors above decide
+            acc["history_eval_rel_l2_vs_direct"] = {"error": str(ex)[:200]}
         del Jd
     # time every path over the same steady-state window
     for name, P in paths.items():

@@ -154,3 +154,24 @@ def test_headline_is_the_fastest_path_meeting_the_bar():
     assert bench.headline_path(rates, {"direct32": True, "direct24": True, "fast": True}) == "fast"
     assert bench.headline_path(rates, {}) == "direct"  # the reference always qualifies
     assert bench.headline_path({"direct": 1.0, "fast": 2.0}, {"fast": False}) == "direct"
+
+
+def test_per_step_history_error_uses_the_reference_history():
+    """Each evaluation gets J^0 .. J^{alpha-2} of the reference march; steps
+    beyond it are skipped."""
+    import bench
+
+    rng = np.random.default_rng(0)
+    J = rng.standard_normal((50, 7))
+    seen = []
+
+    def ref(a, h):
+        seen.append((a, h.shape[0]))
+        return h.sum(axis=0) + 1.0
+
+    def path(a, h):
+        return (h.sum(axis=0) + 1.0) * (1 + 1e-3)
+
+    out = bench.per_step_history_error(ref, path, J, (10, 40, 60))
+    assert set(out) == {"10", "40"} and seen == [(10, 9), (40, 39)]
+    assert all(abs(v - 1e-3) < 1e-12 for v in out.values())
